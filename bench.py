@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark: rays/s and geodesic steps/s of the 1024 x 1024 analytic Kerr image
+(a = 0.9375, i = 60 deg, r_cam = 1000 M, +-20 M, 230 GHz), mixed FP32/FP64 path against
+the plain FP64 path on the same GPU, with the FP64 CPU oracle timed on a bounded sample.
+
+One "step" = one complete render of the image (camera, adaptive RK4 geodesics, plasma,
+emissivity, backward transfer, deterministic flux reduction) through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun each rank renders its own full image (independent units, weak scaling, no
+collective on the data path); the max over ranks of the timed region is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "kerr_analytic_1024x1024_a0.9375_i60_230GHz"
+METRIC = "rays/s and geodesic steps/s at 1024^2 Kerr image, mixed vs FP64 at <=1e-3 flux"
+CPU_SAMPLE_STRIDE = 8  # oracle traces every 8th pixel in each direction (128 x 128 rays)
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(cam: dict, freqs, stride: int, threads: int = 0):
+    """Time the FP64 CPU oracle on the strided pixel subset of the workload."""
+    import oracle
+    from paper_1801_10452_b300 import scenes
+
+    s = oracle.scene(a=cam["spin"], incl_deg=cam["incl_deg"], r_cam=cam["r_cam"], nx=cam["nx"] // stride,
+                     ny=cam["ny"] // stride, amin=cam["alpha_min"], amax=cam["alpha_max"], bmin=cam["beta_min"],
+                     bmax=cam["beta_max"], eps=cam["eps"], r_stop_factor=cam["r_stop_factor"], r_esc=cam["r_escape"],
+                     mass_msun=cam["mass_msun"], dist_pc=cam["distance_pc"], **{
+                         "n0": scenes.ANALYTIC_PLASMA["n0"], "n_pow": scenes.ANALYTIC_PLASMA["n_pow"],
+                         "the0": scenes.ANALYTIC_PLASMA["the0"], "the_pow": scenes.ANALYTIC_PLASMA["the_pow"],
+                         "B0": scenes.ANALYTIC_PLASMA["B0_gauss"], "B_pow": scenes.ANALYTIC_PLASMA["B_pow"]})
+    # The strided camera keeps the full-size pixel pitch: cover every `stride`-th pixel
+    # centre of the full image.
+    da = (cam["alpha_max"] - cam["alpha_min"]) / cam["nx"]
+    db = (cam["beta_max"] - cam["beta_min"]) / cam["ny"]
+    n_s = cam["nx"] // stride
+    # pixel j of the sample = full pixel stride*j + stride//2
+    off = (stride // 2 + 0.5) * da - 0.5 * stride * da
+    s.amin = cam["alpha_min"] + off
+    s.amax = s.amin + n_s * stride * da
+    offb = (stride // 2 + 0.5) * db - 0.5 * stride * db
+    s.bmin = cam["beta_min"] + offb
+    s.bmax = s.bmin + (cam["ny"] // stride) * stride * db
+    oracle.lib()
+    t0 = time.perf_counter()
+    img, steps, status = oracle.render(s, freqs, nthreads=threads)
+    dt = time.perf_counter() - t0
+    # rescale the per-pixel Jy to the full-size pixel solid angle
+    img = img / (stride * stride)
+    return dict(seconds=dt, rays=img[0].size * len(freqs) / len(freqs), steps=int(steps.sum()), img=img,
+                cores=oracle.num_threads() if threads <= 0 else threads)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, a bounded sample per step."""
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return
+    from paper_1801_10452_b300 import scenes
+
+    cam = scenes.HEADLINE
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(cam, scenes.HEADLINE_FREQS, CPU_SAMPLE_STRIDE * 2)
+    secs, rays, steps = 0.0, 0, 0
+    for _ in range(args.steps):
+        r = oracle_sample(cam, scenes.HEADLINE_FREQS, CPU_SAMPLE_STRIDE * 2)
+        secs += r["seconds"]
+        rays += r["rays"]
+        steps += r["steps"]
+    v = rays / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic plasma, deterministic)",
+        "config": {"workload": WORKLOAD, "sample": f"every {CPU_SAMPLE_STRIDE * 2}th pixel per axis per step"},
+        "steps_per_s": steps / secs,
+        "cpu_baseline": {"value": v, "unit": "rays/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": f"{int(rays / args.steps)} rays per step (strided subset of the 1024^2 image)"},
+        "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _time_render(ctx, torch, freqs, image, flush_buf, n, stream):
+    """n renders, L2 flushed before each, device time of the renders only (CUDA events)."""
+    tot = 0.0
+    for _ in range(n):
+        flush_buf.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.render(freqs, image=image, flux=False, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot
+
+
+def run_native(args):
+    import torch
+
+    import paper_1801_10452_b300 as R
+    from paper_1801_10452_b300 import build, scenes
+
+    rank, local_rank, world = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    stream = torch.cuda.current_stream()
+    cam = dict(scenes.HEADLINE)
+    freqs = scenes.HEADLINE_FREQS
+    npix = cam["nx"] * cam["ny"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    ctx64 = R.Context(R.camera_desc(**cam, precision=R.FP64))
+    ctx64.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    image = torch.empty((len(freqs), cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
+    image64 = torch.empty_like(image)
+
+    # warm-up (also sizes the context's buffers)
+    for _ in range(args.warmup):
+        ctx.render(freqs, image=image, flux=False, stream=stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: mixed path ------------------------------------------------------
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ctx.stats_reset()
+    ctx.profile(True)
+    wall0 = time.perf_counter()
+    dev_ms = _time_render(ctx, torch, freqs, image, flush, args.steps, stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    st = ctx.stats()
+    if world > 1:
+        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    ms_step = dev_ms / args.steps
+    rays_step = npix * len(freqs)
+    value = world * rays_step / (ms_step * 1e-3)
+    steps_per_s = world * (st["steps"] / args.steps) / (ms_step * 1e-3)
+    launches = sum(v[1] for v in prof.values())
+
+    # ---- FP64 path on the same workload (the comparison the metric names) ----------------
+    ctx64.render(freqs, image=image64, flux=False, stream=stream)
+    torch.cuda.synchronize()
+    ctx64.stats_reset()
+    ctx64.profile(True)
+    n64 = max(1, min(args.steps, 3))
+    ms64 = _time_render(ctx64, torch, freqs, image64, flush, n64, stream) / n64
+    prof64 = ctx64.profile_read()
+    st64 = ctx64.stats()
+    _, fl_mixed = ctx.render(freqs, image=image, stream=stream)
+    _, fl64 = ctx64.render(freqs, image=image64, stream=stream)
+    torch.cuda.synchronize()
+
+    # ---- end to end through the C ABI with host buffers --------------------------------
+    img_host = np.zeros((len(freqs), cam["ny"], cam["nx"]))
+    ctx.render_host(freqs, want_image=True)
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ctx.render_host(freqs, want_image=True)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_v = world * rays_step / float(np.mean(e2e_t))
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel -------------------------------------------------
+    peaks = _peaks()
+    fma32 = R.measure_fma_peak(False)
+    fma64 = R.measure_fma_peak(True)
+    flops = _flops_per_step()
+    kern = {k: v for k, v in prof.items() if v[1] > 0 and k not in ("reduce",)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_n = kern[dom]
+    st_phase = ctx_phase_steps(st, prof)
+    if dom == "mixed_fp64":
+        fl = flops["fp64_step"] * st["fp64_steps"] / args.steps if flops["fp64_step"] else None
+        peak, pname = fma64, "fp64"
+    else:
+        fl = flops["fp32_step"] * st_phase.get(dom, 0) / args.steps if flops["fp32_step"] else None
+        peak, pname = fma32, "fp32"
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    achieved = fl / (per_launch_ms * 1e-3) / 1e12 if fl else None
+    roof = {"bound": "alu", "pipe": pname, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": f"measured FMA-chain microbenchmark ({pname}) in this run",
+            "flops_per_step": flops, "kernel_ms_per_launch": per_launch_ms}
+    fp64_kernel_ms = prof64["render_fp64"][0] / max(prof64["render_fp64"][1], 1)
+    fl64_launch = flops["fp64_step"] * st64["steps"] / max(prof64["render_fp64"][1], 1) if flops["fp64_step"] else None
+    roof64 = {"kernel": "render_fp64", "achieved": fl64_launch / (fp64_kernel_ms * 1e-3) / 1e12 if fl64_launch else None,
+              "peak": fma64, "unit": "TFLOP/s", "kernel_ms_per_launch": fp64_kernel_ms}
+    roof64["frac"] = roof64["achieved"] / fma64 if roof64["achieved"] else None
+
+    # ---- CPU oracle on a bounded sample of the same workload -----------------------------
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = oracle_sample(cam, freqs, CPU_SAMPLE_STRIDE)
+        cpu = {"value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"], "kind": "oracle",
+               "sample": f"{int(r['rays'])} rays: every {CPU_SAMPLE_STRIDE}th pixel per axis of the 1024^2 image",
+               "steps_per_s": r["steps"] / r["seconds"]}
+        # sampled parity of both GPU images against the oracle
+        o = r["img"]
+        sl = (slice(None), slice(CPU_SAMPLE_STRIDE // 2, None, CPU_SAMPLE_STRIDE), slice(CPU_SAMPLE_STRIDE // 2, None, CPU_SAMPLE_STRIDE))
+        g64 = image64.cpu().numpy()[sl]
+        gmx = image.cpu().numpy()[sl]
+        den = np.maximum(np.abs(o), 1e-12 * np.abs(o).max())
+        cpu["fp64_max_rel_err_sampled"] = float((np.abs(g64 - o) / den).max())
+        cpu["mixed_median_rel_err_sampled"] = float(np.median(np.abs(gmx - o) / den))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (analytic plasma, deterministic)",
+        "config": {"workload": WORKLOAD, "pixels": npix, "freqs_hz": freqs, "precision": "mixed", "r_fp64": cam.get("r_fp64", 6.0),
+                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed render"},
+        "geodesic_steps_per_s": steps_per_s, "steps_per_ray": st["steps"] / (args.steps * npix),
+        "fp64_step_fraction": st["fp64_steps"] / max(st["steps"], 1),
+        "fp64_path": {"value": world * rays_step / (ms64 * 1e-3), "unit": "rays/s", "ms_per_step": ms64,
+                      "geodesic_steps_per_s": world * (st64["steps"] / n64) / (ms64 * 1e-3), "roofline": roof64},
+        "speedup_vs_fp64": ms64 / ms_step,
+        "flux_jy": {"mixed": float(fl_mixed[0]), "fp64": float(fl64[0]),
+                    "mixed_rel_err_vs_fp64": float(abs(fl_mixed[0] / fl64[0] - 1))},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_v, "unit": "rays/s", "h2d_bytes_per_step": 8 * len(freqs),
+                "d2h_bytes_per_step": int(img_host.nbytes) + 8 * len(freqs)},
+        "gpu_launches": launches, "clocks": clocks, "wall_s_timed_region": wall,
+        "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64}, "measured_peaks_file": bool(peaks),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def ctx_phase_steps(st, prof):
+    """Steps per mixed phase: FP64 steps are counted; the FP32 steps are split between the
+    inbound and outbound phases in proportion to their device time."""
+    s32 = st["steps"] - st["fp64_steps"]
+    a = prof.get("mixed_fp32_in", (0, 0))[0]
+    c = prof.get("mixed_fp32_out", (0, 0))[0]
+    tot = a + c
+    if tot <= 0:
+        return {}
+    return {"mixed_fp32_in": s32 * a / tot, "mixed_fp32_out": s32 * c / tot, "mixed_fp64": st["fp64_steps"]}
+
+
+def _flops_per_step():
+    """Algorithmic flops of one geodesic step with its transfer sample (analytic plasma, one
+    frequency), counted from the kernel source: see the flop-count table in the design notes."""
+    from paper_1801_10452_b300 import flopcount
+
+    return flopcount.flops_per_step()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

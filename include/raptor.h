@@ -1,0 +1,223 @@
+/* raptor.h -- C ABI of the B300 ray-tracing / radiative-transfer library.
+ *
+ * The library integrates, for every camera pixel (and frame), one null geodesic backward
+ * from a distant camera through Kerr spacetime and, along it, unpolarised thermal
+ * synchrotron radiative transfer for a set of observing frequencies (Bronzwaer et al.
+ * 2018, "RAPTOR I").  The operations and the passages that define them:
+ *   - camera initial conditions: sec. 2.3, Eqs. 24-28 (Bardeen camera) and Eq. 4;
+ *   - geodesic equation as 8 first-order ODEs, Eqs. 5-6, with the connection of Eq. 2;
+ *   - classical RK4 step, Eqs. 7-15, with the adaptive step of Eqs. 20-23;
+ *   - backward transfer, Eqs. 35-36, per-step formal solution of Eq. 34,
+ *     fluid-frame frequency nu = -k.u (Eq. 30), observed intensity (Eq. 31);
+ *   - thermal synchrotron emissivity and Kirchhoff absorption, Eqs. 41-44;
+ *   - GRMHD unit scaling and R-beta electron temperature, Eqs. 45-46;
+ *   - MKS coordinates and Newton-Raphson theta -> x2, App. A.2; BL -> KS, App. A.1;
+ *   - fast- and slow-light sampling of GRMHD snapshots, sec. 5;
+ *   - flux density in Jy as the sum of pixel intensities times the pixel solid angle
+ *     (sec. 4.2.2, Table 3).
+ *
+ * Conventions for every call:
+ *   - Units: G = c = M = 1 inside; the camera's impact parameters alpha, beta, radii and
+ *     coordinate times are in M.  Frequencies in Hz.  Images in Jy per pixel.
+ *   - Pointers named *_dev are CUDA device pointers; *_host are host pointers.  The caller
+ *     owns every buffer it passes; the library never frees caller memory.  Descriptors are
+ *     copied at call time.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is enqueued on it.
+ *     Calls that return host data (flux_jy_host, stats) synchronise that stream first.
+ *   - Errors: every call returns a raptor_status.  Arguments are validated on the host
+ *     before any launch (RAPTOR_EINVAL, nothing enqueued).  A failing CUDA call returns
+ *     RAPTOR_ECUDA.  raptor_last_error() returns a message for the last failure on that
+ *     context.  No exception or abort crosses this ABI.
+ *   - Threads: a context is used by one host thread at a time.
+ */
+#ifndef RAPTOR_H
+#define RAPTOR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RAPTOR_OK = 0,
+    RAPTOR_EINVAL = 1,       /* invalid argument or descriptor; nothing was enqueued      */
+    RAPTOR_ENOMEM = 2,       /* device or host allocation failed                          */
+    RAPTOR_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed               */
+    RAPTOR_ETIMEOUT = 4,     /* a bounded device-side wait expired (see raptor_stats)     */
+    RAPTOR_ENOPLASMA = 5,    /* render before raptor_load_plasma                          */
+    RAPTOR_EUNSUPPORTED = 6  /* option recognised but not available in this build         */
+} raptor_status;
+
+/* Arithmetic of the integration.
+ *   RAPTOR_FP64:  every step in FP64.
+ *   RAPTOR_MIXED: geodesic steps and transfer in FP32 where r >= r_fp64 and away from radial
+ *                 turning points; FP64 inside r < r_fp64, where |k^r| < turn_kr |k^t|, and
+ *                 for the optical depth once tau > 10.  Rays are moved between FP32 and
+ *                 FP64 work queues so each warp runs one precision.
+ *   RAPTOR_MIXED_MLP: reserved for the learned surrogate (RAPTOR_EUNSUPPORTED here). */
+typedef enum { RAPTOR_FP64 = 0, RAPTOR_MIXED = 1, RAPTOR_MIXED_MLP = 2 } raptor_precision;
+
+typedef enum {
+    RAPTOR_PLASMA_ANALYTIC = 0,  /* n_e = n0 r^n_pow, Theta_e = the0 r^the_pow, B = B0 r^B_pow;
+                                    prograde Keplerian flow for r >= r_isco, free fall from rest
+                                    at infinity inside; toroidal field                     */
+    RAPTOR_PLASMA_GRID_MKS2D = 1 /* axisymmetric GRMHD-shaped snapshots on an MKS grid       */
+} raptor_plasma_kind;
+
+#define RAPTOR_FLAG_K2_EXACT 0x1u      /* exact K2(1/Theta_e) instead of 2 Theta_e^2 (sec. 4.2.2) */
+#define RAPTOR_FLAG_STEP_LINEAR_R 0x2u /* literal d lambda = eps r (no polar limiter)            */
+
+/* Ray termination codes written to status_dev (render_ex) and trace calls. */
+#define RAPTOR_RAY_ESCAPED 0   /* r > r_escape                       */
+#define RAPTOR_RAY_CAPTURED 1  /* r < r_stop_factor * r_horizon      */
+#define RAPTOR_RAY_THICK 2     /* min over frequencies of tau > tau_cut */
+#define RAPTOR_RAY_TRUNCATED 3 /* max_steps reached                  */
+#define RAPTOR_RAY_ERROR 4     /* non-finite state or nu_fluid <= 0  */
+
+typedef struct raptor_ctx raptor_ctx; /* opaque, library-owned */
+
+/* Camera, spacetime and integration settings (sec. 2.2-2.3, Table 2).  Fill with
+ * raptor_camera_desc_default() and override. */
+typedef struct {
+    double spin;          /* a/M, |a| < 1                                         [0.9]   */
+    double mass_msun;     /* black-hole mass M in solar masses                    [4e6]   */
+    double distance_pc;   /* distance D in parsec                                 [7880]  */
+    double r_cam;         /* camera radius (BL), M                                [1000]  */
+    double incl_deg;      /* inclination i, degrees, in (0, 180)                  [60]    */
+    int nx, ny;           /* pixels; pixel (row i, col j) has centre
+                             alpha = alpha_min + (j+1/2) dalpha, beta = beta_min + (i+1/2) dbeta */
+    double alpha_min, alpha_max, beta_min, beta_max; /* image plane, M           [+-20]  */
+    double eps;           /* step scale of Eqs. 20-23 (read in log r)             [0.05]  */
+    double r_stop_factor; /* capture when r < r_stop_factor r_horizon             [1.01]  */
+    double r_escape;      /* escape when r > r_escape                             [1000]  */
+    double tau_cut;       /* stop when every frequency has tau > tau_cut          [inf]   */
+    int max_steps;        /* per-ray step cap; capped rays are counted            [1e5]   */
+    int precision;        /* raptor_precision                                     [FP64]  */
+    unsigned flags;       /* RAPTOR_FLAG_*                                        [0]     */
+    int reserved0;
+    double r_fp64;        /* MIXED: FP64 for r < r_fp64                           [6]     */
+    double turn_kr;       /* MIXED: FP64 where |k^r| < turn_kr |k^t|              [0.05]  */
+    double t_delay;       /* slow light: added to each frame's camera time, M     [r_cam] */
+} raptor_camera_desc;
+
+/* Plasma (sec. 4.2.2, sec. 5).  For GRID_MKS2D, `fields` holds n_snap snapshots, each
+ * 8 FP32 planes [field][x2][x1] in the order rho, u, U1, U2, U3, B1, B2, B3 (HARM
+ * primitives in MKS components; U^i is the velocity relative to the normal observer),
+ * cell-centred on x1 in [x1_min, x1_max] (x1 = ln r) and x2 in [0, 1], with
+ * theta = pi x2 + (1-h)/2 sin(2 pi x2).  Snapshot s is at KS time t0 + s dt_snap. */
+typedef struct {
+    int kind;             /* raptor_plasma_kind                                          */
+    int slow_light;       /* GRID: 1 = interpolate snapshots linearly in ray time (sec. 5) */
+    double n0, n_pow, the0, the_pow, B0_gauss, B_pow; /* ANALYTIC profiles [1e6,-1.5,10,-1,20,-1] */
+    const float* fields;  /* GRID: host pointer (copied) or device pointer, see below     */
+    int n1, n2, n_snap;   /* GRID: sizes; n1, n2 >= 2, n_snap >= 1                        */
+    int fields_on_device; /* GRID: 1 = `fields` is a device pointer (copied device-to-device) */
+    double x1_min, x1_max, h_mks; /* GRID: radial range (ln r) and MKS h in (0, 1]        */
+    double t0, dt_snap;   /* GRID: time of snapshot 0 and spacing, M                      */
+    double mass_unit_g;   /* GRID: mass unit (Eq. 45), grams                             */
+    double r_high, r_low; /* GRID: R-beta parameters (Eq. 46)                             */
+    double gamma_ad;      /* GRID: adiabatic index                                 [4/3]  */
+} raptor_plasma_desc;
+
+/* Fill descriptors with the defaults shown in brackets above. */
+void raptor_camera_desc_default(raptor_camera_desc* desc);
+void raptor_plasma_desc_default(raptor_plasma_desc* desc);
+
+/* Create a context for one camera (sec. 2.3).  Validates desc (EINVAL), selects the
+ * current CUDA device, allocates the context's device work buffers (ENOMEM/ECUDA).
+ * *out receives the context; release it with raptor_destroy. */
+raptor_status raptor_camera_init(const raptor_camera_desc* desc, raptor_ctx** out);
+
+/* Replace the camera settings of an existing context (same rules as camera_init). */
+raptor_status raptor_camera_set(raptor_ctx* ctx, const raptor_camera_desc* desc);
+
+/* Load the plasma model.  ANALYTIC copies the profile constants.  GRID copies the snapshot
+ * array into a context-owned device buffer (host->device or device->device on `stream`);
+ * the caller's buffer may be freed once the call returns. */
+raptor_status raptor_load_plasma(raptor_ctx* ctx, const raptor_plasma_desc* desc, void* stream);
+
+/* Render one image at camera time t_obs (fast light).  freqs_hz[n_freq] is a host array
+ * (1 <= n_freq <= 64).  image_dev: device double [n_freq][ny][nx], Jy per pixel, written
+ * completely.  flux_jy_host: optional host double [n_freq] (NULL to skip; otherwise the
+ * stream is synchronised).  Grid plasma uses snapshot 0 unless slow_light is set. */
+raptor_status raptor_render(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs,
+                            double* image_dev, double* flux_jy_host, void* stream);
+
+/* As raptor_render, for rows [row0, row0 + n_rows) only (image_dev is [n_freq][n_rows][nx]),
+ * fast-light snapshot `snap` for grid plasma, and optional per-pixel diagnostics:
+ * steps_dev (int32 [n_rows][nx], accepted RK4 steps) and status_dev (int32, RAPTOR_RAY_*). */
+raptor_status raptor_render_ex(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs,
+                               int row0, int n_rows, int snap, double* image_dev, double* flux_jy_host,
+                               int* steps_dev, int* status_dev, void* stream);
+
+/* Render an image from host buffers: copies nothing in but the frequencies, renders, copies
+ * the image to image_host (double [n_freq][ny][nx], may be NULL) and the flux to
+ * flux_jy_host (may be NULL), and synchronises `stream`.  Device scratch is context-owned. */
+raptor_status raptor_render_host(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs,
+                                 double* image_host, double* flux_jy_host, void* stream);
+
+/* Light curve (sec. 5): frames f = 0..n_frames-1 at camera times t_obs_host[f]; every
+ * (frame, pixel) ray of every frame goes through one persistent launch.  Slow light when the
+ * grid plasma has slow_light = 1; otherwise frame f uses snapshot first_frame + f (fast
+ * light).  flux_jy_host: host double [n_frames][n_freq] (required; stream synchronised).
+ * images_dev: optional device double [n_frames][n_freq][ny][nx]. */
+raptor_status raptor_lightcurve(raptor_ctx* ctx, const double* freqs_hz, int n_freq,
+                                const double* t_obs_host, int n_frames, int first_frame,
+                                double* flux_jy_host, double* images_dev, void* stream);
+
+/* Trace one ray on the device and record every step: rec_host[n][12] = x^mu (4), k^mu (4),
+ * d lambda, nu_fluid/nu_obs (0 on the terminating step), I_obs and tau of the first
+ * frequency.  Returns up to max_rec records; *n_steps = total steps; *ray_status = RAPTOR_RAY_*.
+ * Synchronises `stream`.  Same arithmetic as raptor_render's FP64 path. */
+raptor_status raptor_trace_ray(raptor_ctx* ctx, double alpha, double beta, double t_obs,
+                               const double* freqs_hz, int n_freq, int max_rec, double* rec_host,
+                               int* n_steps, int* ray_status, double* intensity_host, void* stream);
+
+/* Counters accumulated over all launches since the context was created (synchronises the
+ * last stream used): rays traced, accepted RK4 steps, of which FP64 steps, rays truncated at
+ * max_steps, rays with an error status, learned-surrogate fallbacks. */
+raptor_status raptor_stats(raptor_ctx* ctx, unsigned long long* rays, unsigned long long* steps,
+                           unsigned long long* fp64_steps, unsigned long long* truncated,
+                           unsigned long long* errors, unsigned long long* fallback);
+
+/* Reset the counters of raptor_stats. */
+raptor_status raptor_stats_reset(raptor_ctx* ctx);
+
+/* Launch shape of the persistent kernels (used by the autotuner): threads per block in
+ * {32, 64, 96, 128} and resident blocks per SM (0 = the occupancy maximum). */
+raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm);
+
+/* Per-kernel device time, measured with CUDA events recorded around every kernel launch on
+ * the launch's own stream.  raptor_profile(ctx, 1) clears the accumulators and starts
+ * recording; raptor_profile(ctx, 0) stops.  raptor_profile_read waits for the recorded
+ * events and returns, per kernel slot RAPTOR_KERNEL_* (8 slots), the summed milliseconds
+ * (ms[8], may be NULL) and the number of launches since the last clear (launches[8], may
+ * be NULL; counted whether or not recording is on). */
+#define RAPTOR_KERNEL_RENDER_FP64 0  /* persistent FP64 ray kernel                         */
+#define RAPTOR_KERNEL_MIXED_A 1      /* mixed: FP32 phase on camera rays                   */
+#define RAPTOR_KERNEL_MIXED_B 2      /* mixed: FP64 phase (inner region, turning points)   */
+#define RAPTOR_KERNEL_MIXED_C 3      /* mixed: FP32 phase on outbound rays                 */
+#define RAPTOR_KERNEL_REDUCE 4       /* flux reduction (two launches per render)          */
+#define RAPTOR_KERNEL_TRACE 5        /* single-ray trace                                   */
+#define RAPTOR_KERNEL_LOAD 6         /* grid interleave at load time                       */
+raptor_status raptor_profile(raptor_ctx* ctx, int enable);
+raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches);
+
+/* FMA-chain microbenchmark on the current device: dependent FP64 (fp64 = 1) or FP32
+ * (fp64 = 0) fused multiply-adds on every SM; *tflops = achieved rate (2 flops per FMA).
+ * Measures the arithmetic ceiling used for the rooflines of the ray kernels. */
+raptor_status raptor_measure_fma_peak(int fp64, double* tflops);
+
+/* Message for the last failure on ctx ("" if none).  Valid until the next call on ctx. */
+const char* raptor_last_error(const raptor_ctx* ctx);
+
+/* Release the context and its device buffers (synchronises its device first). */
+void raptor_destroy(raptor_ctx* ctx);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int raptor_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAPTOR_H */

@@ -1,0 +1,295 @@
+"""B300-native backward Kerr ray tracing with synchrotron radiative transfer.
+
+Thin ctypes binding over ``libraptor.so`` (the C ABI of ``include/raptor.h``).  Every step
+of the computation runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch supplies device memory and streams.  Importing works without a GPU,
+but every call that needs the library fails loudly if ``libraptor.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libraptor.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOPLASMA, EUNSUPPORTED = range(7)
+FP64, MIXED, MIXED_MLP = 0, 1, 2
+PLASMA_ANALYTIC, PLASMA_GRID = 0, 1
+FLAG_K2_EXACT, FLAG_STEP_LINEAR_R = 0x1, 0x2
+RAY_ESCAPED, RAY_CAPTURED, RAY_THICK, RAY_TRUNCATED, RAY_ERROR = range(5)
+
+EXPORTS = [
+    "raptor_version", "raptor_camera_desc_default", "raptor_plasma_desc_default", "raptor_camera_init",
+    "raptor_camera_set", "raptor_load_plasma", "raptor_render", "raptor_render_ex", "raptor_render_host",
+    "raptor_lightcurve", "raptor_trace_ray", "raptor_stats", "raptor_stats_reset", "raptor_set_launch",
+    "raptor_last_error", "raptor_destroy", "raptor_profile", "raptor_profile_read", "raptor_measure_fma_peak",
+]
+KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak"]
+
+
+class RaptorError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"raptor status {status}: {msg}")
+        self.status = status
+
+
+class CameraDesc(C.Structure):
+    _fields_ = [
+        ("spin", C.c_double), ("mass_msun", C.c_double), ("distance_pc", C.c_double),
+        ("r_cam", C.c_double), ("incl_deg", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
+        ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("beta_min", C.c_double), ("beta_max", C.c_double),
+        ("eps", C.c_double), ("r_stop_factor", C.c_double), ("r_escape", C.c_double), ("tau_cut", C.c_double),
+        ("max_steps", C.c_int), ("precision", C.c_int), ("flags", C.c_uint), ("reserved0", C.c_int),
+        ("r_fp64", C.c_double), ("turn_kr", C.c_double), ("t_delay", C.c_double),
+    ]
+
+
+class PlasmaDesc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("slow_light", C.c_int),
+        ("n0", C.c_double), ("n_pow", C.c_double), ("the0", C.c_double), ("the_pow", C.c_double),
+        ("B0_gauss", C.c_double), ("B_pow", C.c_double),
+        ("fields", C.c_void_p), ("n1", C.c_int), ("n2", C.c_int), ("n_snap", C.c_int), ("fields_on_device", C.c_int),
+        ("x1_min", C.c_double), ("x1_max", C.c_double), ("h_mks", C.c_double),
+        ("t0", C.c_double), ("dt_snap", C.c_double), ("mass_unit_g", C.c_double),
+        ("r_high", C.c_double), ("r_low", C.c_double), ("gamma_ad", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libraptor.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1801_10452_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, ip, dp, st = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int
+        u64p = C.POINTER(C.c_ulonglong)
+        sig = {
+            "raptor_version": (C.c_int, []),
+            "raptor_camera_desc_default": (None, [C.POINTER(CameraDesc)]),
+            "raptor_plasma_desc_default": (None, [C.POINTER(PlasmaDesc)]),
+            "raptor_camera_init": (st, [C.POINTER(CameraDesc), C.POINTER(vp)]),
+            "raptor_camera_set": (st, [vp, C.POINTER(CameraDesc)]),
+            "raptor_load_plasma": (st, [vp, C.POINTER(PlasmaDesc), vp]),
+            "raptor_render": (st, [vp, dp, C.c_int, C.c_double, vp, dp, vp]),
+            "raptor_render_ex": (st, [vp, dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, vp, dp, vp, vp, vp]),
+            "raptor_render_host": (st, [vp, dp, C.c_int, C.c_double, dp, dp, vp]),
+            "raptor_lightcurve": (st, [vp, dp, C.c_int, dp, C.c_int, C.c_int, dp, vp, vp]),
+            "raptor_trace_ray": (st, [vp, C.c_double, C.c_double, C.c_double, dp, C.c_int, C.c_int, dp, ip, ip, dp, vp]),
+            "raptor_stats": (st, [vp, u64p, u64p, u64p, u64p, u64p, u64p]),
+            "raptor_stats_reset": (st, [vp]),
+            "raptor_set_launch": (st, [vp, C.c_int, C.c_int]),
+            "raptor_last_error": (C.c_char_p, [vp]),
+            "raptor_destroy": (None, [vp]),
+            "raptor_profile": (st, [vp, C.c_int]),
+            "raptor_profile_read": (st, [vp, dp, C.POINTER(C.c_longlong)]),
+            "raptor_measure_fma_peak": (st, [C.c_int, dp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def camera_desc(**kw) -> CameraDesc:
+    d = CameraDesc()
+    lib().raptor_camera_desc_default(C.byref(d))
+    for k, v in kw.items():
+        if not hasattr(d, k):
+            raise AttributeError(k)
+        setattr(d, k, v)
+    return d
+
+
+def plasma_desc(**kw) -> PlasmaDesc:
+    d = PlasmaDesc()
+    lib().raptor_plasma_desc_default(C.byref(d))
+    for k, v in kw.items():
+        if k == "fields":
+            continue
+        if not hasattr(d, k):
+            raise AttributeError(k)
+        setattr(d, k, v)
+    return d
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _freqs(freqs):
+    return np.ascontiguousarray(np.atleast_1d(np.asarray(freqs, dtype=np.float64)))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One camera (sec. 2.3) with its device work buffers."""
+
+    def __init__(self, cam: CameraDesc | None = None, **kw):
+        self.cam = cam if cam is not None else camera_desc(**kw)
+        h = C.c_void_p()
+        st = lib().raptor_camera_init(C.byref(self.cam), C.byref(h))
+        if st != OK:
+            raise RaptorError(st, "raptor_camera_init rejected the camera descriptor")
+        self._h = h
+        self._keep = None
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = lib().raptor_last_error(self._h)
+            raise RaptorError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_camera(self, cam: CameraDesc | None = None, **kw):
+        if cam is None:
+            cam = self.cam
+            for k, v in kw.items():
+                setattr(cam, k, v)
+        self._check(lib().raptor_camera_set(self._h, C.byref(cam)), "raptor_camera_set")
+        self.cam = cam
+
+    def load_plasma(self, desc: PlasmaDesc | None = None, fields=None, stream=None, **kw):
+        """Analytic plasma (default) or a grid: `fields` is a float32 array/tensor
+        [n_snap][8][n2][n1] on the host (numpy) or the device (torch)."""
+        if desc is None:
+            desc = plasma_desc(**kw)
+        if fields is not None:
+            if isinstance(fields, np.ndarray):
+                f = np.ascontiguousarray(fields, dtype=np.float32)
+                desc.fields = f.ctypes.data
+                desc.fields_on_device = 0
+            else:
+                import torch
+
+                f = fields.contiguous().to(torch.float32)
+                desc.fields = f.data_ptr()
+                desc.fields_on_device = 1 if f.is_cuda else 0
+            desc.n_snap, _, desc.n2, desc.n1 = f.shape
+            desc.kind = PLASMA_GRID
+            self._keep = f
+        self._check(lib().raptor_load_plasma(self._h, C.byref(desc), _stream(stream)), "raptor_load_plasma")
+        self.plasma = desc
+        return self
+
+    def render(self, freqs, t_obs=0.0, image=None, stream=None, flux=True, row0=0, n_rows=None, snap=0,
+               steps=None, status=None):
+        """Render into `image` (torch float64 cuda [n_freq][n_rows][nx]; allocated if None).
+        Returns (image, flux_jy numpy [n_freq] or None)."""
+        import torch
+
+        nu = _freqs(freqs)
+        n_rows = self.cam.ny if n_rows is None else n_rows
+        if image is None:
+            image = torch.empty((nu.size, n_rows, self.cam.nx), dtype=torch.float64, device="cuda")
+        fl = np.zeros(nu.size) if flux else None
+        st = lib().raptor_render_ex(
+            self._h, _dp(nu), nu.size, float(t_obs), int(row0), int(n_rows), int(snap), C.c_void_p(image.data_ptr()),
+            _dp(fl) if flux else None, C.c_void_p(steps.data_ptr()) if steps is not None else None,
+            C.c_void_p(status.data_ptr()) if status is not None else None, _stream(stream))
+        self._check(st, "raptor_render_ex")
+        return image, fl
+
+    def render_host(self, freqs, t_obs=0.0, want_image=True, stream=None):
+        nu = _freqs(freqs)
+        img = np.zeros((nu.size, self.cam.ny, self.cam.nx)) if want_image else None
+        fl = np.zeros(nu.size)
+        st = lib().raptor_render_host(self._h, _dp(nu), nu.size, float(t_obs), _dp(img) if want_image else None, _dp(fl),
+                                      _stream(stream))
+        self._check(st, "raptor_render_host")
+        return img, fl
+
+    def lightcurve(self, freqs, t_obs, first_frame=0, images=None, stream=None):
+        nu = _freqs(freqs)
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(t_obs, dtype=np.float64)))
+        fl = np.zeros((t.size, nu.size))
+        st = lib().raptor_lightcurve(self._h, _dp(nu), nu.size, _dp(t), t.size, int(first_frame), _dp(fl),
+                                     C.c_void_p(images.data_ptr()) if images is not None else None, _stream(stream))
+        self._check(st, "raptor_lightcurve")
+        return fl
+
+    def trace_ray(self, alpha, beta, freqs, t_obs=0.0, max_rec=20000, stream=None):
+        nu = _freqs(freqs)
+        rec = np.zeros((max(max_rec, 1), 12))
+        n = C.c_int(0)
+        s = C.c_int(0)
+        Iv = np.zeros(nu.size)
+        st = lib().raptor_trace_ray(self._h, float(alpha), float(beta), float(t_obs), _dp(nu), nu.size, int(max_rec),
+                                    _dp(rec), C.byref(n), C.byref(s), _dp(Iv), _stream(stream))
+        self._check(st, "raptor_trace_ray")
+        return dict(steps=n.value, status=s.value, I=Iv, trace=rec[: min(n.value, max_rec)].copy())
+
+    def stats(self):
+        v = [C.c_ulonglong(0) for _ in range(6)]
+        self._check(lib().raptor_stats(self._h, *[C.byref(x) for x in v]), "raptor_stats")
+        return dict(zip(["rays", "steps", "fp64_steps", "truncated", "errors", "fallback"], [x.value for x in v]))
+
+    def stats_reset(self):
+        self._check(lib().raptor_stats_reset(self._h), "raptor_stats_reset")
+
+    def set_launch(self, threads_per_block, blocks_per_sm):
+        self._check(lib().raptor_set_launch(self._h, int(threads_per_block), int(blocks_per_sm)), "raptor_set_launch")
+
+    def profile(self, enable=True):
+        self._check(lib().raptor_profile(self._h, 1 if enable else 0), "raptor_profile")
+
+    def profile_read(self):
+        """{kernel name: (ms, launches)} since the last profile(True)."""
+        ms = np.zeros(8)
+        n = (C.c_longlong * 8)()
+        self._check(lib().raptor_profile_read(self._h, _dp(ms), n), "raptor_profile_read")
+        return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(8)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().raptor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def measure_fma_peak(fp64: bool) -> float:
+    """Achieved FMA throughput (TFLOP/s) of the current device in FP64 or FP32."""
+    v = C.c_double(0.0)
+    st = lib().raptor_measure_fma_peak(1 if fp64 else 0, C.byref(v))
+    if st != OK:
+        raise RaptorError(st, "raptor_measure_fma_peak")
+    return v.value
+
+
+def pixel_centres(cam: CameraDesc):
+    """(alpha[nx], beta[ny]) pixel centres of the camera (sec. 2.3 image plane)."""
+    da = (cam.alpha_max - cam.alpha_min) / cam.nx
+    db = (cam.beta_max - cam.beta_min) / cam.ny
+    return cam.alpha_min + (np.arange(cam.nx) + 0.5) * da, cam.beta_min + (np.arange(cam.ny) + 0.5) * db

@@ -1,0 +1,748 @@
+// raptor_api.cu -- host implementation of the C ABI declared in include/raptor.h.
+//
+// Validation on the host, context-owned device buffers, launch configuration, the
+// persistent kernels of raptor_kernels_fp64.cuh / raptor_kernels_mixed.cuh and the
+// deterministic flux reduction.  No host-side fallback computes any part of a result.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/raptor.h"
+#include "raptor_kernels_fp64.cuh"
+#include "raptor_kernels_mixed.cuh"
+
+using namespace raptor;
+
+struct raptor_ctx {
+    raptor_camera_desc cam;
+    raptor_plasma_desc plasma;
+    bool has_plasma = false;
+    int device = 0;
+    int num_sms = 0;
+    float* d_grid = nullptr;      // interleaved [snap][n2][n1][8]
+    size_t grid_cap = 0;
+    unsigned long long* d_counters = nullptr;  // [8] work counters
+    unsigned long long* d_stats = nullptr;     // [8]
+    double* d_partial = nullptr;
+    size_t partial_cap = 0;
+    double* d_flux = nullptr;
+    size_t flux_cap = 0;
+    double* d_img = nullptr;      // scratch image (host render, light curves without images)
+    size_t img_cap = 0;
+    double* d_tframes = nullptr;
+    size_t tframes_cap = 0;
+    int* d_trace_int = nullptr;   // [2]
+    double* d_trace_I = nullptr;  // [64]
+    double* d_rec = nullptr;
+    size_t rec_cap = 0;
+    MixedQueues mq;               // mixed-precision hand-off queues
+    size_t mq_cap = 0;
+    std::string err;
+    cudaStream_t last_stream = nullptr;
+    int launch_block = 128;       // threads per block of the persistent kernels
+    int launch_bps = 0;           // blocks per SM (0 = occupancy maximum)
+    // per-kernel CUDA-event timing (raptor_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
+    double prof_ms[kProfSlots] = {0};
+    long long prof_launches[kProfSlots] = {0};
+};
+
+namespace {
+
+cudaEvent_t take_event(raptor_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one kernel launch with events on its stream when profiling is on.
+struct ProfScope {
+    raptor_ctx* c;
+    int slot;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(raptor_ctx* c_, int slot_, cudaStream_t s_) : c(c_), slot(slot_), s(s_) {
+        c->prof_launches[slot] += 1;
+        if (c->prof) {
+            a = take_event(c);
+            b = take_event(c);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ProfScope() {
+        if (c->prof && a && b) {
+            cudaEventRecord(b, s);
+            c->ev_open.push_back({slot, {a, b}});
+        }
+    }
+};
+
+raptor_status fail(raptor_ctx* c, raptor_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define RCK(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? RAPTOR_ENOMEM : RAPTOR_ECUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+template <typename T>
+cudaError_t ensure(T** p, size_t* cap, size_t n) {
+    if (*cap >= n && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+std::string validate_camera(const raptor_camera_desc* d) {
+    if (!d) return "camera descriptor is NULL";
+    if (!std::isfinite(d->spin) || std::fabs(d->spin) >= 1.0) return "spin must satisfy |a| < 1";
+    if (!finite_pos(d->mass_msun)) return "mass_msun must be positive";
+    if (!finite_pos(d->distance_pc)) return "distance_pc must be positive";
+    const double rh = 1.0 + std::sqrt(1.0 - d->spin * d->spin);
+    if (!std::isfinite(d->r_cam) || d->r_cam <= 2.0 * rh || d->r_cam > 1e7) return "r_cam must lie in (2 r_h, 1e7]";
+    if (!std::isfinite(d->incl_deg) || d->incl_deg <= 0.0 || d->incl_deg >= 180.0) return "incl_deg must lie in (0, 180)";
+    if (d->nx < 1 || d->ny < 1 || (long long)d->nx * d->ny > (1LL << 31) - 1) return "nx, ny must be >= 1 with nx*ny < 2^31";
+    if (!(d->alpha_max > d->alpha_min) || !std::isfinite(d->alpha_min) || !std::isfinite(d->alpha_max)) return "alpha range invalid";
+    if (!(d->beta_max > d->beta_min) || !std::isfinite(d->beta_min) || !std::isfinite(d->beta_max)) return "beta range invalid";
+    if (!(d->eps > 0.0) || !(d->eps <= 1.0)) return "eps must lie in (0, 1]";
+    if (!(d->r_stop_factor >= 1.0) || !std::isfinite(d->r_stop_factor)) return "r_stop_factor must be >= 1";
+    if (!std::isfinite(d->r_escape) || d->r_escape < d->r_cam) return "r_escape must be finite and >= r_cam";
+    if (!(d->tau_cut > 0.0)) return "tau_cut must be > 0 (may be +inf)";
+    if (d->max_steps < 1) return "max_steps must be >= 1";
+    if (d->precision < RAPTOR_FP64 || d->precision > RAPTOR_MIXED_MLP) return "unknown precision";
+    if (d->flags & ~(RAPTOR_FLAG_K2_EXACT | RAPTOR_FLAG_STEP_LINEAR_R)) return "unknown flag bits";
+    if (!(d->r_fp64 >= 0.0) || !std::isfinite(d->r_fp64)) return "r_fp64 must be finite and >= 0";
+    if (!(d->turn_kr >= 0.0) || !std::isfinite(d->turn_kr)) return "turn_kr must be finite and >= 0";
+    if (!std::isfinite(d->t_delay)) return "t_delay must be finite";
+    return "";
+}
+
+std::string validate_plasma(const raptor_plasma_desc* d) {
+    if (!d) return "plasma descriptor is NULL";
+    if (d->kind == RAPTOR_PLASMA_ANALYTIC) {
+        const double v[6] = {d->n0, d->n_pow, d->the0, d->the_pow, d->B0_gauss, d->B_pow};
+        for (double x : v)
+            if (!std::isfinite(x)) return "analytic plasma constants must be finite";
+        if (!(d->n0 >= 0.0) || !(d->the0 > 0.0) || !(d->B0_gauss >= 0.0)) return "need n0 >= 0, the0 > 0, B0 >= 0";
+        return "";
+    }
+    if (d->kind != RAPTOR_PLASMA_GRID_MKS2D) return "unknown plasma kind";
+    if (!d->fields) return "grid fields pointer is NULL";
+    if (d->n1 < 2 || d->n2 < 2 || d->n_snap < 1) return "grid needs n1, n2 >= 2 and n_snap >= 1";
+    if ((long long)d->n1 * d->n2 * d->n_snap * 8 > (1LL << 34)) return "grid too large";
+    if (!(d->x1_max > d->x1_min) || !std::isfinite(d->x1_min) || !std::isfinite(d->x1_max)) return "x1 range invalid";
+    if (!(d->h_mks > 0.0) || !(d->h_mks <= 1.0)) return "h_mks must lie in (0, 1]";
+    if (d->n_snap > 1 && !finite_pos(d->dt_snap)) return "dt_snap must be positive";
+    if (!std::isfinite(d->t0)) return "t0 must be finite";
+    if (!finite_pos(d->mass_unit_g)) return "mass_unit_g must be positive";
+    if (!(d->r_high > 0.0) || !(d->r_low > 0.0) || !std::isfinite(d->r_high) || !std::isfinite(d->r_low)) return "R_high, R_low must be positive";
+    if (!(d->gamma_ad > 1.0) || !std::isfinite(d->gamma_ad)) return "gamma_ad must be > 1";
+    return "";
+}
+
+double r_isco_prograde(double a) {
+    const double z1 = 1.0 + std::cbrt(1.0 - a * a) * (std::cbrt(1.0 + a) + std::cbrt(1.0 - a));
+    const double z2 = std::sqrt(3.0 * a * a + z1 * z1);
+    const double sg = a < 0.0 ? -1.0 : 1.0;
+    return 3.0 + z2 - sg * std::sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
+}
+
+// Host-side parameter block shared by every launch of a context.
+Params base_params(const raptor_ctx* c) {
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    const raptor_camera_desc& d = c->cam;
+    p.a = d.spin;
+    p.r_cam = d.r_cam;
+    p.incl = d.incl_deg * kPi / 180.0;
+    p.sin_i = std::sin(p.incl);
+    p.cos_i = std::cos(p.incl);
+    p.nx = d.nx;
+    p.ny = d.ny;
+    p.da = (d.alpha_max - d.alpha_min) / d.nx;
+    p.db = (d.beta_max - d.beta_min) / d.ny;
+    p.amin = d.alpha_min;
+    p.bmin = d.beta_min;
+    p.eps = d.eps;
+    p.r_stop = d.r_stop_factor * (1.0 + std::sqrt(1.0 - d.spin * d.spin));
+    p.r_esc = d.r_escape;
+    p.tau_cut = d.tau_cut;
+    p.max_steps = d.max_steps;
+    p.flags = d.flags;
+    p.Lcm = kG * d.mass_msun * kMsun / (kC * kC);
+    const double D = d.distance_pc * kPc;
+    p.pix_jy = p.da * p.db * p.Lcm * p.Lcm / (D * D) / 1e-23;
+    p.r_fp64 = d.r_fp64;
+    p.turn_kr = d.turn_kr;
+    const raptor_plasma_desc& q = c->plasma;
+    p.kind = q.kind;
+    p.slow = q.slow_light;
+    p.n0 = q.n0;
+    p.n_pow = q.n_pow;
+    p.the0 = q.the0;
+    p.the_pow = q.the_pow;
+    p.B0 = q.B0_gauss;
+    p.B_pow = q.B_pow;
+    p.r_isco = r_isco_prograde(d.spin);
+    if (q.kind == RAPTOR_PLASMA_GRID_MKS2D) {
+        p.grid = c->d_grid;
+        p.n1 = q.n1;
+        p.n2 = q.n2;
+        p.n_snap = q.n_snap;
+        p.x1_min = q.x1_min;
+        p.x1_max = q.x1_max;
+        p.dx1 = (q.x1_max - q.x1_min) / q.n1;
+        p.dx2 = 1.0 / q.n2;
+        p.h_mks = q.h_mks;
+        p.t0 = q.t0;
+        p.dt_snap = q.n_snap > 1 ? q.dt_snap : 1.0;
+        const double rho0 = q.mass_unit_g / (p.Lcm * p.Lcm * p.Lcm);
+        p.rho0_ne = rho0 / (kMe + kMp);
+        p.B_unit = kC * std::sqrt(4.0 * kPi * rho0);
+        p.r_high = q.r_high;
+        p.r_low = q.r_low;
+        p.gam = q.gamma_ad;
+    }
+    return p;
+}
+
+int grid_blocks(const raptor_ctx* c, int per_sm_occ) {
+    const int bps = c->launch_bps > 0 ? std::min(c->launch_bps, per_sm_occ) : per_sm_occ;
+    return std::max(1, bps) * c->num_sms;
+}
+
+template <int NF>
+cudaError_t launch_fp64_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fp64<NF>, c->launch_block, 0);
+    if (e != cudaSuccess) return e;
+    const long long need = (p.n_rays + c->launch_block - 1) / c->launch_block;
+    const long long blocks = std::min<long long>(grid_blocks(c, std::max(occ, 1)), need);
+    ProfScope ps(c, kProfRenderFp64, s);
+    k_render_fp64<NF><<<(int)std::max<long long>(blocks, 1), c->launch_block, 0, s>>>(p, c->d_counters, c->d_stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64(raptor_ctx* c, const Params& p, cudaStream_t s) {
+    if (p.nf <= 1) return launch_fp64_nf<1>(c, p, s);
+    if (p.nf <= 2) return launch_fp64_nf<2>(c, p, s);
+    if (p.nf <= 4) return launch_fp64_nf<4>(c, p, s);
+    if (p.nf <= 8) return launch_fp64_nf<8>(c, p, s);
+    return launch_fp64_nf<16>(c, p, s);
+}
+
+// Mixed precision: phase A (FP32, camera rays) -> phase B (FP64 queue) -> phase C (FP32
+// queue), ordered by the stream.
+template <int NF>
+cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 8, s);
+    if (e != cudaSuccess) return e;
+    int occ32 = 0, occ64 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_mixed_fp32<NF>, c->launch_block, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_mixed_fp64<NF>, c->launch_block, 0);
+    if (e != cudaSuccess) return e;
+    const int b32 = grid_blocks(c, std::max(occ32, 1));
+    const int b64 = grid_blocks(c, std::max(occ64, 1));
+    const long long need = (p.n_rays + c->launch_block - 1) / c->launch_block;
+    {
+        ProfScope ps(c, kProfMixedA, s);
+        k_mixed_fp32<NF><<<(int)std::max<long long>(1, std::min<long long>(b32, need)), c->launch_block, 0, s>>>(
+            p, c->mq, c->d_counters, c->d_stats, 0);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(c, kProfMixedB, s);
+        k_mixed_fp64<NF><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(c, kProfMixedC, s);
+        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats, 1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mixed(raptor_ctx* c, const Params& p, cudaStream_t s) {
+    if (p.nf <= 1) return launch_mixed_nf<1>(c, p, s);
+    if (p.nf <= 2) return launch_mixed_nf<2>(c, p, s);
+    if (p.nf <= 4) return launch_mixed_nf<4>(c, p, s);
+    if (p.nf <= 8) return launch_mixed_nf<8>(c, p, s);
+    return launch_mixed_nf<16>(c, p, s);
+}
+
+// Enqueue every ray of `p` (all frequency chunks), then the flux reduction of `planes`
+// image planes into c->d_flux.
+raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_freq, long long planes_per_frame,
+                       int n_frames, cudaStream_t s) {
+    if (ctx->cam.precision == RAPTOR_MIXED_MLP)
+        return fail(ctx, RAPTOR_EUNSUPPORTED, "RAPTOR_MIXED_MLP is not available in this build");
+    p.nf_total = n_freq;
+    for (int f0 = 0; f0 < n_freq; f0 += 16) {
+        p.f_off = f0;
+        p.nf = std::min(16, n_freq - f0);
+        for (int f = 0; f < p.nf; ++f) p.nu[f] = freqs[f0 + f];
+        if (ctx->cam.precision == RAPTOR_FP64) {
+            RCK(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * 8, s));
+            RCK(launch_fp64(ctx, p, s));
+        } else {
+            const size_t need = (size_t)p.n_rays;
+            if (ctx->mq_cap < need || ctx->mq.nf_cap < p.nf) {
+                free_mixed_queues(ctx->mq);
+                ctx->mq_cap = 0;
+                RCK(alloc_mixed_queues(ctx->mq, need, 16));
+                ctx->mq_cap = need;
+            }
+            RCK(launch_mixed(ctx, p, s));
+        }
+    }
+    // flux: planes = n_frames * n_freq, each n_rows * nx
+    const long long len = (long long)p.n_rows * p.nx;
+    const int planes = n_frames * n_freq;
+    const int chunks = (int)std::min<long long>(256, std::max<long long>(1, len / 4096));
+    RCK(ensure(&ctx->d_partial, &ctx->partial_cap, (size_t)planes * chunks));
+    RCK(ensure(&ctx->d_flux, &ctx->flux_cap, (size_t)planes));
+    dim3 g1(chunks, planes);
+    {
+        ProfScope ps(ctx, kProfReduce, s);
+        k_reduce_partial<<<g1, kRedThreads, 0, s>>>(p.image, len, chunks, ctx->d_partial);
+    }
+    RCK(cudaGetLastError());
+    {
+        ProfScope ps(ctx, kProfReduce, s);
+        k_reduce_final<<<planes, kRedThreads, 0, s>>>(ctx->d_partial, chunks, ctx->d_flux);
+    }
+    RCK(cudaGetLastError());
+    (void)planes_per_frame;
+    return RAPTOR_OK;
+}
+
+raptor_status check_freqs(raptor_ctx* ctx, const double* freqs, int n_freq) {
+    if (!freqs) return fail(ctx, RAPTOR_EINVAL, "freqs_hz is NULL");
+    if (n_freq < 1 || n_freq > 64) return fail(ctx, RAPTOR_EINVAL, "n_freq must lie in [1, 64]");
+    for (int f = 0; f < n_freq; ++f)
+        if (!finite_pos(freqs[f])) return fail(ctx, RAPTOR_EINVAL, "frequencies must be finite and positive");
+    return RAPTOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int raptor_version(void) { return 10000; }
+
+void raptor_camera_desc_default(raptor_camera_desc* d) {
+    if (!d) return;
+    std::memset(d, 0, sizeof(*d));
+    d->spin = 0.9;
+    d->mass_msun = 4.0e6;
+    d->distance_pc = 7.88e3;
+    d->r_cam = 1000.0;
+    d->incl_deg = 60.0;
+    d->nx = d->ny = 64;
+    d->alpha_min = d->beta_min = -20.0;
+    d->alpha_max = d->beta_max = 20.0;
+    d->eps = 0.05;
+    d->r_stop_factor = 1.01;
+    d->r_escape = 1000.0;
+    d->tau_cut = INFINITY;
+    d->max_steps = 100000;
+    d->precision = RAPTOR_FP64;
+    d->flags = 0;
+    d->r_fp64 = 6.0;
+    d->turn_kr = 0.05;
+    d->t_delay = 1000.0;
+}
+
+void raptor_plasma_desc_default(raptor_plasma_desc* d) {
+    if (!d) return;
+    std::memset(d, 0, sizeof(*d));
+    d->kind = RAPTOR_PLASMA_ANALYTIC;
+    d->n0 = 1.0e6;
+    d->n_pow = -1.5;
+    d->the0 = 10.0;
+    d->the_pow = -1.0;
+    d->B0_gauss = 20.0;
+    d->B_pow = -1.0;
+    d->h_mks = 1.0;
+    d->dt_snap = 1.0;
+    d->r_high = d->r_low = 1.0;
+    d->gamma_ad = 4.0 / 3.0;
+}
+
+raptor_status raptor_camera_init(const raptor_camera_desc* desc, raptor_ctx** out) {
+    if (!out) return RAPTOR_EINVAL;
+    *out = nullptr;
+    const std::string v = validate_camera(desc);
+    if (!v.empty()) return RAPTOR_EINVAL;
+    raptor_ctx* ctx = new (std::nothrow) raptor_ctx();
+    if (!ctx) return RAPTOR_ENOMEM;
+    ctx->cam = *desc;
+    raptor_plasma_desc_default(&ctx->plasma);
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_counters, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_stats, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_trace_int, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_trace_I, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+        const raptor_status s = e == cudaErrorMemoryAllocation ? RAPTOR_ENOMEM : RAPTOR_ECUDA;
+        raptor_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_camera_set(raptor_ctx* ctx, const raptor_camera_desc* desc) {
+    if (!ctx) return RAPTOR_EINVAL;
+    const std::string v = validate_camera(desc);
+    if (!v.empty()) return fail(ctx, RAPTOR_EINVAL, v);
+    ctx->cam = *desc;
+    return RAPTOR_OK;
+}
+
+// Transpose [snap][8][n2][n1] planes into interleaved [snap][n2][n1][8] cells.
+__global__ void k_interleave_grid(const float* __restrict__ src, float* __restrict__ dst, long long cells_per_snap, int n_snap) {
+    const long long total = cells_per_snap * n_snap;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total; c += (long long)gridDim.x * blockDim.x) {
+        const long long s = c / cells_per_snap, cell = c - s * cells_per_snap;
+        const float* S = src + s * 8 * cells_per_snap + cell;
+        float4 lo = make_float4(S[0], S[cells_per_snap], S[2 * cells_per_snap], S[3 * cells_per_snap]);
+        float4 hi = make_float4(S[4 * cells_per_snap], S[5 * cells_per_snap], S[6 * cells_per_snap], S[7 * cells_per_snap]);
+        reinterpret_cast<float4*>(dst)[2 * c] = lo;
+        reinterpret_cast<float4*>(dst)[2 * c + 1] = hi;
+    }
+}
+
+raptor_status raptor_load_plasma(raptor_ctx* ctx, const raptor_plasma_desc* desc, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    const std::string v = validate_plasma(desc);
+    if (!v.empty()) return fail(ctx, RAPTOR_EINVAL, v);
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    if (desc->kind == RAPTOR_PLASMA_GRID_MKS2D) {
+        const size_t cells = (size_t)desc->n1 * desc->n2;
+        const size_t n = cells * desc->n_snap * 8;
+        RCK(ensure(&ctx->d_grid, &ctx->grid_cap, n));
+        float* staging = nullptr;
+        RCK(cudaMallocAsync((void**)&staging, n * sizeof(float), s));
+        cudaError_t e = cudaMemcpyAsync(staging, desc->fields, n * sizeof(float),
+                                        desc->fields_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            const int blocks = (int)std::min<size_t>(4096, (cells * desc->n_snap + 255) / 256);
+            ProfScope ps(ctx, kProfLoad, s);
+            k_interleave_grid<<<std::max(blocks, 1), 256, 0, s>>>(staging, ctx->d_grid, (long long)cells, desc->n_snap);
+            e = cudaGetLastError();
+        }
+        cudaError_t e2 = cudaFreeAsync(staging, s);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && !desc->fields_on_device) e = cudaStreamSynchronize(s);  // caller may free its host buffer
+        if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, std::string("load_plasma: ") + cudaGetErrorString(e));
+    }
+    ctx->plasma = *desc;
+    ctx->plasma.fields = nullptr;
+    ctx->has_plasma = true;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_render_ex(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, int row0, int n_rows,
+                               int snap, double* image_dev, double* flux_jy_host, int* steps_dev, int* status_dev,
+                               void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->has_plasma) return fail(ctx, RAPTOR_ENOPLASMA, "raptor_load_plasma has not been called");
+    raptor_status st = check_freqs(ctx, freqs_hz, n_freq);
+    if (st != RAPTOR_OK) return st;
+    if (!image_dev) return fail(ctx, RAPTOR_EINVAL, "image_dev is NULL");
+    if (row0 < 0 || n_rows < 1 || row0 + n_rows > ctx->cam.ny) return fail(ctx, RAPTOR_EINVAL, "row window outside the image");
+    if (!std::isfinite(t_obs)) return fail(ctx, RAPTOR_EINVAL, "t_obs must be finite");
+    if (ctx->plasma.kind == RAPTOR_PLASMA_GRID_MKS2D && (snap < 0 || snap >= ctx->plasma.n_snap))
+        return fail(ctx, RAPTOR_EINVAL, "snap outside [0, n_snap)");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    Params p = base_params(ctx);
+    p.row0 = row0;
+    p.n_rows = n_rows;
+    p.n_pix = n_rows * ctx->cam.nx;
+    p.n_rays = p.n_pix;
+    p.t_cam = t_obs + ctx->cam.t_delay;
+    p.snap = snap;
+    p.image = image_dev;
+    p.steps_out = steps_dev;
+    p.status_out = status_dev;
+    st = run_rays(ctx, p, freqs_hz, n_freq, n_freq, 1, s);
+    if (st != RAPTOR_OK) return st;
+    if (flux_jy_host) {
+        RCK(cudaMemcpyAsync(flux_jy_host, ctx->d_flux, n_freq * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RCK(cudaStreamSynchronize(s));
+    }
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_render(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, double* image_dev,
+                            double* flux_jy_host, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    return raptor_render_ex(ctx, freqs_hz, n_freq, t_obs, 0, ctx->cam.ny, 0, image_dev, flux_jy_host, nullptr, nullptr,
+                            stream);
+}
+
+raptor_status raptor_render_host(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, double* image_host,
+                                 double* flux_jy_host, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    raptor_status st = check_freqs(ctx, freqs_hz, n_freq);
+    if (st != RAPTOR_OK) return st;
+    const size_t n = (size_t)n_freq * ctx->cam.nx * ctx->cam.ny;
+    RCK(ensure(&ctx->d_img, &ctx->img_cap, n));
+    double flux[64];
+    st = raptor_render(ctx, freqs_hz, n_freq, t_obs, ctx->d_img, flux, stream);
+    if (st != RAPTOR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (image_host) {
+        RCK(cudaMemcpyAsync(image_host, ctx->d_img, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RCK(cudaStreamSynchronize(s));
+    }
+    if (flux_jy_host) std::memcpy(flux_jy_host, flux, n_freq * sizeof(double));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_lightcurve(raptor_ctx* ctx, const double* freqs_hz, int n_freq, const double* t_obs_host, int n_frames,
+                                int first_frame, double* flux_jy_host, double* images_dev, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->has_plasma) return fail(ctx, RAPTOR_ENOPLASMA, "raptor_load_plasma has not been called");
+    raptor_status st = check_freqs(ctx, freqs_hz, n_freq);
+    if (st != RAPTOR_OK) return st;
+    if (!t_obs_host || n_frames < 1) return fail(ctx, RAPTOR_EINVAL, "need t_obs_host and n_frames >= 1");
+    if (!flux_jy_host) return fail(ctx, RAPTOR_EINVAL, "flux_jy_host is NULL");
+    for (int f = 0; f < n_frames; ++f)
+        if (!std::isfinite(t_obs_host[f])) return fail(ctx, RAPTOR_EINVAL, "frame times must be finite");
+    const bool grid = ctx->plasma.kind == RAPTOR_PLASMA_GRID_MKS2D;
+    const bool fast = grid && !ctx->plasma.slow_light;
+    if (fast && (first_frame < 0 || first_frame + n_frames > ctx->plasma.n_snap))
+        return fail(ctx, RAPTOR_EINVAL, "fast-light frames need snapshots first_frame .. first_frame + n_frames - 1");
+    const long long npix = (long long)ctx->cam.nx * ctx->cam.ny;
+    if (npix * n_frames > (1LL << 40)) return fail(ctx, RAPTOR_EINVAL, "too many rays");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(ensure(&ctx->d_tframes, &ctx->tframes_cap, (size_t)n_frames));
+    std::vector<double> tf(n_frames);
+    for (int f = 0; f < n_frames; ++f) tf[f] = t_obs_host[f] + ctx->cam.t_delay;
+    RCK(cudaMemcpyAsync(ctx->d_tframes, tf.data(), n_frames * sizeof(double), cudaMemcpyHostToDevice, s));
+    double* img = images_dev;
+    if (!img) {
+        RCK(ensure(&ctx->d_img, &ctx->img_cap, (size_t)npix * n_freq * n_frames));
+        img = ctx->d_img;
+    }
+    Params p = base_params(ctx);
+    p.row0 = 0;
+    p.n_rows = ctx->cam.ny;
+    p.n_pix = (int)npix;
+    p.n_rays = npix * n_frames;
+    p.t_frames = ctx->d_tframes;
+    p.lc_fast = fast ? 1 : 0;
+    p.frame_snap0 = first_frame;
+    p.image = img;
+    st = run_rays(ctx, p, freqs_hz, n_freq, n_freq, n_frames, s);
+    if (st != RAPTOR_OK) return st;
+    RCK(cudaMemcpyAsync(flux_jy_host, ctx->d_flux, (size_t)n_frames * n_freq * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_trace_ray(raptor_ctx* ctx, double alpha, double beta, double t_obs, const double* freqs_hz, int n_freq,
+                               int max_rec, double* rec_host, int* n_steps, int* ray_status, double* intensity_host,
+                               void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->has_plasma) return fail(ctx, RAPTOR_ENOPLASMA, "raptor_load_plasma has not been called");
+    raptor_status st = check_freqs(ctx, freqs_hz, n_freq);
+    if (st != RAPTOR_OK) return st;
+    if (n_freq > 16) return fail(ctx, RAPTOR_EINVAL, "trace supports at most 16 frequencies");
+    if (max_rec < 0 || (max_rec > 0 && !rec_host)) return fail(ctx, RAPTOR_EINVAL, "rec_host needed for max_rec > 0");
+    if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(t_obs)) return fail(ctx, RAPTOR_EINVAL, "non-finite ray");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(ensure(&ctx->d_rec, &ctx->rec_cap, (size_t)std::max(max_rec, 1) * 12));
+    Params p = base_params(ctx);
+    p.nf = n_freq;
+    p.nf_total = n_freq;
+    for (int f = 0; f < n_freq; ++f) p.nu[f] = freqs_hz[f];
+    p.snap = 0;
+    const double tc = t_obs + ctx->cam.t_delay;
+    ProfScope ps(ctx, kProfTrace, s);
+    if (n_freq <= 1)
+        k_trace_fp64<1><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ctx->d_trace_int, ctx->d_trace_int + 1, ctx->d_trace_I);
+    else
+        k_trace_fp64<16><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ctx->d_trace_int, ctx->d_trace_int + 1, ctx->d_trace_I);
+    RCK(cudaGetLastError());
+    int hi[2] = {0, 0};
+    RCK(cudaMemcpyAsync(hi, ctx->d_trace_int, sizeof(hi), cudaMemcpyDeviceToHost, s));
+    double Ih[16];
+    RCK(cudaMemcpyAsync(Ih, ctx->d_trace_I, n_freq * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    const int nrec = std::min(hi[0], max_rec);
+    if (nrec > 0) {
+        RCK(cudaMemcpyAsync(rec_host, ctx->d_rec, (size_t)nrec * 12 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RCK(cudaStreamSynchronize(s));
+    }
+    if (n_steps) *n_steps = hi[0];
+    if (ray_status) *ray_status = hi[1];
+    if (intensity_host) std::memcpy(intensity_host, Ih, n_freq * sizeof(double));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_stats(raptor_ctx* ctx, unsigned long long* rays, unsigned long long* steps,
+                           unsigned long long* fp64_steps, unsigned long long* truncated, unsigned long long* errors,
+                           unsigned long long* fallback) {
+    if (!ctx) return RAPTOR_EINVAL;
+    unsigned long long h[8];
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemcpy(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
+    if (rays) *rays = h[kStatRays];
+    if (steps) *steps = h[kStatSteps];
+    if (fp64_steps) *fp64_steps = h[kStatFp64Steps];
+    if (truncated) *truncated = h[kStatTrunc];
+    if (errors) *errors = h[kStatErr];
+    if (fallback) *fallback = h[kStatFallback];
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_stats_reset(raptor_ctx* ctx) {
+    if (!ctx) return RAPTOR_EINVAL;
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemset(ctx->d_stats, 0, 8 * sizeof(unsigned long long)));
+    return RAPTOR_OK;
+}
+
+const char* raptor_last_error(const raptor_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+void raptor_destroy(raptor_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    cudaFree(ctx->d_grid);
+    cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_stats);
+    cudaFree(ctx->d_partial);
+    cudaFree(ctx->d_flux);
+    cudaFree(ctx->d_img);
+    cudaFree(ctx->d_tframes);
+    cudaFree(ctx->d_trace_int);
+    cudaFree(ctx->d_trace_I);
+    cudaFree(ctx->d_rec);
+    free_mixed_queues(ctx->mq);
+    for (auto& e : ctx->ev_open) {
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+// Launch-shape control used by the autotuner (threads per block, blocks per SM; 0 = max).
+raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (threads_per_block < 32 || threads_per_block > 128 || threads_per_block % 32)
+        return fail(ctx, RAPTOR_EINVAL, "threads_per_block must be 32, 64, 96 or 128");
+    if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(ctx, RAPTOR_EINVAL, "blocks_per_sm must lie in [0, 64]");
+    ctx->launch_block = threads_per_block;
+    ctx->launch_bps = blocks_per_sm;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_profile(raptor_ctx* ctx, int enable) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (enable) {
+        RCK(cudaStreamSynchronize(ctx->last_stream));
+        for (auto& e : ctx->ev_open) {
+            ctx->ev_pool.push_back(e.second.first);
+            ctx->ev_pool.push_back(e.second.second);
+        }
+        ctx->ev_open.clear();
+        for (int i = 0; i < kProfSlots; ++i) {
+            ctx->prof_ms[i] = 0.0;
+            ctx->prof_launches[i] = 0;
+        }
+    }
+    ctx->prof = enable != 0;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches) {
+    if (!ctx) return RAPTOR_EINVAL;
+    for (auto& e : ctx->ev_open) {
+        RCK(cudaEventSynchronize(e.second.second));
+        float t = 0.f;
+        RCK(cudaEventElapsedTime(&t, e.second.first, e.second.second));
+        ctx->prof_ms[e.first] += t;
+        ctx->ev_pool.push_back(e.second.first);
+        ctx->ev_pool.push_back(e.second.second);
+    }
+    ctx->ev_open.clear();
+    for (int i = 0; i < kProfSlots; ++i) {
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (launches) launches[i] = ctx->prof_launches[i];
+    }
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_measure_fma_peak(int fp64, double* tflops) {
+    raptor_ctx* ctx = nullptr;
+    if (!tflops) return RAPTOR_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RAPTOR_ECUDA;
+    const int threads = 256, blocks = sms * 8;
+    const int iters = fp64 ? 2048 : 65536;
+    void* out = nullptr;
+    if (cudaMalloc(&out, (size_t)threads * blocks * sizeof(double)) != cudaSuccess) return RAPTOR_ENOMEM;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a);
+        if (fp64) k_fma_peak<double><<<blocks, threads>>>((double*)out, iters, 1.0);
+        else k_fma_peak<float><<<blocks, threads>>>((float*)out, iters, 1.0f);
+        cudaEventRecord(b);
+        cudaEventSynchronize(b);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        if (rep > 0) best = std::min(best, t);
+    }
+    const cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (e != cudaSuccess) return RAPTOR_ECUDA;
+    *tflops = 2.0 * 16.0 * iters * (double)threads * blocks / (best * 1e-3) / 1e12;
+    (void)ctx;
+    return RAPTOR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// raptor_kernels_fp64.cuh -- persistent FP64 ray-tracing kernel, single-ray trace kernel and
+// the deterministic flux reduction.
+#pragma once
+
+#include "raptor_physics.cuh"
+#include "raptor_grid.cuh"
+
+namespace raptor {
+
+constexpr unsigned kFlagK2Exact = 0x1u;
+constexpr unsigned kFlagLinearR = 0x2u;
+
+enum : int { kEscaped = 0, kCaptured = 1, kThick = 2, kTruncated = 3, kError = 4 };
+
+// Per-kernel profiling slots (raptor_profile_read).
+enum : int { kProfRenderFp64 = 0, kProfMixedA = 1, kProfMixedB = 2, kProfMixedC = 3, kProfReduce = 4, kProfTrace = 5,
+             kProfLoad = 6, kProfPeak = 7, kProfSlots = 8 };
+
+// Stats slots (device unsigned long long[8]).
+enum : int { kStatRays = 0, kStatSteps = 1, kStatFp64Steps = 2, kStatTrunc = 3, kStatErr = 4, kStatFallback = 5,
+             kStatReentry = 6, kStatClamp = 7 };
+
+template <int NF>
+struct RayD {
+    double x[4], k[4];
+    double I[NF], tau[NF];
+    int n;
+    int snap;
+};
+
+// Plasma + frequency ratio at state (x, k) in type T.  Returns 1 emitting, 0 no plasma,
+// -1 error.  On success fills ne, the, B, g = nu_fluid/nu_obs and sinb.
+template <typename T>
+__device__ __forceinline__ int plasma_sample(const Params& p, const T x[4], const T k[4], int snap, T& ne, T& the,
+                                             T& B, T& g, T& sinb) {
+    KSPoint<T> P;
+    ks_point(T(p.a), x[1], x[2], P);
+    T u[4], kc[4];
+    T kb;  // k . b_hat
+    if (p.kind == 0) {
+        const int ok = analytic_velocity(T(p.a), T(p.r_isco), P, u);
+        if (ok < 0) return -1;
+        const T r = x[1];
+        ne = T(p.n0) * Real<T>::pow_(r, T(p.n_pow));
+        the = T(p.the0) * Real<T>::pow_(r, T(p.the_pow));
+        B = T(p.B0) * Real<T>::pow_(r, T(p.B_pow));
+        ks_lower(P, k, kc);
+        g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
+        const T u_phi = P.gtp * u[0] + P.grp * u[1] + P.gpp * u[3];
+        const T kv = kc[3] + u_phi * g;
+        kb = kv * rsq(P.gpp + u_phi * u_phi);
+    } else {
+        T b[4];
+        const int ok = grid_sample<T>(p, P, x, snap, ne, the, B, u, b);
+        if (ok <= 0) return ok;
+        ks_lower(P, k, kc);
+        g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
+        kb = (kc[0] * b[0] + kc[1] * b[1] + kc[2] * b[2] + kc[3] * b[3]) / B;
+    }
+    if (!(g > T(0))) return -1;
+    // cos theta_B = (k_phys . b) / (g |b|) with k_phys = -k
+    T cb = -kb / g;
+    cb = fmin(fmax(cb, T(-1)), T(1));
+    sinb = Real<T>::sqrt_(T(1) - cb * cb);
+    return 1;
+}
+
+// One FP64 step of a ray: adaptive step, RK4, termination, transfer sample.  Returns the
+// termination code or -1 to continue.  dl_out / g_out feed the trace recorder.
+template <int NF>
+__device__ __forceinline__ int step_fp64(const Params& p, RayD<NF>& R, double& dl_out, double& g_out) {
+    const double dl = step_size<double>(p.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
+    rk4_step<double>(p.a, R.x, R.k, dl);
+    R.n += 1;
+    dl_out = dl;
+    g_out = 0.0;
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fin = fin && isfinite(R.x[i]) && isfinite(R.k[i]);
+    if (!fin) return kError;
+    if (R.x[1] < p.r_stop) return kCaptured;
+    if (R.x[1] > p.r_esc) return kEscaped;
+    double ne, the, B, g, sinb;
+    const int ok = plasma_sample<double>(p, R.x, R.k, R.snap, ne, the, B, g, sinb);
+    if (ok < 0) return kError;
+    if (ok > 0) {
+        g_out = g;
+        const double dlcm = dl * p.Lcm;
+        const bool k2x = (p.flags & kFlagK2Exact) != 0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f < p.nf) {
+                double j, S;
+                synchrotron<double>(g * p.nu[f], ne, the, B, sinb, k2x, j, S);
+                rt_update<double, double>(j, S, g, dlcm, R.I[f], R.tau[f]);
+            }
+        }
+    }
+    double tmin = R.tau[0];
+#pragma unroll
+    for (int f = 1; f < NF; ++f)
+        if (f < p.nf) tmin = fmin(tmin, R.tau[f]);
+    if (tmin > p.tau_cut) return kThick;
+    if (R.n >= p.max_steps) return kTruncated;
+    return -1;
+}
+
+// Ray id -> (frame, pixel, row, col); initial state.
+template <int NF>
+__device__ __forceinline__ void init_ray(const Params& p, long long id, RayD<NF>& R, int& frame, int& pix) {
+    frame = (int)(id / p.n_pix);
+    pix = (int)(id - (long long)frame * p.n_pix);
+    const int row = p.row0 + pix / p.nx, col = pix % p.nx;
+    const double alpha = p.amin + (col + 0.5) * p.da;
+    const double beta = p.bmin + (row + 0.5) * p.db;
+    const double tc = p.t_frames ? p.t_frames[frame] : p.t_cam;
+    camera_ray(p, alpha, beta, tc, R.x, R.k);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) { R.I[f] = 0.0; R.tau[f] = 0.0; }
+    R.n = 0;
+    R.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
+}
+
+template <int NF>
+__device__ __forceinline__ void write_ray(const Params& p, int frame, int pix, const double* I, int n, int status) {
+    const long long plane = (long long)p.n_rows * p.nx;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (f < p.nf) p.image[((long long)frame * p.nf_total + p.f_off + f) * plane + pix] = I[f] * p.pix_jy;
+    if (p.steps_out) p.steps_out[pix] = n;
+    if (p.status_out) p.status_out[pix] = status;
+}
+
+__device__ __forceinline__ void warp_add_stats(unsigned long long* stats, unsigned long long rays, unsigned long long steps,
+                                               unsigned long long s64, unsigned long long trunc, unsigned long long err) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rays += __shfl_down_sync(0xffffffffu, rays, o);
+        steps += __shfl_down_sync(0xffffffffu, steps, o);
+        s64 += __shfl_down_sync(0xffffffffu, s64, o);
+        trunc += __shfl_down_sync(0xffffffffu, trunc, o);
+        err += __shfl_down_sync(0xffffffffu, err, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&stats[kStatRays], rays);
+        atomicAdd(&stats[kStatSteps], steps);
+        if (s64) atomicAdd(&stats[kStatFp64Steps], s64);
+        if (trunc) atomicAdd(&stats[kStatTrunc], trunc);
+        if (err) atomicAdd(&stats[kStatErr], err);
+    }
+}
+
+// Warp-aggregated fetch from the global ray counter: lanes whose `need` is set receive
+// consecutive ray ids (or -1 once the queue is drained).  Returns false once drained.
+__device__ __forceinline__ long long warp_fetch(unsigned long long* counter, long long n_total, bool need, bool& drained) {
+    const unsigned m = __ballot_sync(0xffffffffu, need && !drained);
+    long long id = -1;
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (base + __popc(m) >= (unsigned long long)n_total) drained = true;
+        if (need) {
+            const long long cand = (long long)base + __popc(m & ((1u << lane) - 1u));
+            if (cand < n_total) id = cand;
+        }
+    }
+    return id;
+}
+
+// Persistent FP64 kernel: each warp keeps 32 rays in flight and refills a lane from the
+// global work counter as soon as its ray terminates (per-warp compaction of uneven ray
+// lengths).  Blocks must be a multiple of 32 threads.
+template <int NF>
+__global__ void __launch_bounds__(128) k_render_fp64(const Params p, unsigned long long* counter, unsigned long long* stats) {
+    RayD<NF> R;
+    long long id = -1;
+    int frame = 0, pix = 0;
+    bool drained = false;
+    unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0;
+    for (;;) {
+        const long long nid = warp_fetch(counter, p.n_rays, id < 0, drained);
+        if (id < 0 && nid >= 0) {
+            id = nid;
+            init_ray<NF>(p, id, R, frame, pix);
+        }
+        if (!__any_sync(0xffffffffu, id >= 0)) break;
+        if (id >= 0) {
+            double dl, g;
+            const int st = step_fp64<NF>(p, R, dl, g);
+            if (st >= 0) {
+                write_ray<NF>(p, frame, pix, R.I, R.n, st);
+                c_rays += 1;
+                c_steps += (unsigned long long)R.n;
+                c_trunc += (st == kTruncated);
+                c_err += (st == kError);
+                id = -1;
+            }
+        }
+    }
+    warp_add_stats(stats, c_rays, c_steps, c_steps, c_trunc, c_err);
+}
+
+// Single-ray trace with per-step records (same arithmetic as k_render_fp64).
+template <int NF>
+__global__ void k_trace_fp64(const Params p, double alpha, double beta, double t_cam, int max_rec, double* rec, int* out_n,
+                             int* out_status, double* out_I) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    RayD<NF> R;
+    camera_ray(p, alpha, beta, t_cam, R.x, R.k);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) { R.I[f] = 0.0; R.tau[f] = 0.0; }
+    R.n = 0;
+    R.snap = p.snap;
+    int st = -1;
+    while (st < 0) {
+        double dl, g;
+        st = step_fp64<NF>(p, R, dl, g);
+        if (R.n <= max_rec) {
+            double* T = rec + (long long)(R.n - 1) * 12;
+            for (int i = 0; i < 4; ++i) { T[i] = R.x[i]; T[4 + i] = R.k[i]; }
+            T[8] = dl;
+            T[9] = g;
+            T[10] = R.I[0];
+            T[11] = R.tau[0];
+        }
+    }
+    *out_n = R.n;
+    *out_status = st;
+    for (int f = 0; f < NF; ++f)
+        if (f < p.nf) out_I[f] = R.I[f];
+}
+
+// Deterministic two-pass sum of `planes` arrays of `len` doubles: pass 1 (grid chunks x
+// planes) writes fixed-order partial sums, pass 2 (one block per plane) adds them in order.
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum_fixed(double v) {
+    __shared__ double sh[kRedThreads];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const double* __restrict__ data, long long len, int chunks,
+                                                                double* __restrict__ partial) {
+    const int plane = blockIdx.y, c = blockIdx.x;
+    const long long per = (len + chunks - 1) / chunks;
+    const long long b = (long long)c * per, e = min(len, b + per);
+    const double* d = data + (long long)plane * len;
+    double acc = 0.0;
+    for (long long i = b + threadIdx.x; i < e; i += kRedThreads) acc += d[i];
+    const double s = block_sum_fixed(acc);
+    if (threadIdx.x == 0) partial[(long long)plane * chunks + c] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double* __restrict__ partial, int chunks, double* __restrict__ out) {
+    const int plane = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < chunks; i += kRedThreads) acc += partial[(long long)plane * chunks + i];
+    const double s = block_sum_fixed(acc);
+    if (threadIdx.x == 0) out[plane] = s;
+}
+
+// FMA-chain microbenchmark: 16 independent dependent chains per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* out, int iters, T seed) {
+    T a[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) a[c] = seed + T(threadIdx.x + c) * T(1e-7);
+    const T m = T(0.9999999), d = T(1e-7);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) a[c] = fma(a[c], m, d);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) s += a[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace raptor

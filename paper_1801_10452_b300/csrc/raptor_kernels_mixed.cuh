@@ -1,0 +1,309 @@
+// raptor_kernels_mixed.cuh -- mixed FP32/FP64 integration as a three-phase wavefront.
+//
+// B300 executes FP64 at a small fraction of its FP32 rate, and a warp that holds one FP64
+// ray pays the FP64 price for all 32 lanes.  So rays are sorted by precision through two
+// device queues instead of switching precision per lane:
+//   phase A (FP32, persistent): fresh camera rays, integrated while r >= r_fp64 and away
+//     from radial turning points (|k^r| >= turn_kr |k^t|); a ray entering that region is
+//     pushed to the FP64 queue with its state promoted to FP64, and the lane refills.
+//   phase B (FP64, persistent): rays from the FP64 queue, integrated in FP64 until they
+//     terminate or leave the region; leavers are pushed to the FP32 queue.
+//   phase C (FP32, persistent): rays from the FP32 queue, integrated to termination (an
+//     outgoing photon has no further radial turning point; re-entries are counted).
+// The optical depth of a frequency is accumulated in FP64 once it exceeds 10.
+// No kernel waits on another: the phases are ordered by the stream.
+#pragma once
+
+#include "raptor_kernels_fp64.cuh"
+
+namespace raptor {
+
+struct RayQueue {
+    double* xk;       // [8][cap]: x^0..x^3, k^0..k^3
+    double* I;        // [nf_cap][cap]
+    double* tau;      // [nf_cap][cap]
+    int* n;           // [cap] steps so far
+    long long* id;    // [cap] ray id
+};
+
+struct MixedQueues {
+    RayQueue q64, q32;
+    size_t cap = 0;
+    int nf_cap = 0;
+};
+
+// Counter slots in the context's device counter array.
+enum : int { kCntFreshA = 0, kCntPush64 = 1, kCntFetch64 = 2, kCntPush32 = 3, kCntFetch32 = 4 };
+
+inline cudaError_t alloc_queue(RayQueue& q, size_t cap, int nf) {
+    cudaError_t e = cudaMalloc((void**)&q.xk, sizeof(double) * 8 * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&q.I, sizeof(double) * nf * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&q.tau, sizeof(double) * nf * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&q.n, sizeof(int) * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&q.id, sizeof(long long) * cap);
+    return e;
+}
+
+inline void free_queue(RayQueue& q) {
+    cudaFree(q.xk);
+    cudaFree(q.I);
+    cudaFree(q.tau);
+    cudaFree(q.n);
+    cudaFree(q.id);
+    q = RayQueue{nullptr, nullptr, nullptr, nullptr, nullptr};
+}
+
+inline cudaError_t alloc_mixed_queues(MixedQueues& m, size_t cap, int nf) {
+    m.q64 = RayQueue{nullptr, nullptr, nullptr, nullptr, nullptr};
+    m.q32 = m.q64;
+    cudaError_t e = alloc_queue(m.q64, cap, nf);
+    if (e == cudaSuccess) e = alloc_queue(m.q32, cap, nf);
+    if (e == cudaSuccess) {
+        m.cap = cap;
+        m.nf_cap = nf;
+    } else {
+        free_queue(m.q64);
+        free_queue(m.q32);
+    }
+    return e;
+}
+
+inline void free_mixed_queues(MixedQueues& m) {
+    if (m.cap == 0 && !m.q64.xk) return;
+    free_queue(m.q64);
+    free_queue(m.q32);
+    m.cap = 0;
+    m.nf_cap = 0;
+}
+
+// Warp-aggregated push: lanes with `push` set receive consecutive slots.
+__device__ __forceinline__ long long warp_push_slot(unsigned long long* count, bool push) {
+    const unsigned m = __ballot_sync(0xffffffffu, push);
+    long long slot = -1;
+    if (m) {
+        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (push) slot = (long long)base + __popc(m & ((1u << lane) - 1u));
+    }
+    return slot;
+}
+
+template <typename T>
+__device__ __forceinline__ bool in_fp64_region(const Params& p, const T x[4], const T k[4]) {
+    return x[1] < T(p.r_fp64) || fabs(k[1]) < T(p.turn_kr) * fabs(k[0]);
+}
+
+template <int NF>
+struct RayF {
+    float x[4], k[4];
+    float I[NF], tau[NF];
+    double tau_hi[NF];  // optical depth beyond 10 accumulated in FP64
+    int n, snap;
+};
+
+// One FP32 step (same scheme as step_fp64).  Returns termination code or -1.
+template <int NF>
+__device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
+    const float dl = step_size<float>(float(p.eps), (p.flags & kFlagLinearR) != 0, R.x, R.k);
+    rk4_step<float>(float(p.a), R.x, R.k, dl);
+    R.n += 1;
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fin = fin && isfinite(R.x[i]) && isfinite(R.k[i]);
+    if (!fin) return kError;
+    if (R.x[1] < float(p.r_stop)) return kCaptured;
+    if (R.x[1] > float(p.r_esc)) return kEscaped;
+    float ne, the, B, g, sinb;
+    const int ok = plasma_sample<float>(p, R.x, R.k, R.snap, ne, the, B, g, sinb);
+    if (ok < 0) return kError;
+    if (ok > 0) {
+        const float dlcm = dl * float(p.Lcm);
+        const bool k2x = (p.flags & kFlagK2Exact) != 0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f < p.nf) {
+                float j, S;
+                synchrotron<float>(g * float(p.nu[f]), ne, the, B, sinb, k2x, j, S);
+                if (j > 0.f && S > 0.f) {
+                    const float dtau = j / S * g * dlcm;
+                    const float tau_now = R.tau[f] + float(R.tau_hi[f]);
+                    R.I[f] += expf(-tau_now) * S * (-expm1f(-dtau)) / (g * g * g);
+                    if (R.tau[f] + dtau > 10.f || R.tau_hi[f] > 0.0) R.tau_hi[f] += double(dtau);
+                    else R.tau[f] += dtau;
+                }
+            }
+        }
+    }
+    double tmin = double(R.tau[0]) + R.tau_hi[0];
+#pragma unroll
+    for (int f = 1; f < NF; ++f)
+        if (f < p.nf) tmin = fmin(tmin, double(R.tau[f]) + R.tau_hi[f]);
+    if (tmin > p.tau_cut) return kThick;
+    if (R.n >= p.max_steps) return kTruncated;
+    return -1;
+}
+
+template <int NF>
+__device__ __forceinline__ void store_ray(const RayQueue& q, size_t cap, long long slot, long long id, const double x[4],
+                                          const double k[4], const double* I, const double* tau, int n, int nf) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        q.xk[(size_t)i * cap + slot] = x[i];
+        q.xk[(size_t)(4 + i) * cap + slot] = k[i];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (f < nf) {
+            q.I[(size_t)f * cap + slot] = I[f];
+            q.tau[(size_t)f * cap + slot] = tau[f];
+        }
+    q.n[slot] = n;
+    q.id[slot] = id;
+}
+
+// Phase A (from_queue = false) and phase C (from_queue = true), FP32.
+template <int NF>
+__global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues mq, unsigned long long* cnt,
+                                                    unsigned long long* stats, int from_queue) {
+    RayF<NF> R;
+    long long id = -1;
+    int frame = 0, pix = 0;
+    bool drained = false;
+    const long long n_total = from_queue ? (long long)cnt[kCntPush32] : p.n_rays;
+    unsigned long long* fetch = from_queue ? &cnt[kCntFetch32] : &cnt[kCntFreshA];
+    unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0, c_re = 0;
+    for (;;) {
+        const long long nid = warp_fetch(fetch, n_total, id < 0, drained);
+        if (id < 0 && nid >= 0) {
+            if (!from_queue) {
+                RayD<NF> D;
+                init_ray<NF>(p, nid, D, frame, pix);
+                id = nid;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { R.x[i] = float(D.x[i]); R.k[i] = float(D.k[i]); }
+#pragma unroll
+                for (int f = 0; f < NF; ++f) { R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = 0.0; }
+                R.n = 0;
+                R.snap = D.snap;
+            } else {
+                const RayQueue& q = mq.q32;
+                const size_t cap = mq.cap;
+                id = q.id[nid];
+                frame = (int)(id / p.n_pix);
+                pix = (int)(id - (long long)frame * p.n_pix);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    R.x[i] = float(q.xk[(size_t)i * cap + nid]);
+                    R.k[i] = float(q.xk[(size_t)(4 + i) * cap + nid]);
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (f < p.nf) {
+                        R.I[f] = float(q.I[(size_t)f * cap + nid]);
+                        const double t = q.tau[(size_t)f * cap + nid];
+                        if (t > 10.0) { R.tau[f] = 0.f; R.tau_hi[f] = t; }
+                        else { R.tau[f] = float(t); R.tau_hi[f] = 0.0; }
+                    } else {
+                        R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = 0.0;
+                    }
+                }
+                R.n = q.n[nid];
+                R.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
+            }
+        }
+        if (!__any_sync(0xffffffffu, id >= 0)) break;
+        int st = -1;
+        bool push = false;
+        if (id >= 0) {
+            st = step_fp32<NF>(p, R);
+            if (st < 0 && in_fp64_region<float>(p, R.x, R.k)) {
+                if (!from_queue) push = true;
+                else c_re += 1;
+            }
+        }
+        const long long slot = warp_push_slot(&cnt[kCntPush64], push);
+        if (push) {
+            double x[4], k[4], I[NF], tau[NF];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { x[i] = R.x[i]; k[i] = R.k[i]; }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { I[f] = R.I[f]; tau[f] = double(R.tau[f]) + R.tau_hi[f]; }
+            store_ray<NF>(mq.q64, mq.cap, slot, id, x, k, I, tau, R.n, p.nf);
+            id = -1;
+        } else if (id >= 0 && st >= 0) {
+            double I[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) I[f] = R.I[f];
+            write_ray<NF>(p, frame, pix, I, R.n, st);
+            c_rays += 1;
+            c_steps += (unsigned long long)R.n;
+            c_trunc += (st == kTruncated);
+            c_err += (st == kError);
+            id = -1;
+        }
+    }
+    warp_add_stats(stats, c_rays, c_steps, 0, c_trunc, c_err);
+    if (c_re) atomicAdd(&stats[kStatReentry], c_re);
+}
+
+// Phase B: FP64 rays from the FP64 queue.
+template <int NF>
+__global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues mq, unsigned long long* cnt,
+                                                    unsigned long long* stats) {
+    RayD<NF> R;
+    long long id = -1;
+    int frame = 0, pix = 0, n_in = 0;
+    bool drained = false;
+    const long long n_total = (long long)cnt[kCntPush64];
+    unsigned long long c_rays = 0, c_steps = 0, c_64 = 0, c_trunc = 0, c_err = 0;
+    const RayQueue& q = mq.q64;
+    const size_t cap = mq.cap;
+    for (;;) {
+        const long long nid = warp_fetch(&cnt[kCntFetch64], n_total, id < 0, drained);
+        if (id < 0 && nid >= 0) {
+            id = q.id[nid];
+            frame = (int)(id / p.n_pix);
+            pix = (int)(id - (long long)frame * p.n_pix);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                R.x[i] = q.xk[(size_t)i * cap + nid];
+                R.k[i] = q.xk[(size_t)(4 + i) * cap + nid];
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                R.I[f] = f < p.nf ? q.I[(size_t)f * cap + nid] : 0.0;
+                R.tau[f] = f < p.nf ? q.tau[(size_t)f * cap + nid] : 0.0;
+            }
+            R.n = q.n[nid];
+            n_in = R.n;
+            R.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
+        }
+        if (!__any_sync(0xffffffffu, id >= 0)) break;
+        int st = -1;
+        bool push = false;
+        if (id >= 0) {
+            double dl, g;
+            st = step_fp64<NF>(p, R, dl, g);
+            if (st < 0 && !in_fp64_region<double>(p, R.x, R.k)) push = true;
+        }
+        const long long slot = warp_push_slot(&cnt[kCntPush32], push);
+        if (push) {
+            store_ray<NF>(mq.q32, cap, slot, id, R.x, R.k, R.I, R.tau, R.n, p.nf);
+            c_64 += (unsigned long long)(R.n - n_in);
+            id = -1;
+        } else if (id >= 0 && st >= 0) {
+            write_ray<NF>(p, frame, pix, R.I, R.n, st);
+            c_rays += 1;
+            c_steps += (unsigned long long)R.n;
+            c_64 += (unsigned long long)(R.n - n_in);
+            c_trunc += (st == kTruncated);
+            c_err += (st == kError);
+            id = -1;
+        }
+    }
+    warp_add_stats(stats, c_rays, c_steps, c_64, c_trunc, c_err);
+}
+
+}  // namespace raptor

@@ -1,0 +1,182 @@
+// raptor_physics.cuh -- camera, plasma models, emissivity and the backward transfer step.
+#pragma once
+
+#include "raptor_math.cuh"
+
+namespace raptor {
+
+// Kernel parameters (passed by value; lives in the constant bank).
+struct Params {
+    // spacetime / camera
+    double a, r_cam, incl, sin_i, cos_i;
+    double amin, da, bmin, db;
+    int nx, ny, row0, n_rows;
+    // integration
+    double eps, r_stop, r_esc, tau_cut;
+    int max_steps;
+    unsigned flags;
+    // units
+    double Lcm;     // GM/c^2 in cm
+    double pix_jy;  // dalpha dbeta L^2 / D^2 / 1e-23
+    // analytic plasma
+    int kind, slow;
+    double n0, n_pow, the0, the_pow, B0, B_pow, r_isco;
+    // grid plasma (MKS, r0 = 0)
+    const float* grid;  // [n_snap][8][n2][n1]
+    int n1, n2, n_snap, snap;
+    double x1_min, x1_max, dx1, dx2, h_mks, t0, dt_snap;
+    double rho0_ne;     // rho0 / (m_e + m_p): n_e = rho * rho0_ne
+    double B_unit;      // c sqrt(4 pi rho0): B[G] = |b| * B_unit
+    double r_high, r_low, gam;
+    // mixed precision
+    double r_fp64, turn_kr;
+    // frequencies
+    int nf;
+    double nu[16];
+    // work decomposition: ray -> (frame, pixel)
+    long long n_rays;
+    int n_pix;
+    const double* t_frames;  // device [n_frames] camera times (t_obs + t_delay applied)
+    double t_cam;            // single-image camera time
+    int frame_snap0;         // fast-light light curve: snapshot of frame 0
+    int lc_fast;             // 1: frame f samples snapshot frame_snap0 + f
+    // outputs
+    double* image;           // [frame][nf_total][n_rows][nx]
+    int nf_total, f_off;     // frequency chunking: this launch covers [f_off, f_off + nf)
+    int* steps_out;          // optional [n_rows][nx]
+    int* status_out;         // optional [n_rows][nx]
+};
+
+// ------------------------------------------------------------------------------------
+// Camera (sec. 2.3, Eqs. 24-28; App. A.1).  Always FP64.
+// E = 1, L = -alpha sin i, Q = beta^2 + cos^2 i (alpha^2 - a^2),
+// k_theta = sign(beta) sqrt|Q - L^2 cot^2 theta + a^2 cos^2 theta|, k_r from k.k = 0 with
+// the physical photon moving outward at the camera; the state is the backward ray -k.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void camera_ray(const Params& p, double alpha, double beta, double t_cam,
+                                           double x[4], double k[4]) {
+    const double a = p.a, a2 = a * a;
+    const double L = -alpha * p.sin_i;
+    const double Q = beta * beta + p.cos_i * p.cos_i * (alpha * alpha - a2);
+    const double r = p.r_cam;
+    double sn, cs;
+    sincos(p.incl, &sn, &cs);
+    const double cot = cs / sn;
+    const double kt = -1.0, kp = L;
+    const double kh = (beta < 0.0 ? -1.0 : 1.0) * sqrt(fabs(Q - L * L * cot * cot + a2 * cs * cs));
+    // Boyer-Lindquist inverse metric at the camera
+    const double s2 = sn * sn;
+    const double Sig = r * r + a2 * cs * cs, Del = r * r - 2.0 * r + a2;
+    const double A = (r * r + a2) * (r * r + a2) - a2 * Del * s2;
+    const double iSD = 1.0 / (Sig * Del);
+    const double gtt = -A * iSD, gtp = -2.0 * a * r * iSD, grr = Del / Sig, ghh = 1.0 / Sig;
+    const double gpp = (Del - a2 * s2) * iSD / s2;
+    const double rest = gtt * kt * kt + 2.0 * gtp * kt * kp + gpp * kp * kp + ghh * kh * kh;
+    const double kr = sqrt(-rest / grr);
+    // contravariant BL components of the backward ray
+    const double ut = -(gtt * kt + gtp * kp), ur = -(grr * kr), uh = -(ghh * kh), up = -(gtp * kt + gpp * kp);
+    // BL -> KS (App. A.1)
+    k[0] = ut + 2.0 * r / Del * ur;
+    k[1] = ur;
+    k[2] = uh;
+    k[3] = up + a / Del * ur;
+    const double rp = 1.0 + sqrt(1.0 - a2), rm = 1.0 - sqrt(1.0 - a2);
+    const double lg = log((r - rp) / (r - rm));
+    x[0] = t_cam + log(Del) + 2.0 / (rp - rm) * lg;
+    x[1] = r;
+    x[2] = p.incl;
+    x[3] = a / (rp - rm) * lg;
+}
+
+// ------------------------------------------------------------------------------------
+// Plasma sample at a KS point.
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct Sample {
+    T ne, the, B;
+    T u[4];
+    T cosb_num;  // k.v with v = d_phi + u_phi u (toroidal field direction)
+    T vnorm;     // |v|
+    int ok;      // 1 emitting, 0 no plasma, -1 error (not timelike)
+};
+
+// Analytic model of the workload (not in the paper): power-law n_e, Theta_e, B; prograde
+// Keplerian rotation Omega = 1/(r^{3/2} + a) at every theta for r >= r_isco; inside, free
+// fall from rest at infinity (E = 1, L = 0, Q = 0), written in KS without the 1/Delta
+// terms of the BL -> KS transform:
+//   u^t = [P (P^2 + 2 r P + 4 r^2)/(P^2 + 2 r s) - a^2 sin^2] / Sigma,
+//   u^r = -s / Sigma, u^phi = -2 a r / (Sigma (2 r + s)), P = r^2 + a^2, s = sqrt(2 r P).
+template <typename T>
+__device__ __forceinline__ int analytic_velocity(T a, T r_isco, const KSPoint<T>& P, T u[4]) {
+    const T r = P.r;
+    u[2] = T(0);
+    if (r >= r_isco) {
+        const T Om = Real<T>::rcp(r * Real<T>::sqrt_(r) + a);
+        const T nrm = P.gtt + T(2) * Om * P.gtp + Om * Om * P.gpp;
+        if (!(nrm < T(0))) return -1;
+        const T ut = rsq(-nrm);
+        u[0] = ut;
+        u[1] = T(0);
+        u[3] = Om * ut;
+    } else {
+        const T a2 = a * a;
+        const T Pp = r * r + a2;
+        const T s = Real<T>::sqrt_(T(2) * r * Pp);
+        u[0] = (Pp * (Pp * Pp + T(2) * r * Pp + T(4) * r * r) / (Pp * Pp + T(2) * r * s) - a2 * P.s2) * P.iSig;
+        u[1] = -s * P.iSig;
+        u[3] = -T(2) * a * r * P.iSig / (T(2) * r + s);
+    }
+    return 1;
+}
+
+// ------------------------------------------------------------------------------------
+// Thermal synchrotron (Eqs. 41-44).  j [erg s^-1 cm^-3 Hz^-1 sr^-1], S = B_nu.
+// B_nu is written as 2 nu^2 m_e Theta x / expm1(x), x = h nu / (m_e c^2 Theta), which
+// equals Eq. 44 and stays inside FP32 range.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double bessel_k2_exact(double x) {
+    // K_2(x) = int_0^inf exp(-x cosh t) cosh(2 t) dt (DLMF 10.32.9); trapezoidal rule with
+    // step 1/4, whose error decays like exp(-pi^2 / h) for this entire integrand.
+    const double h = 0.25;
+    double sum = 0.5 * exp(-x);
+    for (int n = 1; n < 400; ++n) {
+        const double t = n * h;
+        const double term = exp(-x * cosh(t)) * cosh(2.0 * t);
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return h * sum;
+}
+
+template <typename T>
+__device__ __forceinline__ void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, T& S) {
+    const T nu_c_per_G = T(kQe / (2.0 * kPi * kMe * kC));
+    const T cj = T(1.4142135623730951 * kPi * kQe * kQe / (3.0 * kC));
+    const T hme = T(kH / (kMe * kC * kC));
+    const T x = hme * nu / the;
+    S = T(2.0 * kMe) * nu * nu * the * (x / Real<T>::expm1_(x));
+    j = T(0);
+    const T nu_s = T(2.0 / 9.0) * nu_c_per_G * B * the * the * sinb;
+    if (!(nu_s > T(0))) return;
+    const T X = nu / nu_s;
+    const T X13 = Real<T>::cbrt_(X);
+    if (X13 > Real<T>::exp_cut) return;
+    const T X16 = Real<T>::sqrt_(X13);
+    const T X12 = Real<T>::sqrt_(X);
+    const T fac = X12 + T(1.8877486253633870) * X16;  // 2^(11/12)
+    T K2 = T(2) * the * the;
+    if (k2_exact) K2 = T(bessel_k2_exact(1.0 / double(the)));
+    j = cj * ne * nu_s / K2 * fac * fac * Real<T>::exp_(-X13);
+}
+
+// Backward transfer (Eqs. 35-36, per-step solution of Eq. 34):
+//   dtau = (j/S) g dl L;  I += exp(-tau) S (1 - exp(-dtau)) / g^3;  tau += dtau.
+template <typename T, typename TT>
+__device__ __forceinline__ void rt_update(T j, T S, T g, T dl_cm, T& I, TT& tau) {
+    if (!(j > T(0)) || !(S > T(0))) return;
+    const T dtau = j / S * g * dl_cm;
+    I += Real<T>::exp_(-T(tau)) * S * (-Real<T>::expm1_(-dtau)) / (g * g * g);
+    tau += TT(dtau);
+}
+
+}  // namespace raptor

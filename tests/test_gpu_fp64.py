@@ -1,0 +1,177 @@
+"""FP64 CUDA path vs the FP64 CPU oracle: element-by-element parity (<= 1e-8 relative per
+pixel, <= 1e-10 on the flux), identical step counts and termination codes, per-step trace
+parity, full-size sampled parity and argument validation.  Needs a GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import oracle_kwargs, rel_err
+from paper_1801_10452_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-8
+FLUX_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_1801_10452_b300 import build
+
+    build.build()
+    import paper_1801_10452_b300 as R
+
+    return R
+
+
+def _ctx(R, cam, **over):
+    c = dict(cam)
+    c.update(over)
+    ctx = R.Context(R.camera_desc(**c))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    return ctx
+
+
+def _gpu_render(R, ctx, freqs, n_rows=None, row0=0):
+    import torch
+
+    ny = ctx.cam.ny if n_rows is None else n_rows
+    steps = torch.zeros((ny, ctx.cam.nx), dtype=torch.int32, device="cuda")
+    status = torch.zeros_like(steps)
+    img, fl = ctx.render(freqs, row0=row0, n_rows=ny, steps=steps, status=status)
+    torch.cuda.synchronize()
+    return img.cpu().numpy(), fl, steps.cpu().numpy(), status.cpu().numpy()
+
+
+def test_small_image_fp64_parity(R, ora):
+    """64 x 64, a = 0.9, i = 60 deg, 230 GHz."""
+    cam = scenes.SMALL
+    ctx = _ctx(R, cam)
+    img, fl, st, stat = _gpu_render(R, ctx, scenes.SMALL_FREQS)
+    oimg, ost, ostat = ora.render(ora.scene(**oracle_kwargs(cam)), scenes.SMALL_FREQS)
+    assert np.array_equal(stat, ostat)
+    assert np.array_equal(st, ost)
+    e = rel_err(img, oimg)
+    assert e.max() <= PIX_TOL, e.max()
+    assert abs(fl[0] / oimg.sum() - 1) <= FLUX_TOL
+    assert abs(fl[0] - img.sum()) <= 1e-12 * abs(fl[0])
+
+
+@pytest.mark.parametrize("spin", scenes.SPECTRAL_SPINS)
+def test_ragged_multifrequency_fp64_parity(R, ora, spin):
+    """8 log-spaced frequencies, a ragged 37 x 29 camera (not a multiple of the warp or
+    block size) for each spin of the spectral workload."""
+    cam = dict(scenes.SMALL, spin=spin, nx=37, ny=29)
+    ctx = _ctx(R, cam)
+    img, fl, st, stat = _gpu_render(R, ctx, scenes.SPECTRAL_FREQS)
+    oimg, ost, ostat = ora.render(ora.scene(**oracle_kwargs(cam)), scenes.SPECTRAL_FREQS)
+    assert np.array_equal(st, ost) and np.array_equal(stat, ostat)
+    for f in range(len(scenes.SPECTRAL_FREQS)):
+        e = rel_err(img[f], oimg[f])
+        assert e.max() <= PIX_TOL, (f, e.max())
+        assert abs(fl[f] / oimg[f].sum() - 1) <= FLUX_TOL
+
+
+def test_row_window_equals_full_image(R):
+    cam = dict(scenes.SMALL, nx=32, ny=32)
+    ctx = _ctx(R, cam)
+    full, _, _, _ = _gpu_render(R, ctx, [1e11])
+    part, _, _, _ = _gpu_render(R, ctx, [1e11], n_rows=7, row0=11)
+    assert np.array_equal(part[0], full[0, 11:18])
+
+
+def test_single_pixel_and_many_frequencies(R, ora):
+    """Degenerate sizes: one pixel; 20 frequencies (two frequency chunks of the kernel)."""
+    cam = dict(scenes.SMALL, nx=1, ny=1, alpha_min=4.0, alpha_max=4.5, beta_min=1.0, beta_max=1.5)
+    freqs = list(np.logspace(10, 13, 20))
+    ctx = _ctx(R, cam)
+    img, fl, st, stat = _gpu_render(R, ctx, freqs)
+    oimg, ost, _ = ora.render(ora.scene(**oracle_kwargs(cam)), freqs)
+    assert st[0, 0] == ost[0, 0]
+    assert rel_err(img.ravel(), oimg.ravel()).max() <= PIX_TOL
+
+
+def test_trace_per_step_parity(R, ora):
+    """Per-step states, step sizes, redshift factors, I and tau along selected rays."""
+    cam = scenes.SMALL
+    ctx = _ctx(R, cam)
+    s = ora.scene(**oracle_kwargs(cam))
+    for al, be in [(5.0, 3.0), (-3.0, 0.5), (0.31, -7.9), (15.0, 12.0)]:
+        g = ctx.trace_ray(al, be, [230e9], max_rec=5000)
+        o = ora.trace_ray(s, al, be, [230e9], max_trace=5000)
+        assert g["steps"] == o["steps"] and g["status"] == o["status"]
+        tg, to = g["trace"], o["trace"]
+        scale = np.maximum(np.abs(to), 1e-300)
+        d = np.abs(tg - to)
+        # positions/wave vectors/step sizes to 1e-10 of their magnitude (phi and t grow)
+        assert np.all(d[:, :9] <= 1e-9 * np.maximum(np.abs(to[:, :9]), 1.0))
+        m = to[:, 10] > 0
+        assert np.all(d[m, 10] <= PIX_TOL * scale[m, 10])
+        assert math.isclose(g["I"][0], o["I"][0], rel_tol=PIX_TOL)
+
+
+def test_headline_size_sampled_parity(R, ora):
+    """The 1024 x 1024 headline image in the benchmark's launch configuration, checked on a
+    seeded sample of pixels that the oracle traces one by one."""
+    cam = scenes.HEADLINE
+    ctx = _ctx(R, cam)
+    img, fl, st, stat = _gpu_render(R, ctx, scenes.HEADLINE_FREQS)
+    s = ora.scene(**oracle_kwargs(cam))
+    al, be = R.pixel_centres(ctx.cam)
+    pix = scenes.sample_pixels(cam["nx"], cam["ny"], 64, seed=1024)
+    ref = img[0].max()
+    Lcm = ora.length_unit_cm(cam["mass_msun"])
+    D = cam["distance_pc"] * 3.0856775814913673e18
+    pix_jy = (al[1] - al[0]) * (be[1] - be[0]) * Lcm**2 / D**2 / 1e-23
+    for i, j in pix:
+        o = ora.trace_ray(s, al[j], be[i], scenes.HEADLINE_FREQS)
+        assert st[i, j] == o["steps"] and stat[i, j] == o["status"]
+        ov = o["I"][0] * pix_jy
+        assert abs(img[0, i, j] - ov) <= PIX_TOL * max(abs(ov), 1e-12 * ref)
+    assert np.all(np.isfinite(img)) and np.all(img >= 0)
+    assert abs(fl[0] - img.sum()) <= 1e-12 * fl[0]
+
+
+def test_invalid_arguments_rejected(R):
+    import torch
+
+    with pytest.raises(R.RaptorError) as e:
+        R.Context(R.camera_desc(spin=1.0))
+    assert e.value.status == R.EINVAL
+    with pytest.raises(R.RaptorError):
+        R.Context(R.camera_desc(nx=0))
+    ctx = R.Context(R.camera_desc(nx=8, ny=8))
+    with pytest.raises(R.RaptorError) as e:
+        ctx.render([230e9])
+    assert e.value.status == R.ENOPLASMA
+    ctx.load_plasma(R.plasma_desc())
+    for bad in ([], [-1.0], [float("nan")], list(np.ones(65) * 1e11)):
+        with pytest.raises(R.RaptorError) as e:
+            ctx.render(bad if bad else np.zeros(0))
+        assert e.value.status == R.EINVAL
+    with pytest.raises(R.RaptorError):
+        ctx.render([1e11], row0=5, n_rows=4)
+    with pytest.raises(R.RaptorError) as e:
+        ctx.load_plasma(R.plasma_desc(kind=R.PLASMA_GRID))
+    assert e.value.status == R.EINVAL
+    img, fl = ctx.render([1e11])
+    torch.cuda.synchronize()
+    assert np.isfinite(fl[0])
+
+
+def test_step_cap_counts_truncated_rays(R):
+    import torch
+
+    ctx = _ctx(R, dict(scenes.SMALL, nx=8, ny=8, max_steps=20))
+    steps = torch.zeros((8, 8), dtype=torch.int32, device="cuda")
+    status = torch.zeros_like(steps)
+    ctx.stats_reset()
+    ctx.render([230e9], steps=steps, status=status)
+    st = ctx.stats()
+    assert np.all(steps.cpu().numpy() == 20)
+    assert np.all(status.cpu().numpy() == R.RAY_TRUNCATED)
+    assert st["truncated"] == 64 and st["rays"] == 64 and st["steps"] == 64 * 20

@@ -1,0 +1,88 @@
+"""Mixed FP32/FP64 wavefront path vs the FP64 oracle: <= 1e-3 relative total flux and
+<= 1e-2 per pixel outside a 0.5 M band around the critical curve (where the photon-ring
+Lyapunov amplification makes any arithmetic difference grow).  Needs a GPU."""
+import numpy as np
+import pytest
+
+from helpers import oracle_kwargs, rel_err, ring_mask
+from paper_1801_10452_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+FLUX_TOL = 1e-3
+PIX_TOL = 1e-2
+RING_BAND = 0.5
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1801_10452_b300 import build
+
+    build.build()
+    import paper_1801_10452_b300 as R
+
+    return R
+
+
+def _mixed(R, cam, freqs, **over):
+    import torch
+
+    c = dict(cam, precision=R.MIXED)
+    c.update(over)
+    ctx = R.Context(R.camera_desc(**c))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    ctx.stats_reset()
+    steps = torch.zeros((c["ny"], c["nx"]), dtype=torch.int32, device="cuda")
+    status = torch.zeros_like(steps)
+    img, fl = ctx.render(freqs, steps=steps, status=status)
+    torch.cuda.synchronize()
+    return ctx, img.cpu().numpy(), fl, steps.cpu().numpy(), status.cpu().numpy()
+
+
+def _check(R, cam, img, fl, oimg, tag):
+    al, be = R.pixel_centres(R.camera_desc(**cam))
+    band = ring_mask(al, be, cam["spin"], cam["incl_deg"], RING_BAND)
+    out = []
+    for f in range(img.shape[0]):
+        fe = abs(fl[f] / oimg[f].sum() - 1)
+        pe = rel_err(img[f], oimg[f], floor_frac=1e-6)[~band].max()
+        out.append((fe, pe))
+        assert fe <= FLUX_TOL, (tag, f, fe)
+        assert pe <= PIX_TOL, (tag, f, pe)
+    return out
+
+
+def test_mixed_small_image(R, ora):
+    cam = scenes.SMALL
+    ctx, img, fl, st, stat = _mixed(R, cam, scenes.SMALL_FREQS)
+    oimg, ost, ostat = ora.render(ora.scene(**oracle_kwargs(cam)), scenes.SMALL_FREQS)
+    _check(R, cam, img, fl, oimg, "small")
+    s = ctx.stats()
+    assert s["rays"] == cam["nx"] * cam["ny"]
+    assert 0 < s["fp64_steps"] < s["steps"]
+    # FP32 steps outnumber FP64 steps by far on this scene
+    assert s["fp64_steps"] < 0.5 * s["steps"]
+    assert (stat == ostat).mean() > 0.99
+
+
+@pytest.mark.parametrize("spin", scenes.SPECTRAL_SPINS)
+def test_mixed_spectral_spins(R, ora, spin):
+    cam = dict(scenes.SMALL, spin=spin, nx=48, ny=40)
+    _, img, fl, _, _ = _mixed(R, cam, scenes.SPECTRAL_FREQS)
+    oimg, _, _ = ora.render(ora.scene(**oracle_kwargs(cam)), scenes.SPECTRAL_FREQS)
+    _check(R, cam, img, fl, oimg, f"a={spin}")
+
+
+def test_mixed_all_fp32_and_all_fp64_limits(R, ora):
+    """r_fp64 = 0 and turn_kr = 0 run everything in FP32; a huge r_fp64 runs everything in
+    the FP64 phase, which must then equal the FP64 path to rounding."""
+    cam = dict(scenes.SMALL, nx=24, ny=24)
+    oimg, _, _ = ora.render(ora.scene(**oracle_kwargs(cam)), scenes.SMALL_FREQS)
+    ctx, img32, fl32, _, _ = _mixed(R, cam, scenes.SMALL_FREQS, r_fp64=0.0, turn_kr=0.0)
+    assert ctx.stats()["fp64_steps"] == 0
+    assert abs(fl32[0] / oimg.sum() - 1) < 1e-2
+    ctx, img64, fl64, _, _ = _mixed(R, cam, scenes.SMALL_FREQS, r_fp64=1e6)
+    s = ctx.stats()
+    # the first step from the camera is FP32, every later one FP64
+    assert s["fp64_steps"] == s["steps"] - s["rays"]
+    assert abs(fl64[0] / oimg.sum() - 1) < 1e-6
