@@ -169,39 +169,15 @@ def _time_render(ctx, torch, freqs, image, flush_buf, n, stream):
     return tot
 
 
-def run_native(args):
-    import torch
-
-    import paper_1801_10452_b300 as R
-    from paper_1801_10452_b300 import build, scenes
-
-    rank, local_rank, world = _env_rank()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local_rank)
-    build.build()
-    stream = torch.cuda.current_stream()
-    cam = dict(scenes.HEADLINE)
-    freqs = scenes.HEADLINE_FREQS
-    npix = cam["nx"] * cam["ny"]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED))
-    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
-    ctx64 = R.Context(R.camera_desc(**cam, precision=R.FP64))
-    ctx64.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks):
+    """Warm up, then time args.steps renders of one path; returns measurements."""
+    ctx = R.Context(R.camera_desc(**cam, precision=prec))
+    ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
     image = torch.empty((len(freqs), cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
-    image64 = torch.empty_like(image)
-
-    # warm-up (also sizes the context's buffers)
     for _ in range(args.warmup):
         ctx.render(freqs, image=image, flux=False, stream=stream)
     torch.cuda.synchronize()
-
-    # ---- timed region: mixed path ------------------------------------------------------
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    sampler = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -223,34 +199,65 @@ def run_native(args):
         t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dev_ms = float(t.item())
-    ms_step = dev_ms / args.steps
-    rays_step = npix * len(freqs)
-    value = world * rays_step / (ms_step * 1e-3)
-    steps_per_s = world * (st["steps"] / args.steps) / (ms_step * 1e-3)
-    launches = sum(v[1] for v in prof.values())
+    _, flux = ctx.render(freqs, image=image, stream=stream)
+    torch.cuda.synchronize()
+    return dict(ctx=ctx, image=image, ms=dev_ms / args.steps, wall=wall, clocks=clocks, prof=prof, stats=st, flux=flux)
 
-    # ---- FP64 path on the same workload (the comparison the metric names) ----------------
-    ctx64.render(freqs, image=image64, flux=False, stream=stream)
-    torch.cuda.synchronize()
-    ctx64.stats_reset()
-    ctx64.profile(True)
-    n64 = max(1, min(args.steps, 3))
-    ms64 = _time_render(ctx64, torch, freqs, image64, flush, n64, stream) / n64
-    prof64 = ctx64.profile_read()
-    st64 = ctx64.stats()
-    _, fl_mixed = ctx.render(freqs, image=image, stream=stream)
-    _, fl64 = ctx64.render(freqs, image=image64, stream=stream)
-    torch.cuda.synchronize()
+
+def scenes_mod():
+    from paper_1801_10452_b300 import scenes
+
+    return scenes
+
+
+def run_native(args):
+    import torch
+
+    import paper_1801_10452_b300 as R
+    from paper_1801_10452_b300 import build, scenes
+
+    rank, local_rank, world = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    stream = torch.cuda.current_stream()
+    cam = dict(scenes.HEADLINE, nx=args.size, ny=args.size)
+    freqs = scenes.HEADLINE_FREQS
+    npix = cam["nx"] * cam["ny"]
+    paths = [p for p in args.paths.split(",") if p]
+    workload = WORKLOAD if args.size == 1024 else WORKLOAD.replace("1024x1024", f"{args.size}x{args.size}")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    rays_step = npix * len(freqs)
+
+    res = {}
+    for pth in paths:
+        prec = R.MIXED if pth == "mixed" else R.FP64
+        res[pth] = _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist,
+                               sample_clocks=(rank == 0 and pth == paths[0]))
+    main = res[paths[0]]
+    ms_step = main["ms"]
+    value = world * rays_step / (ms_step * 1e-3)
+    st = main["stats"]
+    steps_per_s = world * (st["steps"] / args.steps) / (ms_step * 1e-3)
+    launches = sum(v[1] for v in main["prof"].values())
 
     # ---- end to end through the C ABI with host buffers --------------------------------
-    img_host = np.zeros((len(freqs), cam["ny"], cam["nx"]))
-    ctx.render_host(freqs, want_image=True)
-    e2e_t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
+    e2e = None
+    if not args.no_e2e:
+        ctx = main["ctx"]
+        img_bytes = 8 * rays_step
         ctx.render_host(freqs, want_image=True)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_v = world * rays_step / float(np.mean(e2e_t))
+        e2e_t = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            ctx.render_host(freqs, want_image=True)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e = {"value": world * rays_step / float(np.mean(e2e_t)), "unit": "rays/s", "h2d_bytes_per_step": 8 * len(freqs),
+               "d2h_bytes_per_step": int(img_bytes) + 8 * len(freqs)}
 
     if rank != 0:
         if world > 1:
@@ -258,69 +265,75 @@ def run_native(args):
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel -------------------------------------------------
-    peaks = _peaks()
+    # ---- rooflines: algorithmic flops (from the kernel source) / measured FMA peaks -------
     fma32 = R.measure_fma_peak(False)
     fma64 = R.measure_fma_peak(True)
     flops = _flops_per_step()
-    kern = {k: v for k, v in prof.items() if v[1] > 0 and k not in ("reduce",)}
-    dom = max(kern, key=lambda k: kern[k][0])
-    dom_ms, dom_n = kern[dom]
-    st_phase = ctx_phase_steps(st, prof)
-    if dom == "mixed_fp64":
-        fl = flops["fp64_step"] * st["fp64_steps"] / args.steps if flops["fp64_step"] else None
-        peak, pname = fma64, "fp64"
-    else:
-        fl = flops["fp32_step"] * st_phase.get(dom, 0) / args.steps if flops["fp32_step"] else None
-        peak, pname = fma32, "fp32"
-    per_launch_ms = dom_ms / max(dom_n, 1)
-    achieved = fl / (per_launch_ms * 1e-3) / 1e12 if fl else None
-    roof = {"bound": "alu", "pipe": pname, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_source": f"measured FMA-chain microbenchmark ({pname}) in this run",
-            "flops_per_step": flops, "kernel_ms_per_launch": per_launch_ms}
-    fp64_kernel_ms = prof64["render_fp64"][0] / max(prof64["render_fp64"][1], 1)
-    fl64_launch = flops["fp64_step"] * st64["steps"] / max(prof64["render_fp64"][1], 1) if flops["fp64_step"] else None
-    roof64 = {"kernel": "render_fp64", "achieved": fl64_launch / (fp64_kernel_ms * 1e-3) / 1e12 if fl64_launch else None,
-              "peak": fma64, "unit": "TFLOP/s", "kernel_ms_per_launch": fp64_kernel_ms}
-    roof64["frac"] = roof64["achieved"] / fma64 if roof64["achieved"] else None
+    roofs = {}
+    for pth, r in res.items():
+        prof, s = r["prof"], r["stats"]
+        for kname, (kms, kn) in prof.items():
+            if kn == 0 or kname in ("reduce", "trace", "load", "peak"):
+                continue
+            if kname == "render_fp64":
+                steps_k, pk, pipe = s["steps"], fma64, "fp64"
+            elif kname == "mixed_fp64":
+                steps_k, pk, pipe = s["fp64_steps"], fma64, "fp64"
+            else:
+                steps_k, pk, pipe = ctx_phase_steps(s, prof).get(kname, 0), fma32, "fp32"
+            fl_launch = flops["fp64_step"] * steps_k / kn
+            per_ms = kms / kn
+            ach = fl_launch / (per_ms * 1e-3) / 1e12
+            roofs[kname] = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                            "frac": ach / pk, "kernel_ms_per_launch": per_ms, "steps_per_launch": steps_k / kn,
+                            "share_of_step": kms / max(1e-9, sum(v[0] for k2, v in prof.items() if k2 not in ("peak",)))}
+    dom_prof = {k: v for k, v in main["prof"].items() if v[1] and k in roofs}
+    dom = max(dom_prof, key=lambda k: dom_prof[k][0])
+    roof = dict(roofs[dom])
+    roof.update({"kernel": dom, "traffic": None, "peak_source": f"FMA-chain microbenchmark ({roof['pipe']}), measured in this run",
+                 "flops_per_step": flops["fp64_step"], "flops_note": "algorithmic, counted from the kernel source, FMA = 2"})
 
     # ---- CPU oracle on a bounded sample of the same workload -----------------------------
     cpu = None
     if not args.no_cpu_baseline:
         r = oracle_sample(cam, freqs, CPU_SAMPLE_STRIDE)
         cpu = {"value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"], "kind": "oracle",
-               "sample": f"{int(r['rays'])} rays: every {CPU_SAMPLE_STRIDE}th pixel per axis of the 1024^2 image",
+               "sample": f"{int(r['rays'])} rays: every {CPU_SAMPLE_STRIDE}th pixel per axis of the {args.size}^2 image",
                "steps_per_s": r["steps"] / r["seconds"]}
-        # sampled parity of both GPU images against the oracle
         o = r["img"]
-        sl = (slice(None), slice(CPU_SAMPLE_STRIDE // 2, None, CPU_SAMPLE_STRIDE), slice(CPU_SAMPLE_STRIDE // 2, None, CPU_SAMPLE_STRIDE))
-        g64 = image64.cpu().numpy()[sl]
-        gmx = image.cpu().numpy()[sl]
-        den = np.maximum(np.abs(o), 1e-12 * np.abs(o).max())
-        cpu["fp64_max_rel_err_sampled"] = float((np.abs(g64 - o) / den).max())
-        cpu["mixed_median_rel_err_sampled"] = float(np.median(np.abs(gmx - o) / den))
+        h = CPU_SAMPLE_STRIDE // 2
+        sl = (slice(None), slice(h, None, CPU_SAMPLE_STRIDE), slice(h, None, CPU_SAMPLE_STRIDE))
+        big = np.abs(o) >= 1e-6 * np.abs(o).max()
+        for pth, rr in res.items():
+            g = rr["image"].cpu().numpy()[sl]
+            den = np.maximum(np.abs(o), 1e-12 * np.abs(o).max())
+            e = np.abs(g - o) / den
+            cpu[f"{pth}_max_rel_err_sampled"] = float(e.max())
+            cpu[f"{pth}_max_rel_err_sampled_bright"] = float(e[big].max())
+            cpu[f"{pth}_flux_rel_err_sampled"] = float(abs(g.sum() / o.sum() - 1))
 
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (analytic plasma, deterministic)",
-        "config": {"workload": WORKLOAD, "pixels": npix, "freqs_hz": freqs, "precision": "mixed", "r_fp64": cam.get("r_fp64", 6.0),
+        "vs_baseline": None, "dtype": "f32+f64" if paths[0] == "mixed" else "f64",
+        "data": "synthetic (analytic plasma, deterministic)",
+        "config": {"workload": workload, "pixels": npix, "freqs_hz": freqs, "precision": paths[0],
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed render"},
         "geodesic_steps_per_s": steps_per_s, "steps_per_ray": st["steps"] / (args.steps * npix),
         "fp64_step_fraction": st["fp64_steps"] / max(st["steps"], 1),
-        "fp64_path": {"value": world * rays_step / (ms64 * 1e-3), "unit": "rays/s", "ms_per_step": ms64,
-                      "geodesic_steps_per_s": world * (st64["steps"] / n64) / (ms64 * 1e-3), "roofline": roof64},
-        "speedup_vs_fp64": ms64 / ms_step,
-        "flux_jy": {"mixed": float(fl_mixed[0]), "fp64": float(fl64[0]),
-                    "mixed_rel_err_vs_fp64": float(abs(fl_mixed[0] / fl64[0] - 1))},
-        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
-        "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": e2e_v, "unit": "rays/s", "h2d_bytes_per_step": 8 * len(freqs),
-                "d2h_bytes_per_step": int(img_host.nbytes) + 8 * len(freqs)},
-        "gpu_launches": launches, "clocks": clocks, "wall_s_timed_region": wall,
-        "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64}, "measured_peaks_file": bool(peaks),
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in main["prof"].items() if v[1]},
+        "roofline": roof, "rooflines": roofs, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": main["clocks"], "wall_s_timed_region": main["wall"],
+        "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64},
     }
+    for pth, r in res.items():
+        if pth == paths[0]:
+            continue
+        line[f"{pth}_path"] = {"value": world * rays_step / (r["ms"] * 1e-3), "unit": "rays/s", "ms_per_step": r["ms"],
+                               "geodesic_steps_per_s": world * (r["stats"]["steps"] / args.steps) / (r["ms"] * 1e-3)}
+        line[f"speedup_vs_{pth}"] = r["ms"] / ms_step
+        line["flux_jy"] = {paths[0]: float(main["flux"][0]), pth: float(r["flux"][0]),
+                           "rel_diff": float(abs(main["flux"][0] / r["flux"][0] - 1))}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -344,7 +357,7 @@ def _flops_per_step():
     frequency), counted from the kernel source: see the flop-count table in the design notes."""
     from paper_1801_10452_b300 import flopcount
 
-    return flopcount.flops_per_step()
+    return flopcount.flops_per_step(1, "analytic")
 
 
 def main():
@@ -354,6 +367,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=1024, help="image side (profiling runs use a smaller case)")
+    ap.add_argument("--paths", default="mixed,fp64", help="comma list of paths to time: mixed, fp64")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -22,7 +22,7 @@ struct NewtonTol<float> { static constexpr float v = 1e-7f; };
 // x2 = theta/pi, resetting to 0.05 outside [0, 1] or where f' vanishes, stopping when the
 // update is below tolerance or after 20 iterations.
 template <typename T>
-__device__ __forceinline__ T newton_x2(T theta, T h) {
+RAPTOR_HD T newton_x2(T theta, T h) {
     T xv = theta * T(1.0 / kPi);
     const T oh = T(1) - h;
     for (int it = 0; it < 20; ++it) {
@@ -47,11 +47,16 @@ __device__ __forceinline__ T newton_x2(T theta, T h) {
 // Bilinear cell-centred interpolation of the 8 primitives of snapshot s at fractional
 // index (fi, fj) (clamped to edge cells).  Vector loads of the interleaved cells.
 template <typename T>
-__device__ __forceinline__ void bilinear8(const Params& p, int s, int i0, int j0, T wi, T wj, T out[8]) {
+RAPTOR_HD void bilinear8(const Params& p, int s, int i0, int j0, T wi, T wj, T out[8]) {
     const float4* g = reinterpret_cast<const float4*>(p.grid) + ((long long)s * p.n2 * p.n1) * 2;
     const long long c00 = ((long long)j0 * p.n1 + i0) * 2, c01 = c00 + (long long)p.n1 * 2;
+#ifdef __CUDA_ARCH__
     const float4 a0 = __ldg(g + c00), a1 = __ldg(g + c00 + 1), b0 = __ldg(g + c00 + 2), b1 = __ldg(g + c00 + 3);
     const float4 c0 = __ldg(g + c01), c1 = __ldg(g + c01 + 1), d0 = __ldg(g + c01 + 2), d1 = __ldg(g + c01 + 3);
+#else
+    const float4 a0 = g[c00], a1 = g[c00 + 1], b0 = g[c00 + 2], b1 = g[c00 + 3];
+    const float4 c0 = g[c01], c1 = g[c01 + 1], d0 = g[c01 + 2], d1 = g[c01 + 3];
+#endif
     const T w00 = (T(1) - wi) * (T(1) - wj), w10 = wi * (T(1) - wj), w01 = (T(1) - wi) * wj, w11 = wi * wj;
     out[0] = w00 * T(a0.x) + w10 * T(b0.x) + w01 * T(c0.x) + w11 * T(d0.x);
     out[1] = w00 * T(a0.y) + w10 * T(b0.y) + w01 * T(c0.y) + w11 * T(d0.y);
@@ -72,7 +77,7 @@ __device__ __forceinline__ void bilinear8(const Params& p, int s, int i0, int j0
 //   T_p/T_e = R_low/(1+beta_p^2) + R_high beta_p^2/(1+beta_p^2),
 //   Theta_e = (m_p/m_e) (gamma_ad - 1) (u/rho) / (1 + T_p/T_e).
 template <typename T>
-__device__ __forceinline__ int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], int snap, T& ne, T& the,
+RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], int snap, T& ne, T& the,
                                            T& B, T u[4], T b[4]) {
     const T r = P.r;
     const T x1 = Real<T>::log_(r);
@@ -142,6 +147,43 @@ __device__ __forceinline__ int grid_sample(const Params& p, const KSPoint<T>& P,
     the = T(kMp / kMe) * gm1 * (uu / rho) / (T(1) + R);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = bk[i] * T(p.B_unit);
+    return 1;
+}
+
+// Plasma + frequency ratio at state (x, k) in type T.  Returns 1 emitting, 0 no plasma,
+// -1 error.  On success fills ne, the, B, g = nu_fluid/nu_obs and sinb.
+template <typename T>
+RAPTOR_HD int plasma_sample(const Params& p, const T x[4], const T k[4], int snap, T& ne, T& the,
+                                             T& B, T& g, T& sinb) {
+    KSPoint<T> P;
+    ks_point(T(p.a), x[1], x[2], P);
+    T u[4], kc[4];
+    T kb;  // k . b_hat
+    if (p.kind == 0) {
+        const int ok = analytic_velocity(T(p.a), T(p.r_isco), P, u);
+        if (ok < 0) return -1;
+        const T r = x[1];
+        ne = T(p.n0) * Real<T>::pow_(r, T(p.n_pow));
+        the = T(p.the0) * Real<T>::pow_(r, T(p.the_pow));
+        B = T(p.B0) * Real<T>::pow_(r, T(p.B_pow));
+        ks_lower(P, k, kc);
+        g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
+        const T u_phi = P.gtp * u[0] + P.grp * u[1] + P.gpp * u[3];
+        const T kv = kc[3] + u_phi * g;
+        kb = kv * rsq(P.gpp + u_phi * u_phi);
+    } else {
+        T b[4];
+        const int ok = grid_sample<T>(p, P, x, snap, ne, the, B, u, b);
+        if (ok <= 0) return ok;
+        ks_lower(P, k, kc);
+        g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
+        kb = (kc[0] * b[0] + kc[1] * b[1] + kc[2] * b[2] + kc[3] * b[3]) / B;
+    }
+    if (!(g > T(0))) return -1;
+    // cos theta_B = (k_phys . b) / (g |b|) with k_phys = -k
+    T cb = -kb / g;
+    cb = fmin(fmax(cb, T(-1)), T(1));
+    sinb = Real<T>::sqrt_(T(1) - cb * cb);
     return 1;
 }
 

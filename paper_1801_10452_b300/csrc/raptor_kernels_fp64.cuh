@@ -28,43 +28,6 @@ struct RayD {
     int snap;
 };
 
-// Plasma + frequency ratio at state (x, k) in type T.  Returns 1 emitting, 0 no plasma,
-// -1 error.  On success fills ne, the, B, g = nu_fluid/nu_obs and sinb.
-template <typename T>
-__device__ __forceinline__ int plasma_sample(const Params& p, const T x[4], const T k[4], int snap, T& ne, T& the,
-                                             T& B, T& g, T& sinb) {
-    KSPoint<T> P;
-    ks_point(T(p.a), x[1], x[2], P);
-    T u[4], kc[4];
-    T kb;  // k . b_hat
-    if (p.kind == 0) {
-        const int ok = analytic_velocity(T(p.a), T(p.r_isco), P, u);
-        if (ok < 0) return -1;
-        const T r = x[1];
-        ne = T(p.n0) * Real<T>::pow_(r, T(p.n_pow));
-        the = T(p.the0) * Real<T>::pow_(r, T(p.the_pow));
-        B = T(p.B0) * Real<T>::pow_(r, T(p.B_pow));
-        ks_lower(P, k, kc);
-        g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
-        const T u_phi = P.gtp * u[0] + P.grp * u[1] + P.gpp * u[3];
-        const T kv = kc[3] + u_phi * g;
-        kb = kv * rsq(P.gpp + u_phi * u_phi);
-    } else {
-        T b[4];
-        const int ok = grid_sample<T>(p, P, x, snap, ne, the, B, u, b);
-        if (ok <= 0) return ok;
-        ks_lower(P, k, kc);
-        g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
-        kb = (kc[0] * b[0] + kc[1] * b[1] + kc[2] * b[2] + kc[3] * b[3]) / B;
-    }
-    if (!(g > T(0))) return -1;
-    // cos theta_B = (k_phys . b) / (g |b|) with k_phys = -k
-    T cb = -kb / g;
-    cb = fmin(fmax(cb, T(-1)), T(1));
-    sinb = Real<T>::sqrt_(T(1) - cb * cb);
-    return 1;
-}
-
 // One FP64 step of a ray: adaptive step, RK4, termination, transfer sample.  Returns the
 // termination code or -1 to continue.  dl_out / g_out feed the trace recorder.
 template <int NF>

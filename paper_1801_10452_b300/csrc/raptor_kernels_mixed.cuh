@@ -6,8 +6,9 @@
 //   phase A (FP32, persistent): fresh camera rays, integrated while r >= r_fp64 and away
 //     from radial turning points (|k^r| >= turn_kr |k^t|); a ray entering that region is
 //     pushed to the FP64 queue with its state promoted to FP64, and the lane refills.
-//   phase B (FP64, persistent): rays from the FP64 queue, integrated in FP64 until they
-//     terminate or leave the region; leavers are pushed to the FP32 queue.
+//   phase B (FP64, persistent): rays from the FP64 queue, geodesic steps in FP64 (their
+//     transfer samples in FP32) until they terminate or leave the region; leavers are
+//     pushed to the FP32 queue.
 //   phase C (FP32, persistent): rays from the FP32 queue, integrated to termination (an
 //     outgoing photon has no further radial turning point; re-entries are counted).
 // The optical depth of a frequency is accumulated in FP64 once it exceeds 10.
@@ -103,6 +104,46 @@ struct RayF {
     int n, snap;
 };
 
+// FP32 transfer sample at (x, k) after a step of length dl (Eqs. 30, 34-36, 41-44): the
+// intensity increments are FP32; a frequency's optical depth moves to FP64 once above 10.
+// TI/TT are the storage types of I and of the low part of tau (float in the FP32 phases,
+// double in the FP64 phase).
+template <int NF, typename TI, typename TT>
+__device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4], const float k[4], float dl, int snap,
+                                              TI* I, TT* tau, double* tau_hi) {
+    float ne, the, B, g, sinb;
+    const int ok = plasma_sample<float>(p, x, k, snap, ne, the, B, g, sinb);
+    if (ok <= 0) return ok;
+    const float dlcm = dl * float(p.Lcm);
+    const bool k2x = (p.flags & kFlagK2Exact) != 0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (f < p.nf) {
+            float j, S;
+            synchrotron<float>(g * float(p.nu[f]), ne, the, B, sinb, k2x, j, S);
+            if (j > 0.f && S > 0.f) {
+                const float dtau = j / S * g * dlcm;
+                const float tau_now = float(tau[f]) + float(tau_hi[f]);
+                I[f] += TI(expf(-tau_now) * S * (-expm1f(-dtau)) / (g * g * g));
+                if (float(tau[f]) + dtau > 10.f || tau_hi[f] > 0.0) tau_hi[f] += double(dtau);
+                else tau[f] += TT(dtau);
+            }
+        }
+    }
+    return 1;
+}
+
+template <int NF, typename TT>
+__device__ __forceinline__ int thick_or_capped(const Params& p, const TT* tau, const double* tau_hi, int n) {
+    double tmin = double(tau[0]) + tau_hi[0];
+#pragma unroll
+    for (int f = 1; f < NF; ++f)
+        if (f < p.nf) tmin = fmin(tmin, double(tau[f]) + tau_hi[f]);
+    if (tmin > p.tau_cut) return kThick;
+    if (n >= p.max_steps) return kTruncated;
+    return -1;
+}
+
 // One FP32 step (same scheme as step_fp64).  Returns termination code or -1.
 template <int NF>
 __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
@@ -115,34 +156,37 @@ __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     if (!fin) return kError;
     if (R.x[1] < float(p.r_stop)) return kCaptured;
     if (R.x[1] > float(p.r_esc)) return kEscaped;
-    float ne, the, B, g, sinb;
-    const int ok = plasma_sample<float>(p, R.x, R.k, R.snap, ne, the, B, g, sinb);
-    if (ok < 0) return kError;
-    if (ok > 0) {
-        const float dlcm = dl * float(p.Lcm);
-        const bool k2x = (p.flags & kFlagK2Exact) != 0;
+    if (rt_sample_fp32<NF, float, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+    return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
+}
+
+// Mixed FP64 phase: the geodesic step in FP64, its transfer sample in FP32 (FP64 optical
+// depth beyond 10), state kept in FP64.
+template <int NF>
+struct RayM {
+    double x[4], k[4];
+    double I[NF];
+    float tau[NF];
+    double tau_hi[NF];
+    int n, snap;
+};
+
+template <int NF>
+__device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF>& R) {
+    const double dl = step_size<double>(p.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
+    rk4_step<double>(p.a, R.x, R.k, dl);
+    R.n += 1;
+    bool fin = true;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            if (f < p.nf) {
-                float j, S;
-                synchrotron<float>(g * float(p.nu[f]), ne, the, B, sinb, k2x, j, S);
-                if (j > 0.f && S > 0.f) {
-                    const float dtau = j / S * g * dlcm;
-                    const float tau_now = R.tau[f] + float(R.tau_hi[f]);
-                    R.I[f] += expf(-tau_now) * S * (-expm1f(-dtau)) / (g * g * g);
-                    if (R.tau[f] + dtau > 10.f || R.tau_hi[f] > 0.0) R.tau_hi[f] += double(dtau);
-                    else R.tau[f] += dtau;
-                }
-            }
-        }
-    }
-    double tmin = double(R.tau[0]) + R.tau_hi[0];
+    for (int i = 0; i < 4; ++i) fin = fin && isfinite(R.x[i]) && isfinite(R.k[i]);
+    if (!fin) return kError;
+    if (R.x[1] < p.r_stop) return kCaptured;
+    if (R.x[1] > p.r_esc) return kEscaped;
+    float xf[4], kf[4];
 #pragma unroll
-    for (int f = 1; f < NF; ++f)
-        if (f < p.nf) tmin = fmin(tmin, double(R.tau[f]) + R.tau_hi[f]);
-    if (tmin > p.tau_cut) return kThick;
-    if (R.n >= p.max_steps) return kTruncated;
-    return -1;
+    for (int i = 0; i < 4; ++i) { xf[i] = float(R.x[i]); kf[i] = float(R.k[i]); }
+    if (rt_sample_fp32<NF, double, float>(p, xf, kf, float(dl), R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+    return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
 }
 
 template <int NF>
@@ -248,11 +292,11 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
     if (c_re) atomicAdd(&stats[kStatReentry], c_re);
 }
 
-// Phase B: FP64 rays from the FP64 queue.
+// Phase B: rays from the FP64 queue; FP64 geodesic steps, FP32 transfer samples.
 template <int NF>
 __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues mq, unsigned long long* cnt,
                                                     unsigned long long* stats) {
-    RayD<NF> R;
+    RayM<NF> R;
     long long id = -1;
     int frame = 0, pix = 0, n_in = 0;
     bool drained = false;
@@ -274,7 +318,9 @@ __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues 
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 R.I[f] = f < p.nf ? q.I[(size_t)f * cap + nid] : 0.0;
-                R.tau[f] = f < p.nf ? q.tau[(size_t)f * cap + nid] : 0.0;
+                const double t = f < p.nf ? q.tau[(size_t)f * cap + nid] : 0.0;
+                if (t > 10.0) { R.tau[f] = 0.f; R.tau_hi[f] = t; }
+                else { R.tau[f] = float(t); R.tau_hi[f] = 0.0; }
             }
             R.n = q.n[nid];
             n_in = R.n;
@@ -284,13 +330,15 @@ __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues 
         int st = -1;
         bool push = false;
         if (id >= 0) {
-            double dl, g;
-            st = step_fp64<NF>(p, R, dl, g);
+            st = step_mixed64<NF>(p, R);
             if (st < 0 && !in_fp64_region<double>(p, R.x, R.k)) push = true;
         }
         const long long slot = warp_push_slot(&cnt[kCntPush32], push);
         if (push) {
-            store_ray<NF>(mq.q32, cap, slot, id, R.x, R.k, R.I, R.tau, R.n, p.nf);
+            double tau[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + R.tau_hi[f];
+            store_ray<NF>(mq.q32, cap, slot, id, R.x, R.k, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
         } else if (id >= 0 && st >= 0) {

@@ -53,7 +53,7 @@ struct Params {
 // k_theta = sign(beta) sqrt|Q - L^2 cot^2 theta + a^2 cos^2 theta|, k_r from k.k = 0 with
 // the physical photon moving outward at the camera; the state is the backward ray -k.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ void camera_ray(const Params& p, double alpha, double beta, double t_cam,
+RAPTOR_HD void camera_ray(const Params& p, double alpha, double beta, double t_cam,
                                            double x[4], double k[4]) {
     const double a = p.a, a2 = a * a;
     const double L = -alpha * p.sin_i;
@@ -107,7 +107,7 @@ struct Sample {
 //   u^t = [P (P^2 + 2 r P + 4 r^2)/(P^2 + 2 r s) - a^2 sin^2] / Sigma,
 //   u^r = -s / Sigma, u^phi = -2 a r / (Sigma (2 r + s)), P = r^2 + a^2, s = sqrt(2 r P).
 template <typename T>
-__device__ __forceinline__ int analytic_velocity(T a, T r_isco, const KSPoint<T>& P, T u[4]) {
+RAPTOR_HD int analytic_velocity(T a, T r_isco, const KSPoint<T>& P, T u[4]) {
     const T r = P.r;
     u[2] = T(0);
     if (r >= r_isco) {
@@ -134,7 +134,7 @@ __device__ __forceinline__ int analytic_velocity(T a, T r_isco, const KSPoint<T>
 // B_nu is written as 2 nu^2 m_e Theta x / expm1(x), x = h nu / (m_e c^2 Theta), which
 // equals Eq. 44 and stays inside FP32 range.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ double bessel_k2_exact(double x) {
+RAPTOR_HD double bessel_k2_exact(double x) {
     // K_2(x) = int_0^inf exp(-x cosh t) cosh(2 t) dt (DLMF 10.32.9); trapezoidal rule with
     // step 1/4, whose error decays like exp(-pi^2 / h) for this entire integrand.
     const double h = 0.25;
@@ -149,7 +149,7 @@ __device__ __forceinline__ double bessel_k2_exact(double x) {
 }
 
 template <typename T>
-__device__ __forceinline__ void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, T& S) {
+RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, T& S) {
     const T nu_c_per_G = T(kQe / (2.0 * kPi * kMe * kC));
     const T cj = T(1.4142135623730951 * kPi * kQe * kQe / (3.0 * kC));
     const T hme = T(kH / (kMe * kC * kC));
@@ -172,7 +172,7 @@ __device__ __forceinline__ void synchrotron(T nu, T ne, T the, T B, T sinb, bool
 // Backward transfer (Eqs. 35-36, per-step solution of Eq. 34):
 //   dtau = (j/S) g dl L;  I += exp(-tau) S (1 - exp(-dtau)) / g^3;  tau += dtau.
 template <typename T, typename TT>
-__device__ __forceinline__ void rt_update(T j, T S, T g, T dl_cm, T& I, TT& tau) {
+RAPTOR_HD void rt_update(T j, T S, T g, T dl_cm, T& I, TT& tau) {
     if (!(j > T(0)) || !(S > T(0))) return;
     const T dtau = j / S * g * dl_cm;
     I += Real<T>::exp_(-T(tau)) * S * (-Real<T>::expm1_(-dtau)) / (g * g * g);
