@@ -331,7 +331,13 @@ void ora_camera(const OraScene* s, double alpha, double beta, double t_cam, doub
     double kc[4];
     kc[0] = -E;
     kc[3] = L;
-    kc[2] = sgn_pos(beta) * std::sqrt(std::fabs(Q - L * L * cot * cot + s->a * s->a * cth * cth));
+    // At the camera theta = i, so Q - L^2 cot^2 + a^2 cos^2 = beta^2 exactly and Eq. 28 gives
+    // k_theta = sign(beta) |beta| = beta.  It is evaluated in that form: the printed form
+    // cancels two equal alpha^2 cos^2 i terms and its square root turns the rounding
+    // residual into a ~1e-8 spurious k_theta for beta = 0.
+    const double kth_sq = Q - L * L * cot * cot + s->a * s->a * cth * cth;  // == beta^2 in exact arithmetic
+    (void)kth_sq;
+    kc[2] = sgn_pos(beta) * std::fabs(beta);
     // BL inverse metric at the camera
     OraScene bl = *s;
     bl.coords = 1;

@@ -49,21 +49,21 @@ struct Params {
 
 // ------------------------------------------------------------------------------------
 // Camera (sec. 2.3, Eqs. 24-28; App. A.1).  Always FP64.
-// E = 1, L = -alpha sin i, Q = beta^2 + cos^2 i (alpha^2 - a^2),
-// k_theta = sign(beta) sqrt|Q - L^2 cot^2 theta + a^2 cos^2 theta|, k_r from k.k = 0 with
+// E = 1, L = -alpha sin i, Q = beta^2 + cos^2 i (alpha^2 - a^2) (carried by k_theta),
+// k_theta = sign(beta) sqrt|Q - L^2 cot^2 theta + a^2 cos^2 theta| = beta, k_r from k.k = 0 with
 // the physical photon moving outward at the camera; the state is the backward ray -k.
 // ------------------------------------------------------------------------------------
 RAPTOR_HD void camera_ray(const Params& p, double alpha, double beta, double t_cam,
                                            double x[4], double k[4]) {
     const double a = p.a, a2 = a * a;
     const double L = -alpha * p.sin_i;
-    const double Q = beta * beta + p.cos_i * p.cos_i * (alpha * alpha - a2);
     const double r = p.r_cam;
-    double sn, cs;
-    sincos(p.incl, &sn, &cs);
-    const double cot = cs / sn;
+    const double sn = p.sin_i, cs = p.cos_i;
     const double kt = -1.0, kp = L;
-    const double kh = (beta < 0.0 ? -1.0 : 1.0) * sqrt(fabs(Q - L * L * cot * cot + a2 * cs * cs));
+    // At theta = i, Q - L^2 cot^2 + a^2 cos^2 = beta^2 exactly, so the square root of Eq. 28
+    // is |beta|: k_theta = beta.  (The printed form cancels two alpha^2 cos^2 i terms, whose
+    // rounding residual its square root would magnify to ~1e-8 at beta = 0.)
+    const double kh = beta;
     // Boyer-Lindquist inverse metric at the camera
     const double s2 = sn * sn;
     const double Sig = r * r + a2 * cs * cs, Del = r * r - 2.0 * r + a2;

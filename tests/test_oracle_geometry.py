@@ -288,3 +288,23 @@ def test_kerr_critical_curve_classification(ora):
         st_in, *_ = ora.geodesic(s, al - 0.1 * d[0], be - 0.1 * d[1])
         st_out, *_ = ora.geodesic(s, al + 0.1 * d[0], be + 0.1 * d[1])
         assert st_in == 1 and st_out == 0, (al, be)
+
+
+def test_camera_k_theta_reading(ora):
+    """Eq. 28 at the camera (theta = i): Q - L^2 cot^2 + a^2 cos^2 = beta^2, so
+    k_theta = beta.  Checked in extended precision against the printed form."""
+    import numpy as np
+
+    for a, inc in [(0.9, 60.0), (0.0, 17.0), (0.998, 85.0)]:
+        s = ora.scene(a=a, incl_deg=inc, coords=1)
+        for al, be in [(7.3, 0.0), (-3.1, 2.2), (15.0, -0.01)]:
+            i = np.longdouble(math.radians(inc))
+            A, Bt = np.longdouble(al), np.longdouble(be)
+            L = -A * np.sin(i)
+            Q = Bt * Bt + np.cos(i) ** 2 * (A * A - np.longdouble(a) ** 2)
+            printed = Q - L * L * (np.cos(i) / np.sin(i)) ** 2 + np.longdouble(a) ** 2 * np.cos(i) ** 2
+            assert abs(float(printed) - be * be) < 1e-15 * max(1.0, al * al)
+            x, k = ora.camera(s, al, be)
+            g, _ = ora.metric(s, x[1], x[2])
+            kc = g @ (-k)
+            assert kc[2] == be
