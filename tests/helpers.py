@@ -58,3 +58,25 @@ def oracle_kwargs(cam: dict, plasma: dict | None = None) -> dict:
         if k in cam:
             out[k] = cam[k]
     return out
+
+
+def grid_oracle_scene(ora, cam, fields, meta, model, slow=0, t0=0.0, snap=0):
+    """Oracle scene for a grid workload (same arrays the library receives)."""
+    kw = oracle_kwargs(cam)
+    s = ora.scene(**kw)
+    ora.attach_grid(s, fields, meta["x1_min"], meta["x1_max"], meta["h_mks"])
+    s.mass_unit_g = model["mass_unit_g"]
+    s.r_high = model["r_high"]
+    s.r_low = model["r_low"]
+    s.gamma_ad = meta["gamma_ad"]
+    s.t0 = t0
+    s.dt_snap = meta["dt_snap"]
+    s.slow_light = slow
+    s.snap = snap
+    return s
+
+
+def grid_plasma_kwargs(meta, model, slow=0, t0=0.0):
+    return dict(slow_light=slow, x1_min=meta["x1_min"], x1_max=meta["x1_max"], h_mks=meta["h_mks"], t0=t0,
+                dt_snap=meta["dt_snap"], mass_unit_g=model["mass_unit_g"], r_high=model["r_high"],
+                r_low=model["r_low"], gamma_ad=meta["gamma_ad"])
