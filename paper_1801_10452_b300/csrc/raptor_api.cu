@@ -302,6 +302,7 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
     if (ctx->cam.precision == RAPTOR_MIXED_MLP)
         return fail(ctx, RAPTOR_EUNSUPPORTED, "RAPTOR_MIXED_MLP is not available in this build");
     p.nf_total = n_freq;
+    p.i_unscale = ctx->cam.precision == RAPTOR_FP64 ? 1.0 : kIUnscale;
     for (int f0 = 0; f0 < n_freq; f0 += 16) {
         p.f_off = f0;
         p.nf = std::min(16, n_freq - f0);
@@ -590,6 +591,7 @@ raptor_status raptor_trace_ray(raptor_ctx* ctx, double alpha, double beta, doubl
     ctx->last_stream = s;
     RCK(ensure(&ctx->d_rec, &ctx->rec_cap, (size_t)std::max(max_rec, 1) * 12));
     Params p = base_params(ctx);
+    p.i_unscale = 1.0;
     p.nf = n_freq;
     p.nf_total = n_freq;
     for (int f = 0; f < n_freq; ++f) p.nu[f] = freqs_hz[f];

@@ -89,7 +89,7 @@ __device__ __forceinline__ void write_ray(const Params& p, int frame, int pix, c
     const long long plane = (long long)p.n_rows * p.nx;
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-        if (f < p.nf) p.image[((long long)frame * p.nf_total + p.f_off + f) * plane + pix] = I[f] * p.pix_jy;
+        if (f < p.nf) p.image[((long long)frame * p.nf_total + p.f_off + f) * plane + pix] = I[f] * p.i_unscale * p.pix_jy;
     if (p.steps_out) p.steps_out[pix] = n;
     if (p.status_out) p.status_out[pix] = status;
 }

@@ -104,10 +104,16 @@ struct RayF {
     int n, snap;
 };
 
-// FP32 transfer sample at (x, k) after a step of length dl (Eqs. 30, 34-36, 41-44): the
-// intensity increments are FP32; a frequency's optical depth moves to FP64 once above 10.
-// TI/TT are the storage types of I and of the low part of tau (float in the FP32 phases,
-// double in the FP64 phase).
+// FP32 transfer sample at (x, k) after a step of length dl (Eqs. 30, 34-36, 41-44).
+// Intensities are carried scaled by kIScale = 2^100: the emissivity's exponential tail
+// reaches ~1e-60 cgs, far below FP32's smallest normal number.  The per-step increment of
+// the formal solution, exp(-tau) S (1 - exp(-dtau)) / g^3, is written as
+// exp(-tau) j dl L F(dtau) / g^2 with F(x) = (1 - exp(-x)) / x, so no factor underflows.
+// A frequency's optical depth moves to FP64 once above 10.  TI/TT are the storage types
+// of I and of the low part of tau (float in the FP32 phases, double in the FP64 phase).
+constexpr float kIScale = 1.2676506002282294e30f;      // 2^100
+constexpr double kIUnscale = 7.888609052210118e-31;    // 2^-100
+
 template <int NF, typename TI, typename TT>
 __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4], const float k[4], float dl, int snap,
                                               TI* I, TT* tau, double* tau_hi) {
@@ -115,16 +121,19 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
     const int ok = plasma_sample<float>(p, x, k, snap, ne, the, B, g, sinb);
     if (ok <= 0) return ok;
     const float dlcm = dl * float(p.Lcm);
+    const float gdl_unscaled = g * dlcm * float(kIUnscale);
+    const float ig2 = 1.f / (g * g);
     const bool k2x = (p.flags & kFlagK2Exact) != 0;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (f < p.nf) {
             float j, S;
-            synchrotron<float>(g * float(p.nu[f]), ne, the, B, sinb, k2x, j, S);
+            synchrotron<float>(g * float(p.nu[f]), ne, the, B, sinb, k2x, j, S, kIScale);
             if (j > 0.f && S > 0.f) {
-                const float dtau = j / S * g * dlcm;
+                const float dtau = j / S * gdl_unscaled;
+                const float F = dtau > 1e-4f ? -expm1f(-dtau) / dtau : 1.f - 0.5f * dtau;
                 const float tau_now = float(tau[f]) + float(tau_hi[f]);
-                I[f] += TI(expf(-tau_now) * S * (-expm1f(-dtau)) / (g * g * g));
+                I[f] += TI(expf(-tau_now) * j * dlcm * F * ig2);
                 if (float(tau[f]) + dtau > 10.f || tau_hi[f] > 0.0) tau_hi[f] += double(dtau);
                 else tau[f] += TT(dtau);
             }

@@ -42,6 +42,7 @@ struct Params {
     int lc_fast;             // 1: frame f samples snapshot frame_snap0 + f
     // outputs
     double* image;           // [frame][nf_total][n_rows][nx]
+    double i_unscale;        // stored intensity = I * i_unscale (1 for FP64; 2^-100 for the FP32 scaling)
     int nf_total, f_off;     // frequency chunking: this launch covers [f_off, f_off + nf)
     int* steps_out;          // optional [n_rows][nx]
     int* status_out;         // optional [n_rows][nx]
@@ -148,10 +149,12 @@ RAPTOR_HD double bessel_k2_exact(double x) {
     return h * sum;
 }
 
+// `jscale` multiplies j (the FP32 transfer carries emissivities scaled by 2^100 so that the
+// exponential tail of Eq. 41 stays inside FP32 range; the FP64 path passes 1).
 template <typename T>
-RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, T& S) {
+RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, T& S, T jscale = T(1)) {
     const T nu_c_per_G = T(kQe / (2.0 * kPi * kMe * kC));
-    const T cj = T(1.4142135623730951 * kPi * kQe * kQe / (3.0 * kC));
+    const T cj = T(1.4142135623730951 * kPi * kQe * kQe / (3.0 * kC)) * jscale;
     const T hme = T(kH / (kMe * kC * kC));
     const T x = hme * nu / the;
     S = T(2.0 * kMe) * nu * nu * the * (x / Real<T>::expm1_(x));

@@ -120,7 +120,7 @@ def test_trace_per_step_parity(R, ora):
     s = ora.scene(**oracle_kwargs(cam))
     for al, be in [(5.0, 3.0), (-3.0, 0.5), (0.31, -7.9), (15.0, 12.0)]:
         g = ctx.trace_ray(al, be, [230e9], max_rec=5000)
-        o = ora.trace_ray(s, al, be, [230e9], max_trace=5000)
+        o = ora.trace_ray(s, al, be, [230e9], max_trace=5000, t_cam=ctx.cam.t_delay)
         assert g["steps"] == o["steps"] and g["status"] == o["status"]
         tg, to = g["trace"], o["trace"]
         scale = np.maximum(np.abs(to), 1e-300)
