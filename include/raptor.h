@@ -207,6 +207,29 @@ raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launch
  * Measures the arithmetic ceiling used for the rooflines of the ray kernels. */
 raptor_status raptor_measure_fma_peak(int fp64, double* tflops);
 
+/* Allocation-free rendering (the paper has no counterpart).  Some callers cannot allocate
+ * device memory: a host program whose own memory pool already holds the GPU's memory, or a
+ * code path that must not call cudaMalloc/cudaFree after start-up because those calls can
+ * synchronise the device.  raptor_render_noalloc renders like raptor_render (FP64 path,
+ * analytic plasma) without any allocation: no context, no cudaMalloc/cudaFree, no
+ * allocating library call.  The caller passes the descriptors, the host frequency array,
+ * image_dev (device double [n_freq][ny][nx], Jy per pixel) and flux_dev (device double
+ * [n_freq], may be NULL); work is enqueued on `stream` and the call returns without waiting.
+ * The kernels' scratch (ray counters and partial flux sums) lives in one static device
+ * array of RAPTOR_NOALLOC_SCRATCH_BYTES on every device that loads the library, held until
+ * the process exits and shared by every call; each call clears what must start at zero.
+ * Calls whose GPU work overlaps in time (other streams or host threads) race on that array:
+ * the caller must serialise them.  The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream capture.
+ * Limits: cam->precision must be RAPTOR_FP64 (else RAPTOR_EINVAL); plasma->kind must be
+ * RAPTOR_PLASMA_ANALYTIC (else RAPTOR_EUNSUPPORTED); 1 <= n_freq <= RAPTOR_NOALLOC_MAX_FREQ
+ * (else RAPTOR_EINVAL).  Invalid descriptors return RAPTOR_EINVAL before any launch. */
+#define RAPTOR_NOALLOC_MAX_FREQ 64
+#define RAPTOR_NOALLOC_SCRATCH_BYTES 131584
+raptor_status raptor_render_noalloc(const raptor_camera_desc* cam, const raptor_plasma_desc* plasma,
+                                    const double* freqs_hz, int n_freq, double t_obs, double* image_dev,
+                                    double* flux_dev, void* stream);
+
 /* Message for the last failure on ctx ("" if none).  Valid until the next call on ctx. */
 const char* raptor_last_error(const raptor_ctx* ctx);
 

@@ -27,6 +27,7 @@ EXPORTS = [
     "raptor_camera_set", "raptor_load_plasma", "raptor_render", "raptor_render_ex", "raptor_render_host",
     "raptor_lightcurve", "raptor_trace_ray", "raptor_stats", "raptor_stats_reset", "raptor_set_launch",
     "raptor_last_error", "raptor_destroy", "raptor_profile", "raptor_profile_read", "raptor_measure_fma_peak",
+    "raptor_render_noalloc",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak"]
 
@@ -92,6 +93,7 @@ def lib():
             "raptor_profile": (st, [vp, C.c_int]),
             "raptor_profile_read": (st, [vp, dp, C.POINTER(C.c_longlong)]),
             "raptor_measure_fma_peak": (st, [C.c_int, dp]),
+            "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

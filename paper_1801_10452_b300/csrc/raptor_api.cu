@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -675,6 +676,105 @@ raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int bloc
     ctx->launch_block = threads_per_block;
     ctx->launch_bps = blocks_per_sm;
     return RAPTOR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free rendering (raptor_render_noalloc).
+//
+// For callers that cannot allocate device memory (a host program whose pool already owns
+// the GPU's memory, or a path that must not call cudaMalloc/cudaFree after start-up since
+// those calls can synchronise the device).  The FP64 persistent kernel and the flux
+// reduction need scratch beyond their inputs and outputs: the ray counter, the stats
+// counters and the partial flux sums.  Here they live in one file-scope device array,
+// g_noalloc_scratch, of RAPTOR_NOALLOC_SCRATCH_BYTES per device, held until the process
+// exits and shared by every call.  In host code the symbol is only a stand-in: its device
+// address is looked up once per device, with that device current, on the first call.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocCounterOff = 0;    // 8 x u64 ray/phase counters
+constexpr size_t kNoAllocStatsOff = 256;    // 8 x u64 stats
+constexpr size_t kNoAllocPartialOff = 512;  // [RAPTOR_NOALLOC_MAX_FREQ][256] partial flux sums
+constexpr int kNoAllocChunks = 256;
+constexpr size_t kNoAllocBytes = kNoAllocPartialOff + sizeof(double) * RAPTOR_NOALLOC_MAX_FREQ * kNoAllocChunks;
+static_assert(kNoAllocBytes == RAPTOR_NOALLOC_SCRATCH_BYTES, "scratch size must match the header");
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of the scratch array on device `dev` (which must be current).
+static cudaError_t noalloc_scratch(int dev, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+raptor_status raptor_render_noalloc(const raptor_camera_desc* cam, const raptor_plasma_desc* plasma, const double* freqs_hz,
+                                    int n_freq, double t_obs, double* image_dev, double* flux_dev, void* stream) {
+    if (!validate_camera(cam).empty() || !validate_plasma(plasma).empty()) return RAPTOR_EINVAL;
+    if (cam->precision != RAPTOR_FP64) return RAPTOR_EINVAL;
+    if (plasma->kind != RAPTOR_PLASMA_ANALYTIC) return RAPTOR_EUNSUPPORTED;
+    if (!freqs_hz || n_freq < 1 || n_freq > RAPTOR_NOALLOC_MAX_FREQ || !image_dev || !std::isfinite(t_obs))
+        return RAPTOR_EINVAL;
+    for (int f = 0; f < n_freq; ++f)
+        if (!finite_pos(freqs_hz[f])) return RAPTOR_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RAPTOR_ECUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return RAPTOR_EINVAL;
+    void* scratch = nullptr;
+    if (noalloc_scratch(dev, &scratch) != cudaSuccess) return RAPTOR_ECUDA;
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    // A stack context that only borrows the scratch: no device memory is allocated.
+    raptor_ctx tmp;
+    tmp.cam = *cam;
+    tmp.plasma = *plasma;
+    tmp.plasma.fields = nullptr;
+    tmp.has_plasma = true;
+    tmp.device = dev;
+    if (cudaDeviceGetAttribute(&tmp.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RAPTOR_ECUDA;
+    tmp.d_counters = reinterpret_cast<unsigned long long*>(base + kNoAllocCounterOff);
+    tmp.d_stats = reinterpret_cast<unsigned long long*>(base + kNoAllocStatsOff);
+    double* partial = reinterpret_cast<double*>(base + kNoAllocPartialOff);
+    cudaStream_t s = (cudaStream_t)stream;
+    Params p = base_params(&tmp);
+    p.row0 = 0;
+    p.n_rows = cam->ny;
+    p.n_pix = cam->nx * cam->ny;
+    p.n_rays = p.n_pix;
+    p.t_cam = t_obs + cam->t_delay;
+    p.snap = 0;
+    p.image = image_dev;
+    p.i_unscale = 1.0;
+    p.nf_total = n_freq;
+    cudaError_t e = cudaMemsetAsync(tmp.d_stats, 0, 8 * sizeof(unsigned long long), s);
+    for (int f0 = 0; f0 < n_freq && e == cudaSuccess; f0 += 16) {
+        p.f_off = f0;
+        p.nf = std::min(16, n_freq - f0);
+        for (int f = 0; f < p.nf; ++f) p.nu[f] = freqs_hz[f0 + f];
+        e = cudaMemsetAsync(tmp.d_counters, 0, 8 * sizeof(unsigned long long), s);  // ray counter starts at zero
+        if (e == cudaSuccess) e = launch_fp64(&tmp, p, s);
+    }
+    if (e == cudaSuccess) {
+        const long long len = (long long)p.n_rows * p.nx;
+        const int chunks = (int)std::min<long long>(kNoAllocChunks, std::max<long long>(1, len / 4096));
+        k_reduce_partial<<<dim3(chunks, n_freq), kRedThreads, 0, s>>>(image_dev, len, chunks, partial);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && flux_dev) {
+            k_reduce_final<<<n_freq, kRedThreads, 0, s>>>(partial, chunks, flux_dev);
+            e = cudaGetLastError();
+        }
+    }
+    tmp.d_counters = nullptr;
+    tmp.d_stats = nullptr;
+    return e == cudaSuccess ? RAPTOR_OK : RAPTOR_ECUDA;
 }
 
 raptor_status raptor_profile(raptor_ctx* ctx, int enable) {
