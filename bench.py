@@ -174,6 +174,7 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
     ctx = R.Context(R.camera_desc(**cam, precision=prec))
     ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
     image = torch.empty((len(freqs), cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
+    tuned = None if args.no_autotune else ctx.autotune(freqs, stream=stream)
     for _ in range(args.warmup):
         ctx.render(freqs, image=image, flux=False, stream=stream)
     torch.cuda.synchronize()
@@ -201,7 +202,8 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
         dev_ms = float(t.item())
     _, flux = ctx.render(freqs, image=image, stream=stream)
     torch.cuda.synchronize()
-    return dict(ctx=ctx, image=image, ms=dev_ms / args.steps, wall=wall, clocks=clocks, prof=prof, stats=st, flux=flux)
+    return dict(ctx=ctx, image=image, ms=dev_ms / args.steps, wall=wall, clocks=clocks, prof=prof, stats=st, flux=flux,
+                tuned=tuned)
 
 
 def scenes_mod():
@@ -325,6 +327,7 @@ def run_native(args):
         "roofline": roof, "rooflines": roofs, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": main["clocks"], "wall_s_timed_region": main["wall"],
         "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64},
+        "launch": main["tuned"],
     }
     for pth, r in res.items():
         if pth == paths[0]:
@@ -368,6 +371,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--size", type=int, default=1024, help="image side (profiling runs use a smaller case)")
     ap.add_argument("--paths", default="mixed,fp64", help="comma list of paths to time: mixed, fp64")
     args = ap.parse_args()

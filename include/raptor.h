@@ -183,8 +183,17 @@ raptor_status raptor_stats(raptor_ctx* ctx, unsigned long long* rays, unsigned l
 raptor_status raptor_stats_reset(raptor_ctx* ctx);
 
 /* Launch shape of the persistent kernels (used by the autotuner): threads per block in
- * {32, 64, 96, 128} and resident blocks per SM (0 = the occupancy maximum). */
-raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm);
+ * {32, 64, 96, 128}, resident blocks per SM of the FP64 and FP32 ray kernels, and of the
+ * mixed path's FP64 passes (0 = the occupancy maximum). */
+raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm, int blocks_per_sm_fp64);
+
+/* Autotuner: renders the context's camera once per candidate launch shape (threads per
+ * block {64, 128}; blocks per SM of the ray kernels {max, 2, 3, 4}; for RAPTOR_MIXED also
+ * blocks per SM of the FP64 passes {1, 2, 3, 4}), times each with CUDA events on `stream`
+ * (best of two), keeps the fastest on the context and returns it (outputs may be NULL).
+ * Uses a context-owned image buffer; synchronises `stream`. */
+raptor_status raptor_autotune(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, int* best_block,
+                              int* best_bps, int* best_bps64, double* best_ms, void* stream);
 
 /* Per-kernel device time, measured with CUDA events recorded around every kernel launch on
  * the launch's own stream.  raptor_profile(ctx, 1) clears the accumulators and starts

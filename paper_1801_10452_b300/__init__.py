@@ -27,7 +27,7 @@ EXPORTS = [
     "raptor_camera_set", "raptor_load_plasma", "raptor_render", "raptor_render_ex", "raptor_render_host",
     "raptor_lightcurve", "raptor_trace_ray", "raptor_stats", "raptor_stats_reset", "raptor_set_launch",
     "raptor_last_error", "raptor_destroy", "raptor_profile", "raptor_profile_read", "raptor_measure_fma_peak",
-    "raptor_render_noalloc",
+    "raptor_render_noalloc", "raptor_autotune",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak"]
 
@@ -87,12 +87,13 @@ def lib():
             "raptor_trace_ray": (st, [vp, C.c_double, C.c_double, C.c_double, dp, C.c_int, C.c_int, dp, ip, ip, dp, vp]),
             "raptor_stats": (st, [vp, u64p, u64p, u64p, u64p, u64p, u64p]),
             "raptor_stats_reset": (st, [vp]),
-            "raptor_set_launch": (st, [vp, C.c_int, C.c_int]),
+            "raptor_set_launch": (st, [vp, C.c_int, C.c_int, C.c_int]),
             "raptor_last_error": (C.c_char_p, [vp]),
             "raptor_destroy": (None, [vp]),
             "raptor_profile": (st, [vp, C.c_int]),
             "raptor_profile_read": (st, [vp, dp, C.POINTER(C.c_longlong)]),
             "raptor_measure_fma_peak": (st, [C.c_int, dp]),
+            "raptor_autotune": (st, [vp, dp, C.c_int, C.c_double, ip, ip, ip, dp, vp]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -250,8 +251,18 @@ class Context:
     def stats_reset(self):
         self._check(lib().raptor_stats_reset(self._h), "raptor_stats_reset")
 
-    def set_launch(self, threads_per_block, blocks_per_sm):
-        self._check(lib().raptor_set_launch(self._h, int(threads_per_block), int(blocks_per_sm)), "raptor_set_launch")
+    def set_launch(self, threads_per_block, blocks_per_sm, blocks_per_sm_fp64=2):
+        self._check(lib().raptor_set_launch(self._h, int(threads_per_block), int(blocks_per_sm), int(blocks_per_sm_fp64)),
+                    "raptor_set_launch")
+
+    def autotune(self, freqs, t_obs=0.0, stream=None):
+        """Choose the fastest launch shape for this camera; returns it with its time."""
+        nu = _freqs(freqs)
+        tb, bps, b64 = C.c_int(0), C.c_int(0), C.c_int(0)
+        ms = C.c_double(0.0)
+        self._check(lib().raptor_autotune(self._h, _dp(nu), nu.size, float(t_obs), C.byref(tb), C.byref(bps), C.byref(b64),
+                                          C.byref(ms), _stream(stream)), "raptor_autotune")
+        return dict(threads_per_block=tb.value, blocks_per_sm=bps.value, blocks_per_sm_fp64=b64.value, ms=ms.value)
 
     def profile(self, enable=True):
         self._check(lib().raptor_profile(self._h, 1 if enable else 0), "raptor_profile")

@@ -65,6 +65,8 @@ struct Real<Cnt> {
 namespace raptor {
 template <>
 struct NewtonTol<Cnt> { static constexpr double v = 1e-14; };
+template <>
+Cnt pv<Cnt>(double d, float) { return Cnt(d); }
 }  // namespace raptor
 
 using namespace raptor;

@@ -48,6 +48,7 @@ struct raptor_ctx {
     cudaStream_t last_stream = nullptr;
     int launch_block = 128;       // threads per block of the persistent kernels
     int launch_bps = 0;           // blocks per SM (0 = occupancy maximum)
+    int launch_bps64 = 2;         // blocks per SM of the mixed path's FP64 passes
     // per-kernel CUDA-event timing (raptor_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -171,6 +172,20 @@ double r_isco_prograde(double a) {
     return 3.0 + z2 - sg * std::sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
 }
 
+// FP32 copies of the scalar parameters (frequencies are copied when they are set).
+void fill_float_params(Params& p) {
+    ParamsF& f = p.f;
+    f.a = (float)p.a; f.eps = (float)p.eps; f.r_stop = (float)p.r_stop; f.r_esc = (float)p.r_esc;
+    f.Lcm = (float)p.Lcm; f.tau_cut = (float)p.tau_cut;
+    f.n0 = (float)p.n0; f.n_pow = (float)p.n_pow; f.the0 = (float)p.the0; f.the_pow = (float)p.the_pow;
+    f.B0 = (float)p.B0; f.B_pow = (float)p.B_pow; f.r_isco = (float)p.r_isco;
+    f.x1_min = (float)p.x1_min; f.x1_max = (float)p.x1_max; f.dx1 = (float)p.dx1; f.dx2 = (float)p.dx2;
+    f.h_mks = (float)p.h_mks; f.t0 = (float)p.t0; f.dt_snap = (float)p.dt_snap; f.rho0_ne = (float)p.rho0_ne;
+    f.B_unit = (float)p.B_unit; f.r_high = (float)p.r_high; f.r_low = (float)p.r_low; f.gam = (float)p.gam;
+    f.r_fp64 = (float)p.r_fp64; f.turn_kr = (float)p.turn_kr;
+    for (int i = 0; i < 16; ++i) f.nu[i] = (float)p.nu[i];
+}
+
 // Host-side parameter block shared by every launch of a context.
 Params base_params(const raptor_ctx* c) {
     Params p;
@@ -227,6 +242,7 @@ Params base_params(const raptor_ctx* c) {
         p.r_low = q.r_low;
         p.gam = q.gamma_ad;
     }
+    fill_float_params(p);
     return p;
 }
 
@@ -255,18 +271,20 @@ cudaError_t launch_fp64(raptor_ctx* c, const Params& p, cudaStream_t s) {
     return launch_fp64_nf<16>(c, p, s);
 }
 
-// Mixed precision: phase A (FP32, camera rays) -> phase B (FP64 queue) -> phase C (FP32
-// queue), ordered by the stream.
+// Mixed precision: phase A (FP32, camera rays) -> phase B (FP64 queue, in passes of growing
+// step budget) -> phase C (FP32 queue), ordered by the stream.
+constexpr int kPassBudget[kMaxPasses] = {16, 32, 48, 64, 96, 128, 256, 1 << 30};
+
 template <int NF>
 cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 8, s);
+    cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s);
     if (e != cudaSuccess) return e;
     int occ32 = 0, occ64 = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_mixed_fp32<NF>, c->launch_block, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_mixed_fp64<NF>, c->launch_block, 0);
     if (e != cudaSuccess) return e;
     const int b32 = grid_blocks(c, std::max(occ32, 1));
-    const int b64 = grid_blocks(c, std::max(occ64, 1));
+    const int b64 = c->num_sms * std::max(1, c->launch_bps64 > 0 ? std::min(c->launch_bps64, occ64) : occ64);
     const long long need = (p.n_rays + c->launch_block - 1) / c->launch_block;
     {
         ProfScope ps(c, kProfMixedA, s);
@@ -275,12 +293,13 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    {
+    for (int pass = 0; pass < kMaxPasses; ++pass) {
         ProfScope ps(c, kProfMixedB, s);
-        k_mixed_fp64<NF><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats);
+        k_mixed_fp64<NF><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats, pass,
+                                                                        kPassBudget[pass]);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     {
         ProfScope ps(c, kProfMixedC, s);
         k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats, 1);
@@ -308,8 +327,9 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
         p.f_off = f0;
         p.nf = std::min(16, n_freq - f0);
         for (int f = 0; f < p.nf; ++f) p.nu[f] = freqs[f0 + f];
+        for (int f = 0; f < 16; ++f) p.f.nu[f] = (float)p.nu[f];
         if (ctx->cam.precision == RAPTOR_FP64) {
-            RCK(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * 8, s));
+            RCK(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s));
             RCK(launch_fp64(ctx, p, s));
         } else {
             const size_t need = (size_t)p.n_rays;
@@ -407,7 +427,7 @@ raptor_status raptor_camera_init(const raptor_camera_desc* desc, raptor_ctx** ou
     raptor_plasma_desc_default(&ctx->plasma);
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_counters, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_counters, kNumCounters * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_stats, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_trace_int, 2 * sizeof(int));
@@ -668,13 +688,15 @@ void raptor_destroy(raptor_ctx* ctx) {
 }
 
 // Launch-shape control used by the autotuner (threads per block, blocks per SM; 0 = max).
-raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm) {
+raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm, int blocks_per_sm_fp64) {
     if (!ctx) return RAPTOR_EINVAL;
     if (threads_per_block < 32 || threads_per_block > 128 || threads_per_block % 32)
         return fail(ctx, RAPTOR_EINVAL, "threads_per_block must be 32, 64, 96 or 128");
-    if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(ctx, RAPTOR_EINVAL, "blocks_per_sm must lie in [0, 64]");
+    if (blocks_per_sm < 0 || blocks_per_sm > 64 || blocks_per_sm_fp64 < 0 || blocks_per_sm_fp64 > 64)
+        return fail(ctx, RAPTOR_EINVAL, "blocks per SM must lie in [0, 64]");
     ctx->launch_block = threads_per_block;
     ctx->launch_bps = blocks_per_sm;
+    ctx->launch_bps64 = blocks_per_sm_fp64;
     return RAPTOR_OK;
 }
 
@@ -775,6 +797,71 @@ raptor_status raptor_render_noalloc(const raptor_camera_desc* cam, const raptor_
     tmp.d_counters = nullptr;
     tmp.d_stats = nullptr;
     return e == cudaSuccess ? RAPTOR_OK : RAPTOR_ECUDA;
+}
+
+raptor_status raptor_autotune(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, int* best_block,
+                              int* best_bps, int* best_bps64, double* best_ms, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!ctx->has_plasma) return fail(ctx, RAPTOR_ENOPLASMA, "raptor_load_plasma has not been called");
+    raptor_status st = check_freqs(ctx, freqs_hz, n_freq);
+    if (st != RAPTOR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)n_freq * ctx->cam.nx * ctx->cam.ny;
+    RCK(ensure(&ctx->d_img, &ctx->img_cap, n));
+    const bool mixed = ctx->cam.precision == RAPTOR_MIXED;
+    const int blocks[2] = {64, 128};
+    const int bpss[4] = {0, 2, 3, 4};
+    const int bps64s[4] = {1, 2, 3, 4};
+    const int n64 = mixed ? 4 : 1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    RCK(cudaEventCreate(&a));
+    RCK(cudaEventCreate(&b));
+    double best = 1e300;
+    int bb = ctx->launch_block, bp = ctx->launch_bps, b64 = ctx->launch_bps64;
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    for (int tb : blocks) {
+        for (int bps : bpss) {
+            if (tb == 64 && bps > 0) continue;  // 64-thread blocks only at occupancy maximum
+            for (int k = 0; k < n64; ++k) {
+                ctx->launch_block = tb;
+                ctx->launch_bps = tb == 64 ? 2 * bps : bps;
+                ctx->launch_bps64 = mixed ? (tb == 64 ? 2 * bps64s[k] : bps64s[k]) : ctx->launch_bps64;
+                float t_best = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    cudaEventRecord(a, s);
+                    st = raptor_render(ctx, freqs_hz, n_freq, t_obs, ctx->d_img, nullptr, stream);
+                    cudaEventRecord(b, s);
+                    if (st != RAPTOR_OK) break;
+                    if (cudaEventSynchronize(b) != cudaSuccess) { st = RAPTOR_ECUDA; break; }
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, a, b);
+                    t_best = std::min(t_best, t);
+                }
+                if (st != RAPTOR_OK) break;
+                if (t_best < best) {
+                    best = t_best;
+                    bb = ctx->launch_block;
+                    bp = ctx->launch_bps;
+                    b64 = ctx->launch_bps64;
+                }
+            }
+            if (st != RAPTOR_OK) break;
+        }
+        if (st != RAPTOR_OK) break;
+    }
+    ctx->prof = prof;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->launch_block = bb;
+    ctx->launch_bps = bp;
+    ctx->launch_bps64 = b64;
+    if (st != RAPTOR_OK) return st;
+    if (best_block) *best_block = bb;
+    if (best_bps) *best_bps = bp;
+    if (best_bps64) *best_bps64 = b64;
+    if (best_ms) *best_ms = best;
+    return RAPTOR_OK;
 }
 
 raptor_status raptor_profile(raptor_ctx* ctx, int enable) {

@@ -81,11 +81,11 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
                                            T& B, T u[4], T b[4]) {
     const T r = P.r;
     const T x1 = Real<T>::log_(r);
-    if (x1 < T(p.x1_min) || x1 > T(p.x1_max)) return 0;
-    const T h = T(p.h_mks);
+    if (x1 < RAPTOR_P(T, x1_min) || x1 > RAPTOR_P(T, x1_max)) return 0;
+    const T h = RAPTOR_P(T, h_mks);
     const T x2 = newton_x2<T>(x[2], h);
-    T fi = (x1 - T(p.x1_min)) / T(p.dx1) - T(0.5);
-    T fj = x2 / T(p.dx2) - T(0.5);
+    T fi = (x1 - RAPTOR_P(T, x1_min)) / RAPTOR_P(T, dx1) - T(0.5);
+    T fj = x2 / RAPTOR_P(T, dx2) - T(0.5);
     int i0 = (int)floor(fi), j0 = (int)floor(fj);
     T wi = fi - T(i0), wj = fj - T(j0);
     if (i0 < 0) { i0 = 0; wi = T(0); }
@@ -94,7 +94,7 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     if (j0 > p.n2 - 2) { j0 = p.n2 - 2; wj = T(1); }
     T q[8];
     if (p.slow && p.n_snap > 1) {
-        T fs = (x[0] - T(p.t0)) / T(p.dt_snap);
+        T fs = (x[0] - RAPTOR_P(T, t0)) / RAPTOR_P(T, dt_snap);
         fs = fmin(fmax(fs, T(0)), T(p.n_snap - 1));
         int s0 = (int)floor(fs);
         if (s0 > p.n_snap - 2) s0 = p.n_snap - 2;
@@ -138,15 +138,15 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     ks_lower(P, bk, bc);
     const T bsq = bc[0] * bk[0] + bc[1] * bk[1] + bc[2] * bk[2] + bc[3] * bk[3];
     if (!(bsq > T(0))) return 0;
-    const T gm1 = T(p.gam) - T(1);
-    ne = rho * T(p.rho0_ne);
-    B = Real<T>::sqrt_(bsq) * T(p.B_unit);
+    const T gm1 = RAPTOR_P(T, gam) - T(1);
+    ne = rho * RAPTOR_P(T, rho0_ne);
+    B = Real<T>::sqrt_(bsq) * RAPTOR_P(T, B_unit);
     const T betap = gm1 * uu / (T(0.5) * bsq);
     const T b2p = betap * betap;
-    const T R = T(p.r_low) / (T(1) + b2p) + T(p.r_high) * b2p / (T(1) + b2p);
+    const T R = RAPTOR_P(T, r_low) / (T(1) + b2p) + RAPTOR_P(T, r_high) * b2p / (T(1) + b2p);
     the = T(kMp / kMe) * gm1 * (uu / rho) / (T(1) + R);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = bk[i] * T(p.B_unit);
+    for (int i = 0; i < 4; ++i) b[i] = bk[i] * RAPTOR_P(T, B_unit);
     return 1;
 }
 
@@ -156,16 +156,16 @@ template <typename T>
 RAPTOR_HD int plasma_sample(const Params& p, const T x[4], const T k[4], int snap, T& ne, T& the,
                                              T& B, T& g, T& sinb) {
     KSPoint<T> P;
-    ks_point(T(p.a), x[1], x[2], P);
+    ks_point(RAPTOR_P(T, a), x[1], x[2], P);
     T u[4], kc[4];
     T kb;  // k . b_hat
     if (p.kind == 0) {
-        const int ok = analytic_velocity(T(p.a), T(p.r_isco), P, u);
+        const int ok = analytic_velocity(RAPTOR_P(T, a), RAPTOR_P(T, r_isco), P, u);
         if (ok < 0) return -1;
         const T r = x[1];
-        ne = T(p.n0) * Real<T>::pow_(r, T(p.n_pow));
-        the = T(p.the0) * Real<T>::pow_(r, T(p.the_pow));
-        B = T(p.B0) * Real<T>::pow_(r, T(p.B_pow));
+        ne = RAPTOR_P(T, n0) * Real<T>::pow_(r, RAPTOR_P(T, n_pow));
+        the = RAPTOR_P(T, the0) * Real<T>::pow_(r, RAPTOR_P(T, the_pow));
+        B = RAPTOR_P(T, B0) * Real<T>::pow_(r, RAPTOR_P(T, B_pow));
         ks_lower(P, k, kc);
         g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
         const T u_phi = P.gtp * u[0] + P.grp * u[1] + P.gpp * u[3];

@@ -28,13 +28,14 @@ struct RayQueue {
 };
 
 struct MixedQueues {
-    RayQueue q64, q32;
+    RayQueue q64, q64b, q32;  // q64 / q64b alternate as input and re-queue target of the FP64 passes
     size_t cap = 0;
     int nf_cap = 0;
 };
 
-// Counter slots in the context's device counter array.
-enum : int { kCntFreshA = 0, kCntPush64 = 1, kCntFetch64 = 2, kCntPush32 = 3, kCntFetch32 = 4 };
+// Counter slots in the context's device counter array (kNumCounters entries).
+enum : int { kCntFreshA = 0, kCntPush64 = 1, kCntPush32 = 3, kCntFetch32 = 4, kCntPassFetch = 8, kCntPassOut = 16,
+             kMaxPasses = 8, kNumCounters = 32 };
 
 inline cudaError_t alloc_queue(RayQueue& q, size_t cap, int nf) {
     cudaError_t e = cudaMalloc((void**)&q.xk, sizeof(double) * 8 * cap);
@@ -56,14 +57,17 @@ inline void free_queue(RayQueue& q) {
 
 inline cudaError_t alloc_mixed_queues(MixedQueues& m, size_t cap, int nf) {
     m.q64 = RayQueue{nullptr, nullptr, nullptr, nullptr, nullptr};
+    m.q64b = m.q64;
     m.q32 = m.q64;
     cudaError_t e = alloc_queue(m.q64, cap, nf);
+    if (e == cudaSuccess) e = alloc_queue(m.q64b, cap, nf);
     if (e == cudaSuccess) e = alloc_queue(m.q32, cap, nf);
     if (e == cudaSuccess) {
         m.cap = cap;
         m.nf_cap = nf;
     } else {
         free_queue(m.q64);
+        free_queue(m.q64b);
         free_queue(m.q32);
     }
     return e;
@@ -72,6 +76,7 @@ inline cudaError_t alloc_mixed_queues(MixedQueues& m, size_t cap, int nf) {
 inline void free_mixed_queues(MixedQueues& m) {
     if (m.cap == 0 && !m.q64.xk) return;
     free_queue(m.q64);
+    free_queue(m.q64b);
     free_queue(m.q32);
     m.cap = 0;
     m.nf_cap = 0;
@@ -93,7 +98,7 @@ __device__ __forceinline__ long long warp_push_slot(unsigned long long* count, b
 
 template <typename T>
 __device__ __forceinline__ bool in_fp64_region(const Params& p, const T x[4], const T k[4]) {
-    return x[1] < T(p.r_fp64) || fabs(k[1]) < T(p.turn_kr) * fabs(k[0]);
+    return x[1] < RAPTOR_P(T, r_fp64) || fabs(k[1]) < RAPTOR_P(T, turn_kr) * fabs(k[0]);
 }
 
 template <int NF>
@@ -120,7 +125,7 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
     float ne, the, B, g, sinb;
     const int ok = plasma_sample<float>(p, x, k, snap, ne, the, B, g, sinb);
     if (ok <= 0) return ok;
-    const float dlcm = dl * float(p.Lcm);
+    const float dlcm = dl * p.f.Lcm;
     const float gdl_unscaled = g * dlcm * float(kIUnscale);
     const float ig2 = 1.f / (g * g);
     const bool k2x = (p.flags & kFlagK2Exact) != 0;
@@ -128,7 +133,7 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
     for (int f = 0; f < NF; ++f) {
         if (f < p.nf) {
             float j, S;
-            synchrotron<float>(g * float(p.nu[f]), ne, the, B, sinb, k2x, j, S, kIScale);
+            synchrotron<float>(g * p.f.nu[f], ne, the, B, sinb, k2x, j, S, kIScale);
             if (j > 0.f && S > 0.f) {
                 const float dtau = j / S * gdl_unscaled;
                 const float F = dtau > 1e-4f ? -expm1f(-dtau) / dtau : 1.f - 0.5f * dtau;
@@ -144,11 +149,23 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
 
 template <int NF, typename TT>
 __device__ __forceinline__ int thick_or_capped(const Params& p, const TT* tau, const double* tau_hi, int n) {
-    double tmin = double(tau[0]) + tau_hi[0];
+    bool hi = false;
 #pragma unroll
-    for (int f = 1; f < NF; ++f)
-        if (f < p.nf) tmin = fmin(tmin, double(tau[f]) + tau_hi[f]);
-    if (tmin > p.tau_cut) return kThick;
+    for (int f = 0; f < NF; ++f)
+        if (f < p.nf) hi = hi || (tau_hi[f] > 0.0);
+    if (!hi) {
+        float tmin = float(tau[0]);
+#pragma unroll
+        for (int f = 1; f < NF; ++f)
+            if (f < p.nf) tmin = fminf(tmin, float(tau[f]));
+        if (tmin > p.f.tau_cut) return kThick;
+    } else {
+        double tmin = double(tau[0]) + tau_hi[0];
+#pragma unroll
+        for (int f = 1; f < NF; ++f)
+            if (f < p.nf) tmin = fmin(tmin, double(tau[f]) + tau_hi[f]);
+        if (tmin > p.tau_cut) return kThick;
+    }
     if (n >= p.max_steps) return kTruncated;
     return -1;
 }
@@ -156,15 +173,15 @@ __device__ __forceinline__ int thick_or_capped(const Params& p, const TT* tau, c
 // One FP32 step (same scheme as step_fp64).  Returns termination code or -1.
 template <int NF>
 __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
-    const float dl = step_size<float>(float(p.eps), (p.flags & kFlagLinearR) != 0, R.x, R.k);
-    rk4_step<float>(float(p.a), R.x, R.k, dl);
+    const float dl = step_size<float>(p.f.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
+    rk4_step<float>(p.f.a, R.x, R.k, dl);
     R.n += 1;
     bool fin = true;
 #pragma unroll
     for (int i = 0; i < 4; ++i) fin = fin && isfinite(R.x[i]) && isfinite(R.k[i]);
     if (!fin) return kError;
-    if (R.x[1] < float(p.r_stop)) return kCaptured;
-    if (R.x[1] > float(p.r_esc)) return kEscaped;
+    if (R.x[1] < p.f.r_stop) return kCaptured;
+    if (R.x[1] > p.f.r_esc) return kEscaped;
     if (rt_sample_fp32<NF, float, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
     return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
 }
@@ -301,20 +318,25 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
     if (c_re) atomicAdd(&stats[kStatReentry], c_re);
 }
 
-// Phase B: rays from the FP64 queue; FP64 geodesic steps, FP32 transfer samples.
+// Phase B, pass `pass`: rays from the FP64 queue; FP64 geodesic steps, FP32 transfer
+// samples.  A ray runs at most `budget` steps in this pass; if it is still in the FP64
+// region then, it is re-queued for the next pass.  Every pass therefore starts with full
+// warps, and the ragged end of a pass lasts at most `budget` steps, instead of one long
+// tail in which a few long inner-region rays occupy otherwise empty warps.
 template <int NF>
 __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues mq, unsigned long long* cnt,
-                                                    unsigned long long* stats) {
+                                                    unsigned long long* stats, int pass, int budget) {
     RayM<NF> R;
     long long id = -1;
     int frame = 0, pix = 0, n_in = 0;
     bool drained = false;
-    const long long n_total = (long long)cnt[kCntPush64];
+    const long long n_total = (long long)(pass == 0 ? cnt[kCntPush64] : cnt[kCntPassOut + pass - 1]);
     unsigned long long c_rays = 0, c_steps = 0, c_64 = 0, c_trunc = 0, c_err = 0;
-    const RayQueue& q = mq.q64;
+    const RayQueue& q = (pass & 1) ? mq.q64b : mq.q64;
+    const RayQueue& qr = (pass & 1) ? mq.q64 : mq.q64b;
     const size_t cap = mq.cap;
     for (;;) {
-        const long long nid = warp_fetch(&cnt[kCntFetch64], n_total, id < 0, drained);
+        const long long nid = warp_fetch(&cnt[kCntPassFetch + pass], n_total, id < 0, drained);
         if (id < 0 && nid >= 0) {
             id = q.id[nid];
             frame = (int)(id / p.n_pix);
@@ -337,17 +359,21 @@ __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues 
         }
         if (!__any_sync(0xffffffffu, id >= 0)) break;
         int st = -1;
-        bool push = false;
+        bool push = false, requeue = false;
         if (id >= 0) {
             st = step_mixed64<NF>(p, R);
-            if (st < 0 && !in_fp64_region<double>(p, R.x, R.k)) push = true;
+            if (st < 0) {
+                if (!in_fp64_region<double>(p, R.x, R.k)) push = true;
+                else if (R.n - n_in >= budget) requeue = true;
+            }
         }
         const long long slot = warp_push_slot(&cnt[kCntPush32], push);
-        if (push) {
+        const long long rslot = warp_push_slot(&cnt[kCntPassOut + pass], requeue);
+        if (push || requeue) {
             double tau[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + R.tau_hi[f];
-            store_ray<NF>(mq.q32, cap, slot, id, R.x, R.k, R.I, tau, R.n, p.nf);
+            store_ray<NF>(push ? mq.q32 : qr, cap, push ? slot : rslot, id, R.x, R.k, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
         } else if (id >= 0 && st >= 0) {

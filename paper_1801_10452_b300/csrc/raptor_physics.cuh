@@ -5,6 +5,16 @@
 
 namespace raptor {
 
+// FP32 copies of the scalar parameters, converted once on the host so that the FP32 code
+// paths run no double -> float conversion (B300 executes FP64 conversions slowly).
+struct ParamsF {
+    float a, eps, r_stop, r_esc, Lcm, tau_cut;
+    float n0, n_pow, the0, the_pow, B0, B_pow, r_isco;
+    float x1_min, x1_max, dx1, dx2, h_mks, t0, dt_snap, rho0_ne, B_unit, r_high, r_low, gam;
+    float r_fp64, turn_kr;
+    float nu[16];
+};
+
 // Kernel parameters (passed by value; lives in the constant bank).
 struct Params {
     // spacetime / camera
@@ -46,7 +56,17 @@ struct Params {
     int nf_total, f_off;     // frequency chunking: this launch covers [f_off, f_off + nf)
     int* steps_out;          // optional [n_rows][nx]
     int* status_out;         // optional [n_rows][nx]
+    ParamsF f;               // FP32 copies (filled by the host)
 };
+
+// Parameter in the arithmetic type T: the double field for FP64, its FP32 copy for FP32.
+template <typename T>
+RAPTOR_HD T pv(double d, float f);
+template <>
+RAPTOR_HD double pv<double>(double d, float) { return d; }
+template <>
+RAPTOR_HD float pv<float>(double, float f) { return f; }
+#define RAPTOR_P(T, name) pv<T>(p.name, p.f.name)
 
 // ------------------------------------------------------------------------------------
 // Camera (sec. 2.3, Eqs. 24-28; App. A.1).  Always FP64.

@@ -91,3 +91,25 @@ def test_mixed_all_fp32_and_all_fp64_limits(R, ora):
     # the first step from the camera is FP32, every later one FP64
     assert s["fp64_steps"] == s["steps"] - s["rays"]
     assert abs(fl64[0] / oimg.sum() - 1) < 1e-6
+
+
+def test_results_independent_of_launch_shape(R):
+    """The autotuner may pick any launch shape: every ray's arithmetic and the flux
+    reduction are independent of it, so images and fluxes are bit-identical."""
+    import torch
+
+    for prec in (R.FP64, R.MIXED):
+        cam = dict(scenes.SMALL, nx=40, ny=36, precision=prec)
+        ctx = R.Context(R.camera_desc(**cam))
+        ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+        ref, fref = ctx.render(scenes.SPECTRAL_FREQS[:3])
+        ref = ref.cpu().numpy()
+        for tb, bps, b64 in [(64, 0, 1), (128, 2, 4), (96, 3, 2)]:
+            ctx.set_launch(tb, bps, b64)
+            img, fl = ctx.render(scenes.SPECTRAL_FREQS[:3])
+            assert np.array_equal(img.cpu().numpy(), ref) and np.array_equal(fl, fref)
+        best = ctx.autotune(scenes.SPECTRAL_FREQS[:3])
+        assert best["threads_per_block"] in (64, 128) and best["ms"] > 0
+        img, fl = ctx.render(scenes.SPECTRAL_FREQS[:3])
+        torch.cuda.synchronize()
+        assert np.array_equal(img.cpu().numpy(), ref)
