@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "kerr_analytic_1024x1024_a0.9375_i60_230GHz"
-METRIC = "rays/s and geodesic steps/s at 1024^2 Kerr image, mixed vs FP64 at <=1e-3 flux"
+METRIC = "rays/s and geodesic steps/s at 1024^2 Kerr image, mixed+MLP vs FP64 at <=1e-3 flux"
 CPU_SAMPLE_STRIDE = 8  # oracle traces every 8th pixel in each direction (128 x 128 rays)
 
 
@@ -169,10 +169,37 @@ def _time_render(ctx, torch, freqs, image, flush_buf, n, stream):
     return tot
 
 
-def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks):
+def train_surrogate(R, torch, cam, steps, n_train):
+    """Train the learned far-field surrogate on integrator-generated rays (not timed as part
+    of a render step); returns its parameters and a summary."""
+    ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED_MLP))
+    ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, y = ctx.surrogate_generate(n_train, seed=0x1801104520000005)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    ctx.surrogate_init(y, seed=7)
+    t1 = time.perf_counter()
+    ctx.surrogate_train(x, y, steps, lr=2e-3, lr_final=2e-5, seed=11)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    xh, yh = ctx.surrogate_generate(50_000, seed=0x1801104520000006)
+    err = np.abs(ctx.surrogate_eval(xh).cpu().numpy() - yh.cpu().numpy())
+    names = ["dt", "ln_r", "theta", "phi", "k_theta", "k_r"]
+    summ = {"rays": n_train, "steps": steps, "batch": 4096, "generate_s": t_gen, "train_s": t_train,
+            "heldout_median_abs_err": dict(zip(names, np.median(err, 0).tolist())),
+            "heldout_p99_abs_err": dict(zip(names, np.percentile(err, 99, axis=0).tolist())),
+            "range": "alpha, beta in +-20 M; a in [0, 0.99]; i in [5, 85] deg"}
+    return ctx.surrogate_get(), summ
+
+
+def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks, params=None):
     """Warm up, then time args.steps renders of one path; returns measurements."""
     ctx = R.Context(R.camera_desc(**cam, precision=prec))
     ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
+    if params is not None:
+        ctx.surrogate_set(params)
     image = torch.empty((len(freqs), cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
     tuned = None if args.no_autotune else ctx.autotune(freqs, stream=stream)
     for _ in range(args.warmup):
@@ -235,11 +262,14 @@ def run_native(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     rays_step = npix * len(freqs)
 
+    params, sur = None, None
+    if "mlp" in paths:
+        params, sur = train_surrogate(R, torch, cam, args.train_steps, args.train_rays)
     res = {}
     for pth in paths:
-        prec = R.MIXED if pth == "mixed" else R.FP64
+        prec = {"mlp": R.MIXED_MLP, "mixed": R.MIXED, "fp64": R.FP64}[pth]
         res[pth] = _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist,
-                               sample_clocks=(rank == 0 and pth == paths[0]))
+                               sample_clocks=(rank == 0 and pth == paths[0]), params=params if pth == "mlp" else None)
     main = res[paths[0]]
     ms_step = main["ms"]
     value = world * rays_step / (ms_step * 1e-3)
@@ -268,6 +298,7 @@ def run_native(args):
         return
 
     # ---- rooflines: algorithmic flops (from the kernel source) / measured FMA peaks -------
+    peaks = _peaks()
     fma32 = R.measure_fma_peak(False)
     fma64 = R.measure_fma_peak(True)
     flops = _flops_per_step()
@@ -276,6 +307,16 @@ def run_native(args):
         prof, s = r["prof"], r["stats"]
         for kname, (kms, kn) in prof.items():
             if kn == 0 or kname in ("reduce", "trace", "load", "peak"):
+                continue
+            if kname == "surrogate":
+                # network inference: 2 x (4*256 + 2*256^2 + 256*8) flops per ray on the BF16 path
+                fl_launch = 2.0 * (4 * 256 + 2 * 256 * 256 + 256 * 8) * npix / kn
+                per_ms = kms / kn
+                ach = fl_launch / (per_ms * 1e-3) / 1e12
+                pkb = peaks.get("bf16_tflops", 1800.0)
+                roofs[pth + ":" + kname] = {"bound": "tensor", "achieved": ach, "peak": pkb, "unit": "TFLOP/s",
+                                            "frac": ach / pkb, "kernel_ms_per_launch": per_ms,
+                                            "note": "whole surrogate stage (inputs, fused MLP, state rebuild) timed as one"}
                 continue
             if kname == "render_fp64":
                 steps_k, pk, pipe = s["steps"], fma64, "fp64"
@@ -286,12 +327,12 @@ def run_native(args):
             fl_launch = flops["fp64_step"] * steps_k / kn
             per_ms = kms / kn
             ach = fl_launch / (per_ms * 1e-3) / 1e12
-            roofs[kname] = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+            roofs[pth + ":" + kname] = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                             "frac": ach / pk, "kernel_ms_per_launch": per_ms, "steps_per_launch": steps_k / kn,
                             "share_of_step": kms / max(1e-9, sum(v[0] for k2, v in prof.items() if k2 not in ("peak",)))}
-    dom_prof = {k: v for k, v in main["prof"].items() if v[1] and k in roofs}
+    dom_prof = {k: v for k, v in main["prof"].items() if v[1] and (paths[0] + ":" + k) in roofs}
     dom = max(dom_prof, key=lambda k: dom_prof[k][0])
-    roof = dict(roofs[dom])
+    roof = dict(roofs[paths[0] + ":" + dom])
     roof.update({"kernel": dom, "traffic": None, "peak_source": f"FMA-chain microbenchmark ({roof['pipe']}), measured in this run",
                  "flops_per_step": flops["fp64_step"], "flops_note": "algorithmic, counted from the kernel source, FMA = 2"})
 
@@ -317,7 +358,7 @@ def run_native(args):
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if paths[0] == "mixed" else "f64",
+        "vs_baseline": None, "dtype": {"mlp": "f32+f64+bf16", "mixed": "f32+f64", "fp64": "f64"}[paths[0]],
         "data": "synthetic (analytic plasma, deterministic)",
         "config": {"workload": workload, "pixels": npix, "freqs_hz": freqs, "precision": paths[0],
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed render"},
@@ -328,6 +369,7 @@ def run_native(args):
         "gpu_launches": launches, "clocks": main["clocks"], "wall_s_timed_region": main["wall"],
         "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64},
         "launch": main["tuned"],
+        "surrogate": sur,
     }
     for pth, r in res.items():
         if pth == paths[0]:
@@ -335,8 +377,10 @@ def run_native(args):
         line[f"{pth}_path"] = {"value": world * rays_step / (r["ms"] * 1e-3), "unit": "rays/s", "ms_per_step": r["ms"],
                                "geodesic_steps_per_s": world * (r["stats"]["steps"] / args.steps) / (r["ms"] * 1e-3)}
         line[f"speedup_vs_{pth}"] = r["ms"] / ms_step
-        line["flux_jy"] = {paths[0]: float(main["flux"][0]), pth: float(r["flux"][0]),
-                           "rel_diff": float(abs(main["flux"][0] / r["flux"][0] - 1))}
+    line["flux_jy"] = {pth: float(r["flux"][0]) for pth, r in res.items()}
+    if "fp64" in res:
+        line["flux_rel_err_vs_fp64"] = {pth: float(abs(r["flux"][0] / res["fp64"]["flux"][0] - 1))
+                                        for pth, r in res.items() if pth != "fp64"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -373,7 +417,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--size", type=int, default=1024, help="image side (profiling runs use a smaller case)")
-    ap.add_argument("--paths", default="mixed,fp64", help="comma list of paths to time: mixed, fp64")
+    ap.add_argument("--paths", default="mlp,mixed,fp64", help="comma list of paths to time (first = value): mlp, mixed, fp64")
+    ap.add_argument("--train-steps", type=int, default=16000)
+    ap.add_argument("--train-rays", type=int, default=1_000_000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

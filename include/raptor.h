@@ -47,13 +47,20 @@ typedef enum {
     RAPTOR_EUNSUPPORTED = 6  /* option recognised but not available in this build         */
 } raptor_status;
 
+/* Returned by the learned-surrogate calls (RAPTOR_MIXED_MLP) before a surrogate exists. */
+#define RAPTOR_ENOSURROGATE RAPTOR_EUNSUPPORTED
+
 /* Arithmetic of the integration.
  *   RAPTOR_FP64:  every step in FP64.
  *   RAPTOR_MIXED: geodesic steps and transfer in FP32 where r >= r_fp64 and away from radial
  *                 turning points; FP64 inside r < r_fp64, where |k^r| < turn_kr |k^t|, and
  *                 for the optical depth once tau > 10.  Rays are moved between FP32 and
  *                 FP64 work queues so each warp runs one precision.
- *   RAPTOR_MIXED_MLP: reserved for the learned surrogate (RAPTOR_EUNSUPPORTED here). */
+ *   RAPTOR_MIXED_MLP: RAPTOR_MIXED, with every ray outside the critical curve and a band
+ *                 around it started from the learned surrogate's prediction of the state
+ *                 after 60 steps (see raptor_surrogate_*), and rays leaving r > r_exit on
+ *                 the way out stopped (transfer beyond r_exit neglected).  Needs a trained
+ *                 or loaded surrogate (else RAPTOR_EUNSUPPORTED). */
 typedef enum { RAPTOR_FP64 = 0, RAPTOR_MIXED = 1, RAPTOR_MIXED_MLP = 2 } raptor_precision;
 
 typedef enum {
@@ -195,12 +202,68 @@ raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int bloc
 raptor_status raptor_autotune(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, int* best_block,
                               int* best_bps, int* best_bps64, double* best_ms, void* stream);
 
+/* ---- Learned surrogate (the benchmark spec's learned part; the paper has none) -------------------
+ * A 4-layer, 256-wide MLP maps (alpha, beta, a, i) to the FP64 integrator's state after 60
+ * adaptive RK4 steps from the camera (t - t_cam, ln r, theta, phi and the signs of k^theta,
+ * k^r; the wave vector is rebuilt from E, L, Q).  Training data come from the integrator
+ * itself; forward and backward run in the library's kernels (hidden layers on BF16 tensor
+ * cores with FP32 accumulation), optimiser Adam.  The surrogate lives in the context. */
+
+/* Number of FP32 parameters (weights, biases and the input/output normalisation). */
+int raptor_surrogate_param_count(void);
+
+/* Training set: n samples with alpha, beta uniform over the context's image plane, spin
+ * uniform in [spin_min, spin_max], inclination uniform in [incl_min, incl_max] degrees
+ * (counter-based generator seeded by `seed`).  inputs_dev: device float [n][4] = (alpha,
+ * beta, a, i_deg).  states_dev (optional, device double [n][6]) receives the integrator's
+ * state after 60 steps (FP64, same arithmetic as the FP64 path) as (t - t_cam, ln r, theta,
+ * phi, k^theta, k^r); targets_dev (device double [n][6]) the same state minus a fixed
+ * flat-space baseline (straight line advanced by the same step rule), which the network
+ * learns. */
+raptor_status raptor_surrogate_generate(raptor_ctx* ctx, long long n, unsigned long long seed, double spin_min,
+                                        double spin_max, double incl_min_deg, double incl_max_deg, float* inputs_dev,
+                                        double* targets_dev, double* states_dev, void* stream);
+
+/* Initialise the network (seeded uniform weights) and its output normalisation from the
+ * first min(n, 65536) targets; resets the optimiser.  Synchronises `stream`. */
+raptor_status raptor_surrogate_init(raptor_ctx* ctx, const double* targets_dev, long long n, unsigned long long seed,
+                                    void* stream);
+
+/* `steps` Adam steps on batches of 4096 samples drawn (with replacement, counter-based,
+ * `seed`) from the n samples; learning rate cosine-decayed from lr to lr_final.
+ * loss_host (optional, [steps]) receives each batch's mean squared error (normalised
+ * outputs); when given, every step synchronises `stream`. */
+raptor_status raptor_surrogate_train(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                     int steps, double lr, double lr_final, unsigned long long seed, double* loss_host,
+                                     void* stream);
+
+/* Loss and parameter gradient of one batch of n samples (n a multiple of 128, <= 4096) at
+ * the current parameters, without an update: grad_host receives the gradient of every
+ * weight and bias (raptor_surrogate_param_count() - 24 floats), loss_host the loss. */
+raptor_status raptor_surrogate_grad(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                    float* grad_host, double* loss_host, void* stream);
+
+/* Predictions for n inputs (device float [n][4]) into pred_dev (device double [n][6], same
+ * units as the targets).  Synchronises `stream`. */
+raptor_status raptor_surrogate_eval(raptor_ctx* ctx, const float* inputs_dev, long long n, double* pred_dev, void* stream);
+
+/* Copy the parameters out / in (host float [raptor_surrogate_param_count()]); `set` makes the
+ * context's surrogate ready without training. */
+raptor_status raptor_surrogate_get(raptor_ctx* ctx, float* params_host, int n);
+raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, int n);
+
+/* Fallback: rays whose pixel centre lies inside the critical curve (Bardeen's closed form)
+ * or within fallback_band M of it start at the camera (exact integration) [0.5]; r_exit:
+ * outbound rays stop at r > r_exit in RAPTOR_MIXED_MLP (0 = off) [50]. */
+raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit);
+
 /* Per-kernel device time, measured with CUDA events recorded around every kernel launch on
  * the launch's own stream.  raptor_profile(ctx, 1) clears the accumulators and starts
  * recording; raptor_profile(ctx, 0) stops.  raptor_profile_read waits for the recorded
- * events and returns, per kernel slot RAPTOR_KERNEL_* (8 slots), the summed milliseconds
- * (ms[8], may be NULL) and the number of launches since the last clear (launches[8], may
- * be NULL; counted whether or not recording is on). */
+ * events and returns, per kernel slot RAPTOR_KERNEL_* (10 slots), the summed milliseconds
+ * (ms[10], may be NULL) and the number of launches since the last clear (launches[10],
+ * may be NULL; counted whether or not recording is on).  A slot covers all the kernels of
+ * one stage (e.g. the surrogate slot times its inference as one interval). */
 #define RAPTOR_KERNEL_RENDER_FP64 0  /* persistent FP64 ray kernel                         */
 #define RAPTOR_KERNEL_MIXED_A 1      /* mixed: FP32 phase on camera rays                   */
 #define RAPTOR_KERNEL_MIXED_B 2      /* mixed: FP64 phase (inner region, turning points)   */
@@ -208,6 +271,9 @@ raptor_status raptor_autotune(raptor_ctx* ctx, const double* freqs_hz, int n_fre
 #define RAPTOR_KERNEL_REDUCE 4       /* flux reduction (two launches per render)          */
 #define RAPTOR_KERNEL_TRACE 5        /* single-ray trace                                   */
 #define RAPTOR_KERNEL_LOAD 6         /* grid interleave at load time                       */
+#define RAPTOR_KERNEL_PEAK 7         /* unused by the renders                              */
+#define RAPTOR_KERNEL_SURROGATE 8    /* surrogate inference and start states of a render   */
+#define RAPTOR_KERNEL_TRAIN 9        /* surrogate data generation and training             */
 raptor_status raptor_profile(raptor_ctx* ctx, int enable);
 raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches);
 

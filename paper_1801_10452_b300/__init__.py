@@ -27,9 +27,12 @@ EXPORTS = [
     "raptor_camera_set", "raptor_load_plasma", "raptor_render", "raptor_render_ex", "raptor_render_host",
     "raptor_lightcurve", "raptor_trace_ray", "raptor_stats", "raptor_stats_reset", "raptor_set_launch",
     "raptor_last_error", "raptor_destroy", "raptor_profile", "raptor_profile_read", "raptor_measure_fma_peak",
-    "raptor_render_noalloc", "raptor_autotune",
+    "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
+    "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
+    "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config",
 ]
-KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak"]
+KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
+                "surrogate", "train"]
 
 
 class RaptorError(RuntimeError):
@@ -94,6 +97,16 @@ def lib():
             "raptor_profile_read": (st, [vp, dp, C.POINTER(C.c_longlong)]),
             "raptor_measure_fma_peak": (st, [C.c_int, dp]),
             "raptor_autotune": (st, [vp, dp, C.c_int, C.c_double, ip, ip, ip, dp, vp]),
+            "raptor_surrogate_param_count": (C.c_int, []),
+            "raptor_surrogate_generate": (st, [vp, C.c_longlong, C.c_ulonglong, C.c_double, C.c_double, C.c_double,
+                                               C.c_double, vp, vp, vp, vp]),
+            "raptor_surrogate_init": (st, [vp, vp, C.c_longlong, C.c_ulonglong, vp]),
+            "raptor_surrogate_train": (st, [vp, vp, vp, C.c_longlong, C.c_int, C.c_double, C.c_double, C.c_ulonglong, dp, vp]),
+            "raptor_surrogate_grad": (st, [vp, vp, vp, C.c_longlong, C.POINTER(C.c_float), dp, vp]),
+            "raptor_surrogate_eval": (st, [vp, vp, C.c_longlong, vp, vp]),
+            "raptor_surrogate_get": (st, [vp, C.POINTER(C.c_float), C.c_int]),
+            "raptor_surrogate_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
+            "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -269,10 +282,67 @@ class Context:
 
     def profile_read(self):
         """{kernel name: (ms, launches)} since the last profile(True)."""
-        ms = np.zeros(8)
-        n = (C.c_longlong * 8)()
+        ms = np.zeros(10)
+        n = (C.c_longlong * 10)()
         self._check(lib().raptor_profile_read(self._h, _dp(ms), n), "raptor_profile_read")
-        return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(8)}
+        return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(10)}
+
+    # ---- learned surrogate -------------------------------------------------------------
+    def surrogate_generate(self, n, seed=0x1801104520000005, spin=(0.0, 0.99), incl=(5.0, 85.0), states=False,
+                           stream=None):
+        """Integrator-generated training set: (inputs float32 [n][4], targets float64 [n][6]
+        [, raw states float64 [n][6]])."""
+        import torch
+
+        x = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        y = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+        z = torch.empty((n, 6), dtype=torch.float64, device="cuda") if states else None
+        self._check(lib().raptor_surrogate_generate(self._h, int(n), int(seed), float(spin[0]), float(spin[1]), float(incl[0]),
+                                                    float(incl[1]), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                    C.c_void_p(z.data_ptr()) if states else None, _stream(stream)),
+                    "raptor_surrogate_generate")
+        return (x, y, z) if states else (x, y)
+
+    def surrogate_init(self, targets, seed=7, stream=None):
+        self._check(lib().raptor_surrogate_init(self._h, C.c_void_p(targets.data_ptr()), int(targets.shape[0]), int(seed),
+                                                _stream(stream)), "raptor_surrogate_init")
+
+    def surrogate_train(self, inputs, targets, steps, lr=2e-3, lr_final=2e-5, seed=11, record_loss=False, stream=None):
+        loss = np.zeros(steps) if record_loss else None
+        self._check(lib().raptor_surrogate_train(self._h, C.c_void_p(inputs.data_ptr()), C.c_void_p(targets.data_ptr()),
+                                                 int(inputs.shape[0]), int(steps), float(lr), float(lr_final), int(seed),
+                                                 _dp(loss) if record_loss else None, _stream(stream)), "raptor_surrogate_train")
+        return loss
+
+    def surrogate_grad(self, inputs, targets, stream=None):
+        n = lib().raptor_surrogate_param_count() - 24
+        g = np.zeros(n, dtype=np.float32)
+        L = C.c_double(0.0)
+        self._check(lib().raptor_surrogate_grad(self._h, C.c_void_p(inputs.data_ptr()), C.c_void_p(targets.data_ptr()),
+                                                int(inputs.shape[0]), g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(L),
+                                                _stream(stream)), "raptor_surrogate_grad")
+        return g, L.value
+
+    def surrogate_eval(self, inputs, stream=None):
+        import torch
+
+        pred = torch.empty((inputs.shape[0], 6), dtype=torch.float64, device="cuda")
+        self._check(lib().raptor_surrogate_eval(self._h, C.c_void_p(inputs.data_ptr()), int(inputs.shape[0]),
+                                                C.c_void_p(pred.data_ptr()), _stream(stream)), "raptor_surrogate_eval")
+        return pred
+
+    def surrogate_get(self):
+        n = lib().raptor_surrogate_param_count()
+        P = np.zeros(n, dtype=np.float32)
+        self._check(lib().raptor_surrogate_get(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), n), "raptor_surrogate_get")
+        return P
+
+    def surrogate_set(self, P):
+        P = np.ascontiguousarray(P, dtype=np.float32)
+        self._check(lib().raptor_surrogate_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size), "raptor_surrogate_set")
+
+    def surrogate_config(self, fallback_band=0.5, r_exit=50.0):
+        self._check(lib().raptor_surrogate_config(self._h, float(fallback_band), float(r_exit)), "raptor_surrogate_config")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -17,6 +17,7 @@
 #include "../../include/raptor.h"
 #include "raptor_kernels_fp64.cuh"
 #include "raptor_kernels_mixed.cuh"
+#include "raptor_surrogate.cuh"
 
 using namespace raptor;
 
@@ -49,6 +50,26 @@ struct raptor_ctx {
     int launch_block = 128;       // threads per block of the persistent kernels
     int launch_bps = 0;           // blocks per SM (0 = occupancy maximum)
     int launch_bps64 = 2;         // blocks per SM of the mixed path's FP64 passes
+    // learned surrogate
+    bool sur_ready = false;
+    float* s_P = nullptr;            // parameters (MlpLayout::SIZE)
+    float* s_G = nullptr;            // gradients
+    float* s_m1 = nullptr;           // Adam moments
+    float* s_m2 = nullptr;
+    __nv_bfloat16* s_w = nullptr;    // w2, w2t, w3, w3t (4 x 256 x 256)
+    long long s_rows = 0;            // work-buffer rows
+    float *s_x = nullptr, *s_z1 = nullptr, *s_z2 = nullptr, *s_z3 = nullptr, *s_out = nullptr, *s_dout = nullptr;
+    float *s_dzf = nullptr, *s_dh = nullptr;
+    __nv_bfloat16 *s_h1 = nullptr, *s_h2 = nullptr, *s_h3 = nullptr, *s_dzb = nullptr;
+    double* s_y = nullptr;
+    double* s_loss = nullptr;        // per-block loss partials
+    float* s_in = nullptr;           // render: network inputs [rays][4]
+    unsigned char* s_fb = nullptr;   // render: fallback flags
+    double* s_start = nullptr;       // render: start states [8][rays]
+    size_t s_ray_cap = 0;
+    double2* s_curve = nullptr;      // critical curve points
+    double s_band = 0.5, s_r_exit = 50.0;
+    unsigned long long s_step = 0;   // Adam step counter
     // per-kernel CUDA-event timing (raptor_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -315,12 +336,16 @@ cudaError_t launch_mixed(raptor_ctx* c, const Params& p, cudaStream_t s) {
     return launch_mixed_nf<16>(c, p, s);
 }
 
+raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t s);
+
 // Enqueue every ray of `p` (all frequency chunks), then the flux reduction of `planes`
 // image planes into c->d_flux.
 raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_freq, long long planes_per_frame,
                        int n_frames, cudaStream_t s) {
-    if (ctx->cam.precision == RAPTOR_MIXED_MLP)
-        return fail(ctx, RAPTOR_EUNSUPPORTED, "RAPTOR_MIXED_MLP is not available in this build");
+    if (ctx->cam.precision == RAPTOR_MIXED_MLP) {
+        const raptor_status st = prepare_surrogate_render(ctx, p, s);
+        if (st != RAPTOR_OK) return st;
+    }
     p.nf_total = n_freq;
     p.i_unscale = ctx->cam.precision == RAPTOR_FP64 ? 1.0 : kIUnscale;
     for (int f0 = 0; f0 < n_freq; f0 += 16) {
@@ -679,6 +704,10 @@ void raptor_destroy(raptor_ctx* ctx) {
     cudaFree(ctx->d_trace_I);
     cudaFree(ctx->d_rec);
     free_mixed_queues(ctx->mq);
+    void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
+                  ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
+                  ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->s_curve};
+    for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.second.first);
         cudaEventDestroy(e.second.second);
@@ -688,6 +717,408 @@ void raptor_destroy(raptor_ctx* ctx) {
 }
 
 // Launch-shape control used by the autotuner (threads per block, blocks per SM; 0 = max).
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Learned surrogate (host orchestration of raptor_surrogate.cuh)
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr long long kSurRows = 4096;  // rows per training batch / inference chunk (multiple of 128)
+
+uint64_t splitmix(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+cudaError_t sur_alloc(raptor_ctx* c) {
+    cudaError_t e = cudaSuccess;
+    if (!c->s_P) {
+        const size_t n = MlpLayout::SIZE;
+        e = cudaMalloc((void**)&c->s_P, n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_G, n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_m1, n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_m2, n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_w, 4 * kHid * kHid * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMemset(c->s_G, 0, n * sizeof(float));
+        if (e != cudaSuccess) return e;
+    }
+    if (c->s_rows < kSurRows) {
+        const long long R = kSurRows;
+        float** f32[] = {&c->s_z1, &c->s_z2, &c->s_z3, &c->s_dzf, &c->s_dh};
+        for (float** q : f32) {
+            if (e == cudaSuccess) e = cudaMalloc((void**)q, R * kHid * sizeof(float));
+        }
+        __nv_bfloat16** b16[] = {&c->s_h1, &c->s_h2, &c->s_h3, &c->s_dzb};
+        for (__nv_bfloat16** q : b16) {
+            if (e == cudaSuccess) e = cudaMalloc((void**)q, R * kHid * sizeof(__nv_bfloat16));
+        }
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_x, R * kIn * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_out, R * kOut * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_dout, R * kOut * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_y, R * kOutUsed * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_loss, 1024 * sizeof(double));
+        if (e == cudaSuccess) c->s_rows = R;
+    }
+    return e;
+}
+
+int ew_blocks(long long n) { return (int)std::min<long long>(8192, std::max<long long>(1, (n + 255) / 256)); }
+
+__nv_bfloat16* w2b(raptor_ctx* c) { return c->s_w; }
+__nv_bfloat16* w2t(raptor_ctx* c) { return c->s_w + kHid * kHid; }
+__nv_bfloat16* w3b(raptor_ctx* c) { return c->s_w + 2 * kHid * kHid; }
+__nv_bfloat16* w3t(raptor_ctx* c) { return c->s_w + 3 * kHid * kHid; }
+
+// Forward pass on `rows` rows already in c->s_x (rows_valid of them real).
+cudaError_t sur_forward(raptor_ctx* c, long long rows, long long rows_valid, cudaStream_t s) {
+    k_mlp_layer1<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_P, c->s_x, rows, rows_valid, c->s_z1, c->s_h1);
+    dim3 g(kHid / kGBN, (unsigned)(rows / kGBM));
+    k_gemm_bf16<true, true><<<g, 256, 0, s>>>(c->s_h1, kHid, w2b(c), kHid, c->s_z2, kHid, rows, kHid, kHid);
+    k_bias_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_z2, c->s_P + MlpLayout::B2, rows, c->s_h2);
+    k_gemm_bf16<true, true><<<g, 256, 0, s>>>(c->s_h2, kHid, w3b(c), kHid, c->s_z3, kHid, rows, kHid, kHid);
+    k_bias_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_z3, c->s_P + MlpLayout::B3, rows, c->s_h3);
+    k_mlp_layer4<<<ew_blocks(rows * 32), 256, 0, s>>>(c->s_P, c->s_h3, rows, c->s_out);
+    return cudaGetLastError();
+}
+
+// Loss and gradient of the batch in (s_x, s_y) into s_G; loss partials in s_loss[0..nb).
+cudaError_t sur_backward(raptor_ctx* c, long long rows, int* nb_out, cudaStream_t s) {
+    const int nb = 64;
+    *nb_out = nb;
+    float* G = c->s_G;
+    k_mse_grad<<<nb, 256, 0, s>>>(c->s_P, c->s_out, c->s_y, rows, c->s_dout, c->s_loss);
+    k_colred<float, __nv_bfloat16><<<kOut * kHid, 256, 0, s>>>(c->s_dout, kOut, c->s_h3, kHid, rows, kOut, kHid,
+                                                                 G + MlpLayout::W4);
+    k_colred<float, float><<<kOut, 256, 0, s>>>(nullptr, 0, c->s_dout, kOut, rows, 1, kOut, G + MlpLayout::B4);
+    k_back_layer4<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_P, c->s_dout, c->s_z3, rows, c->s_dzf, c->s_dzb);
+    // layer 3: dW3 = dz3^T h2, db3, dh2 = dz3 W3
+    dim3 gw(kHid / kGBN, kHid / kGBM), ga(kHid / kGBN, (unsigned)(rows / kGBM));
+    k_gemm_bf16<false, false><<<gw, 256, 0, s>>>(c->s_dzb, kHid, c->s_h2, kHid, G + MlpLayout::W3, kHid, kHid, kHid, rows);
+    k_colred<float, float><<<kHid, 256, 0, s>>>(nullptr, 0, c->s_dzf, kHid, rows, 1, kHid, G + MlpLayout::B3);
+    k_gemm_bf16<true, true><<<ga, 256, 0, s>>>(c->s_dzb, kHid, w3t(c), kHid, c->s_dh, kHid, rows, kHid, kHid);
+    k_back_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_dh, c->s_z2, rows * kHid, c->s_dzf, c->s_dzb);
+    // layer 2
+    k_gemm_bf16<false, false><<<gw, 256, 0, s>>>(c->s_dzb, kHid, c->s_h1, kHid, G + MlpLayout::W2, kHid, kHid, kHid, rows);
+    k_colred<float, float><<<kHid, 256, 0, s>>>(nullptr, 0, c->s_dzf, kHid, rows, 1, kHid, G + MlpLayout::B2);
+    k_gemm_bf16<true, true><<<ga, 256, 0, s>>>(c->s_dzb, kHid, w2t(c), kHid, c->s_dh, kHid, rows, kHid, kHid);
+    k_back_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_dh, c->s_z1, rows * kHid, c->s_dzf, nullptr);
+    // layer 1
+    k_grad_w1<<<kHid * kIn, 256, 0, s>>>(c->s_P, c->s_dzf, c->s_x, rows, G);
+    k_colred<float, float><<<kHid, 256, 0, s>>>(nullptr, 0, c->s_dzf, kHid, rows, 1, kHid, G + MlpLayout::B1);
+    return cudaGetLastError();
+}
+
+// Evaluate n rows of raw inputs into normalised outputs out_dev [n][kOut] (fused kernel).
+cudaError_t sur_eval_rows(raptor_ctx* c, const float* inputs, long long n, float* out_dev, cudaStream_t s) {
+    const long long blocks = (n + kFRows - 1) / kFRows;
+    k_mlp_fused<<<(unsigned)blocks, 256, 0, s>>>(c->s_P, w2b(c), w3b(c), inputs, n, out_dev);
+    return cudaGetLastError();
+}
+
+// Critical curve on the image plane (Bardeen 1973): photon-orbit radius r gives
+// xi = L/E, eta = Q/E^2; alpha = -xi / sin i, beta = +-sqrt(eta + a^2 cos^2 i - xi^2 cot^2 i).
+std::vector<double> critical_curve(double a, double incl, int n) {
+    std::vector<double> pts;
+    const double ci = std::cos(incl), si = std::sin(incl);
+    if (std::fabs(a) < 1e-6) {
+        const double b = 3.0 * std::sqrt(3.0);
+        for (int k = 0; k < n; ++k) {
+            const double t = 2.0 * kPi * k / n;
+            pts.push_back(b * std::cos(t));
+            pts.push_back(b * std::sin(t));
+        }
+        return pts;
+    }
+    const double aa = std::fabs(a);
+    const double rp = 2.0 * (1.0 + std::cos(2.0 / 3.0 * std::acos(-aa))), rm = 2.0 * (1.0 + std::cos(2.0 / 3.0 * std::acos(aa)));
+    const int half = n / 2;
+    const int fine = 16 * half;
+    std::vector<double> all;
+    for (int k = 0; k < fine; ++k) {
+        const double r = rp + (rm - rp) * k / (fine - 1.0);
+        const double xi = -(r * r * r - 3.0 * r * r + a * a * r + a * a) / (a * (r - 1.0));
+        const double eta = r * r * r * (4.0 * a * a - r * (r - 3.0) * (r - 3.0)) / (a * a * (r - 1.0) * (r - 1.0));
+        const double b2 = eta + a * a * ci * ci - xi * xi * ci * ci / (si * si);
+        if (b2 >= 0.0) {
+            all.push_back(-xi / si);
+            all.push_back(std::sqrt(b2));
+        }
+    }
+    // keep `half` evenly spaced points of the visible arc (beta >= 0), mirror to beta < 0
+    const size_t na = all.size() / 2;
+    std::vector<double> up;
+    for (int q = 0; q < half && na > 0; ++q) {
+        const size_t k = na == 1 ? 0 : (size_t)((double)q * (na - 1) / (half - 1));
+        up.push_back(all[2 * k]);
+        up.push_back(all[2 * k + 1]);
+    }
+    const size_t m = up.size() / 2;
+    // closed polygon: upper arc forwards, lower arc backwards
+    for (size_t q = 0; q < m; ++q) { pts.push_back(up[2 * q]); pts.push_back(up[2 * q + 1]); }
+    for (size_t q = m; q-- > 0;) { pts.push_back(up[2 * q]); pts.push_back(-up[2 * q + 1]); }
+    return pts;
+}
+
+}  // namespace
+
+extern "C" {
+
+int raptor_surrogate_param_count(void) { return MlpLayout::SIZE; }
+
+raptor_status raptor_surrogate_generate(raptor_ctx* ctx, long long n, unsigned long long seed, double spin_min,
+                                        double spin_max, double incl_min_deg, double incl_max_deg, float* inputs_dev,
+                                        double* targets_dev, double* states_dev, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (n < 1 || !inputs_dev || !targets_dev) return fail(ctx, RAPTOR_EINVAL, "need n >= 1 and output buffers");
+    if (!(spin_min >= 0.0 && spin_max >= spin_min && spin_max < 1.0)) return fail(ctx, RAPTOR_EINVAL, "spin range invalid");
+    if (!(incl_min_deg > 0.0 && incl_max_deg >= incl_min_deg && incl_max_deg < 180.0))
+        return fail(ctx, RAPTOR_EINVAL, "inclination range invalid");
+    SurrogateRange R{ctx->cam.alpha_min, ctx->cam.alpha_max, ctx->cam.beta_min, ctx->cam.beta_max, spin_min, spin_max,
+                     incl_min_deg, incl_max_deg, ctx->cam.r_cam, ctx->cam.eps};
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    {
+        ProfScope ps(ctx, kProfTrain, s);
+        k_surrogate_data<<<ctx->num_sms * 8, 128, 0, s>>>(R, seed, n, inputs_dev, targets_dev, states_dev);
+    }
+    RCK(cudaGetLastError());
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_init(raptor_ctx* ctx, const double* targets_dev, long long n, unsigned long long seed,
+                                    void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!targets_dev || n < 2) return fail(ctx, RAPTOR_EINVAL, "need targets and n >= 2");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(sur_alloc(ctx));
+    const long long m = std::min<long long>(n, 65536);
+    std::vector<double> y((size_t)m * kOutUsed);
+    RCK(cudaMemcpyAsync(y.data(), targets_dev, y.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    std::vector<float> P(MlpLayout::SIZE, 0.f);
+    uint64_t st = seed ^ 0x5EEDull;
+    auto uni = [&](double lim) { return (float)(lim * (2.0 * ((splitmix(st) >> 11) * (1.0 / 9007199254740992.0)) - 1.0)); };
+    for (int i = 0; i < kHid * kIn; ++i) P[MlpLayout::W1 + i] = uni(std::sqrt(6.0 / kIn));
+    for (int i = 0; i < kHid * kHid; ++i) P[MlpLayout::W2 + i] = uni(std::sqrt(6.0 / kHid));
+    for (int i = 0; i < kHid * kHid; ++i) P[MlpLayout::W3 + i] = uni(std::sqrt(6.0 / kHid));
+    for (int i = 0; i < kOut * kHid; ++i) P[MlpLayout::W4 + i] = uni(std::sqrt(3.0 / kHid));
+    // input normalisation (scale, shift): alpha, beta over the camera; a in [0, 1]; i in degrees
+    const double ha = 0.5 * (ctx->cam.alpha_max - ctx->cam.alpha_min), hb = 0.5 * (ctx->cam.beta_max - ctx->cam.beta_min);
+    const float scale[4] = {(float)(1.0 / ha), (float)(1.0 / hb), 2.0f, 1.0f / 40.0f};
+    const float shift[4] = {(float)(0.5 * (ctx->cam.alpha_max + ctx->cam.alpha_min)),
+                            (float)(0.5 * (ctx->cam.beta_max + ctx->cam.beta_min)), 0.5f, 45.0f};
+    for (int c = 0; c < 4; ++c) {
+        P[MlpLayout::NORM + c] = scale[c];
+        P[MlpLayout::NORM + 4 + c] = shift[c];
+    }
+    for (int q = 0; q < kOut; ++q) {
+        double mu = 0.0, var = 0.0;
+        if (q < kOutUsed) {
+            for (long long i = 0; i < m; ++i) mu += y[i * kOutUsed + q];
+            mu /= m;
+            for (long long i = 0; i < m; ++i) var += (y[i * kOutUsed + q] - mu) * (y[i * kOutUsed + q] - mu);
+            var /= (m - 1);
+        }
+        P[MlpLayout::NORM + 8 + q] = (float)mu;
+        P[MlpLayout::NORM + 16 + q] = (float)std::max(std::sqrt(var), 1e-6);
+    }
+    RCK(cudaMemcpyAsync(ctx->s_P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    RCK(cudaMemsetAsync(ctx->s_m1, 0, MlpLayout::SIZE * sizeof(float), s));
+    RCK(cudaMemsetAsync(ctx->s_m2, 0, MlpLayout::SIZE * sizeof(float), s));
+    k_refresh_bf16<<<256, 256, 0, s>>>(ctx->s_P, w2b(ctx), w2t(ctx), w3b(ctx), w3t(ctx));
+    RCK(cudaGetLastError());
+    RCK(cudaStreamSynchronize(s));
+    ctx->s_step = 0;
+    ctx->sur_ready = true;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_train(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                     int steps, double lr, double lr_final, unsigned long long seed, double* loss_host,
+                                     void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!ctx->sur_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "surrogate not initialised");
+    if (!inputs_dev || !targets_dev || n < 1 || steps < 1 || !(lr > 0.0) || !(lr_final > 0.0))
+        return fail(ctx, RAPTOR_EINVAL, "invalid training arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(sur_alloc(ctx));
+    const float b1 = 0.9f, b2 = 0.999f;
+    ProfScope ps(ctx, kProfTrain, s);
+    for (int it = 0; it < steps; ++it) {
+        k_gather_batch<<<ew_blocks(kSurRows), 256, 0, s>>>(inputs_dev, targets_dev, n, kSurRows, seed, (long long)ctx->s_step,
+                                                          ctx->s_x, ctx->s_y);
+        RCK(sur_forward(ctx, kSurRows, kSurRows, s));
+        int nb = 0;
+        RCK(sur_backward(ctx, kSurRows, &nb, s));
+        ctx->s_step += 1;
+        // cosine decay from lr to lr_final; Adam bias corrections folded into the step size
+        const double frac = steps > 1 ? (double)it / (steps - 1) : 1.0;
+        const double lr_it = lr_final + 0.5 * (lr - lr_final) * (1.0 + std::cos(kPi * frac));
+        const double t = (double)ctx->s_step;
+        const float lr_t = (float)(lr_it * std::sqrt(1.0 - std::pow(b2, t)) / (1.0 - std::pow(b1, t)));
+        k_adam<<<ew_blocks(MlpLayout::NORM), 256, 0, s>>>(ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, MlpLayout::NORM, lr_t, b1,
+                                                         b2, 1e-8f);
+        k_refresh_bf16<<<256, 256, 0, s>>>(ctx->s_P, w2b(ctx), w2t(ctx), w3b(ctx), w3t(ctx));
+        RCK(cudaGetLastError());
+        if (loss_host) {
+            double parts[64];
+            RCK(cudaMemcpyAsync(parts, ctx->s_loss, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+            RCK(cudaStreamSynchronize(s));
+            double L = 0.0;
+            for (int q = 0; q < nb; ++q) L += parts[q];
+            loss_host[it] = L / (double)(kSurRows * kOutUsed);
+        }
+    }
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_grad(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                    float* grad_host, double* loss_host, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!ctx->sur_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "surrogate not initialised");
+    if (!inputs_dev || !targets_dev || n < 1 || n > kSurRows || n % kGBM != 0)
+        return fail(ctx, RAPTOR_EINVAL, "n must be a multiple of 128 and at most 4096");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(cudaMemcpyAsync(ctx->s_x, inputs_dev, n * kIn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    RCK(cudaMemcpyAsync(ctx->s_y, targets_dev, n * kOutUsed * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RCK(sur_forward(ctx, n, n, s));
+    int nb = 0;
+    RCK(sur_backward(ctx, n, &nb, s));
+    if (grad_host) RCK(cudaMemcpyAsync(grad_host, ctx->s_G, MlpLayout::NORM * sizeof(float), cudaMemcpyDeviceToHost, s));
+    double parts[64];
+    RCK(cudaMemcpyAsync(parts, ctx->s_loss, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    if (loss_host) {
+        double L = 0.0;
+        for (int q = 0; q < nb; ++q) L += parts[q];
+        *loss_host = L / (double)(n * kOutUsed);
+    }
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_eval(raptor_ctx* ctx, const float* inputs_dev, long long n, double* pred_dev, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!ctx->sur_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "surrogate not initialised");
+    if (!inputs_dev || !pred_dev || n < 1) return fail(ctx, RAPTOR_EINVAL, "invalid arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    float* out = nullptr;
+    RCK(cudaMallocAsync((void**)&out, n * kOut * sizeof(float), s));
+    cudaError_t e = sur_eval_rows(ctx, inputs_dev, n, out, s);
+    std::vector<float> Pn(24);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Pn.data(), ctx->s_P + MlpLayout::NORM, 24 * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    std::vector<float> o;
+    if (e == cudaSuccess) {
+        o.resize((size_t)n * kOut);
+        e = cudaMemcpyAsync(o.data(), out, o.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFreeAsync(out, s);
+    if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, cudaGetErrorString(e));
+    std::vector<double> pr((size_t)n * kOutUsed);
+    for (long long i = 0; i < n; ++i)
+        for (int q = 0; q < kOutUsed; ++q)
+            pr[i * kOutUsed + q] = (double)o[i * kOut + q] * (double)Pn[16 + q] + (double)Pn[8 + q];
+    RCK(cudaMemcpyAsync(pred_dev, pr.data(), pr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    RCK(cudaStreamSynchronize(s));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_get(raptor_ctx* ctx, float* params_host, int n) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!ctx->sur_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "surrogate not initialised");
+    if (!params_host || n != MlpLayout::SIZE) return fail(ctx, RAPTOR_EINVAL, "n must equal raptor_surrogate_param_count()");
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemcpy(params_host, ctx->s_P, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, int n) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!params_host || n != MlpLayout::SIZE) return fail(ctx, RAPTOR_EINVAL, "n must equal raptor_surrogate_param_count()");
+    RCK(sur_alloc(ctx));
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemcpy(ctx->s_P, params_host, n * sizeof(float), cudaMemcpyHostToDevice));
+    RCK(cudaMemset(ctx->s_m1, 0, n * sizeof(float)));
+    RCK(cudaMemset(ctx->s_m2, 0, n * sizeof(float)));
+    k_refresh_bf16<<<256, 256>>>(ctx->s_P, w2b(ctx), w2t(ctx), w3b(ctx), w3t(ctx));
+    RCK(cudaGetLastError());
+    RCK(cudaDeviceSynchronize());
+    ctx->sur_ready = true;
+    ctx->s_step = 0;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!(fallback_band >= 0.0) || !std::isfinite(fallback_band) || !(r_exit >= 0.0) || !std::isfinite(r_exit))
+        return fail(ctx, RAPTOR_EINVAL, "fallback_band and r_exit must be finite and >= 0");
+    ctx->s_band = fallback_band;
+    ctx->s_r_exit = r_exit;
+    return RAPTOR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// RAPTOR_MIXED_MLP: predicted start states for every non-fallback ray, then the mixed path.
+raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t s) {
+    if (!ctx->sur_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "RAPTOR_MIXED_MLP needs a trained or loaded surrogate");
+    RCK(sur_alloc(ctx));
+    const size_t rays = (size_t)p.n_rays;
+    if (ctx->s_ray_cap < rays) {
+        cudaFree(ctx->s_in);
+        cudaFree(ctx->s_fb);
+        cudaFree(ctx->s_start);
+        ctx->s_in = nullptr;
+        ctx->s_fb = nullptr;
+        ctx->s_start = nullptr;
+        ctx->s_ray_cap = 0;
+        RCK(cudaMalloc((void**)&ctx->s_in, rays * kIn * sizeof(float)));
+        RCK(cudaMalloc((void**)&ctx->s_fb, rays));
+        RCK(cudaMalloc((void**)&ctx->s_start, rays * 8 * sizeof(double)));
+        ctx->s_ray_cap = rays;
+    }
+    const int n_curve = 512;
+    if (!ctx->s_curve) RCK(cudaMalloc((void**)&ctx->s_curve, n_curve * sizeof(double2)));
+    std::vector<double> cc = critical_curve(p.a, p.incl, n_curve);
+    const int nc = (int)(cc.size() / 2);
+    RCK(cudaMemcpyAsync(ctx->s_curve, cc.data(), cc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    float* out = nullptr;
+    RCK(cudaMallocAsync((void**)&out, rays * kOut * sizeof(float), s));
+    {
+        ProfScope ps(ctx, kProfSurrogate, s);
+        k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_curve, nc, ctx->s_band, ctx->s_in, ctx->s_fb);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = sur_eval_rows(ctx, ctx->s_in, (long long)rays, out, s);
+        if (e == cudaSuccess) {
+            k_surrogate_states<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_P, out, ctx->s_start);
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(out, s);
+        if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, std::string("surrogate: ") + cudaGetErrorString(e));
+    }
+    p.start_xk = ctx->s_start;
+    p.fallback = ctx->s_fb;
+    p.start_n = kSurrogateSteps;
+    p.r_exit = ctx->s_r_exit;
+    p.r_exit_f = (float)ctx->s_r_exit;
+    return RAPTOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm, int blocks_per_sm_fp64) {
     if (!ctx) return RAPTOR_EINVAL;
     if (threads_per_block < 32 || threads_per_block > 128 || threads_per_block % 32)

@@ -16,6 +16,7 @@
 #pragma once
 
 #include "raptor_kernels_fp64.cuh"
+#include "raptor_surrogate.cuh"
 
 namespace raptor {
 
@@ -182,6 +183,7 @@ __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     if (!fin) return kError;
     if (R.x[1] < p.f.r_stop) return kCaptured;
     if (R.x[1] > p.f.r_esc) return kEscaped;
+    if (p.r_exit > 0.0 && R.x[1] > p.r_exit_f && R.k[1] > 0.f) return kEscaped;  // surrogate path only
     if (rt_sample_fp32<NF, float, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
     return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
 }
@@ -249,13 +251,26 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
         if (id < 0 && nid >= 0) {
             if (!from_queue) {
                 RayD<NF> D;
-                init_ray<NF>(p, nid, D, frame, pix);
                 id = nid;
+                if (p.start_xk && !p.fallback[nid]) {
+                    // learned surrogate: start from the predicted state after start_n steps
+                    frame = (int)(nid / p.n_pix);
+                    pix = (int)(nid - (long long)frame * p.n_pix);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        D.x[i] = p.start_xk[(long long)i * p.n_rays + nid];
+                        D.k[i] = p.start_xk[(long long)(4 + i) * p.n_rays + nid];
+                    }
+                    D.n = p.start_n;
+                    D.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
+                } else {
+                    init_ray<NF>(p, nid, D, frame, pix);
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { R.x[i] = float(D.x[i]); R.k[i] = float(D.k[i]); }
 #pragma unroll
                 for (int f = 0; f < NF; ++f) { R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = 0.0; }
-                R.n = 0;
+                R.n = D.n;
                 R.snap = D.snap;
             } else {
                 const RayQueue& q = mq.q32;

@@ -57,6 +57,14 @@ struct Params {
     int* steps_out;          // optional [n_rows][nx]
     int* status_out;         // optional [n_rows][nx]
     ParamsF f;               // FP32 copies (filled by the host)
+    // learned surrogate (RAPTOR_MIXED_MLP): predicted start states [8][n_rays] (x^mu, k^mu),
+    // per-ray fallback flags (start at the camera), the step count of a predicted state,
+    // and the outbound exit radius beyond which the transfer is neglected (0 = off)
+    const double* start_xk;
+    const unsigned char* fallback;
+    int start_n;
+    double r_exit;
+    float r_exit_f;
 };
 
 // Parameter in the arithmetic type T: the double field for FP64, its FP32 copy for FP32.
@@ -74,12 +82,10 @@ RAPTOR_HD float pv<float>(double, float f) { return f; }
 // k_theta = sign(beta) sqrt|Q - L^2 cot^2 theta + a^2 cos^2 theta| = beta, k_r from k.k = 0 with
 // the physical photon moving outward at the camera; the state is the backward ray -k.
 // ------------------------------------------------------------------------------------
-RAPTOR_HD void camera_ray(const Params& p, double alpha, double beta, double t_cam,
-                                           double x[4], double k[4]) {
-    const double a = p.a, a2 = a * a;
-    const double L = -alpha * p.sin_i;
-    const double r = p.r_cam;
-    const double sn = p.sin_i, cs = p.cos_i;
+RAPTOR_HD void camera_ray_ai(double a, double sn, double cs, double incl, double r, double alpha, double beta,
+                             double t_cam, double x[4], double k[4]) {
+    const double a2 = a * a;
+    const double L = -alpha * sn;
     const double kt = -1.0, kp = L;
     // At theta = i, Q - L^2 cot^2 + a^2 cos^2 = beta^2 exactly, so the square root of Eq. 28
     // is |beta|: k_theta = beta.  (The printed form cancels two alpha^2 cos^2 i terms, whose
@@ -105,8 +111,12 @@ RAPTOR_HD void camera_ray(const Params& p, double alpha, double beta, double t_c
     const double lg = log((r - rp) / (r - rm));
     x[0] = t_cam + log(Del) + 2.0 / (rp - rm) * lg;
     x[1] = r;
-    x[2] = p.incl;
+    x[2] = incl;
     x[3] = a / (rp - rm) * lg;
+}
+
+RAPTOR_HD void camera_ray(const Params& p, double alpha, double beta, double t_cam, double x[4], double k[4]) {
+    camera_ray_ai(p.a, p.sin_i, p.cos_i, p.incl, p.r_cam, alpha, beta, t_cam, x, k);
 }
 
 // ------------------------------------------------------------------------------------

@@ -1,0 +1,146 @@
+"""Learned surrogate (RAPTOR_MIXED_MLP): integrator-generated training data against the
+FP64 oracle, the library's BF16 backward pass against the FP64 network oracle, training
+that generalises to held-out rays, render parity against the FP64 oracle, and the gain of the
+trained network over the same path without it.  Needs a GPU."""
+import time
+
+import numpy as np
+import pytest
+
+from helpers import oracle_kwargs, rel_err, ring_mask
+from oracle import mlp
+from paper_1801_10452_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+FLUX_TOL = 1e-3
+PIX_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1801_10452_b300 import build
+
+    build.build()
+    import paper_1801_10452_b300 as R
+
+    return R
+
+
+@pytest.fixture(scope="module")
+def trained(R):
+    """A network trained on the full range of the learned workload (a in [0, 0.99],
+    i in [5, 85] deg, +-20 M), shared by the render tests."""
+    import torch
+
+    ctx = R.Context(R.camera_desc(**scenes.SMALL, precision=R.MIXED_MLP))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    x, y = ctx.surrogate_generate(1_000_000, seed=5)
+    ctx.surrogate_init(y, seed=7)
+    loss = ctx.surrogate_train(x, y, 16000, lr=2e-3, lr_final=2e-5, seed=11)
+    torch.cuda.synchronize()
+    return ctx.surrogate_get()
+
+
+def test_training_data_is_the_integrator_state(R, ora):
+    """The generator's raw states equal the oracle's FP64 geodesic after 60 steps."""
+    ctx = R.Context(R.camera_desc(**scenes.SMALL))
+    x, y, z = ctx.surrogate_generate(96, seed=3, states=True)
+    xs, zs = x.cpu().numpy(), z.cpu().numpy()
+    for i in range(96):
+        al, be, a, inc = map(float, xs[i])
+        s = ora.scene(a=a, incl_deg=inc)
+        st, xf, kf, n = ora.geodesic(s, al, be, max_steps=60)
+        x0, _ = ora.camera(s, al, be)
+        assert n == 60
+        ref = np.array([xf[0] - x0[0], np.log(xf[1]), xf[2], xf[3], kf[2], kf[1]])
+        assert np.all(np.abs(zs[i] - ref) <= 1e-9 * np.maximum(np.abs(ref), 1.0)), (i, zs[i] - ref)
+
+
+def test_backward_pass_matches_fp64_oracle(R):
+    """Gradient of the batch loss from the library's kernels (BF16 hidden layers, FP32
+    accumulation) against the FP64 chain rule of oracle/mlp.py, per parameter tensor."""
+    ctx = R.Context(R.camera_desc(**scenes.SMALL))
+    x, y = ctx.surrogate_generate(4096, seed=13)
+    ctx.surrogate_init(y, seed=17)
+    ctx.surrogate_train(x, y, 50, lr=1e-3, lr_final=1e-3, seed=1)  # move off the initial weights
+    P = ctx.surrogate_get().astype(np.float64)
+    xb, yb = x[:512].contiguous(), y[:512].contiguous()
+    g, L = ctx.surrogate_grad(xb, yb)
+    xo, yo = xb.cpu().numpy().astype(np.float64), yb.cpu().numpy()
+    go = mlp.grad(P, xo, yo)
+    Lo = mlp.loss(P, xo, yo)
+    assert abs(L / Lo - 1) < 2e-3
+    for a, b in [(mlp.W1, mlp.B1), (mlp.B1, mlp.W2), (mlp.W2, mlp.B2), (mlp.B2, mlp.W3), (mlp.W3, mlp.B3),
+                 (mlp.B3, mlp.W4), (mlp.W4, mlp.B4), (mlp.B4, mlp.NORM)]:
+        e = np.linalg.norm(g[a:b] - go[a:b]) / np.linalg.norm(go[a:b])
+        assert e < 2e-2, (a, b, e)
+        cos = np.dot(g[a:b], go[a:b]) / (np.linalg.norm(g[a:b]) * np.linalg.norm(go[a:b]))
+        assert cos > 0.9998, (a, b, cos)
+
+
+def test_training_generalises(R):
+    ctx = R.Context(R.camera_desc(**scenes.SMALL))
+    x, y = ctx.surrogate_generate(300_000, seed=21)
+    xh, yh = ctx.surrogate_generate(20_000, seed=22)
+    ctx.surrogate_init(y, seed=23)
+    loss = ctx.surrogate_train(x, y, 3000, lr=2e-3, lr_final=2e-5, seed=24, record_loss=True)
+    assert np.mean(loss[-100:]) < 1e-3 * np.mean(loss[:10])
+    pred = ctx.surrogate_eval(xh).cpu().numpy()
+    err = np.abs(pred - yh.cpu().numpy())
+    # held-out median errors of theta and ln r (the quantities the hand-off is sensitive to)
+    assert np.median(err[:, 2]) < 5e-5 and np.median(err[:, 1]) < 1e-4
+
+
+def _render(R, cam, prec, freqs, params=None):
+    import torch
+
+    ctx = R.Context(R.camera_desc(**cam, precision=prec))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    if params is not None:
+        ctx.surrogate_set(params)
+    img, fl = ctx.render(freqs)
+    torch.cuda.synchronize()
+    return ctx, img.cpu().numpy(), fl
+
+
+@pytest.mark.parametrize("spin", [0.9, 0.5])
+def test_mixed_mlp_render_parity(R, ora, trained, spin):
+    """RAPTOR_MIXED_MLP against the FP64 oracle: flux within 1e-3 and pixels outside the
+    critical-curve band within 1e-2 (inside the band and the shadow the exact integrator runs)."""
+    cam = dict(scenes.SMALL, spin=spin, nx=48, ny=40)
+    freqs = [1e10, 230e9]
+    _, img, fl = _render(R, cam, R.MIXED_MLP, freqs, trained)
+    oimg, _, _ = ora.render(ora.scene(**oracle_kwargs(cam)), freqs)
+    al, be = R.pixel_centres(R.camera_desc(**cam))
+    band = ring_mask(al, be, spin, cam["incl_deg"], 0.5)
+    for f in range(len(freqs)):
+        assert abs(fl[f] / oimg[f].sum() - 1) <= FLUX_TOL
+        assert rel_err(img[f], oimg[f], floor_frac=1e-6)[~band].max() <= PIX_TOL
+
+
+def test_surrogate_gain_over_the_method_without_it(R, trained):
+    """What the trained network gains: the 512^2 spectral-scene image (a = 0.9375) rendered by
+    the mixed path with and without the surrogate, both checked against the FP64 GPU path
+    at the same 1e-3 flux bound; the learned path must be faster."""
+    import torch
+
+    cam = dict(scenes.SPECTRAL, spin=0.9375)
+    freqs = [230e9]
+    c64, i64, f64 = _render(R, cam, R.FP64, freqs)
+    res = {}
+    for prec in (R.MIXED, R.MIXED_MLP):
+        ctx, img, fl = _render(R, cam, prec, freqs, trained if prec == R.MIXED_MLP else None)
+        assert abs(fl[0] / f64[0] - 1) <= FLUX_TOL
+        out = torch.empty((1, cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
+        best = 1e9
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.render(freqs, image=out, flux=False)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        res[prec] = best
+    gain = res[R.MIXED] / res[R.MIXED_MLP]
+    print(f"surrogate gain at 512^2: {gain:.3f}x (mixed {res[R.MIXED] * 1e3:.2f} ms, mixed+MLP {res[R.MIXED_MLP] * 1e3:.2f} ms)")
+    assert gain > 1.0
