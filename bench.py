@@ -194,9 +194,9 @@ def train_surrogate(R, torch, cam, steps, n_train):
     return ctx.surrogate_get(), summ
 
 
-def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks, params=None):
+def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks, params=None, flags=0):
     """Warm up, then time args.steps renders of one path; returns measurements."""
-    ctx = R.Context(R.camera_desc(**cam, precision=prec))
+    ctx = R.Context(R.camera_desc(**cam, precision=prec, flags=flags))
     ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
     if params is not None:
         ctx.surrogate_set(params)
@@ -263,13 +263,15 @@ def run_native(args):
     rays_step = npix * len(freqs)
 
     params, sur = None, None
-    if "mlp" in paths:
+    if any(p.startswith("mlp") for p in paths):
         params, sur = train_surrogate(R, torch, cam, args.train_steps, args.train_rays)
     res = {}
     for pth in paths:
-        prec = {"mlp": R.MIXED_MLP, "mixed": R.MIXED, "fp64": R.FP64}[pth]
+        prec = {"mlp": R.MIXED_MLP, "mixed": R.MIXED, "fp64": R.FP64, "mlp_df": R.MIXED_MLP, "mixed_df": R.MIXED}[pth]
+        flags = R.FLAG_INNER_DF64 if pth.endswith("_df") else 0
         res[pth] = _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist,
-                               sample_clocks=(rank == 0 and pth == paths[0]), params=params if pth == "mlp" else None)
+                               sample_clocks=(rank == 0 and pth == paths[0]),
+                               params=params if pth.startswith("mlp") else None, flags=flags)
     main = res[paths[0]]
     ms_step = main["ms"]
     value = world * rays_step / (ms_step * 1e-3)
@@ -321,7 +323,8 @@ def run_native(args):
             if kname == "render_fp64":
                 steps_k, pk, pipe = s["steps"], fma64, "fp64"
             elif kname == "mixed_fp64":
-                steps_k, pk, pipe = s["fp64_steps"], fma64, "fp64"
+                steps_k, pk, pipe = s["fp64_steps"], (fma32 if pth.endswith("_df") else fma64), (
+                    "fp32 (double-float)" if pth.endswith("_df") else "fp64")
             else:
                 steps_k, pk, pipe = ctx_phase_steps(s, prof).get(kname, 0), fma32, "fp32"
             fl_launch = flops["fp64_step"] * steps_k / kn
@@ -358,7 +361,9 @@ def run_native(args):
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"mlp": "f32+f64+bf16", "mixed": "f32+f64", "fp64": "f64"}[paths[0]],
+        "vs_baseline": None,
+        "dtype": {"mlp": "f32+f64+bf16", "mixed": "f32+f64", "fp64": "f64", "mlp_df": "f32+df64+bf16",
+                  "mixed_df": "f32+df64"}[paths[0]],
         "data": "synthetic (analytic plasma, deterministic)",
         "config": {"workload": workload, "pixels": npix, "freqs_hz": freqs, "precision": paths[0],
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed render"},
@@ -417,7 +422,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--size", type=int, default=1024, help="image side (profiling runs use a smaller case)")
-    ap.add_argument("--paths", default="mlp,mixed,fp64", help="comma list of paths to time (first = value): mlp, mixed, fp64")
+    ap.add_argument("--paths", default="mlp,mixed,fp64,mlp_df,mixed_df",
+                    help="comma list of paths to time (first = value): mlp, mixed, fp64, mlp_df, mixed_df")
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-rays", type=int, default=1_000_000)
     args = ap.parse_args()

@@ -72,6 +72,9 @@ typedef enum {
 
 #define RAPTOR_FLAG_K2_EXACT 0x1u      /* exact K2(1/Theta_e) instead of 2 Theta_e^2 (sec. 4.2.2) */
 #define RAPTOR_FLAG_STEP_LINEAR_R 0x2u /* literal d lambda = eps r (no polar limiter)            */
+#define RAPTOR_FLAG_INNER_DF64 0x4u    /* MIXED/MIXED_MLP: inner-region geodesic steps in double-
+                                          float arithmetic on the FP32 pipe (48-bit significand,
+                                          ~1e-14 relative) instead of native FP64              */
 
 /* Ray termination codes written to status_dev (render_ex) and trace calls. */
 #define RAPTOR_RAY_ESCAPED 0   /* r > r_escape                       */

@@ -156,7 +156,7 @@ std::string validate_camera(const raptor_camera_desc* d) {
     if (!(d->tau_cut > 0.0)) return "tau_cut must be > 0 (may be +inf)";
     if (d->max_steps < 1) return "max_steps must be >= 1";
     if (d->precision < RAPTOR_FP64 || d->precision > RAPTOR_MIXED_MLP) return "unknown precision";
-    if (d->flags & ~(RAPTOR_FLAG_K2_EXACT | RAPTOR_FLAG_STEP_LINEAR_R)) return "unknown flag bits";
+    if (d->flags & ~(RAPTOR_FLAG_K2_EXACT | RAPTOR_FLAG_STEP_LINEAR_R | RAPTOR_FLAG_INNER_DF64)) return "unknown flag bits";
     if (!(d->r_fp64 >= 0.0) || !std::isfinite(d->r_fp64)) return "r_fp64 must be finite and >= 0";
     if (!(d->turn_kr >= 0.0) || !std::isfinite(d->turn_kr)) return "turn_kr must be finite and >= 0";
     if (!std::isfinite(d->t_delay)) return "t_delay must be finite";
@@ -301,8 +301,11 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s);
     if (e != cudaSuccess) return e;
     int occ32 = 0, occ64 = 0;
+    const bool df = (p.flags & kFlagInnerDf64) != 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_mixed_fp32<NF>, c->launch_block, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_mixed_fp64<NF>, c->launch_block, 0);
+    if (e == cudaSuccess)
+        e = df ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_mixed_fp64<NF, df64>, c->launch_block, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_mixed_fp64<NF, double>, c->launch_block, 0);
     if (e != cudaSuccess) return e;
     const int b32 = grid_blocks(c, std::max(occ32, 1));
     const int b64 = c->num_sms * std::max(1, c->launch_bps64 > 0 ? std::min(c->launch_bps64, occ64) : occ64);
@@ -316,8 +319,12 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < kMaxPasses; ++pass) {
         ProfScope ps(c, kProfMixedB, s);
-        k_mixed_fp64<NF><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats, pass,
-                                                                        kPassBudget[pass]);
+        if (df)
+            k_mixed_fp64<NF, df64><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats, pass,
+                                                                              kPassBudget[pass]);
+        else
+            k_mixed_fp64<NF, double><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats,
+                                                                                pass, kPassBudget[pass]);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

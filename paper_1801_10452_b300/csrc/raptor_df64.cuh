@@ -1,0 +1,146 @@
+// raptor_df64.cuh -- double-float ("df64") arithmetic on the FP32 pipe.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2: a 48-bit
+// significand (relative rounding ~2^-48 ~ 3.6e-15) with FP32's exponent range.  On B300 one
+// FP64 instruction costs about as much issue bandwidth as 73 FP32 instructions, while a
+// df64 add or multiply is ~10 FP32 instructions, so df64 delivers FP64-class precision for
+// the inner-region geodesic steps several times faster than native FP64.
+//
+// The building blocks are the classical error-free transformations:
+//   two-sum (Knuth, TAOCP vol. 2, 4.2.2): s = a + b exactly as s + e;
+//   fast-two-sum (Dekker 1971) for |a| >= |b|;
+//   two-product with a fused multiply-add: p = a b exactly as p + fma(a, b, -p).
+// Division uses one Newton correction of the float quotient; sin/cos reduce the argument by
+// multiples of pi/2 (pi/2 stored as three floats) and sum the Taylor series of sin and cos
+// on [-pi/4, pi/4] in df64 (terms to x^19 / 19! and x^18 / 18!).
+#pragma once
+
+#include "raptor_math.cuh"
+
+namespace raptor {
+// The type and its overloads live in a nested namespace and are found by argument-dependent
+// lookup, so they do not hide the global fmin/fmax/fabs for double arguments.
+namespace dfns {
+
+struct df64 {
+    float hi, lo;
+    constexpr RAPTOR_HD df64() : hi(0.f), lo(0.f) {}
+    constexpr RAPTOR_HD df64(float h, float l) : hi(h), lo(l) {}
+    // from a double (constants fold at compile time; run-time conversions cost FP64 work)
+    constexpr RAPTOR_HD df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    constexpr RAPTOR_HD df64(int i) : hi((float)i), lo(0.f) {}
+    RAPTOR_HD explicit operator double() const { return (double)hi + (double)lo; }
+    RAPTOR_HD explicit operator float() const { return hi + lo; }
+};
+
+RAPTOR_HD df64 df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return df64(s, b - (s - a));
+}
+RAPTOR_HD df64 df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return df64(s, (a - (s - bb)) + (b - bb));
+}
+RAPTOR_HD df64 df_two_prod(float a, float b) {
+    const float p = a * b;
+    return df64(p, fmaf(a, b, -p));
+}
+
+RAPTOR_HD df64 operator+(df64 a, df64 b) {
+    df64 s = df_two_sum(a.hi, b.hi);
+    df64 t = df_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+RAPTOR_HD df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+RAPTOR_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
+RAPTOR_HD df64 operator*(df64 a, df64 b) {
+    df64 p = df_two_prod(a.hi, b.hi);
+    p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+    return df_fast_two_sum(p.hi, p.lo);
+}
+RAPTOR_HD df64 operator/(df64 a, df64 b) {
+    // q1 = a/b in float, r = a - q1 b (df64), q2 = r/b in float; q = q1 + q2, one more
+    // correction for the last bits
+    const float q1 = a.hi / b.hi;
+    df64 r = a - b * df64(q1, 0.f);
+    const float q2 = r.hi / b.hi;
+    r = r - b * df64(q2, 0.f);
+    const float q3 = r.hi / b.hi;
+    df64 q = df_fast_two_sum(q1, q2);
+    return q + df64(q3, 0.f);
+}
+RAPTOR_HD df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+RAPTOR_HD df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
+RAPTOR_HD df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
+RAPTOR_HD bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+RAPTOR_HD bool operator>(df64 a, df64 b) { return b < a; }
+RAPTOR_HD bool operator>=(df64 a, df64 b) { return !(a < b); }
+RAPTOR_HD bool operator<=(df64 a, df64 b) { return !(b < a); }
+RAPTOR_HD df64 fabs(df64 a) { return a.hi < 0.f ? -a : a; }
+RAPTOR_HD df64 fmin(df64 a, df64 b) { return a < b ? a : b; }
+RAPTOR_HD df64 fmax(df64 a, df64 b) { return a < b ? b : a; }
+
+
+RAPTOR_HD df64 df_sqrt(df64 a) {
+    // one Newton step on the float square root: s = sqrt(a_hi), s + (a - s^2) / (2 s)
+    if (!(a.hi > 0.f)) return df64(0.f, 0.f);
+    const float s = sqrtf(a.hi);
+    const df64 e = a - df_two_prod(s, s);
+    return df_fast_two_sum(s, e.hi / (2.f * s));
+}
+
+// sin and cos of x (any moderate argument; the geodesic code passes theta in (0, pi)).
+RAPTOR_HD void df_sincos(df64 x, df64* s_out, df64* c_out) {
+    // pi/2 = P1 + P2 + P3 (three floats; residual ~1e-23)
+    const float P1 = 1.57079637f, P2 = -4.37113883e-08f, P3 = -1.71512451e-15f;
+    const float kf = rintf((x.hi + x.lo) * 0.636619747f);
+    df64 r = x - df_two_prod(kf, P1);
+    r = r - df_two_prod(kf, P2);
+    r = r - df64(kf * P3, 0.f);
+    const int q = ((int)kf) & 3;
+    const df64 r2 = r * r;
+    // Taylor series on |r| <= pi/4 in r^2 (Horner): (-1)^n/(2n+1)! and (-1)^n/(2n)! as float pairs
+    const float so[20] = {1.f, 0.f, -0.166666672f, 4.96705388e-09f, 0.00833333377f, -4.34617203e-10f,
+                          -0.000198412701f, 2.72559687e-12f, 2.75573188e-06f, 3.79357122e-14f, -2.50521079e-08f,
+                          -4.41762304e-16f, 1.60590444e-10f, -5.35252651e-18f, -7.64716361e-13f, -1.22007105e-20f,
+                          2.81145736e-15f, -1.04620847e-22f, -8.22063508e-18f, -1.6814781e-25f};
+    const float ce[20] = {1.f, 0.f, -0.5f, 0.f, 0.0416666679f, -1.24176347e-09f, -0.00138888892f, 3.36310944e-11f,
+                          2.48015876e-05f, -3.40699609e-13f, -2.755732e-07f, 7.57511221e-15f, 2.08767559e-09f,
+                          1.10828391e-16f, -1.14707454e-11f, -2.37220769e-19f, 4.77947726e-14f, 7.62544404e-22f,
+                          -1.56192068e-16f, -1.54044715e-24f};
+    df64 ps(0.f, 0.f), pc(0.f, 0.f);
+#pragma unroll
+    for (int n = 9; n >= 0; --n) {
+        ps = ps * r2 + df64(so[2 * n], so[2 * n + 1]);
+        pc = pc * r2 + df64(ce[2 * n], ce[2 * n + 1]);
+    }
+    const df64 sr = ps * r, cr = pc;
+    // quadrant: sin(r + q pi/2), cos(r + q pi/2)
+    if (q == 0) { *s_out = sr; *c_out = cr; }
+    else if (q == 1) { *s_out = cr; *c_out = -sr; }
+    else if (q == 2) { *s_out = -sr; *c_out = -cr; }
+    else { *s_out = -cr; *c_out = sr; }
+}
+
+RAPTOR_HD void sc(df64 v, df64* s, df64* c) { df_sincos(v, s, c); }
+RAPTOR_HD df64 rsq(df64 v) { return df64(1.0) / df_sqrt(v); }
+
+}  // namespace dfns
+using dfns::df64;
+using dfns::df_fast_two_sum;
+using dfns::df_sincos;
+using dfns::df_sqrt;
+using dfns::df_two_prod;
+using dfns::df_two_sum;
+
+template <>
+struct Real<df64> {
+    static RAPTOR_HD df64 sqrt_(df64 v) { return df_sqrt(v); }
+    static RAPTOR_HD df64 rcp(df64 v) { return df64(1.0) / v; }
+};
+
+}  // namespace raptor

@@ -9,6 +9,7 @@ namespace raptor {
 
 constexpr unsigned kFlagK2Exact = 0x1u;
 constexpr unsigned kFlagLinearR = 0x2u;
+constexpr unsigned kFlagInnerDf64 = 0x4u;
 
 enum : int { kEscaped = 0, kCaptured = 1, kThick = 2, kTruncated = 3, kError = 4 };
 

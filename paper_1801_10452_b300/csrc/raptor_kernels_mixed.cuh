@@ -17,6 +17,7 @@
 
 #include "raptor_kernels_fp64.cuh"
 #include "raptor_surrogate.cuh"
+#include "raptor_df64.cuh"
 
 namespace raptor {
 
@@ -188,32 +189,69 @@ __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
 }
 
-// Mixed FP64 phase: the geodesic step in FP64, its transfer sample in FP32 (FP64 optical
-// depth beyond 10), state kept in FP64.
-template <int NF>
+// Mixed FP64 phase: the geodesic step in FP64 (S = double) or in double-float arithmetic
+// on the FP32 pipe (S = df64, RAPTOR_FLAG_INNER_DF64), its transfer sample in FP32 (FP64
+// optical depth beyond 10).
+template <typename S>
+struct StateT;
+template <>
+struct StateT<double> {
+    static __device__ __forceinline__ double from(double d) { return d; }
+    static __device__ __forceinline__ double to(double v) { return v; }
+    static __device__ __forceinline__ float f(double v) { return (float)v; }
+    static __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+};
+template <>
+struct StateT<df64> {
+    static __device__ __forceinline__ df64 from(double d) { return df64(d); }
+    static __device__ __forceinline__ double to(df64 v) { return (double)v.hi + (double)v.lo; }
+    static __device__ __forceinline__ float f(df64 v) { return v.hi + v.lo; }
+    static __device__ __forceinline__ bool finite(df64 v) { return isfinite(v.hi) && isfinite(v.lo); }
+};
+
+template <int NF, typename S = double>
 struct RayM {
-    double x[4], k[4];
+    S x[4], k[4];
     double I[NF];
     float tau[NF];
     double tau_hi[NF];
     int n, snap;
 };
 
-template <int NF>
-__device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF>& R) {
-    const double dl = step_size<double>(p.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
-    rk4_step<double>(p.a, R.x, R.k, dl);
-    R.n += 1;
-    bool fin = true;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) fin = fin && isfinite(R.x[i]) && isfinite(R.k[i]);
-    if (!fin) return kError;
-    if (R.x[1] < p.r_stop) return kCaptured;
-    if (R.x[1] > p.r_esc) return kEscaped;
+template <int NF, typename S>
+__device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF, S>& R, S a) {
     float xf[4], kf[4];
+    if constexpr (std::is_same<S, double>::value) {
+        const double dl = step_size<double>(p.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
+        rk4_step<double>(p.a, R.x, R.k, dl);
+        R.n += 1;
+        bool fin = true;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) { xf[i] = float(R.x[i]); kf[i] = float(R.k[i]); }
-    if (rt_sample_fp32<NF, double, float>(p, xf, kf, float(dl), R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+        for (int i = 0; i < 4; ++i) fin = fin && isfinite(R.x[i]) && isfinite(R.k[i]);
+        if (!fin) return kError;
+        if (R.x[1] < p.r_stop) return kCaptured;
+        if (R.x[1] > p.r_esc) return kEscaped;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { xf[i] = float(R.x[i]); kf[i] = float(R.k[i]); }
+        if (rt_sample_fp32<NF, double, float>(p, xf, kf, float(dl), R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+    } else {
+        // step size from the FP32 view of the state (the rule is a heuristic; its value only
+        // needs to be a smooth function of the state), RK4 in df64
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { xf[i] = StateT<S>::f(R.x[i]); kf[i] = StateT<S>::f(R.k[i]); }
+        const float dl = step_size<float>(p.f.eps, (p.flags & kFlagLinearR) != 0, xf, kf);
+        rk4_step<S>(a, R.x, R.k, S(dl, 0.f));
+        R.n += 1;
+        bool fin = true;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) fin = fin && StateT<S>::finite(R.x[i]) && StateT<S>::finite(R.k[i]);
+        if (!fin) return kError;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { xf[i] = StateT<S>::f(R.x[i]); kf[i] = StateT<S>::f(R.k[i]); }
+        if (xf[1] < p.f.r_stop) return kCaptured;
+        if (xf[1] > p.f.r_esc) return kEscaped;
+        if (rt_sample_fp32<NF, double, float>(p, xf, kf, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+    }
     return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
 }
 
@@ -338,10 +376,11 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
 // region then, it is re-queued for the next pass.  Every pass therefore starts with full
 // warps, and the ragged end of a pass lasts at most `budget` steps, instead of one long
 // tail in which a few long inner-region rays occupy otherwise empty warps.
-template <int NF>
+template <int NF, typename S = double>
 __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues mq, unsigned long long* cnt,
                                                     unsigned long long* stats, int pass, int budget) {
-    RayM<NF> R;
+    RayM<NF, S> R;
+    const S a_s = StateT<S>::from(p.a);
     long long id = -1;
     int frame = 0, pix = 0, n_in = 0;
     bool drained = false;
@@ -358,8 +397,8 @@ __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues 
             pix = (int)(id - (long long)frame * p.n_pix);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                R.x[i] = q.xk[(size_t)i * cap + nid];
-                R.k[i] = q.xk[(size_t)(4 + i) * cap + nid];
+                R.x[i] = StateT<S>::from(q.xk[(size_t)i * cap + nid]);
+                R.k[i] = StateT<S>::from(q.xk[(size_t)(4 + i) * cap + nid]);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -376,19 +415,24 @@ __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues 
         int st = -1;
         bool push = false, requeue = false;
         if (id >= 0) {
-            st = step_mixed64<NF>(p, R);
+            st = step_mixed64<NF, S>(p, R, a_s);
             if (st < 0) {
-                if (!in_fp64_region<double>(p, R.x, R.k)) push = true;
+                float xf[4], kf[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { xf[i] = StateT<S>::f(R.x[i]); kf[i] = StateT<S>::f(R.k[i]); }
+                if (!in_fp64_region<float>(p, xf, kf)) push = true;
                 else if (R.n - n_in >= budget) requeue = true;
             }
         }
         const long long slot = warp_push_slot(&cnt[kCntPush32], push);
         const long long rslot = warp_push_slot(&cnt[kCntPassOut + pass], requeue);
         if (push || requeue) {
-            double tau[NF];
+            double tau[NF], xd[4], kd[4];
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + R.tau_hi[f];
-            store_ray<NF>(push ? mq.q32 : qr, cap, push ? slot : rslot, id, R.x, R.k, R.I, tau, R.n, p.nf);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { xd[i] = StateT<S>::to(R.x[i]); kd[i] = StateT<S>::to(R.k[i]); }
+            store_ray<NF>(push ? mq.q32 : qr, cap, push ? slot : rslot, id, xd, kd, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
         } else if (id >= 0 && st >= 0) {

@@ -120,10 +120,11 @@ RAPTOR_HD void surrogate_targets(double a, double incl_deg, double r_cam, double
 __global__ void k_surrogate_data(SurrogateRange R, uint64_t seed, long long n, float* __restrict__ inputs,
                                  double* __restrict__ targets, double* __restrict__ raw) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double al = R.amin + (R.amax - R.amin) * u01(seed, i, 0);
-        const double be = R.bmin + (R.bmax - R.bmin) * u01(seed, i, 1);
-        const double a = R.smin + (R.smax - R.smin) * u01(seed, i, 2);
-        const double inc = R.imin + (R.imax - R.imin) * u01(seed, i, 3);
+        // inputs are stored (and later evaluated) in FP32: the targets use the same values
+        const double al = (double)(float)(R.amin + (R.amax - R.amin) * u01(seed, i, 0));
+        const double be = (double)(float)(R.bmin + (R.bmax - R.bmin) * u01(seed, i, 1));
+        const double a = (double)(float)(R.smin + (R.smax - R.smin) * u01(seed, i, 2));
+        const double inc = (double)(float)(R.imin + (R.imax - R.imin) * u01(seed, i, 3));
         inputs[i * kIn + 0] = (float)al;
         inputs[i * kIn + 1] = (float)be;
         inputs[i * kIn + 2] = (float)a;

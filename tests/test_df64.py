@@ -1,0 +1,22 @@
+"""Double-float (df64) arithmetic used by the optional inner-region path: compiled for the
+host with nvcc and checked against long double on seeded random operands.  CPU only."""
+import json
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "paper_1801_10452_b300", "csrc", "df64_check.cu")
+
+
+def test_df64_accuracy(tmp_path):
+    exe = str(tmp_path / "df64_check")
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-o", exe, SRC], check=True, capture_output=True)
+    r = json.loads(subprocess.run([exe], check=True, capture_output=True, text=True).stdout)
+    # a 48-bit significand: a few units of 2^-48 = 3.6e-15 per operation
+    for k in ("add", "mul", "div", "sqrt", "sin_abs", "cos_abs"):
+        assert r[k] < 3e-14, (k, r[k])

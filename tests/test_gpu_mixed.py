@@ -113,3 +113,16 @@ def test_results_independent_of_launch_shape(R):
         img, fl = ctx.render(scenes.SPECTRAL_FREQS[:3])
         torch.cuda.synchronize()
         assert np.array_equal(img.cpu().numpy(), ref)
+
+
+def test_inner_region_in_double_float(R, ora):
+    """RAPTOR_FLAG_INNER_DF64: the inner-region steps in double-float arithmetic meet the same
+    bounds against the FP64 oracle as native FP64, and stay close to the native-FP64 mixed path."""
+    cam = dict(scenes.SMALL, nx=48, ny=40)
+    freqs = [1e10, 230e9]
+    _, img_df, fl_df, st_df, _ = _mixed(R, cam, freqs, flags=R.FLAG_INNER_DF64)
+    _, img_64, fl_64, st_64, _ = _mixed(R, cam, freqs)
+    oimg, ost, _ = ora.render(ora.scene(**oracle_kwargs(cam)), freqs)
+    _check(R, cam, img_df, fl_df, oimg, "df64")
+    assert np.all(np.abs(fl_df / fl_64 - 1) < 1e-5)
+    assert (st_df == ost).mean() > 0.99
