@@ -12,7 +12,7 @@
 //   two-product with a fused multiply-add: p = a b exactly as p + fma(a, b, -p).
 // Division uses one Newton correction of the float quotient; sin/cos reduce the argument by
 // multiples of pi/2 (pi/2 stored as three floats) and sum the Taylor series of sin and cos
-// on [-pi/4, pi/4] in df64 (terms to x^19 / 19! and x^18 / 18!).
+// on [-pi/4, pi/4] (terms to x^15 / 15! and x^16 / 16!; the small high-order terms in float).
 #pragma once
 
 #include "raptor_math.cuh"
@@ -47,12 +47,12 @@ RAPTOR_HD df64 df_two_prod(float a, float b) {
     return df64(p, fmaf(a, b, -p));
 }
 
+// Addition with one error-free transformation of the leading parts: the low parts are
+// added in plain float, so the error is bounded by a few units of 2^-48 of |a| + |b|
+// (not of |a + b|), like the rounding of the operands themselves.
 RAPTOR_HD df64 operator+(df64 a, df64 b) {
     df64 s = df_two_sum(a.hi, b.hi);
-    df64 t = df_two_sum(a.lo, b.lo);
-    s.lo += t.hi;
-    s = df_fast_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
+    s.lo += a.lo + b.lo;
     return df_fast_two_sum(s.hi, s.lo);
 }
 RAPTOR_HD df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
@@ -62,14 +62,30 @@ RAPTOR_HD df64 operator*(df64 a, df64 b) {
     p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
     return df_fast_two_sum(p.hi, p.lo);
 }
+// b * q for a float q: the leading product exact, the low part's product rounded.
+RAPTOR_HD df64 df_mul_f(df64 b, float q) {
+    df64 p = df_two_prod(b.hi, q);
+    p.lo = fmaf(b.lo, q, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+// Approximate float reciprocal (a few ulp): it only seeds quotients that the df64
+// residuals below correct.
+RAPTOR_HD float df_rcp_approx(float v) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(1.f, v);
+#else
+    return 1.f / v;
+#endif
+}
 RAPTOR_HD df64 operator/(df64 a, df64 b) {
-    // q1 = a/b in float, r = a - q1 b (df64), q2 = r/b in float; q = q1 + q2, one more
-    // correction for the last bits
-    const float q1 = a.hi / b.hi;
-    df64 r = a - b * df64(q1, 0.f);
-    const float q2 = r.hi / b.hi;
-    r = r - b * df64(q2, 0.f);
-    const float q3 = r.hi / b.hi;
+    // q1 = a/b from the float reciprocal, r = a - q1 b in df64, q2 = r/b; a second residual
+    // gives the last bits: q = q1 + q2 + q3
+    const float rb = df_rcp_approx(b.hi);
+    const float q1 = a.hi * rb;
+    df64 r = a - df_mul_f(b, q1);
+    const float q2 = r.hi * rb;
+    r = r - df_mul_f(b, q2);
+    const float q3 = r.hi * rb;
     df64 q = df_fast_two_sum(q1, q2);
     return q + df64(q3, 0.f);
 }
@@ -90,7 +106,7 @@ RAPTOR_HD df64 df_sqrt(df64 a) {
     if (!(a.hi > 0.f)) return df64(0.f, 0.f);
     const float s = sqrtf(a.hi);
     const df64 e = a - df_two_prod(s, s);
-    return df_fast_two_sum(s, e.hi / (2.f * s));
+    return df_fast_two_sum(s, e.hi * (0.5f * df_rcp_approx(s)));
 }
 
 // sin and cos of x (any moderate argument; the geodesic code passes theta in (0, pi)).
@@ -112,12 +128,20 @@ RAPTOR_HD void df_sincos(df64 x, df64* s_out, df64* c_out) {
                           2.48015876e-05f, -3.40699609e-13f, -2.755732e-07f, 7.57511221e-15f, 2.08767559e-09f,
                           1.10828391e-16f, -1.14707454e-11f, -2.37220769e-19f, 4.77947726e-14f, 7.62544404e-22f,
                           -1.56192068e-16f, -1.54044715e-24f};
-    df64 ps(0.f, 0.f), pc(0.f, 0.f);
+    // Terms whose size on |r| <= pi/4 is below ~2^-24 (sin from r^11, cos from r^12) need
+    // only float precision: that tail is summed in float and the leading terms in df64.
+    // Truncation: the first omitted terms, r^17 / 17! and r^18 / 18!, are below 5e-17.
+    const float r2f = r2.hi;
+    float ts = 0.f, tc = 0.f;
 #pragma unroll
-    for (int n = 9; n >= 0; --n) {
-        ps = ps * r2 + df64(so[2 * n], so[2 * n + 1]);
-        pc = pc * r2 + df64(ce[2 * n], ce[2 * n + 1]);
-    }
+    for (int n = 7; n >= 5; --n) ts = fmaf(ts, r2f, so[2 * n]);
+#pragma unroll
+    for (int n = 8; n >= 6; --n) tc = fmaf(tc, r2f, ce[2 * n]);
+    df64 ps(ts, 0.f), pc(tc, 0.f);
+#pragma unroll
+    for (int n = 4; n >= 0; --n) ps = ps * r2 + df64(so[2 * n], so[2 * n + 1]);
+#pragma unroll
+    for (int n = 5; n >= 0; --n) pc = pc * r2 + df64(ce[2 * n], ce[2 * n + 1]);
     const df64 sr = ps * r, cr = pc;
     // quadrant: sin(r + q pi/2), cos(r + q pi/2)
     if (q == 0) { *s_out = sr; *c_out = cr; }

@@ -240,7 +240,7 @@ __device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF, S>& R, S a
 #pragma unroll
         for (int i = 0; i < 4; ++i) { xf[i] = StateT<S>::f(R.x[i]); kf[i] = StateT<S>::f(R.k[i]); }
         const float dl = step_size<float>(p.f.eps, (p.flags & kFlagLinearR) != 0, xf, kf);
-        rk4_step<S>(a, R.x, R.k, S(dl, 0.f));
+        rk4_step_rolled<S>(a, R.x, R.k, S(dl, 0.f));
         R.n += 1;
         bool fin = true;
 #pragma unroll
