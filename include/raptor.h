@@ -53,9 +53,10 @@ typedef enum {
 /* Arithmetic of the integration.
  *   RAPTOR_FP64:  every step in FP64.
  *   RAPTOR_MIXED: geodesic steps and transfer in FP32 where r >= r_fp64 and away from radial
- *                 turning points; FP64 inside r < r_fp64, where |k^r| < turn_kr |k^t|, and
- *                 for the optical depth once tau > 10.  Rays are moved between FP32 and
- *                 FP64 work queues so each warp runs one precision.
+ *                 turning points; FP64 inside r < r_fp64 and where |k^r| < turn_kr |k^t|;
+ *                 the optical depth beyond tau = 10 with a 48-bit significand (compensated
+ *                 float pair).  Rays are moved between FP32 and FP64 work queues so each
+ *                 warp runs one precision.
  *   RAPTOR_MIXED_MLP: RAPTOR_MIXED, with every ray outside the critical curve and a band
  *                 around it started from the learned surrogate's prediction of the state
  *                 after 60 steps (see raptor_surrogate_*), and rays leaving r > r_exit on

@@ -163,9 +163,17 @@ RAPTOR_HD int plasma_sample(const Params& p, const T x[4], const T k[4], int sna
         const int ok = analytic_velocity(RAPTOR_P(T, a), RAPTOR_P(T, r_isco), P, u);
         if (ok < 0) return -1;
         const T r = x[1];
-        ne = RAPTOR_P(T, n0) * Real<T>::pow_(r, RAPTOR_P(T, n_pow));
-        the = RAPTOR_P(T, the0) * Real<T>::pow_(r, RAPTOR_P(T, the_pow));
-        B = RAPTOR_P(T, B0) * Real<T>::pow_(r, RAPTOR_P(T, B_pow));
+        if constexpr (std::is_same<T, float>::value) {
+            // three power laws of one radius: one logarithm, three exponentials
+            const float l2r = log2f(r);
+            ne = p.f.n0 * exp2f(p.f.n_pow * l2r);
+            the = p.f.the0 * exp2f(p.f.the_pow * l2r);
+            B = p.f.B0 * exp2f(p.f.B_pow * l2r);
+        } else {
+            ne = RAPTOR_P(T, n0) * Real<T>::pow_(r, RAPTOR_P(T, n_pow));
+            the = RAPTOR_P(T, the0) * Real<T>::pow_(r, RAPTOR_P(T, the_pow));
+            B = RAPTOR_P(T, B0) * Real<T>::pow_(r, RAPTOR_P(T, B_pow));
+        }
         ks_lower(P, k, kc);
         g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
         const T u_phi = P.gtp * u[0] + P.grp * u[1] + P.gpp * u[3];

@@ -11,7 +11,10 @@
 //     pushed to the FP32 queue.
 //   phase C (FP32, persistent): rays from the FP32 queue, integrated to termination (an
 //     outgoing photon has no further radial turning point; re-entries are counted).
-// The optical depth of a frequency is accumulated in FP64 once it exceeds 10.
+// The optical depth of a frequency beyond 10 is accumulated with a 48-bit significand
+// (compensated float pair), so the per-step loops of all phases issue no FP64 instruction
+// for the transfer: on B300 one FP64 compare or conversion occupies the FP64 pipe for as
+// long as ~70 FP32 instructions.
 // No kernel waits on another: the phases are ordered by the stream.
 #pragma once
 
@@ -106,24 +109,35 @@ __device__ __forceinline__ bool in_fp64_region(const Params& p, const T x[4], co
 template <int NF>
 struct RayF {
     float x[4], k[4];
+    float xl[4], kl[4];  // low parts of the compensated state (rk4_step_comp)
     float I[NF], tau[NF];
-    double tau_hi[NF];  // optical depth beyond 10 accumulated in FP64
+    df64 tau_hi[NF];  // optical depth beyond 10, compensated sum (zero while unused)
     int n, snap;
 };
+
+// Split a queued optical depth into the float part (<= 10) and the compensated high part.
+__device__ __forceinline__ void split_f(double v, float& hi, float& lo) {
+    hi = float(v);
+    lo = float(v - double(hi));
+}
+
+__device__ __forceinline__ void tau_split(double t, float& lo, df64& hi) {
+    if (t > 10.0) { lo = 0.f; hi = df64(t); }
+    else { lo = float(t); hi = df64(0.f, 0.f); }
+}
 
 // FP32 transfer sample at (x, k) after a step of length dl (Eqs. 30, 34-36, 41-44).
 // Intensities are carried scaled by kIScale = 2^100: the emissivity's exponential tail
 // reaches ~1e-60 cgs, far below FP32's smallest normal number.  The per-step increment of
 // the formal solution, exp(-tau) S (1 - exp(-dtau)) / g^3, is written as
 // exp(-tau) j dl L F(dtau) / g^2 with F(x) = (1 - exp(-x)) / x, so no factor underflows.
-// A frequency's optical depth moves to FP64 once above 10.  TI/TT are the storage types
-// of I and of the low part of tau (float in the FP32 phases, double in the FP64 phase).
+// A frequency's optical depth moves to the compensated accumulator once above 10.
 constexpr float kIScale = 1.2676506002282294e30f;      // 2^100
 constexpr double kIUnscale = 7.888609052210118e-31;    // 2^-100
 
-template <int NF, typename TI, typename TT>
+template <int NF, typename TI>
 __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4], const float k[4], float dl, int snap,
-                                              TI* I, TT* tau, double* tau_hi) {
+                                              TI* I, float* tau, df64* tau_hi) {
     float ne, the, B, g, sinb;
     const int ok = plasma_sample<float>(p, x, k, snap, ne, the, B, g, sinb);
     if (ok <= 0) return ok;
@@ -139,35 +153,23 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
             if (j > 0.f && S > 0.f) {
                 const float dtau = j / S * gdl_unscaled;
                 const float F = dtau > 1e-4f ? -expm1f(-dtau) / dtau : 1.f - 0.5f * dtau;
-                const float tau_now = float(tau[f]) + float(tau_hi[f]);
+                const float tau_now = tau[f] + tau_hi[f].hi;
                 I[f] += TI(expf(-tau_now) * j * dlcm * F * ig2);
-                if (float(tau[f]) + dtau > 10.f || tau_hi[f] > 0.0) tau_hi[f] += double(dtau);
-                else tau[f] += TT(dtau);
+                if (tau_hi[f].hi > 0.f || tau[f] + dtau > 10.f) tau_hi[f] = tau_hi[f] + df64(dtau, 0.f);
+                else tau[f] += dtau;
             }
         }
     }
     return 1;
 }
 
-template <int NF, typename TT>
-__device__ __forceinline__ int thick_or_capped(const Params& p, const TT* tau, const double* tau_hi, int n) {
-    bool hi = false;
+template <int NF>
+__device__ __forceinline__ int thick_or_capped(const Params& p, const float* tau, const df64* tau_hi, int n) {
+    float tmin = tau[0] + (tau_hi[0].hi + tau_hi[0].lo);
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
-        if (f < p.nf) hi = hi || (tau_hi[f] > 0.0);
-    if (!hi) {
-        float tmin = float(tau[0]);
-#pragma unroll
-        for (int f = 1; f < NF; ++f)
-            if (f < p.nf) tmin = fminf(tmin, float(tau[f]));
-        if (tmin > p.f.tau_cut) return kThick;
-    } else {
-        double tmin = double(tau[0]) + tau_hi[0];
-#pragma unroll
-        for (int f = 1; f < NF; ++f)
-            if (f < p.nf) tmin = fmin(tmin, double(tau[f]) + tau_hi[f]);
-        if (tmin > p.tau_cut) return kThick;
-    }
+    for (int f = 1; f < NF; ++f)
+        if (f < p.nf) tmin = fminf(tmin, tau[f] + (tau_hi[f].hi + tau_hi[f].lo));
+    if (tmin > p.f.tau_cut) return kThick;
     if (n >= p.max_steps) return kTruncated;
     return -1;
 }
@@ -176,7 +178,7 @@ __device__ __forceinline__ int thick_or_capped(const Params& p, const TT* tau, c
 template <int NF>
 __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     const float dl = step_size<float>(p.f.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
-    rk4_step<float>(p.f.a, R.x, R.k, dl);
+    rk4_step_comp(p.f.a, R.x, R.xl, R.k, R.kl, dl);
     R.n += 1;
     bool fin = true;
 #pragma unroll
@@ -184,14 +186,14 @@ __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     if (!fin) return kError;
     if (R.x[1] < p.f.r_stop) return kCaptured;
     if (R.x[1] > p.f.r_esc) return kEscaped;
-    if (p.r_exit > 0.0 && R.x[1] > p.r_exit_f && R.k[1] > 0.f) return kEscaped;  // surrogate path only
-    if (rt_sample_fp32<NF, float, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
-    return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
+    if (p.r_exit_f > 0.f && R.x[1] > p.r_exit_f && R.k[1] > 0.f) return kEscaped;  // surrogate path only
+    if (rt_sample_fp32<NF, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+    return thick_or_capped<NF>(p, R.tau, R.tau_hi, R.n);
 }
 
 // Mixed FP64 phase: the geodesic step in FP64 (S = double) or in double-float arithmetic
-// on the FP32 pipe (S = df64, RAPTOR_FLAG_INNER_DF64), its transfer sample in FP32 (FP64
-// optical depth beyond 10).
+// on the FP32 pipe (S = df64, RAPTOR_FLAG_INNER_DF64), its transfer sample in FP32 (optical
+// depth beyond 10 in the compensated accumulator).
 template <typename S>
 struct StateT;
 template <>
@@ -209,12 +211,18 @@ struct StateT<df64> {
     static __device__ __forceinline__ bool finite(df64 v) { return isfinite(v.hi) && isfinite(v.lo); }
 };
 
+// Intensity accumulator of the FP64 phase: FP64 next to FP64 steps (one FP64 add per sample
+// beside hundreds of FP64 step instructions), FP32 next to double-float steps, which issue
+// no FP64 instruction at all.
+template <typename S>
+using AccI = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+
 template <int NF, typename S = double>
 struct RayM {
     S x[4], k[4];
-    double I[NF];
+    AccI<S> I[NF];
     float tau[NF];
-    double tau_hi[NF];
+    df64 tau_hi[NF];
     int n, snap;
 };
 
@@ -233,7 +241,7 @@ __device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF, S>& R, S a
         if (R.x[1] > p.r_esc) return kEscaped;
 #pragma unroll
         for (int i = 0; i < 4; ++i) { xf[i] = float(R.x[i]); kf[i] = float(R.k[i]); }
-        if (rt_sample_fp32<NF, double, float>(p, xf, kf, float(dl), R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+        if (rt_sample_fp32<NF, double>(p, xf, kf, float(dl), R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
     } else {
         // step size from the FP32 view of the state (the rule is a heuristic; its value only
         // needs to be a smooth function of the state), RK4 in df64
@@ -250,14 +258,14 @@ __device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF, S>& R, S a
         for (int i = 0; i < 4; ++i) { xf[i] = StateT<S>::f(R.x[i]); kf[i] = StateT<S>::f(R.k[i]); }
         if (xf[1] < p.f.r_stop) return kCaptured;
         if (xf[1] > p.f.r_esc) return kEscaped;
-        if (rt_sample_fp32<NF, double, float>(p, xf, kf, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+        if (rt_sample_fp32<NF, float>(p, xf, kf, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
     }
-    return thick_or_capped<NF, float>(p, R.tau, R.tau_hi, R.n);
+    return thick_or_capped<NF>(p, R.tau, R.tau_hi, R.n);
 }
 
-template <int NF>
+template <int NF, typename TI>
 __device__ __forceinline__ void store_ray(const RayQueue& q, size_t cap, long long slot, long long id, const double x[4],
-                                          const double k[4], const double* I, const double* tau, int n, int nf) {
+                                          const double k[4], const TI* I, const double* tau, int n, int nf) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         q.xk[(size_t)i * cap + slot] = x[i];
@@ -266,7 +274,7 @@ __device__ __forceinline__ void store_ray(const RayQueue& q, size_t cap, long lo
 #pragma unroll
     for (int f = 0; f < NF; ++f)
         if (f < nf) {
-            q.I[(size_t)f * cap + slot] = I[f];
+            q.I[(size_t)f * cap + slot] = double(I[f]);
             q.tau[(size_t)f * cap + slot] = tau[f];
         }
     q.n[slot] = n;
@@ -305,9 +313,9 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
                     init_ray<NF>(p, nid, D, frame, pix);
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) { R.x[i] = float(D.x[i]); R.k[i] = float(D.k[i]); }
+                for (int i = 0; i < 4; ++i) { split_f(D.x[i], R.x[i], R.xl[i]); split_f(D.k[i], R.k[i], R.kl[i]); }
 #pragma unroll
-                for (int f = 0; f < NF; ++f) { R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = 0.0; }
+                for (int f = 0; f < NF; ++f) { R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = df64(0.f, 0.f); }
                 R.n = D.n;
                 R.snap = D.snap;
             } else {
@@ -318,18 +326,16 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
                 pix = (int)(id - (long long)frame * p.n_pix);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    R.x[i] = float(q.xk[(size_t)i * cap + nid]);
-                    R.k[i] = float(q.xk[(size_t)(4 + i) * cap + nid]);
+                    split_f(q.xk[(size_t)i * cap + nid], R.x[i], R.xl[i]);
+                    split_f(q.xk[(size_t)(4 + i) * cap + nid], R.k[i], R.kl[i]);
                 }
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     if (f < p.nf) {
                         R.I[f] = float(q.I[(size_t)f * cap + nid]);
-                        const double t = q.tau[(size_t)f * cap + nid];
-                        if (t > 10.0) { R.tau[f] = 0.f; R.tau_hi[f] = t; }
-                        else { R.tau[f] = float(t); R.tau_hi[f] = 0.0; }
+                        tau_split(q.tau[(size_t)f * cap + nid], R.tau[f], R.tau_hi[f]);
                     } else {
-                        R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = 0.0;
+                        R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = df64(0.f, 0.f);
                     }
                 }
                 R.n = q.n[nid];
@@ -348,12 +354,12 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
         }
         const long long slot = warp_push_slot(&cnt[kCntPush64], push);
         if (push) {
-            double x[4], k[4], I[NF], tau[NF];
+            double x[4], k[4], tau[NF];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { x[i] = R.x[i]; k[i] = R.k[i]; }
+            for (int i = 0; i < 4; ++i) { x[i] = double(R.x[i]) + double(R.xl[i]); k[i] = double(R.k[i]) + double(R.kl[i]); }
 #pragma unroll
-            for (int f = 0; f < NF; ++f) { I[f] = R.I[f]; tau[f] = double(R.tau[f]) + R.tau_hi[f]; }
-            store_ray<NF>(mq.q64, mq.cap, slot, id, x, k, I, tau, R.n, p.nf);
+            for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
+            store_ray<NF>(mq.q64, mq.cap, slot, id, x, k, R.I, tau, R.n, p.nf);
             id = -1;
         } else if (id >= 0 && st >= 0) {
             double I[NF];
@@ -376,8 +382,13 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
 // region then, it is re-queued for the next pass.  Every pass therefore starts with full
 // warps, and the ragged end of a pass lasts at most `budget` steps, instead of one long
 // tail in which a few long inner-region rays occupy otherwise empty warps.
+// Double-float steps are FP32-issue bound: ask for at least 4 resident blocks (16 warps)
+// per SM so that latency is hidden; the FP64 variant is FP64-pipe bound and needs no cap.
+template <typename S>
+constexpr int kMixed64MinBlocks = std::is_same<S, df64>::value ? 4 : 1;
+
 template <int NF, typename S = double>
-__global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues mq, unsigned long long* cnt,
+__global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const Params p, MixedQueues mq, unsigned long long* cnt,
                                                     unsigned long long* stats, int pass, int budget) {
     RayM<NF, S> R;
     const S a_s = StateT<S>::from(p.a);
@@ -402,10 +413,8 @@ __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues 
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                R.I[f] = f < p.nf ? q.I[(size_t)f * cap + nid] : 0.0;
-                const double t = f < p.nf ? q.tau[(size_t)f * cap + nid] : 0.0;
-                if (t > 10.0) { R.tau[f] = 0.f; R.tau_hi[f] = t; }
-                else { R.tau[f] = float(t); R.tau_hi[f] = 0.0; }
+                R.I[f] = f < p.nf ? AccI<S>(q.I[(size_t)f * cap + nid]) : AccI<S>(0);
+                tau_split(f < p.nf ? q.tau[(size_t)f * cap + nid] : 0.0, R.tau[f], R.tau_hi[f]);
             }
             R.n = q.n[nid];
             n_in = R.n;
@@ -429,14 +438,17 @@ __global__ void __launch_bounds__(128) k_mixed_fp64(const Params p, MixedQueues 
         if (push || requeue) {
             double tau[NF], xd[4], kd[4];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + R.tau_hi[f];
+            for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) { xd[i] = StateT<S>::to(R.x[i]); kd[i] = StateT<S>::to(R.k[i]); }
             store_ray<NF>(push ? mq.q32 : qr, cap, push ? slot : rslot, id, xd, kd, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
         } else if (id >= 0 && st >= 0) {
-            write_ray<NF>(p, frame, pix, R.I, R.n, st);
+            double I[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) I[f] = R.I[f];
+            write_ray<NF>(p, frame, pix, I, R.n, st);
             c_rays += 1;
             c_steps += (unsigned long long)R.n;
             c_64 += (unsigned long long)(R.n - n_in);

@@ -80,7 +80,9 @@ def test_mixed_spectral_spins(R, ora, spin):
 
 def test_mixed_all_fp32_and_all_fp64_limits(R, ora):
     """r_fp64 = 0 and turn_kr = 0 run everything in FP32; a huge r_fp64 runs everything in
-    the FP64 phase, which must then equal the FP64 path to rounding."""
+    the FP64 phase, which must then equal the FP64 path to the rounding of its FP32 transfer
+    samples: a few ulp (u = 6e-8) per sample, amplified in the emissivity's exp(-X^(1/3)) by
+    up to X^(1/3) ~ 30 on this Wien-tail scene: a bound of 4e-6 (~70 u)."""
     cam = dict(scenes.SMALL, nx=24, ny=24)
     oimg, _, _ = ora.render(ora.scene(**oracle_kwargs(cam)), scenes.SMALL_FREQS)
     ctx, img32, fl32, _, _ = _mixed(R, cam, scenes.SMALL_FREQS, r_fp64=0.0, turn_kr=0.0)
@@ -90,7 +92,7 @@ def test_mixed_all_fp32_and_all_fp64_limits(R, ora):
     s = ctx.stats()
     # the first step from the camera is FP32, every later one FP64
     assert s["fp64_steps"] == s["steps"] - s["rays"]
-    assert abs(fl64[0] / oimg.sum() - 1) < 1e-6
+    assert abs(fl64[0] / oimg.sum() - 1) < 4e-6
 
 
 def test_results_independent_of_launch_shape(R):
