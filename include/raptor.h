@@ -256,6 +256,18 @@ raptor_status raptor_surrogate_eval(raptor_ctx* ctx, const float* inputs_dev, lo
 raptor_status raptor_surrogate_get(raptor_ctx* ctx, float* params_host, int n);
 raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, int n);
 
+/* Kernel of the surrogate's inference (raptor_surrogate_eval and RAPTOR_MIXED_MLP renders):
+ *   RAPTOR_MLP_TCGEN05 (default): hidden layers on the 5th-generation tensor cores
+ *     (tcgen05.mma, accumulators in tensor memory, weights resident in shared memory);
+ *   RAPTOR_MLP_MMA_SYNC: one fused kernel on warp-level mma.sync BF16 instructions.
+ * Both compute the training forward pass's arithmetic (BF16 operands, FP32 accumulation)
+ * and differ only in FP32 summation order.  A tensor-core wait that exceeds 2 s makes the
+ * next synchronising call (raptor_surrogate_eval, a render that returns fluxes) fail with
+ * RAPTOR_ECUDA.  RAPTOR_EINVAL for another value. */
+#define RAPTOR_MLP_TCGEN05 0
+#define RAPTOR_MLP_MMA_SYNC 1
+raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind);
+
 /* Fallback: rays whose pixel centre lies inside the critical curve (Bardeen's closed form)
  * or within fallback_band M of it start at the camera (exact integration) [0.5]; r_exit:
  * outbound rays stop at r > r_exit in RAPTOR_MIXED_MLP (0 = off) [50]. */
@@ -264,8 +276,8 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 /* Per-kernel device time, measured with CUDA events recorded around every kernel launch on
  * the launch's own stream.  raptor_profile(ctx, 1) clears the accumulators and starts
  * recording; raptor_profile(ctx, 0) stops.  raptor_profile_read waits for the recorded
- * events and returns, per kernel slot RAPTOR_KERNEL_* (10 slots), the summed milliseconds
- * (ms[10], may be NULL) and the number of launches since the last clear (launches[10],
+ * events and returns, per kernel slot RAPTOR_KERNEL_* (11 slots), the summed milliseconds
+ * (ms[11], may be NULL) and the number of launches since the last clear (launches[11],
  * may be NULL; counted whether or not recording is on).  A slot covers all the kernels of
  * one stage (e.g. the surrogate slot times its inference as one interval). */
 #define RAPTOR_KERNEL_RENDER_FP64 0  /* persistent FP64 ray kernel                         */
@@ -276,8 +288,10 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 #define RAPTOR_KERNEL_TRACE 5        /* single-ray trace                                   */
 #define RAPTOR_KERNEL_LOAD 6         /* grid interleave at load time                       */
 #define RAPTOR_KERNEL_PEAK 7         /* unused by the renders                              */
-#define RAPTOR_KERNEL_SURROGATE 8    /* surrogate inference and start states of a render   */
+#define RAPTOR_KERNEL_SURROGATE 8    /* surrogate stage of a render (interval includes the  */
+                                     /* network; launches count its own two kernels)       */
 #define RAPTOR_KERNEL_TRAIN 9        /* surrogate data generation and training             */
+#define RAPTOR_KERNEL_SURROGATE_MLP 10 /* the network inside RAPTOR_KERNEL_SURROGATE        */
 raptor_status raptor_profile(raptor_ctx* ctx, int enable);
 raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches);
 

@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOPLASMA, EUNSUPPORTED = range(7)
 FP64, MIXED, MIXED_MLP = 0, 1, 2
 PLASMA_ANALYTIC, PLASMA_GRID = 0, 1
 FLAG_K2_EXACT, FLAG_STEP_LINEAR_R, FLAG_INNER_DF64 = 0x1, 0x2, 0x4
+MLP_TCGEN05, MLP_MMA_SYNC = 0, 1
 RAY_ESCAPED, RAY_CAPTURED, RAY_THICK, RAY_TRUNCATED, RAY_ERROR = range(5)
 
 EXPORTS = [
@@ -29,10 +30,10 @@ EXPORTS = [
     "raptor_last_error", "raptor_destroy", "raptor_profile", "raptor_profile_read", "raptor_measure_fma_peak",
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
-    "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config",
+    "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
-                "surrogate", "train"]
+                "surrogate", "train", "surrogate_mlp"]
 
 
 class RaptorError(RuntimeError):
@@ -107,6 +108,7 @@ def lib():
             "raptor_surrogate_get": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_surrogate_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
+            "raptor_surrogate_kernel": (st, [vp, C.c_int]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -282,10 +284,11 @@ class Context:
 
     def profile_read(self):
         """{kernel name: (ms, launches)} since the last profile(True)."""
-        ms = np.zeros(10)
-        n = (C.c_longlong * 10)()
+        k = len(KERNEL_NAMES)
+        ms = np.zeros(k)
+        n = (C.c_longlong * k)()
         self._check(lib().raptor_profile_read(self._h, _dp(ms), n), "raptor_profile_read")
-        return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(10)}
+        return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(k)}
 
     # ---- learned surrogate -------------------------------------------------------------
     def surrogate_generate(self, n, seed=0x1801104520000005, spin=(0.0, 0.99), incl=(5.0, 85.0), states=False,
@@ -340,6 +343,10 @@ class Context:
     def surrogate_set(self, P):
         P = np.ascontiguousarray(P, dtype=np.float32)
         self._check(lib().raptor_surrogate_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size), "raptor_surrogate_set")
+
+    def surrogate_kernel(self, kind):
+        """Inference kernel: MLP_TCGEN05 (default) or MLP_MMA_SYNC."""
+        self._check(lib().raptor_surrogate_kernel(self._h, int(kind)), "raptor_surrogate_kernel")
 
     def surrogate_config(self, fallback_band=0.5, r_exit=50.0):
         self._check(lib().raptor_surrogate_config(self._h, float(fallback_band), float(r_exit)), "raptor_surrogate_config")

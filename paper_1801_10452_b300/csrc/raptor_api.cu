@@ -18,6 +18,7 @@
 #include "raptor_kernels_fp64.cuh"
 #include "raptor_kernels_mixed.cuh"
 #include "raptor_surrogate.cuh"
+#include "raptor_mlp_tc.cuh"
 
 using namespace raptor;
 
@@ -56,7 +57,11 @@ struct raptor_ctx {
     float* s_G = nullptr;            // gradients
     float* s_m1 = nullptr;           // Adam moments
     float* s_m2 = nullptr;
-    __nv_bfloat16* s_w = nullptr;    // w2, w2t, w3, w3t (4 x 256 x 256)
+    __nv_bfloat16* s_w = nullptr;    // w2, w2t, w3, w3t, then w2, w3 in the tcgen05 operand layout (6 x 256 x 256)
+    int s_kernel = RAPTOR_MLP_TCGEN05;  // inference kernel
+    int* s_err = nullptr;            // device flag: a tensor-core wait ran out
+    __nv_bfloat16* s_h2tc = nullptr; // tcgen05 inference: h2 tiles (64 KB each)
+    size_t s_h2tc_tiles = 0;
     long long s_rows = 0;            // work-buffer rows
     float *s_x = nullptr, *s_z1 = nullptr, *s_z2 = nullptr, *s_z3 = nullptr, *s_out = nullptr, *s_dout = nullptr;
     float *s_dzf = nullptr, *s_dh = nullptr;
@@ -67,7 +72,7 @@ struct raptor_ctx {
     unsigned char* s_fb = nullptr;   // render: fallback flags
     double* s_start = nullptr;       // render: start states [8][rays]
     size_t s_ray_cap = 0;
-    double2* s_curve = nullptr;      // critical curve points
+    float2* s_curve = nullptr;       // critical curve points (FP32)
     double s_band = 0.5, s_r_exit = 50.0;
     unsigned long long s_step = 0;   // Adam step counter
     // per-kernel CUDA-event timing (raptor_profile)
@@ -91,14 +96,15 @@ cudaEvent_t take_event(raptor_ctx* c) {
     return e;
 }
 
-// Bracket one kernel launch with events on its stream when profiling is on.
+// Bracket one kernel launch (or `kernels` launches) with events on its stream when
+// profiling is on; the slot's launch counter counts kernels.
 struct ProfScope {
     raptor_ctx* c;
     int slot;
     cudaStream_t s;
     cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(raptor_ctx* c_, int slot_, cudaStream_t s_) : c(c_), slot(slot_), s(s_) {
-        c->prof_launches[slot] += 1;
+    ProfScope(raptor_ctx* c_, int slot_, cudaStream_t s_, int kernels = 1) : c(c_), slot(slot_), s(s_) {
+        c->prof_launches[slot] += kernels;
         if (c->prof) {
             a = take_event(c);
             b = take_event(c);
@@ -344,6 +350,7 @@ cudaError_t launch_mixed(raptor_ctx* c, const Params& p, cudaStream_t s) {
 }
 
 raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t s);
+raptor_status check_tc_err(raptor_ctx* ctx);
 
 // Enqueue every ray of `p` (all frequency chunks), then the flux reduction of `planes`
 // image planes into c->d_flux.
@@ -555,6 +562,7 @@ raptor_status raptor_render_ex(raptor_ctx* ctx, const double* freqs_hz, int n_fr
     if (flux_jy_host) {
         RCK(cudaMemcpyAsync(flux_jy_host, ctx->d_flux, n_freq * sizeof(double), cudaMemcpyDeviceToHost, s));
         RCK(cudaStreamSynchronize(s));
+        if (ctx->cam.precision == RAPTOR_MIXED_MLP) return check_tc_err(ctx);
     }
     return RAPTOR_OK;
 }
@@ -713,7 +721,7 @@ void raptor_destroy(raptor_ctx* ctx) {
     free_mixed_queues(ctx->mq);
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
-                  ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->s_curve};
+                  ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->s_curve, ctx->s_err, ctx->s_h2tc};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.second.first);
@@ -749,7 +757,9 @@ cudaError_t sur_alloc(raptor_ctx* c) {
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_G, n * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_m1, n * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_m2, n * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_w, 4 * kHid * kHid * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_w, 6 * kHid * kHid * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->s_err, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->s_G, 0, n * sizeof(float));
         if (e != cudaSuccess) return e;
     }
@@ -779,6 +789,15 @@ __nv_bfloat16* w2b(raptor_ctx* c) { return c->s_w; }
 __nv_bfloat16* w2t(raptor_ctx* c) { return c->s_w + kHid * kHid; }
 __nv_bfloat16* w3b(raptor_ctx* c) { return c->s_w + 2 * kHid * kHid; }
 __nv_bfloat16* w3t(raptor_ctx* c) { return c->s_w + 3 * kHid * kHid; }
+__nv_bfloat16* wtc(raptor_ctx* c) { return c->s_w + 4 * kHid * kHid; }  // [2][256 x 256], operand layout
+
+// BF16 copies of the hidden weights (GEMM layouts and the tcgen05 operand layout) from the
+// FP32 master parameters.
+cudaError_t refresh_weights(raptor_ctx* c, cudaStream_t s) {
+    k_refresh_bf16<<<256, 256, 0, s>>>(c->s_P, w2b(c), w2t(c), w3b(c), w3t(c));
+    k_tc_pack<<<256, 256, 0, s>>>(c->s_P, wtc(c));
+    return cudaGetLastError();
+}
 
 // Forward pass on `rows` rows already in c->s_x (rows_valid of them real).
 cudaError_t sur_forward(raptor_ctx* c, long long rows, long long rows_valid, cudaStream_t s) {
@@ -819,11 +838,42 @@ cudaError_t sur_backward(raptor_ctx* c, long long rows, int* nb_out, cudaStream_
     return cudaGetLastError();
 }
 
-// Evaluate n rows of raw inputs into normalised outputs out_dev [n][kOut] (fused kernel).
+// Evaluate n rows of raw inputs into normalised outputs out_dev [n][kOut]: two persistent
+// tcgen05 kernels (one CTA per SM, each hidden layer's weights resident in shared memory)
+// or the fused mma.sync kernel.
 cudaError_t sur_eval_rows(raptor_ctx* c, const float* inputs, long long n, float* out_dev, cudaStream_t s) {
-    const long long blocks = (n + kFRows - 1) / kFRows;
-    k_mlp_fused<<<(unsigned)blocks, 256, 0, s>>>(c->s_P, w2b(c), w3b(c), inputs, n, out_dev);
+    if (c->s_kernel == RAPTOR_MLP_MMA_SYNC) {
+        const long long blocks = (n + kFRows - 1) / kFRows;
+        k_mlp_fused<<<(unsigned)blocks, 256, 0, s>>>(c->s_P, w2b(c), w3b(c), inputs, n, out_dev);
+        return cudaGetLastError();
+    }
+    const long long tiles = (n + kTcRows - 1) / kTcRows;
+    cudaError_t e = cudaSuccess;
+    if ((size_t)tiles > c->s_h2tc_tiles) {
+        e = cudaFree(c->s_h2tc);
+        c->s_h2tc = nullptr;
+        c->s_h2tc_tiles = 0;
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_h2tc, (size_t)tiles * kTcTileBytes);
+        if (e != cudaSuccess) return e;
+        c->s_h2tc_tiles = (size_t)tiles;
+    }
+    e = cudaFuncSetAttribute(k_mlp_tc12, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc12Smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc34, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc34Smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<long long>(tiles, c->num_sms);
+    k_mlp_tc12<<<grid, kTcThreads, kTc12Smem, s>>>(c->s_P, wtc(c), inputs, n, c->s_h2tc, c->s_err);
+    k_mlp_tc34<<<grid, kTcThreads, kTc34Smem, s>>>(c->s_P, wtc(c) + kHid * kHid, c->s_h2tc, n, out_dev, c->s_err);
     return cudaGetLastError();
+}
+
+// After a synchronisation: report (and clear) a tensor-core wait that ran out.
+raptor_status check_tc_err(raptor_ctx* ctx) {
+    if (!ctx->s_err) return RAPTOR_OK;
+    int flag = 0;
+    RCK(cudaMemcpy(&flag, ctx->s_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return RAPTOR_OK;
+    RCK(cudaMemset(ctx->s_err, 0, sizeof(int)));
+    return fail(ctx, RAPTOR_ECUDA, "surrogate inference: a tensor-core wait exceeded its time limit");
 }
 
 // Critical curve on the image plane (Bardeen 1973): photon-orbit radius r gives
@@ -937,7 +987,7 @@ raptor_status raptor_surrogate_init(raptor_ctx* ctx, const double* targets_dev, 
     RCK(cudaMemcpyAsync(ctx->s_P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     RCK(cudaMemsetAsync(ctx->s_m1, 0, MlpLayout::SIZE * sizeof(float), s));
     RCK(cudaMemsetAsync(ctx->s_m2, 0, MlpLayout::SIZE * sizeof(float), s));
-    k_refresh_bf16<<<256, 256, 0, s>>>(ctx->s_P, w2b(ctx), w2t(ctx), w3b(ctx), w3t(ctx));
+    RCK(refresh_weights(ctx, s));
     RCK(cudaGetLastError());
     RCK(cudaStreamSynchronize(s));
     ctx->s_step = 0;
@@ -971,7 +1021,7 @@ raptor_status raptor_surrogate_train(raptor_ctx* ctx, const float* inputs_dev, c
         const float lr_t = (float)(lr_it * std::sqrt(1.0 - std::pow(b2, t)) / (1.0 - std::pow(b1, t)));
         k_adam<<<ew_blocks(MlpLayout::NORM), 256, 0, s>>>(ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, MlpLayout::NORM, lr_t, b1,
                                                          b2, 1e-8f);
-        k_refresh_bf16<<<256, 256, 0, s>>>(ctx->s_P, w2b(ctx), w2t(ctx), w3b(ctx), w3t(ctx));
+        RCK(refresh_weights(ctx, s));
         RCK(cudaGetLastError());
         if (loss_host) {
             double parts[64];
@@ -1030,6 +1080,8 @@ raptor_status raptor_surrogate_eval(raptor_ctx* ctx, const float* inputs_dev, lo
     }
     cudaFreeAsync(out, s);
     if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, cudaGetErrorString(e));
+    const raptor_status te = check_tc_err(ctx);
+    if (te != RAPTOR_OK) return te;
     std::vector<double> pr((size_t)n * kOutUsed);
     for (long long i = 0; i < n; ++i)
         for (int q = 0; q < kOutUsed; ++q)
@@ -1056,11 +1108,18 @@ raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, in
     RCK(cudaMemcpy(ctx->s_P, params_host, n * sizeof(float), cudaMemcpyHostToDevice));
     RCK(cudaMemset(ctx->s_m1, 0, n * sizeof(float)));
     RCK(cudaMemset(ctx->s_m2, 0, n * sizeof(float)));
-    k_refresh_bf16<<<256, 256>>>(ctx->s_P, w2b(ctx), w2t(ctx), w3b(ctx), w3t(ctx));
+    RCK(refresh_weights(ctx, nullptr));
     RCK(cudaGetLastError());
     RCK(cudaDeviceSynchronize());
     ctx->sur_ready = true;
     ctx->s_step = 0;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (kind != RAPTOR_MLP_TCGEN05 && kind != RAPTOR_MLP_MMA_SYNC) return fail(ctx, RAPTOR_EINVAL, "unknown surrogate kernel");
+    ctx->s_kernel = kind;
     return RAPTOR_OK;
 }
 
@@ -1095,18 +1154,35 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
         RCK(cudaMalloc((void**)&ctx->s_start, rays * 8 * sizeof(double)));
         ctx->s_ray_cap = rays;
     }
-    const int n_curve = 512;
-    if (!ctx->s_curve) RCK(cudaMalloc((void**)&ctx->s_curve, n_curve * sizeof(double2)));
-    std::vector<double> cc = critical_curve(p.a, p.incl, n_curve);
+    const int n_curve = kMaxCurve;
+    if (!ctx->s_curve) RCK(cudaMalloc((void**)&ctx->s_curve, n_curve * sizeof(float2)));
+    const std::vector<double> cc = critical_curve(p.a, p.incl, n_curve);
     const int nc = (int)(cc.size() / 2);
-    RCK(cudaMemcpyAsync(ctx->s_curve, cc.data(), cc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    // FP32 vertices (pageable source: the copy is staged before the call returns) and the
+    // bounding box grown by the band
+    std::vector<float2> cf(nc);
+    float4 box = make_float4(3e38f, -3e38f, 3e38f, -3e38f);
+    for (int q = 0; q < nc; ++q) {
+        cf[q] = make_float2((float)cc[2 * q], (float)cc[2 * q + 1]);
+        box.x = std::min(box.x, cf[q].x);
+        box.y = std::max(box.y, cf[q].x);
+        box.z = std::min(box.z, cf[q].y);
+        box.w = std::max(box.w, cf[q].y);
+    }
+    const float grow = (float)ctx->s_band + 1e-3f;
+    box = make_float4(box.x - grow, box.y + grow, box.z - grow, box.w + grow);
+    if (nc > 0) RCK(cudaMemcpyAsync(ctx->s_curve, cf.data(), nc * sizeof(float2), cudaMemcpyHostToDevice, s));
     float* out = nullptr;
     RCK(cudaMallocAsync((void**)&out, rays * kOut * sizeof(float), s));
     {
-        ProfScope ps(ctx, kProfSurrogate, s);
-        k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_curve, nc, ctx->s_band, ctx->s_in, ctx->s_fb);
+        ProfScope ps(ctx, kProfSurrogate, s, 2);  // inputs and start states; the network nests below
+        k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_curve, nc, (float)ctx->s_band, box,
+                                                                       ctx->s_in, ctx->s_fb);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = sur_eval_rows(ctx, ctx->s_in, (long long)rays, out, s);
+        if (e == cudaSuccess) {
+            ProfScope pm(ctx, kProfSurrogateMlp, s, ctx->s_kernel == RAPTOR_MLP_MMA_SYNC ? 1 : 2);
+            e = sur_eval_rows(ctx, ctx->s_in, (long long)rays, out, s);
+        }
         if (e == cudaSuccess) {
             k_surrogate_states<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_P, out, ctx->s_start);
             e = cudaGetLastError();

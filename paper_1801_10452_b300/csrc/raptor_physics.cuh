@@ -82,8 +82,8 @@ RAPTOR_HD float pv<float>(double, float f) { return f; }
 // k_theta = sign(beta) sqrt|Q - L^2 cot^2 theta + a^2 cos^2 theta| = beta, k_r from k.k = 0 with
 // the physical photon moving outward at the camera; the state is the backward ray -k.
 // ------------------------------------------------------------------------------------
-RAPTOR_HD void camera_ray_ai(double a, double sn, double cs, double incl, double r, double alpha, double beta,
-                             double t_cam, double x[4], double k[4]) {
+// Wave vector of the camera ray through (alpha, beta) (KS components of the backward ray).
+RAPTOR_HD void camera_k_ai(double a, double sn, double cs, double r, double alpha, double beta, double k[4]) {
     const double a2 = a * a;
     const double L = -alpha * sn;
     const double kt = -1.0, kp = L;
@@ -107,12 +107,24 @@ RAPTOR_HD void camera_ray_ai(double a, double sn, double cs, double incl, double
     k[1] = ur;
     k[2] = uh;
     k[3] = up + a / Del * ur;
+}
+
+// KS position of the camera (the same for every pixel): BL (t_cam, r, incl, 0) -> KS.
+RAPTOR_HD void camera_x_ai(double a, double incl, double r, double t_cam, double x[4]) {
+    const double a2 = a * a;
+    const double Del = r * r - 2.0 * r + a2;
     const double rp = 1.0 + sqrt(1.0 - a2), rm = 1.0 - sqrt(1.0 - a2);
     const double lg = log((r - rp) / (r - rm));
     x[0] = t_cam + log(Del) + 2.0 / (rp - rm) * lg;
     x[1] = r;
     x[2] = incl;
     x[3] = a / (rp - rm) * lg;
+}
+
+RAPTOR_HD void camera_ray_ai(double a, double sn, double cs, double incl, double r, double alpha, double beta,
+                             double t_cam, double x[4], double k[4]) {
+    camera_k_ai(a, sn, cs, r, alpha, beta, k);
+    camera_x_ai(a, incl, r, t_cam, x);
 }
 
 RAPTOR_HD void camera_ray(const Params& p, double alpha, double beta, double t_cam, double x[4], double k[4]) {

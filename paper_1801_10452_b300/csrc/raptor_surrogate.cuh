@@ -154,7 +154,9 @@ struct MlpLayout {
     static constexpr int SIZE = NORM + 24;
 };
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// SiLU with the hardware exponential and reciprocal (the argument of exp is capped at 80 so
+// that 1 + e^-z stays inside the approximate division's range; below z = -80, silu is ~0).
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(fminf(-z, 80.f))); }
 __device__ __forceinline__ float dsilu(float z) {
     const float s = 1.f / (1.f + __expf(-z));
     return s * (1.f + z * (1.f - s));
@@ -592,41 +594,50 @@ RAPTOR_HD void surrogate_state(double a, double sn_i, double cs_i, double alpha,
 }
 
 // Per ray of a render: network inputs (alpha, beta, a, i in degrees) and the fallback flag:
-// pixel centre within `band` M of the critical curve (n_curve points in order around the
-// closed curve) or inside it (captured rays, whose near-horizon emission is too sensitive
-// to the hand-off state for the surrogate's accuracy).
-__global__ void k_surrogate_prepare(const Params p, const double2* __restrict__ curve, int n_curve, double band,
-                                    float* __restrict__ inputs, unsigned char* __restrict__ fallback) {
+// pixel centre within `band` M of the critical curve (n_curve <= kMaxCurve points in order
+// around the closed curve, FP32) or inside it (captured rays, whose near-horizon emission is
+// too sensitive to the hand-off state for the surrogate's accuracy).  Pixels outside the
+// curve's bounding box grown by the band (`box` = alpha_min, alpha_max, beta_min, beta_max)
+// are neither, and skip the polygon loop.
+constexpr int kMaxCurve = 512;
+__global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const float2* __restrict__ curve, int n_curve,
+                                                           float band, float4 box, float* __restrict__ inputs,
+                                                           unsigned char* __restrict__ fallback) {
+    __shared__ float2 sc[kMaxCurve];
+    for (int c = threadIdx.x; c < n_curve; c += blockDim.x) sc[c] = curve[c];
+    __syncthreads();
+    const float a_f = p.f.a, inc_deg = (float)(p.incl * (180.0 / kPi));
+    const float band2 = band * band;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < p.n_rays;
          id += (long long)gridDim.x * blockDim.x) {
         const int frame = (int)(id / p.n_pix);
         const int pix = (int)(id - (long long)frame * p.n_pix);
         const int row = p.row0 + pix / p.nx, col = pix % p.nx;
-        const double al = p.amin + (col + 0.5) * p.da, be = p.bmin + (row + 0.5) * p.db;
-        inputs[id * kIn + 0] = (float)al;
-        inputs[id * kIn + 1] = (float)be;
-        inputs[id * kIn + 2] = (float)p.a;
-        inputs[id * kIn + 3] = (float)(p.incl * (180.0 / kPi));
-        // FP32 distance to the curve and even-odd inside test (captured rays lie inside the
-        // closed critical curve); the band edge needs no more precision.
-        float d2 = 3.0e38f;
-        bool inside = false;
-        const float alf = (float)al, bef = (float)be;
-        for (int c = 0; c < n_curve; ++c) {
-            const float x1 = (float)curve[c].x, y1 = (float)curve[c].y;
-            const int c2 = c + 1 < n_curve ? c + 1 : 0;
-            const float x2 = (float)curve[c2].x, y2 = (float)curve[c2].y;
-            const float dx = alf - x1, dy = bef - y1;
-            d2 = fminf(d2, dx * dx + dy * dy);
-            if ((y1 > bef) != (y2 > bef) && alf < x1 + (bef - y1) * (x2 - x1) / (y2 - y1)) inside = !inside;
+        const float alf = (float)(p.amin + (col + 0.5) * p.da), bef = (float)(p.bmin + (row + 0.5) * p.db);
+        reinterpret_cast<float4*>(inputs)[id] = make_float4(alf, bef, a_f, inc_deg);
+        unsigned char fb = 0;
+        if (alf >= box.x && alf <= box.y && bef >= box.z && bef <= box.w) {
+            // distance to the curve's vertices and even-odd inside test, in FP32 (the band
+            // edge needs no more precision)
+            float d2 = 3.0e38f;
+            bool inside = false;
+            for (int c = 0; c < n_curve; ++c) {
+                const float2 v1 = sc[c], v2 = sc[c + 1 < n_curve ? c + 1 : 0];
+                const float dx = alf - v1.x, dy = bef - v1.y;
+                d2 = fminf(d2, dx * dx + dy * dy);
+                if ((v1.y > bef) != (v2.y > bef) && alf < v1.x + (bef - v1.y) * (v2.x - v1.x) / (v2.y - v1.y)) inside = !inside;
+            }
+            fb = (inside || d2 < band2) ? 1 : 0;
         }
-        fallback[id] = (inside || d2 < (float)(band * band)) ? 1 : 0;
+        fallback[id] = fb;
     }
 }
 
 // Denormalise the network outputs and rebuild the start states [8][n_rays].
 __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, const float* __restrict__ out,
                                    double* __restrict__ start_xk) {
+    double xc[4];  // camera position at t_cam = 0 (the same for every pixel)
+    camera_x_ai(p.a, p.incl, p.r_cam, 0.0, xc);
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < p.n_rays;
          id += (long long)gridDim.x * blockDim.x) {
         const int frame = (int)(id / p.n_pix);
@@ -636,7 +647,11 @@ __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, 
         // KS state of the camera ray for this frame, and the flat-space baseline
         double x0[4], k0[4];
         const double tc = p.t_frames ? p.t_frames[frame] : p.t_cam;
-        camera_ray(p, al, be, tc, x0, k0);
+        camera_k_ai(p.a, p.sin_i, p.cos_i, p.r_cam, al, be, k0);
+        x0[0] = tc + xc[0];
+        x0[1] = xc[1];
+        x0[2] = xc[2];
+        x0[3] = xc[3];
         float base[kOutUsed];
         surrogate_baseline(x0, k0, p.f.eps, base);
         double pred[kOutUsed];
