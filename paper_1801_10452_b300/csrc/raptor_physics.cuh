@@ -82,31 +82,37 @@ RAPTOR_HD float pv<float>(double, float f) { return f; }
 // k_theta = sign(beta) sqrt|Q - L^2 cot^2 theta + a^2 cos^2 theta| = beta, k_r from k.k = 0 with
 // the physical photon moving outward at the camera; the state is the backward ray -k.
 // ------------------------------------------------------------------------------------
-// Wave vector of the camera ray through (alpha, beta) (KS components of the backward ray).
-RAPTOR_HD void camera_k_ai(double a, double sn, double cs, double r, double alpha, double beta, double k[4]) {
-    const double a2 = a * a;
-    const double L = -alpha * sn;
-    const double kt = -1.0, kp = L;
+// Wave vector of the camera ray through (alpha, beta) (KS components of the backward ray),
+// in arithmetic type T (FP64 for the integrator; FP32 for the learned surrogate's baseline).
+template <typename T>
+RAPTOR_HD void camera_k_t(T a, T sn, T cs, T r, T alpha, T beta, T k[4]) {
+    const T a2 = a * a;
+    const T L = -alpha * sn;
+    const T kt = T(-1), kp = L;
     // At theta = i, Q - L^2 cot^2 + a^2 cos^2 = beta^2 exactly, so the square root of Eq. 28
     // is |beta|: k_theta = beta.  (The printed form cancels two alpha^2 cos^2 i terms, whose
     // rounding residual its square root would magnify to ~1e-8 at beta = 0.)
-    const double kh = beta;
+    const T kh = beta;
     // Boyer-Lindquist inverse metric at the camera
-    const double s2 = sn * sn;
-    const double Sig = r * r + a2 * cs * cs, Del = r * r - 2.0 * r + a2;
-    const double A = (r * r + a2) * (r * r + a2) - a2 * Del * s2;
-    const double iSD = 1.0 / (Sig * Del);
-    const double gtt = -A * iSD, gtp = -2.0 * a * r * iSD, grr = Del / Sig, ghh = 1.0 / Sig;
-    const double gpp = (Del - a2 * s2) * iSD / s2;
-    const double rest = gtt * kt * kt + 2.0 * gtp * kt * kp + gpp * kp * kp + ghh * kh * kh;
-    const double kr = sqrt(-rest / grr);
+    const T s2 = sn * sn;
+    const T Sig = r * r + a2 * cs * cs, Del = r * r - T(2) * r + a2;
+    const T A = (r * r + a2) * (r * r + a2) - a2 * Del * s2;
+    const T iSD = T(1) / (Sig * Del);
+    const T gtt = -A * iSD, gtp = -T(2) * a * r * iSD, grr = Del / Sig, ghh = T(1) / Sig;
+    const T gpp = (Del - a2 * s2) * iSD / s2;
+    const T rest = gtt * kt * kt + T(2) * gtp * kt * kp + gpp * kp * kp + ghh * kh * kh;
+    const T kr = Real<T>::sqrt_(-rest / grr);
     // contravariant BL components of the backward ray
-    const double ut = -(gtt * kt + gtp * kp), ur = -(grr * kr), uh = -(ghh * kh), up = -(gtp * kt + gpp * kp);
+    const T ut = -(gtt * kt + gtp * kp), ur = -(grr * kr), uh = -(ghh * kh), up = -(gtp * kt + gpp * kp);
     // BL -> KS (App. A.1)
-    k[0] = ut + 2.0 * r / Del * ur;
+    k[0] = ut + T(2) * r / Del * ur;
     k[1] = ur;
     k[2] = uh;
     k[3] = up + a / Del * ur;
+}
+
+RAPTOR_HD void camera_k_ai(double a, double sn, double cs, double r, double alpha, double beta, double k[4]) {
+    camera_k_t<double>(a, sn, cs, r, alpha, beta, k);
 }
 
 // KS position of the camera (the same for every pixel): BL (t_cam, r, incl, 0) -> KS.

@@ -51,43 +51,55 @@ struct SurrogateRange {
 
 // Flat-space baseline: the camera ray's initial state (KS at r_cam) continued as a straight
 // line (r, theta, phi read as spherical coordinates, M -> 0), advanced by the same step rule
-// for kSurrogateSteps steps, in FP32.  It is a fixed, smooth function of the inputs; the
+// for kSurrogateSteps steps, all in FP32.  It is a fixed, smooth function of the inputs; the
 // network learns only the difference between the integrator and this baseline (the
 // gravitational deflection and delay, a few per cent), which BF16 layers resolve far better
 // than the state itself.  Output as the targets: dt, ln r, theta, phi, k^theta, k^r.
-RAPTOR_HD void surrogate_baseline(const double x0[4], const double k0[4], float eps, float out[kOutUsed]) {
-    const float r = (float)x0[1], th = (float)x0[2], ph = (float)x0[3];
+RAPTOR_HD void surrogate_baseline(const float x0[4], const float k0[4], float eps, float out[kOutUsed]) {
+    const float r = x0[1], th = x0[2], ph = x0[3];
     const float st = sinf(th), ct = cosf(th), sp = sinf(ph), cp = cosf(ph);
     // position and velocity in Cartesian components
     float px = r * st * cp, py = r * st * sp, pz = r * ct;
-    const float kr = (float)k0[1], kh = (float)k0[2], kp = (float)k0[3];
+    const float kr = k0[1], kh = k0[2], kp = k0[3];
     const float vx = kr * st * cp + r * kh * ct * cp - r * st * kp * sp;
     const float vy = kr * st * sp + r * kh * ct * sp + r * st * kp * cp;
     const float vz = kr * ct - r * kh * st;
-    const float kt = (float)k0[0];
-    float lam = 0.f;
-    float xs[4], ks[4];
+    const float kt = k0[0];
+    float lam = 0.f, rr = r, thn = th, vr = kr, vth = kh;
     for (int n = 0; n <= kSurrogateSteps; ++n) {
-        const float rr = sqrtf(px * px + py * py + pz * pz);
-        const float rho = sqrtf(px * px + py * py);
-        const float thn = atan2f(rho, pz), phn = atan2f(py, px);
-        const float sth = rho / rr, cth = pz / rr, cph = px / fmaxf(rho, 1e-30f), sph = py / fmaxf(rho, 1e-30f);
-        const float vr = (vx * px + vy * py + vz * pz) / rr;
-        const float vth = (vx * cth * cph + vy * cth * sph - vz * sth) / rr;
-        const float vph = (-vx * sph + vy * cph) / fmaxf(rho, 1e-30f);
-        xs[0] = kt * lam; xs[1] = rr; xs[2] = thn; xs[3] = phn;
-        ks[0] = kt; ks[1] = vr; ks[2] = vth; ks[3] = vph;
+        // spherical components: r, theta and the rates dr, dtheta, dphi per unit lambda
+        const float rho2 = px * px + py * py;
+        rr = sqrtf(rho2 + pz * pz);
+        const float rho = sqrtf(rho2), irr = 1.f / rr;
+        thn = atan2f(rho, pz);
+        const float vp = vx * px + vy * py;
+        vr = (vp + vz * pz) * irr;
+        vth = (pz * vp / fmaxf(rho, 1e-30f) - vz * rho) * irr * irr;
         if (n == kSurrogateSteps) break;
+        const float vph = (vy * px - vx * py) / fmaxf(rho2, 1e-30f);
+        const float xs[4] = {0.f, rr, thn, 0.f}, ks[4] = {kt, vr, vth, vph};
         const float dl = step_size<float>(eps, false, xs, ks);
-        px += vx * dl; py += vy * dl; pz += vz * dl;
+        px += vx * dl;
+        py += vy * dl;
+        pz += vz * dl;
         lam += dl;
     }
-    out[0] = xs[0];
-    out[1] = logf(xs[1]);
-    out[2] = xs[2];
-    out[3] = xs[3];
-    out[4] = ks[2];
-    out[5] = ks[1];
+    out[0] = kt * lam;
+    out[1] = logf(rr);
+    out[2] = thn;
+    out[3] = atan2f(py, px);
+    out[4] = vth;
+    out[5] = vr;
+}
+
+// The baseline of the ray through (alpha, beta) from the camera parameters: the camera wave
+// vector in FP32 (phi0: the camera's KS azimuth).  Training and rendering both use this.
+RAPTOR_HD void surrogate_base(float a, float sn_i, float cs_i, float incl, float r_cam, float phi0, float alpha, float beta,
+                              float eps, float out[kOutUsed]) {
+    float k0[4];
+    camera_k_t<float>(a, sn_i, cs_i, r_cam, alpha, beta, k0);
+    const float x0[4] = {0.f, r_cam, incl, phi0};
+    surrogate_baseline(x0, k0, eps, out);
 }
 
 // Integrator state after kSurrogateSteps steps (FP64) minus the baseline: the targets
@@ -95,10 +107,12 @@ RAPTOR_HD void surrogate_baseline(const double x0[4], const double k0[4], float 
 RAPTOR_HD void surrogate_targets(double a, double incl_deg, double r_cam, double eps, double alpha, double beta,
                                  double out[kOutUsed], double* raw = nullptr) {
     const double inc = incl_deg * (kPi / 180.0);
+    const double sn = sin(inc), cs = cos(inc);
     double x[4], k[4];
-    camera_ray_ai(a, sin(inc), cos(inc), inc, r_cam, alpha, beta, 0.0, x, k);
+    camera_ray_ai(a, sn, cs, inc, r_cam, alpha, beta, 0.0, x, k);
     float base[kOutUsed];
-    surrogate_baseline(x, k, (float)eps, base);
+    surrogate_base((float)a, (float)sn, (float)cs, (float)inc, (float)r_cam, (float)x[3], (float)alpha, (float)beta,
+                   (float)eps, base);
     const double t0 = x[0];
     for (int n = 0; n < kSurrogateSteps; ++n) rk4_step<double>(a, x, k, step_size<double>(eps, false, x, k));
     out[0] = x[0] - t0 - base[0];
@@ -558,35 +572,39 @@ __global__ void k_gather_batch(const float* __restrict__ x, const double* __rest
 }
 
 // ---------------------------------------------------------------------------------------
-// Reconstruction of the integrator state from a prediction (FP64): position from the
-// network; k_t = 1 and k_phi = -L of the backward ray; |k_theta| from the Carter constant
-// with the predicted sign of k^theta; k^r from the null condition with the predicted sign.
+// Reconstruction of the integrator state from a prediction (FP32: the prediction's own
+// error, ~1e-5 of the state, is far above FP32 rounding): position from the network
+// (x[0] the offset from the camera's KS time); k_t = 1 and k_phi = -L of the backward ray;
+// |k_theta| from the Carter constant with the predicted sign of k^theta; k^r from the null
+// condition with the predicted sign.
 // ---------------------------------------------------------------------------------------
-RAPTOR_HD void surrogate_state(double a, double sn_i, double cs_i, double alpha, double beta, const double pred[kOutUsed],
-                               double t_cam_ks, double x[4], double k[4]) {
-    const double a2 = a * a;
-    const double L = -alpha * sn_i;                              // physical photon, E = 1
-    const double Q = beta * beta + cs_i * cs_i * (alpha * alpha - a2);
-    const double r = exp(pred[1]), th = pred[2];
-    x[0] = t_cam_ks + pred[0];
+RAPTOR_HD void surrogate_state(float a, float sn_i, float cs_i, float alpha, float beta, const float pred[kOutUsed],
+                               float x[4], float k[4]) {
+    const float a2 = a * a;
+    const float L = -alpha * sn_i;                              // physical photon, E = 1
+    const float Q = beta * beta + cs_i * cs_i * (alpha * alpha - a2);
+    const float r = expf(pred[1]), th = pred[2];
+    x[0] = pred[0];
     x[1] = r;
     x[2] = th;
     x[3] = pred[3];
-    const double sn = sin(th), cs = cos(th), s2 = sn * sn;
-    const double Sig = r * r + a2 * cs * cs, iS = 1.0 / Sig, z = 2.0 * r * iS;
-    const double Del = r * r - 2.0 * r + a2;
-    double Th = Q + a2 * cs * cs - L * L * cs * cs / s2;
-    if (Th < 0.0) Th = 0.0;
-    const double kct = 1.0, kcp = -L;                            // backward-ray covariant components
-    const double kch = (pred[4] >= 0.0 ? 1.0 : -1.0) * sqrt(Th);  // sign(k_theta) = sign(k^theta)
+    float sn, cs;
+    sc(th, &sn, &cs);
+    const float s2 = sn * sn;
+    const float Sig = r * r + a2 * cs * cs, iS = 1.f / Sig, z = 2.f * r * iS;
+    const float Del = r * r - 2.f * r + a2;
+    float Th = Q + a2 * cs * cs - L * L * cs * cs / s2;
+    if (Th < 0.f) Th = 0.f;
+    const float kct = 1.f, kcp = -L;                            // backward-ray covariant components
+    const float kch = (pred[4] >= 0.f ? 1.f : -1.f) * sqrtf(Th);  // sign(k_theta) = sign(k^theta)
     // KS inverse metric
-    const double gtt = -(1.0 + z), gtr = z, grr = Del * iS, grp = a * iS, ghh = iS, gpp = iS / s2;
-    const double Bq = gtr * kct + grp * kcp;
-    const double Cq = gtt * kct * kct + ghh * kch * kch + gpp * kcp * kcp;
-    double D = Bq * Bq - grr * Cq;
-    if (D < 0.0) D = 0.0;
-    const double kr_up = (pred[5] >= 0.0 ? 1.0 : -1.0) * sqrt(D);  // k^r = Bq + grr k_r
-    const double kcr = (kr_up - Bq) / grr;
+    const float gtt = -(1.f + z), gtr = z, grr = Del * iS, grp = a * iS, ghh = iS, gpp = iS / s2;
+    const float Bq = gtr * kct + grp * kcp;
+    const float Cq = gtt * kct * kct + ghh * kch * kch + gpp * kcp * kcp;
+    float D = Bq * Bq - grr * Cq;
+    if (D < 0.f) D = 0.f;
+    const float kr_up = (pred[5] >= 0.f ? 1.f : -1.f) * sqrtf(D);  // k^r = Bq + grr k_r
+    const float kcr = (kr_up - Bq) / grr;
     k[0] = gtt * kct + gtr * kcr;
     k[1] = kr_up;
     k[2] = ghh * kch;
@@ -633,37 +651,42 @@ __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const
     }
 }
 
-// Denormalise the network outputs and rebuild the start states [8][n_rays].
+// Denormalise the network outputs and rebuild the start states [8][n_rays] (FP32 except the
+// camera time and the pixel centres).
 __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, const float* __restrict__ out,
                                    double* __restrict__ start_xk) {
     double xc[4];  // camera position at t_cam = 0 (the same for every pixel)
     camera_x_ai(p.a, p.incl, p.r_cam, 0.0, xc);
+    const float af = p.f.a, sif = (float)p.sin_i, cif = (float)p.cos_i, incf = (float)p.incl, rcf = (float)p.r_cam;
+    const float ph0 = (float)xc[3];
+    float mu[kOutUsed], sd[kOutUsed];
+#pragma unroll
+    for (int q = 0; q < kOutUsed; ++q) {
+        mu[q] = P[MlpLayout::NORM + 8 + q];
+        sd[q] = P[MlpLayout::NORM + 16 + q];
+    }
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < p.n_rays;
          id += (long long)gridDim.x * blockDim.x) {
         const int frame = (int)(id / p.n_pix);
         const int pix = (int)(id - (long long)frame * p.n_pix);
         const int row = p.row0 + pix / p.nx, col = pix % p.nx;
-        const double al = p.amin + (col + 0.5) * p.da, be = p.bmin + (row + 0.5) * p.db;
-        // KS state of the camera ray for this frame, and the flat-space baseline
-        double x0[4], k0[4];
-        const double tc = p.t_frames ? p.t_frames[frame] : p.t_cam;
-        camera_k_ai(p.a, p.sin_i, p.cos_i, p.r_cam, al, be, k0);
-        x0[0] = tc + xc[0];
-        x0[1] = xc[1];
-        x0[2] = xc[2];
-        x0[3] = xc[3];
+        const float al = (float)(p.amin + (col + 0.5) * p.da), be = (float)(p.bmin + (row + 0.5) * p.db);
         float base[kOutUsed];
-        surrogate_baseline(x0, k0, p.f.eps, base);
-        double pred[kOutUsed];
-        for (int q = 0; q < kOutUsed; ++q)
-            pred[q] = (double)base[q] + (double)out[id * kOut + q] * (double)P[MlpLayout::NORM + 16 + q] +
-                      (double)P[MlpLayout::NORM + 8 + q];
-        double x[4], k[4];
-        surrogate_state(p.a, p.sin_i, p.cos_i, al, be, pred, x0[0], x, k);
-        for (int i = 0; i < 4; ++i) {
-            start_xk[(long long)i * p.n_rays + id] = x[i];
-            start_xk[(long long)(4 + i) * p.n_rays + id] = k[i];
-        }
+        surrogate_base(af, sif, cif, incf, rcf, ph0, al, be, p.f.eps, base);
+        const float4 o0 = reinterpret_cast<const float4*>(out)[2 * id];
+        const float4 o1 = reinterpret_cast<const float4*>(out)[2 * id + 1];
+        const float o[kOutUsed] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y};
+        float pred[kOutUsed];
+#pragma unroll
+        for (int q = 0; q < kOutUsed; ++q) pred[q] = base[q] + (o[q] * sd[q] + mu[q]);
+        float x[4], k[4];
+        surrogate_state(af, sif, cif, al, be, pred, x, k);
+        const double tc = p.t_frames ? p.t_frames[frame] : p.t_cam;
+        start_xk[id] = tc + xc[0] + (double)x[0];
+#pragma unroll
+        for (int i = 1; i < 4; ++i) start_xk[(long long)i * p.n_rays + id] = (double)x[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) start_xk[(long long)(4 + i) * p.n_rays + id] = (double)k[i];
     }
 }
 
