@@ -198,6 +198,13 @@ raptor_status raptor_stats_reset(raptor_ctx* ctx);
  * mixed path's FP64 passes (0 = the occupancy maximum). */
 raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm, int blocks_per_sm_fp64);
 
+/* Mixed path scheduling: rays whose pixel centre lies within crit_band M of the critical
+ * curve (Bardeen's closed form) form phase A1 and run their FP64 phase on a second stream,
+ * concurrently with the other rays' phases A2, B and C [0.5].  Only the schedule changes:
+ * every ray's arithmetic, and so every result, is the same for any crit_band >= 0.
+ * RAPTOR_EINVAL for a negative or non-finite band. */
+raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band);
+
 /* Autotuner: renders the context's camera once per candidate launch shape (threads per
  * block {64, 128}; blocks per SM of the ray kernels {max, 2, 3, 4}; for RAPTOR_MIXED also
  * blocks per SM of the FP64 passes {1, 2, 3, 4}), times each with CUDA events on `stream`

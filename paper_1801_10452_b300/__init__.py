@@ -31,6 +31,7 @@ EXPORTS = [
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
+    "raptor_mixed_config",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp"]
@@ -109,6 +110,7 @@ def lib():
             "raptor_surrogate_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
+            "raptor_mixed_config": (st, [vp, C.c_double]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -343,6 +345,10 @@ class Context:
     def surrogate_set(self, P):
         P = np.ascontiguousarray(P, dtype=np.float32)
         self._check(lib().raptor_surrogate_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size), "raptor_surrogate_set")
+
+    def mixed_config(self, crit_band=0.5):
+        """Near-critical band (M) whose rays run their FP64 phase on the second stream."""
+        self._check(lib().raptor_mixed_config(self._h, float(crit_band)), "raptor_mixed_config")
 
     def surrogate_kernel(self, kind):
         """Inference kernel: MLP_TCGEN05 (default) or MLP_MMA_SYNC."""

@@ -46,6 +46,15 @@ struct raptor_ctx {
     size_t rec_cap = 0;
     MixedQueues mq;               // mixed-precision hand-off queues
     size_t mq_cap = 0;
+    int* d_crit = nullptr;        // mixed path: near-critical ray ids (phase A1)
+    int* d_rest = nullptr;        // mixed path: the other ray ids (phase A2)
+    cudaStream_t s_long = nullptr;  // second stream of the mixed path (B-long)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    double crit_band = 0.5;       // M: near-critical band of the mixed path's B-long
+    float2* d_curve = nullptr;    // critical curve (FP32 vertices) of the current (a, i)
+    int n_curve = 0;
+    float4 curve_box = make_float4(0.f, 0.f, 0.f, 0.f);  // its bounding box
+    double curve_a = -1.0, curve_incl = -1.0;
     std::string err;
     cudaStream_t last_stream = nullptr;
     int launch_block = 128;       // threads per block of the persistent kernels
@@ -72,7 +81,6 @@ struct raptor_ctx {
     unsigned char* s_fb = nullptr;   // render: fallback flags
     double* s_start = nullptr;       // render: start states [8][rays]
     size_t s_ray_cap = 0;
-    float2* s_curve = nullptr;       // critical curve points (FP32)
     double s_band = 0.5, s_r_exit = 50.0;
     unsigned long long s_step = 0;   // Adam step counter
     // per-kernel CUDA-event timing (raptor_profile)
@@ -298,13 +306,61 @@ cudaError_t launch_fp64(raptor_ctx* c, const Params& p, cudaStream_t s) {
     return launch_fp64_nf<16>(c, p, s);
 }
 
-// Mixed precision: phase A (FP32, camera rays) -> phase B (FP64 queue, in passes of growing
-// step budget) -> phase C (FP32 queue), ordered by the stream.
+std::vector<double> critical_curve(double a, double incl, int n);
+int ew_blocks(long long n);
+
+// The critical curve of the camera's (a, i) as kMaxCurve FP32 vertices on the device, and its
+// bounding box (recomputed when a or i change).  The host vector is pageable: the copy is
+// staged before cudaMemcpyAsync returns.
+cudaError_t upload_curve(raptor_ctx* c, const Params& p, cudaStream_t s) {
+    if (!c->d_curve) {
+        cudaError_t e = cudaMalloc((void**)&c->d_curve, kMaxCurve * sizeof(float2));
+        if (e != cudaSuccess) return e;
+    }
+    if (c->curve_a == p.a && c->curve_incl == p.incl) return cudaSuccess;
+    const std::vector<double> cc = critical_curve(p.a, p.incl, kMaxCurve);
+    const int nc = (int)(cc.size() / 2);
+    std::vector<float2> cf(nc);
+    float4 box = make_float4(3e38f, -3e38f, 3e38f, -3e38f);
+    for (int q = 0; q < nc; ++q) {
+        cf[q] = make_float2((float)cc[2 * q], (float)cc[2 * q + 1]);
+        box.x = std::min(box.x, cf[q].x);
+        box.y = std::max(box.y, cf[q].x);
+        box.z = std::min(box.z, cf[q].y);
+        box.w = std::max(box.w, cf[q].y);
+    }
+    if (nc > 0) {
+        cudaError_t e = cudaMemcpyAsync(c->d_curve, cf.data(), nc * sizeof(float2), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    c->n_curve = nc;
+    c->curve_box = box;
+    c->curve_a = p.a;
+    c->curve_incl = p.incl;
+    return cudaSuccess;
+}
+
+// Mixed precision (per frequency chunk): split the rays into near-critical and other
+// (k_select_critical); phase A1 on the near-critical rays; snapshot of the FP64 queue; fork:
+// B-long (their FP64 phase, no step budget) on the context's second stream; on the caller's
+// stream phase A2, the FP64 passes of growing step budget on the other queued rays, phase C
+// on their leavers; join; phase C on B-long's leavers.
 constexpr int kPassBudget[kMaxPasses] = {16, 32, 48, 64, 96, 128, 256, 1 << 30};
+
+template <int NF, typename S>
+cudaError_t launch_fp64_phase(raptor_ctx* c, const Params& p, const PhaseIO& io, int blocks, cudaStream_t s) {
+    ProfScope ps(c, kProfMixedB, s);
+    k_mixed_fp64<NF, S><<<std::max(1, blocks), c->launch_block, 0, s>>>(p, io, c->mq.cap, c->d_counters, c->d_stats);
+    return cudaGetLastError();
+}
 
 template <int NF>
 cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s);
+    if (e == cudaSuccess) e = upload_curve(c, p, s);
+    if (e == cudaSuccess && !c->s_long) e = cudaStreamCreateWithFlags(&c->s_long, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->ev_fork) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->ev_join) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
     int occ32 = 0, occ64 = 0;
     const bool df = (p.flags & kFlagInnerDf64) != 0;
@@ -316,27 +372,96 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     const int b32 = grid_blocks(c, std::max(occ32, 1));
     const int b64 = c->num_sms * std::max(1, c->launch_bps64 > 0 ? std::min(c->launch_bps64, occ64) : occ64);
     const long long need = (p.n_rays + c->launch_block - 1) / c->launch_block;
+    const int bA = (int)std::max<long long>(1, std::min<long long>(b32, need));
+    const MixedQueues& mq = c->mq;
+    unsigned long long* cnt = c->d_counters;
+    auto fp64_phase = [&](const PhaseIO& io, int blocks, cudaStream_t st) {
+        return df ? launch_fp64_phase<NF, df64>(c, p, io, blocks, st) : launch_fp64_phase<NF, double>(c, p, io, blocks, st);
+    };
+    // near-critical / other split
+    const float grow = (float)c->crit_band + 1e-3f;
+    const float4 box = make_float4(c->curve_box.x - grow, c->curve_box.y + grow, c->curve_box.z - grow, c->curve_box.w + grow);
+    k_select_critical<<<ew_blocks(p.n_rays), 256, 0, s>>>(p, c->d_curve, c->n_curve, (float)c->crit_band, box, c->d_crit,
+                                                          c->d_rest, cnt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // phase A1
+    PhaseIO a1{};
+    a1.fresh = c->d_crit;
+    a1.push = mq.q64;
+    a1.fetch = kCntFreshCrit;
+    a1.total = kCntListCrit;
+    a1.push_cnt = kCntPush64;
+    a1.requeue_cnt = -1;
     {
         ProfScope ps(c, kProfMixedA, s);
-        k_mixed_fp32<NF><<<(int)std::max<long long>(1, std::min<long long>(b32, need)), c->launch_block, 0, s>>>(
-            p, c->mq, c->d_counters, c->d_stats, 0);
+        k_mixed_fp32<NF><<<bA, c->launch_block, 0, s>>>(p, a1, mq.cap, cnt, c->d_stats);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    k_snapshot64<<<1, 1, 0, s>>>(cnt);
+    e = cudaGetLastError();
+    // fork: B-long on the second stream
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    PhaseIO bl{};
+    bl.in = mq.q64;
+    bl.push = mq.q32l;
+    bl.fetch = kCntLongFetch;
+    bl.total = kCntSnap64;
+    bl.push_cnt = kCntPush32L;
+    bl.requeue_cnt = -1;
+    bl.budget = 1 << 30;
+    e = fp64_phase(bl, b64, c->s_long);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->s_long);
+    if (e != cudaSuccess) return e;
+    // phase A2
+    PhaseIO a2 = a1;
+    a2.fresh = c->d_rest;
+    a2.fetch = kCntFreshRest;
+    a2.total = kCntListRest;
+    {
+        ProfScope ps(c, kProfMixedA, s);
+        k_mixed_fp32<NF><<<bA, c->launch_block, 0, s>>>(p, a2, mq.cap, cnt, c->d_stats);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // FP64 passes on the other rays: q64 [snapshot, end) -> q64b -> q64c -> q64b ...
     for (int pass = 0; pass < kMaxPasses; ++pass) {
-        ProfScope ps(c, kProfMixedB, s);
-        if (df)
-            k_mixed_fp64<NF, df64><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats, pass,
-                                                                              kPassBudget[pass]);
-        else
-            k_mixed_fp64<NF, double><<<std::max(1, b64), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats,
-                                                                                pass, kPassBudget[pass]);
-        e = cudaGetLastError();
+        PhaseIO b{};
+        b.in = pass == 0 ? mq.q64 : ((pass & 1) ? mq.q64b : mq.q64c);
+        b.requeue = (pass & 1) ? mq.q64c : mq.q64b;
+        b.push = mq.q32;
+        b.fetch = kCntPassFetch + pass;
+        b.total = pass == 0 ? kCntPush64 : kCntPassOut + pass - 1;
+        b.push_cnt = kCntPush32;
+        b.requeue_cnt = pass + 1 < kMaxPasses ? kCntPassOut + pass : -1;
+        b.budget = kPassBudget[pass];
+        e = fp64_phase(b, b64, s);
         if (e != cudaSuccess) return e;
     }
+    // phase C on the passes' leavers, then (after the join) on B-long's
+    PhaseIO cc{};
+    cc.in = mq.q32;
+    cc.fetch = kCntFetch32;
+    cc.total = kCntPush32;
+    cc.push_cnt = -1;
+    cc.requeue_cnt = -1;
     {
         ProfScope ps(c, kProfMixedC, s);
-        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, c->mq, c->d_counters, c->d_stats, 1);
+        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, cc, mq.cap, cnt, c->d_stats);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+    if (e != cudaSuccess) return e;
+    PhaseIO cl = cc;
+    cl.in = mq.q32l;
+    cl.fetch = kCntFetch32L;
+    cl.total = kCntPush32L;
+    {
+        ProfScope ps(c, kProfMixedC, s);
+        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, cl, mq.cap, cnt, c->d_stats);
     }
     return cudaGetLastError();
 }
@@ -372,10 +497,16 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
             RCK(launch_fp64(ctx, p, s));
         } else {
             const size_t need = (size_t)p.n_rays;
+            if (p.n_rays > 0x7fffffffLL) return fail(ctx, RAPTOR_EINVAL, "the mixed path takes at most 2^31 - 1 rays per call");
             if (ctx->mq_cap < need || ctx->mq.nf_cap < p.nf) {
                 free_mixed_queues(ctx->mq);
+                cudaFree(ctx->d_crit);
+                cudaFree(ctx->d_rest);
+                ctx->d_crit = ctx->d_rest = nullptr;
                 ctx->mq_cap = 0;
                 RCK(alloc_mixed_queues(ctx->mq, need, 16));
+                RCK(cudaMalloc((void**)&ctx->d_crit, need * sizeof(int)));
+                RCK(cudaMalloc((void**)&ctx->d_rest, need * sizeof(int)));
                 ctx->mq_cap = need;
             }
             RCK(launch_mixed(ctx, p, s));
@@ -719,9 +850,13 @@ void raptor_destroy(raptor_ctx* ctx) {
     cudaFree(ctx->d_trace_I);
     cudaFree(ctx->d_rec);
     free_mixed_queues(ctx->mq);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->s_long) cudaStreamDestroy(ctx->s_long);
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
-                  ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->s_curve, ctx->s_err, ctx->s_h2tc};
+                  ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
+                  ctx->d_crit, ctx->d_rest};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.second.first);
@@ -1116,6 +1251,13 @@ raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, in
     return RAPTOR_OK;
 }
 
+raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!(crit_band >= 0.0) || !std::isfinite(crit_band)) return fail(ctx, RAPTOR_EINVAL, "crit_band must be finite and >= 0");
+    ctx->crit_band = crit_band;
+    return RAPTOR_OK;
+}
+
 raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind) {
     if (!ctx) return RAPTOR_EINVAL;
     if (kind != RAPTOR_MLP_TCGEN05 && kind != RAPTOR_MLP_MMA_SYNC) return fail(ctx, RAPTOR_EINVAL, "unknown surrogate kernel");
@@ -1154,29 +1296,16 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
         RCK(cudaMalloc((void**)&ctx->s_start, rays * 8 * sizeof(double)));
         ctx->s_ray_cap = rays;
     }
-    const int n_curve = kMaxCurve;
-    if (!ctx->s_curve) RCK(cudaMalloc((void**)&ctx->s_curve, n_curve * sizeof(float2)));
-    const std::vector<double> cc = critical_curve(p.a, p.incl, n_curve);
-    const int nc = (int)(cc.size() / 2);
-    // FP32 vertices (pageable source: the copy is staged before the call returns) and the
-    // bounding box grown by the band
-    std::vector<float2> cf(nc);
-    float4 box = make_float4(3e38f, -3e38f, 3e38f, -3e38f);
-    for (int q = 0; q < nc; ++q) {
-        cf[q] = make_float2((float)cc[2 * q], (float)cc[2 * q + 1]);
-        box.x = std::min(box.x, cf[q].x);
-        box.y = std::max(box.y, cf[q].x);
-        box.z = std::min(box.z, cf[q].y);
-        box.w = std::max(box.w, cf[q].y);
-    }
+    RCK(upload_curve(ctx, p, s));
+    const int nc = ctx->n_curve;
     const float grow = (float)ctx->s_band + 1e-3f;
-    box = make_float4(box.x - grow, box.y + grow, box.z - grow, box.w + grow);
-    if (nc > 0) RCK(cudaMemcpyAsync(ctx->s_curve, cf.data(), nc * sizeof(float2), cudaMemcpyHostToDevice, s));
+    const float4 box = make_float4(ctx->curve_box.x - grow, ctx->curve_box.y + grow, ctx->curve_box.z - grow,
+                                   ctx->curve_box.w + grow);
     float* out = nullptr;
     RCK(cudaMallocAsync((void**)&out, rays * kOut * sizeof(float), s));
     {
         ProfScope ps(ctx, kProfSurrogate, s, 2);  // inputs and start states; the network nests below
-        k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_curve, nc, (float)ctx->s_band, box,
+        k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->d_curve, nc, (float)ctx->s_band, box,
                                                                        ctx->s_in, ctx->s_fb);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) {

@@ -1,21 +1,26 @@
 // raptor_kernels_mixed.cuh -- mixed FP32/FP64 integration as a three-phase wavefront.
 //
 // B300 executes FP64 at a small fraction of its FP32 rate, and a warp that holds one FP64
-// ray pays the FP64 price for all 32 lanes.  So rays are sorted by precision through two
-// device queues instead of switching precision per lane:
+// ray pays the FP64 price for all 32 lanes.  So rays are sorted by precision through device
+// queues instead of switching precision per lane:
 //   phase A (FP32, persistent): fresh camera rays, integrated while r >= r_fp64 and away
 //     from radial turning points (|k^r| >= turn_kr |k^t|); a ray entering that region is
 //     pushed to the FP64 queue with its state promoted to FP64, and the lane refills.
 //   phase B (FP64, persistent): rays from the FP64 queue, geodesic steps in FP64 (their
 //     transfer samples in FP32) until they terminate or leave the region; leavers are
-//     pushed to the FP32 queue.
-//   phase C (FP32, persistent): rays from the FP32 queue, integrated to termination (an
+//     pushed to an FP32 queue.
+//   phase C (FP32, persistent): rays from the FP32 queues, integrated to termination (an
 //     outgoing photon has no further radial turning point; re-entries are counted).
+// Rays near the critical curve orbit the photon sphere and need ~10^3 sequential FP64
+// steps: their chain of steps, not the total work, bounds the frame.  They are selected
+// first (phase A1), and their FP64 phase runs on a second stream (B-long) while the other
+// rays go through phases A2, B and C on the first.  Every launch works on a range of a queue
+// fixed before it starts (a snapshot of the push counter, taken in stream order), so no
+// kernel waits on another.
 // The optical depth of a frequency beyond 10 is accumulated with a 48-bit significand
 // (compensated float pair), so the per-step loops of all phases issue no FP64 instruction
 // for the transfer: on B300 one FP64 compare or conversion occupies the FP64 pipe for as
 // long as ~70 FP32 instructions.
-// No kernel waits on another: the phases are ordered by the stream.
 #pragma once
 
 #include "raptor_kernels_fp64.cuh"
@@ -33,14 +38,44 @@ struct RayQueue {
 };
 
 struct MixedQueues {
-    RayQueue q64, q64b, q32;  // q64 / q64b alternate as input and re-queue target of the FP64 passes
+    RayQueue q64;         // phase A -> FP64 (A1's rays first, then A2's)
+    RayQueue q64b, q64c;  // re-queue targets of the FP64 passes (alternating)
+    RayQueue q32;         // FP64 passes -> phase C
+    RayQueue q32l;        // B-long -> phase C (its own queue: B-long runs concurrently with C)
     size_t cap = 0;
     int nf_cap = 0;
 };
 
 // Counter slots in the context's device counter array (kNumCounters entries).
-enum : int { kCntFreshA = 0, kCntPush64 = 1, kCntPush32 = 3, kCntFetch32 = 4, kCntPassFetch = 8, kCntPassOut = 16,
-             kMaxPasses = 8, kNumCounters = 32 };
+enum : int {
+    kCntListCrit = 0,    // length of the near-critical id list (phase A1)
+    kCntListRest = 1,    // length of the other id list (phase A2)
+    kCntFreshCrit = 2,   // fetch counters of the two lists
+    kCntFreshRest = 3,
+    kCntPush64 = 4,      // q64 push counter
+    kCntSnap64 = 5,      // q64 length after A1: B-long's range is [0, kCntSnap64)
+    kCntLongFetch = 6,
+    kCntPush32L = 7,     // q32l push counter
+    kCntPush32 = 8,      // q32 push counter
+    kCntFetch32 = 9,
+    kCntFetch32L = 10,
+    kCntPassFetch = 16,  // per pass: fetch counters (pass 0 starts at kCntSnap64)
+    kCntPassOut = 24,    // per pass: re-queue push counters
+    kMaxPasses = 8,
+    kNumCounters = 32
+};
+
+// Input, outputs and counter slots of one launch of the mixed kernels.
+struct PhaseIO {
+    const int* fresh;     // phase A: ray ids to start (nullptr: rays come from `in`)
+    RayQueue in;          // queued input
+    RayQueue push;        // phase A: FP64 queue; FP64 launches: leavers (FP32 queue)
+    RayQueue requeue;     // FP64 passes: rays still in the region after `budget` steps
+    int fetch, total;     // fetch counter slot; slot holding the number of input entries
+    int push_cnt;         // push counter slot of `push` (phase C: -1, re-entries are counted)
+    int requeue_cnt;      // push counter slot of `requeue` (-1: no re-queue)
+    int budget;           // FP64 launches: steps per ray in this launch
+};
 
 inline cudaError_t alloc_queue(RayQueue& q, size_t cap, int nf) {
     cudaError_t e = cudaMalloc((void**)&q.xk, sizeof(double) * 8 * cap);
@@ -60,31 +95,26 @@ inline void free_queue(RayQueue& q) {
     q = RayQueue{nullptr, nullptr, nullptr, nullptr, nullptr};
 }
 
+inline void free_mixed_queues(MixedQueues& m) {
+    RayQueue* all[] = {&m.q64, &m.q64b, &m.q64c, &m.q32, &m.q32l};
+    for (RayQueue* q : all) free_queue(*q);
+    m.cap = 0;
+    m.nf_cap = 0;
+}
+
 inline cudaError_t alloc_mixed_queues(MixedQueues& m, size_t cap, int nf) {
-    m.q64 = RayQueue{nullptr, nullptr, nullptr, nullptr, nullptr};
-    m.q64b = m.q64;
-    m.q32 = m.q64;
-    cudaError_t e = alloc_queue(m.q64, cap, nf);
-    if (e == cudaSuccess) e = alloc_queue(m.q64b, cap, nf);
-    if (e == cudaSuccess) e = alloc_queue(m.q32, cap, nf);
+    RayQueue* all[] = {&m.q64, &m.q64b, &m.q64c, &m.q32, &m.q32l};
+    for (RayQueue* q : all) *q = RayQueue{nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (RayQueue* q : all)
+        if (e == cudaSuccess) e = alloc_queue(*q, cap, nf);
     if (e == cudaSuccess) {
         m.cap = cap;
         m.nf_cap = nf;
     } else {
-        free_queue(m.q64);
-        free_queue(m.q64b);
-        free_queue(m.q32);
+        free_mixed_queues(m);
     }
     return e;
-}
-
-inline void free_mixed_queues(MixedQueues& m) {
-    if (m.cap == 0 && !m.q64.xk) return;
-    free_queue(m.q64);
-    free_queue(m.q64b);
-    free_queue(m.q32);
-    m.cap = 0;
-    m.nf_cap = 0;
 }
 
 // Warp-aggregated push: lanes with `push` set receive consecutive slots.
@@ -281,36 +311,59 @@ __device__ __forceinline__ void store_ray(const RayQueue& q, size_t cap, long lo
     q.id[slot] = id;
 }
 
-// Phase A (from_queue = false) and phase C (from_queue = true), FP32.
+// Load queued ray `nid` of q into FP32 lane state (compensated pairs from the FP64 state).
 template <int NF>
-__global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues mq, unsigned long long* cnt,
-                                                    unsigned long long* stats, int from_queue) {
+__device__ __forceinline__ long long load_ray_f(const Params& p, const RayQueue& q, size_t cap, long long nid, RayF<NF>& R) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        split_f(q.xk[(size_t)i * cap + nid], R.x[i], R.xl[i]);
+        split_f(q.xk[(size_t)(4 + i) * cap + nid], R.k[i], R.kl[i]);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (f < p.nf) {
+            R.I[f] = float(q.I[(size_t)f * cap + nid]);
+            tau_split(q.tau[(size_t)f * cap + nid], R.tau[f], R.tau_hi[f]);
+        } else {
+            R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = df64(0.f, 0.f);
+        }
+    }
+    R.n = q.n[nid];
+    return q.id[nid];
+}
+
+// FP32 phases.  Phase A (io.fresh set): camera rays (or the surrogate's predicted states)
+// from the id list; rays entering the FP64 region go to io.push.  Phase C: rays from io.in,
+// integrated to termination (re-entries into the region are counted, not moved).
+template <int NF>
+__global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, size_t cap, unsigned long long* cnt,
+                                                    unsigned long long* stats) {
     RayF<NF> R;
     long long id = -1;
     int frame = 0, pix = 0;
     bool drained = false;
-    const long long n_total = from_queue ? (long long)cnt[kCntPush32] : p.n_rays;
-    unsigned long long* fetch = from_queue ? &cnt[kCntFetch32] : &cnt[kCntFreshA];
+    const bool fresh = io.fresh != nullptr;
+    const long long n_total = (long long)cnt[io.total];
     unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0, c_re = 0;
     for (;;) {
-        const long long nid = warp_fetch(fetch, n_total, id < 0, drained);
+        const long long nid = warp_fetch(&cnt[io.fetch], n_total, id < 0, drained);
         if (id < 0 && nid >= 0) {
-            if (!from_queue) {
+            if (fresh) {
                 RayD<NF> D;
-                id = nid;
-                if (p.start_xk && !p.fallback[nid]) {
+                id = io.fresh[nid];
+                if (p.start_xk && !p.fallback[id]) {
                     // learned surrogate: start from the predicted state after start_n steps
-                    frame = (int)(nid / p.n_pix);
-                    pix = (int)(nid - (long long)frame * p.n_pix);
+                    frame = (int)(id / p.n_pix);
+                    pix = (int)(id - (long long)frame * p.n_pix);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        D.x[i] = p.start_xk[(long long)i * p.n_rays + nid];
-                        D.k[i] = p.start_xk[(long long)(4 + i) * p.n_rays + nid];
+                        D.x[i] = p.start_xk[(long long)i * p.n_rays + id];
+                        D.k[i] = p.start_xk[(long long)(4 + i) * p.n_rays + id];
                     }
                     D.n = p.start_n;
                     D.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
                 } else {
-                    init_ray<NF>(p, nid, D, frame, pix);
+                    init_ray<NF>(p, id, D, frame, pix);
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { split_f(D.x[i], R.x[i], R.xl[i]); split_f(D.k[i], R.k[i], R.kl[i]); }
@@ -319,26 +372,9 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
                 R.n = D.n;
                 R.snap = D.snap;
             } else {
-                const RayQueue& q = mq.q32;
-                const size_t cap = mq.cap;
-                id = q.id[nid];
+                id = load_ray_f<NF>(p, io.in, cap, nid, R);
                 frame = (int)(id / p.n_pix);
                 pix = (int)(id - (long long)frame * p.n_pix);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    split_f(q.xk[(size_t)i * cap + nid], R.x[i], R.xl[i]);
-                    split_f(q.xk[(size_t)(4 + i) * cap + nid], R.k[i], R.kl[i]);
-                }
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if (f < p.nf) {
-                        R.I[f] = float(q.I[(size_t)f * cap + nid]);
-                        tau_split(q.tau[(size_t)f * cap + nid], R.tau[f], R.tau_hi[f]);
-                    } else {
-                        R.I[f] = 0.f; R.tau[f] = 0.f; R.tau_hi[f] = df64(0.f, 0.f);
-                    }
-                }
-                R.n = q.n[nid];
                 R.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
             }
         }
@@ -348,18 +384,18 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
         if (id >= 0) {
             st = step_fp32<NF>(p, R);
             if (st < 0 && in_fp64_region<float>(p, R.x, R.k)) {
-                if (!from_queue) push = true;
+                if (fresh) push = true;
                 else c_re += 1;
             }
         }
-        const long long slot = warp_push_slot(&cnt[kCntPush64], push);
+        const long long slot = fresh ? warp_push_slot(&cnt[io.push_cnt], push) : -1;
         if (push) {
             double x[4], k[4], tau[NF];
 #pragma unroll
             for (int i = 0; i < 4; ++i) { x[i] = double(R.x[i]) + double(R.xl[i]); k[i] = double(R.k[i]) + double(R.kl[i]); }
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
-            store_ray<NF>(mq.q64, mq.cap, slot, id, x, k, R.I, tau, R.n, p.nf);
+            store_ray<NF>(io.push, cap, slot, id, x, k, R.I, tau, R.n, p.nf);
             id = -1;
         } else if (id >= 0 && st >= 0) {
             double I[NF];
@@ -377,32 +413,30 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, MixedQueues 
     if (c_re) atomicAdd(&stats[kStatReentry], c_re);
 }
 
-// Phase B, pass `pass`: rays from the FP64 queue; FP64 geodesic steps, FP32 transfer
-// samples.  A ray runs at most `budget` steps in this pass; if it is still in the FP64
-// region then, it is re-queued for the next pass.  Every pass therefore starts with full
-// warps, and the ragged end of a pass lasts at most `budget` steps, instead of one long
-// tail in which a few long inner-region rays occupy otherwise empty warps.
+// FP64 phase: rays from io.in; FP64 (or double-float) geodesic steps, FP32 transfer samples.
+// A ray runs at most io.budget steps in this launch; if it is still in the FP64 region then,
+// it goes to io.requeue for the next pass.  Each pass therefore starts with full warps and
+// its ragged end lasts at most `budget` steps.  Leavers go to io.push (an FP32 queue).
 // Double-float steps are FP32-issue bound: ask for at least 4 resident blocks (16 warps)
 // per SM so that latency is hidden; the FP64 variant is FP64-pipe bound and needs no cap.
 template <typename S>
 constexpr int kMixed64MinBlocks = std::is_same<S, df64>::value ? 4 : 1;
 
 template <int NF, typename S = double>
-__global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const Params p, MixedQueues mq, unsigned long long* cnt,
-                                                    unsigned long long* stats, int pass, int budget) {
+__global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const Params p, PhaseIO io, size_t cap,
+                                                                          unsigned long long* cnt, unsigned long long* stats) {
     RayM<NF, S> R;
     const S a_s = StateT<S>::from(p.a);
     long long id = -1;
     int frame = 0, pix = 0, n_in = 0;
     bool drained = false;
-    const long long n_total = (long long)(pass == 0 ? cnt[kCntPush64] : cnt[kCntPassOut + pass - 1]);
+    const long long n_total = (long long)cnt[io.total];
+    const bool can_requeue = io.requeue_cnt >= 0;
     unsigned long long c_rays = 0, c_steps = 0, c_64 = 0, c_trunc = 0, c_err = 0;
-    const RayQueue& q = (pass & 1) ? mq.q64b : mq.q64;
-    const RayQueue& qr = (pass & 1) ? mq.q64 : mq.q64b;
-    const size_t cap = mq.cap;
     for (;;) {
-        const long long nid = warp_fetch(&cnt[kCntPassFetch + pass], n_total, id < 0, drained);
+        const long long nid = warp_fetch(&cnt[io.fetch], n_total, id < 0, drained);
         if (id < 0 && nid >= 0) {
+            const RayQueue& q = io.in;
             id = q.id[nid];
             frame = (int)(id / p.n_pix);
             pix = (int)(id - (long long)frame * p.n_pix);
@@ -430,18 +464,18 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { xf[i] = StateT<S>::f(R.x[i]); kf[i] = StateT<S>::f(R.k[i]); }
                 if (!in_fp64_region<float>(p, xf, kf)) push = true;
-                else if (R.n - n_in >= budget) requeue = true;
+                else if (can_requeue && R.n - n_in >= io.budget) requeue = true;
             }
         }
-        const long long slot = warp_push_slot(&cnt[kCntPush32], push);
-        const long long rslot = warp_push_slot(&cnt[kCntPassOut + pass], requeue);
+        const long long slot = warp_push_slot(&cnt[io.push_cnt], push);
+        const long long rslot = can_requeue ? warp_push_slot(&cnt[io.requeue_cnt], requeue) : -1;
         if (push || requeue) {
             double tau[NF], xd[4], kd[4];
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) { xd[i] = StateT<S>::to(R.x[i]); kd[i] = StateT<S>::to(R.k[i]); }
-            store_ray<NF>(push ? mq.q32 : qr, cap, push ? slot : rslot, id, xd, kd, R.I, tau, R.n, p.nf);
+            store_ray<NF>(push ? io.push : io.requeue, cap, push ? slot : rslot, id, xd, kd, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
         } else if (id >= 0 && st >= 0) {
@@ -458,6 +492,54 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
         }
     }
     warp_add_stats(stats, c_rays, c_steps, c_64, c_trunc, c_err);
+}
+
+// Split the rays of a render into the near-critical list (pixel centre within `band` M of
+// the critical curve, n_curve <= kMaxCurve FP32 vertices; `box` its bounding box grown by the
+// band) and the rest, as id lists of counts cnt[kCntListCrit] and cnt[kCntListRest].
+// Warp-aggregated appends: the order within a list is not deterministic, and nothing
+// downstream depends on it (every ray's arithmetic is its own).
+__global__ void __launch_bounds__(256) k_select_critical(const Params p, const float2* __restrict__ curve, int n_curve,
+                                                         float band, float4 box, int* __restrict__ crit,
+                                                         int* __restrict__ rest, unsigned long long* cnt) {
+    __shared__ float2 sc[kMaxCurve];
+    for (int c = threadIdx.x; c < n_curve; c += blockDim.x) sc[c] = curve[c];
+    __syncthreads();
+    const float band2 = band * band;
+    const long long n = p.n_rays;
+    // whole warps iterate together (the appends are warp-collective)
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const long long id = base + (threadIdx.x & 31);
+        bool is_crit = false;
+        if (id < n) {
+            const int frame = (int)(id / p.n_pix);
+            const int pix = (int)(id - (long long)frame * p.n_pix);
+            const int row = p.row0 + pix / p.nx, col = pix % p.nx;
+            const float alf = (float)(p.amin + (col + 0.5) * p.da), bef = (float)(p.bmin + (row + 0.5) * p.db);
+            if (alf >= box.x && alf <= box.y && bef >= box.z && bef <= box.w) {
+                float d2 = 3.0e38f;
+                for (int c = 0; c < n_curve; ++c) {
+                    const float dx = alf - sc[c].x, dy = bef - sc[c].y;
+                    d2 = fminf(d2, dx * dx + dy * dy);
+                }
+                is_crit = d2 < band2;
+            }
+        }
+        const long long sc_slot = warp_push_slot(&cnt[kCntListCrit], id < n && is_crit);
+        const long long sr_slot = warp_push_slot(&cnt[kCntListRest], id < n && !is_crit);
+        if (id < n) {
+            if (is_crit) crit[sc_slot] = (int)id;
+            else rest[sr_slot] = (int)id;
+        }
+    }
+}
+
+// Stream-ordered snapshot after phase A1: B-long takes q64 entries [0, n), the first FP64
+// pass starts fetching at n.
+__global__ void k_snapshot64(unsigned long long* cnt) {
+    cnt[kCntSnap64] = cnt[kCntPush64];
+    cnt[kCntPassFetch] = cnt[kCntPush64];
 }
 
 }  // namespace raptor
