@@ -200,10 +200,15 @@ raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int bloc
 
 /* Mixed path scheduling: rays whose pixel centre lies within crit_band M of the critical
  * curve (Bardeen's closed form) form phase A1 and run their FP64 phase on a second stream,
- * concurrently with the other rays' phases A2, B and C [0.5].  Only the schedule changes:
- * every ray's arithmetic, and so every result, is the same for any crit_band >= 0.
- * RAPTOR_EINVAL for a negative or non-finite band. */
-raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band);
+ * concurrently with the other rays' phases A2, B and C [0.5].  The other rays' FP64 phase
+ * runs in n_passes passes (1..8): pass k continues each ray for at most budgets[k] steps
+ * and re-queues the unfinished ones for pass k + 1; the last pass has no limit (budgets may
+ * be NULL: the default schedule).  After c_split passes (0: never) the leavers so far go
+ * through phase C on a third stream while the later passes run [0].  Only the schedule
+ * changes: every ray's arithmetic, and so every result, is the same for any setting.
+ * RAPTOR_EINVAL for a negative or non-finite band, n_passes outside 1..8, a budget < 1 or
+ * a negative c_split. */
+raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int c_split);
 
 /* Autotuner: renders the context's camera once per candidate launch shape (threads per
  * block {64, 128}; blocks per SM of the ray kernels {max, 2, 3, 4}; for RAPTOR_MIXED also

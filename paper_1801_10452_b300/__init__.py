@@ -110,7 +110,7 @@ def lib():
             "raptor_surrogate_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
-            "raptor_mixed_config": (st, [vp, C.c_double]),
+            "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -346,9 +346,17 @@ class Context:
         P = np.ascontiguousarray(P, dtype=np.float32)
         self._check(lib().raptor_surrogate_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size), "raptor_surrogate_set")
 
-    def mixed_config(self, crit_band=0.5):
-        """Near-critical band (M) whose rays run their FP64 phase on the second stream."""
-        self._check(lib().raptor_mixed_config(self._h, float(crit_band)), "raptor_mixed_config")
+    def mixed_config(self, crit_band=0.5, budgets=None, c_split=0):
+        """Schedule of the mixed path: the near-critical band (M) whose rays run their FP64
+        phase on the second stream, the step budgets of the other rays' FP64 passes (None:
+        the default; the last pass is unlimited), and the pass after which phase C starts on
+        a third stream (0: never)."""
+        if budgets is None:
+            self._check(lib().raptor_mixed_config(self._h, float(crit_band), 8, None, int(c_split)), "raptor_mixed_config")
+        else:
+            b = (C.c_int * max(1, len(budgets)))(*[int(v) for v in budgets])
+            self._check(lib().raptor_mixed_config(self._h, float(crit_band), len(budgets) + 1, b, int(c_split)),
+                        "raptor_mixed_config")
 
     def surrogate_kernel(self, kind):
         """Inference kernel: MLP_TCGEN05 (default) or MLP_MMA_SYNC."""

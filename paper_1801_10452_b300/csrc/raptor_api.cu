@@ -49,8 +49,12 @@ struct raptor_ctx {
     int* d_crit = nullptr;        // mixed path: near-critical ray ids (phase A1)
     int* d_rest = nullptr;        // mixed path: the other ray ids (phase A2)
     cudaStream_t s_long = nullptr;  // second stream of the mixed path (B-long)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t s_c1 = nullptr;    // third stream (phase C1)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork_c = nullptr, ev_join_c = nullptr;
+    int c_split = 0;              // phase C1 starts after this many FP64 passes (0: no split)
     double crit_band = 0.5;       // M: near-critical band of the mixed path's B-long
+    int n_passes = 8;             // FP64 passes of the other rays and their step budgets
+    int pass_budget[8] = {16, 32, 48, 64, 96, 128, 256, 1 << 30};
     float2* d_curve = nullptr;    // critical curve (FP32 vertices) of the current (a, i)
     int n_curve = 0;
     float4 curve_box = make_float4(0.f, 0.f, 0.f, 0.f);  // its bounding box
@@ -359,8 +363,10 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s);
     if (e == cudaSuccess) e = upload_curve(c, p, s);
     if (e == cudaSuccess && !c->s_long) e = cudaStreamCreateWithFlags(&c->s_long, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !c->ev_fork) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess && !c->ev_join) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->s_c1) e = cudaStreamCreateWithFlags(&c->s_c1, cudaStreamNonBlocking);
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join, &c->ev_fork_c, &c->ev_join_c};
+    for (cudaEvent_t* ev : evs)
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
     int occ32 = 0, occ64 = 0;
     const bool df = (p.flags & kFlagInnerDf64) != 0;
@@ -427,8 +433,33 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // phase C template (FP32 queue -> termination)
+    PhaseIO cc{};
+    cc.in = mq.q32;
+    cc.fetch = kCntFetch32;
+    cc.total = kCntPush32;
+    cc.push_cnt = -1;
+    cc.requeue_cnt = -1;
+    const bool split_c = c->c_split > 0 && c->c_split < c->n_passes;
     // FP64 passes on the other rays: q64 [snapshot, end) -> q64b -> q64c -> q64b ...
-    for (int pass = 0; pass < kMaxPasses; ++pass) {
+    for (int pass = 0; pass < c->n_passes; ++pass) {
+        if (split_c && pass == c->c_split) {
+            // fork: phase C1 on the leavers so far, concurrently with the later passes
+            k_snapshot32<<<1, 1, 0, s>>>(cnt);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork_c, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_c1, c->ev_fork_c, 0);
+            if (e != cudaSuccess) return e;
+            PhaseIO c1 = cc;
+            c1.total = kCntSnap32;
+            {
+                ProfScope ps(c, kProfMixedC, c->s_c1);
+                k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, c->s_c1>>>(p, c1, mq.cap, cnt, c->d_stats);
+            }
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_c, c->s_c1);
+            if (e != cudaSuccess) return e;
+        }
         PhaseIO b{};
         b.in = pass == 0 ? mq.q64 : ((pass & 1) ? mq.q64b : mq.q64c);
         b.requeue = (pass & 1) ? mq.q64c : mq.q64b;
@@ -436,23 +467,21 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
         b.fetch = kCntPassFetch + pass;
         b.total = pass == 0 ? kCntPush64 : kCntPassOut + pass - 1;
         b.push_cnt = kCntPush32;
-        b.requeue_cnt = pass + 1 < kMaxPasses ? kCntPassOut + pass : -1;
-        b.budget = kPassBudget[pass];
+        b.requeue_cnt = pass + 1 < c->n_passes ? kCntPassOut + pass : -1;
+        b.budget = pass + 1 < c->n_passes ? c->pass_budget[pass] : (1 << 30);
         e = fp64_phase(b, b64, s);
         if (e != cudaSuccess) return e;
     }
-    // phase C on the passes' leavers, then (after the join) on B-long's
-    PhaseIO cc{};
-    cc.in = mq.q32;
-    cc.fetch = kCntFetch32;
-    cc.total = kCntPush32;
-    cc.push_cnt = -1;
-    cc.requeue_cnt = -1;
+    // phase C (C2 after a split: the leavers from the snapshot on), then, after the joins,
+    // on B-long's leavers
+    PhaseIO c2 = cc;
+    if (split_c) c2.fetch = kCntFetch32b;
     {
         ProfScope ps(c, kProfMixedC, s);
-        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, cc, mq.cap, cnt, c->d_stats);
+        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, c2, mq.cap, cnt, c->d_stats);
     }
     e = cudaGetLastError();
+    if (e == cudaSuccess && split_c) e = cudaStreamWaitEvent(s, c->ev_join_c, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
     if (e != cudaSuccess) return e;
     PhaseIO cl = cc;
@@ -850,9 +879,11 @@ void raptor_destroy(raptor_ctx* ctx) {
     cudaFree(ctx->d_trace_I);
     cudaFree(ctx->d_rec);
     free_mixed_queues(ctx->mq);
-    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_fork_c, ctx->ev_join_c};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->s_long) cudaStreamDestroy(ctx->s_long);
+    if (ctx->s_c1) cudaStreamDestroy(ctx->s_c1);
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
                   ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
@@ -1251,10 +1282,18 @@ raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, in
     return RAPTOR_OK;
 }
 
-raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band) {
+raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int c_split) {
     if (!ctx) return RAPTOR_EINVAL;
     if (!(crit_band >= 0.0) || !std::isfinite(crit_band)) return fail(ctx, RAPTOR_EINVAL, "crit_band must be finite and >= 0");
+    if (n_passes < 1 || n_passes > kMaxPasses) return fail(ctx, RAPTOR_EINVAL, "n_passes must lie in [1, 8]");
+    if (budgets)
+        for (int k = 0; k + 1 < n_passes; ++k)
+            if (budgets[k] < 1) return fail(ctx, RAPTOR_EINVAL, "pass budgets must be >= 1");
+    if (c_split < 0) return fail(ctx, RAPTOR_EINVAL, "c_split must be >= 0");
     ctx->crit_band = crit_band;
+    ctx->c_split = c_split;
+    ctx->n_passes = budgets ? n_passes : kMaxPasses;
+    for (int k = 0; k < kMaxPasses; ++k) ctx->pass_budget[k] = budgets ? (k + 1 < n_passes ? budgets[k] : (1 << 30)) : kPassBudget[k];
     return RAPTOR_OK;
 }
 

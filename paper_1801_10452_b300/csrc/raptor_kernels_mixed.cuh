@@ -14,9 +14,10 @@
 // Rays near the critical curve orbit the photon sphere and need ~10^3 sequential FP64
 // steps: their chain of steps, not the total work, bounds the frame.  They are selected
 // first (phase A1), and their FP64 phase runs on a second stream (B-long) while the other
-// rays go through phases A2, B and C on the first.  Every launch works on a range of a queue
-// fixed before it starts (a snapshot of the push counter, taken in stream order), so no
-// kernel waits on another.
+// rays go through phases A2, B and C on the first; the leavers of the early FP64 passes go
+// through phase C on a third stream (C1) while the later passes, whose ends are mostly
+// idle, run.  Every launch works on a range of a queue fixed before it starts (a snapshot
+// of the push counter, taken in stream order), so no kernel waits on another.
 // The optical depth of a frequency beyond 10 is accumulated with a 48-bit significand
 // (compensated float pair), so the per-step loops of all phases issue no FP64 instruction
 // for the transfer: on B300 one FP64 compare or conversion occupies the FP64 pipe for as
@@ -59,6 +60,8 @@ enum : int {
     kCntPush32 = 8,      // q32 push counter
     kCntFetch32 = 9,
     kCntFetch32L = 10,
+    kCntSnap32 = 11,     // q32 length after the early passes: phase C1's range is [0, kCntSnap32)
+    kCntFetch32b = 12,   // phase C2's fetch counter (starts at kCntSnap32)
     kCntPassFetch = 16,  // per pass: fetch counters (pass 0 starts at kCntSnap64)
     kCntPassOut = 24,    // per pass: re-queue push counters
     kMaxPasses = 8,
@@ -540,6 +543,13 @@ __global__ void __launch_bounds__(256) k_select_critical(const Params p, const f
 __global__ void k_snapshot64(unsigned long long* cnt) {
     cnt[kCntSnap64] = cnt[kCntPush64];
     cnt[kCntPassFetch] = cnt[kCntPush64];
+}
+
+// Stream-ordered snapshot after the early FP64 passes: phase C1 (third stream) takes q32
+// entries [0, n) while the later passes run; phase C2 fetches from n on.
+__global__ void k_snapshot32(unsigned long long* cnt) {
+    cnt[kCntSnap32] = cnt[kCntPush32];
+    cnt[kCntFetch32b] = cnt[kCntPush32];
 }
 
 }  // namespace raptor
