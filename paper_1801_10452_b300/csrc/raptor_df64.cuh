@@ -151,6 +151,9 @@ RAPTOR_HD void df_sincos(df64 x, df64* s_out, df64* c_out) {
 }
 
 RAPTOR_HD void sc(df64 v, df64* s, df64* c) { df_sincos(v, s, c); }
+// exact scalings by powers of two: two FP32 multiplies instead of a double-float product
+RAPTOR_HD df64 twice(df64 v) { return df64(2.f * v.hi, 2.f * v.lo); }
+RAPTOR_HD df64 halve(df64 v) { return df64(0.5f * v.hi, 0.5f * v.lo); }
 RAPTOR_HD df64 rsq(df64 v) { return df64(1.0) / df_sqrt(v); }
 
 }  // namespace dfns
@@ -160,6 +163,12 @@ using dfns::df_sincos;
 using dfns::df_sqrt;
 using dfns::df_two_prod;
 using dfns::df_two_sum;
+
+// one double-float division per force evaluation instead of two
+template <>
+struct JointInverse<df64> {
+    static constexpr bool value = true;
+};
 
 template <>
 struct Real<df64> {
