@@ -49,3 +49,22 @@ def flops_per_step(n_freq: int = 1, plasma: str = "analytic") -> dict:
     total = c["geodesic_step"]["flops"] + sample + n_freq * c["per_frequency"]["flops"]
     return {"fp64_step": total, "fp32_step": total, "geodesic_only": c["geodesic_step"]["flops"],
             "sample": sample, "per_frequency": c["per_frequency"]["flops"]}
+
+
+# FP32 instructions of one double-float operation, counted from raptor_df64.cuh: add
+# (two-sum 6, two adds, fast-two-sum 3) 11; multiply (product, error FMA, two cross FMAs,
+# fast-two-sum 3) 7; division (approximate reciprocal, two residual products and
+# subtractions, three quotient products, renormalisation) ~45; sincos (argument reduction,
+# two Horner chains in double-float with float tails, quadrant selection) ~300.
+DF64_FP32_INSTR = {"add": 11, "mul": 7, "div": 45, "sincos": 300}
+
+
+def df64_instructions_per_step(n_freq: int = 1, plasma: str = "analytic") -> dict:
+    """FP32 instructions of one double-float geodesic step (its transfer sample runs in FP32:
+    one instruction per flop), and the resulting instructions per algorithmic flop."""
+    c = counts()
+    g = c["geodesic_step"]
+    geo = sum(DF64_FP32_INSTR[k] * g[k] for k in DF64_FP32_INSTR)
+    f = flops_per_step(n_freq, plasma)
+    instr = geo + f["sample"] + n_freq * f["per_frequency"]
+    return {"fp32_instructions": instr, "flops": f["fp64_step"], "instructions_per_flop": instr / f["fp64_step"]}
