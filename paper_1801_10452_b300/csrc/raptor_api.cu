@@ -235,6 +235,7 @@ Params base_params(const raptor_ctx* c) {
     p.incl = d.incl_deg * kPi / 180.0;
     p.sin_i = std::sin(p.incl);
     p.cos_i = std::cos(p.incl);
+    camera_x_terms(p.a, p.r_cam, &p.cam_logdel, &p.cam_tterm, &p.cam_phi);
     p.nx = d.nx;
     p.ny = d.ny;
     p.da = (d.alpha_max - d.alpha_min) / d.nx;

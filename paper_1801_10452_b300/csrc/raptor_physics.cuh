@@ -57,6 +57,9 @@ struct Params {
     int* steps_out;          // optional [n_rows][nx]
     int* status_out;         // optional [n_rows][nx]
     ParamsF f;               // FP32 copies (filled by the host)
+    // camera position terms of the BL -> KS map at r_cam (per render, filled by the host):
+    // x^0 = (t_cam + cam_logdel) + cam_tterm, x^3 = cam_phi
+    double cam_logdel, cam_tterm, cam_phi;
     // learned surrogate (RAPTOR_MIXED_MLP): predicted start states [8][n_rays] (x^mu, k^mu),
     // per-ray fallback flags (start at the camera), the step count of a predicted state,
     // and the outbound exit radius beyond which the transfer is neglected (0 = off)
@@ -133,8 +136,26 @@ RAPTOR_HD void camera_ray_ai(double a, double sn, double cs, double incl, double
     camera_x_ai(a, incl, r, t_cam, x);
 }
 
+// The camera position terms that depend on (a, r_cam) only, in the order camera_x_ai adds
+// them: x^0 = (t_cam + log Delta) + 2 / (r+ - r-) ln((r - r+)/(r - r-)).
+RAPTOR_HD void camera_x_terms(double a, double r, double* logdel, double* tterm, double* phi) {
+    const double a2 = a * a;
+    const double Del = r * r - 2.0 * r + a2;
+    const double rp = 1.0 + sqrt(1.0 - a2), rm = 1.0 - sqrt(1.0 - a2);
+    const double lg = log((r - rp) / (r - rm));
+    *logdel = log(Del);
+    *tterm = 2.0 / (rp - rm) * lg;
+    *phi = a / (rp - rm) * lg;
+}
+
+// Camera ray of a render: the wave vector per pixel, the position from the per-render terms
+// (no logarithm or square root per ray).
 RAPTOR_HD void camera_ray(const Params& p, double alpha, double beta, double t_cam, double x[4], double k[4]) {
-    camera_ray_ai(p.a, p.sin_i, p.cos_i, p.incl, p.r_cam, alpha, beta, t_cam, x, k);
+    camera_k_ai(p.a, p.sin_i, p.cos_i, p.r_cam, alpha, beta, k);
+    x[0] = t_cam + p.cam_logdel + p.cam_tterm;
+    x[1] = p.r_cam;
+    x[2] = p.incl;
+    x[3] = p.cam_phi;
 }
 
 // ------------------------------------------------------------------------------------
