@@ -31,7 +31,7 @@
 namespace raptor {
 
 struct RayQueue {
-    double* xk;       // [8][cap]: x^0..x^3, k^0..k^3
+    float2* xk;       // [8][cap]: x^0..x^3, k^0..k^3 as unevaluated float pairs (hi, lo)
     double* I;        // [nf_cap][cap]
     double* tau;      // [nf_cap][cap]
     int* n;           // [cap] steps so far
@@ -81,7 +81,7 @@ struct PhaseIO {
 };
 
 inline cudaError_t alloc_queue(RayQueue& q, size_t cap, int nf) {
-    cudaError_t e = cudaMalloc((void**)&q.xk, sizeof(double) * 8 * cap);
+    cudaError_t e = cudaMalloc((void**)&q.xk, sizeof(float2) * 8 * cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&q.I, sizeof(double) * nf * cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&q.tau, sizeof(double) * nf * cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&q.n, sizeof(int) * cap);
@@ -232,14 +232,19 @@ struct StateT;
 template <>
 struct StateT<double> {
     static __device__ __forceinline__ double from(double d) { return d; }
-    static __device__ __forceinline__ double to(double v) { return v; }
+    static __device__ __forceinline__ double from2(float2 v) { return double(v.x) + double(v.y); }
+    static __device__ __forceinline__ float2 to2(double v) {
+        const float hi = float(v);
+        return make_float2(hi, float(v - double(hi)));
+    }
     static __device__ __forceinline__ float f(double v) { return (float)v; }
     static __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 };
 template <>
 struct StateT<df64> {
     static __device__ __forceinline__ df64 from(double d) { return df64(d); }
-    static __device__ __forceinline__ double to(df64 v) { return (double)v.hi + (double)v.lo; }
+    static __device__ __forceinline__ df64 from2(float2 v) { return df64(v.x, v.y); }
+    static __device__ __forceinline__ float2 to2(df64 v) { return make_float2(v.hi, v.lo); }
     static __device__ __forceinline__ float f(df64 v) { return v.hi + v.lo; }
     static __device__ __forceinline__ bool finite(df64 v) { return isfinite(v.hi) && isfinite(v.lo); }
 };
@@ -296,9 +301,12 @@ __device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF, S>& R, S a
     return thick_or_capped<NF>(p, R.tau, R.tau_hi, R.n);
 }
 
+// Queue entry `slot`: the state as float pairs (FP32 phases store their compensated state as
+// is; the FP64 phase splits FP64 values, which keeps 48 of their 53 bits, the precision of
+// the double-float arithmetic), per-frequency I and tau in FP64, step count, ray id.
 template <int NF, typename TI>
-__device__ __forceinline__ void store_ray(const RayQueue& q, size_t cap, long long slot, long long id, const double x[4],
-                                          const double k[4], const TI* I, const double* tau, int n, int nf) {
+__device__ __forceinline__ void store_ray(const RayQueue& q, size_t cap, long long slot, long long id, const float2 x[4],
+                                          const float2 k[4], const TI* I, const double* tau, int n, int nf) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         q.xk[(size_t)i * cap + slot] = x[i];
@@ -319,8 +327,11 @@ template <int NF>
 __device__ __forceinline__ long long load_ray_f(const Params& p, const RayQueue& q, size_t cap, long long nid, RayF<NF>& R) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        split_f(q.xk[(size_t)i * cap + nid], R.x[i], R.xl[i]);
-        split_f(q.xk[(size_t)(4 + i) * cap + nid], R.k[i], R.kl[i]);
+        const float2 xv = q.xk[(size_t)i * cap + nid], kv = q.xk[(size_t)(4 + i) * cap + nid];
+        R.x[i] = xv.x;
+        R.xl[i] = xv.y;
+        R.k[i] = kv.x;
+        R.kl[i] = kv.y;
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -393,9 +404,10 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, 
         }
         const long long slot = fresh ? warp_push_slot(&cnt[io.push_cnt], push) : -1;
         if (push) {
-            double x[4], k[4], tau[NF];
+            float2 x[4], k[4];
+            double tau[NF];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { x[i] = double(R.x[i]) + double(R.xl[i]); k[i] = double(R.k[i]) + double(R.kl[i]); }
+            for (int i = 0; i < 4; ++i) { x[i] = make_float2(R.x[i], R.xl[i]); k[i] = make_float2(R.k[i], R.kl[i]); }
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
             store_ray<NF>(io.push, cap, slot, id, x, k, R.I, tau, R.n, p.nf);
@@ -445,8 +457,8 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
             pix = (int)(id - (long long)frame * p.n_pix);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                R.x[i] = StateT<S>::from(q.xk[(size_t)i * cap + nid]);
-                R.k[i] = StateT<S>::from(q.xk[(size_t)(4 + i) * cap + nid]);
+                R.x[i] = StateT<S>::from2(q.xk[(size_t)i * cap + nid]);
+                R.k[i] = StateT<S>::from2(q.xk[(size_t)(4 + i) * cap + nid]);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -473,11 +485,12 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
         const long long slot = warp_push_slot(&cnt[io.push_cnt], push);
         const long long rslot = can_requeue ? warp_push_slot(&cnt[io.requeue_cnt], requeue) : -1;
         if (push || requeue) {
-            double tau[NF], xd[4], kd[4];
+            double tau[NF];
+            float2 xd[4], kd[4];
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { xd[i] = StateT<S>::to(R.x[i]); kd[i] = StateT<S>::to(R.k[i]); }
+            for (int i = 0; i < 4; ++i) { xd[i] = StateT<S>::to2(R.x[i]); kd[i] = StateT<S>::to2(R.k[i]); }
             store_ray<NF>(push ? io.push : io.requeue, cap, push ? slot : rslot, id, xd, kd, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
