@@ -83,7 +83,7 @@ struct raptor_ctx {
     double* s_loss = nullptr;        // per-block loss partials
     float* s_in = nullptr;           // render: network inputs [rays][4]
     unsigned char* s_fb = nullptr;   // render: fallback flags
-    double* s_start = nullptr;       // render: start states [8][rays]
+    float2* s_start = nullptr;       // render: start states [8][rays] (float pairs)
     size_t s_ray_cap = 0;
     double s_band = 0.5, s_r_exit = 50.0;
     unsigned long long s_step = 0;   // Adam step counter
@@ -223,6 +223,20 @@ void fill_float_params(Params& p) {
     f.B_unit = (float)p.B_unit; f.r_high = (float)p.r_high; f.r_low = (float)p.r_low; f.gam = (float)p.gam;
     f.r_fp64 = (float)p.r_fp64; f.turn_kr = (float)p.turn_kr;
     for (int i = 0; i < 16; ++i) f.nu[i] = (float)p.nu[i];
+    auto pair = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    f.a_p = pair(p.a);
+    f.sin_i_p = pair(p.sin_i);
+    f.cos_i_p = pair(p.cos_i);
+    f.r_cam_p = pair(p.r_cam);
+    f.incl_p = pair(p.incl);
+    f.cam_phi_p = pair(p.cam_phi);
+    f.amin_p = pair(p.amin);
+    f.da_p = pair(p.da);
+    f.bmin_p = pair(p.bmin);
+    f.db_p = pair(p.db);
 }
 
 // Host-side parameter block shared by every launch of a context.
@@ -1333,7 +1347,7 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
         ctx->s_ray_cap = 0;
         RCK(cudaMalloc((void**)&ctx->s_in, rays * kIn * sizeof(float)));
         RCK(cudaMalloc((void**)&ctx->s_fb, rays));
-        RCK(cudaMalloc((void**)&ctx->s_start, rays * 8 * sizeof(double)));
+        RCK(cudaMalloc((void**)&ctx->s_start, rays * 8 * sizeof(float2)));
         ctx->s_ray_cap = rays;
     }
     RCK(upload_curve(ctx, p, s));

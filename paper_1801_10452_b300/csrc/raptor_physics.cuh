@@ -13,6 +13,8 @@ struct ParamsF {
     float x1_min, x1_max, dx1, dx2, h_mks, t0, dt_snap, rho0_ne, B_unit, r_high, r_low, gam;
     float r_fp64, turn_kr;
     float nu[16];
+    // camera parameters as unevaluated float pairs (hi, lo) for the double-float camera
+    float2 a_p, sin_i_p, cos_i_p, r_cam_p, incl_p, cam_phi_p, amin_p, da_p, bmin_p, db_p;
 };
 
 // Kernel parameters (passed by value; lives in the constant bank).
@@ -63,7 +65,7 @@ struct Params {
     // learned surrogate (RAPTOR_MIXED_MLP): predicted start states [8][n_rays] (x^mu, k^mu),
     // per-ray fallback flags (start at the camera), the step count of a predicted state,
     // and the outbound exit radius beyond which the transfer is neglected (0 = off)
-    const double* start_xk;
+    const float2* start_xk;  // float pairs (hi, lo)
     const unsigned char* fallback;
     int start_n;
     double r_exit;

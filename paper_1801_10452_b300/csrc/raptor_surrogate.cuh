@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const
 // Denormalise the network outputs and rebuild the start states [8][n_rays] (FP32 except the
 // camera time and the pixel centres).
 __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, const float* __restrict__ out,
-                                   double* __restrict__ start_xk) {
+                                   float2* __restrict__ start_xk) {
     double xc[4];  // camera position at t_cam = 0 (the same for every pixel)
     camera_x_ai(p.a, p.incl, p.r_cam, 0.0, xc);
     const float af = p.f.a, sif = (float)p.sin_i, cif = (float)p.cos_i, incf = (float)p.incl, rcf = (float)p.r_cam;
@@ -682,11 +682,13 @@ __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, 
         float x[4], k[4];
         surrogate_state(af, sif, cif, al, be, pred, x, k);
         const double tc = p.t_frames ? p.t_frames[frame] : p.t_cam;
-        start_xk[id] = tc + xc[0] + (double)x[0];
+        const double t = tc + xc[0] + (double)x[0];
+        const float th = (float)t;
+        start_xk[id] = make_float2(th, (float)(t - (double)th));
 #pragma unroll
-        for (int i = 1; i < 4; ++i) start_xk[(long long)i * p.n_rays + id] = (double)x[i];
+        for (int i = 1; i < 4; ++i) start_xk[(long long)i * p.n_rays + id] = make_float2(x[i], 0.f);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) start_xk[(long long)(4 + i) * p.n_rays + id] = (double)k[i];
+        for (int i = 0; i < 4; ++i) start_xk[(long long)(4 + i) * p.n_rays + id] = make_float2(k[i], 0.f);
     }
 }
 
