@@ -210,6 +210,16 @@ raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int bloc
  * a negative c_split. */
 raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int c_split);
 
+/* CUDA graphs (enable != 0, the default): the second raptor_render / raptor_render_ex /
+ * raptor_lightcurve call with the same arguments, context settings and device buffers
+ * captures its whole launch sequence (both streams of the mixed path) into a graph, and
+ * later identical calls replay it with one launch; light curves keep their frame times in a
+ * context buffer, so a batch of frames with new times replays the same graph.  Calls made
+ * while profiling is on run directly.  raptor_graph_stats returns the number of captures and
+ * replays so far (outputs may be NULL). */
+raptor_status raptor_graph_config(raptor_ctx* ctx, int enable);
+raptor_status raptor_graph_stats(raptor_ctx* ctx, long long* captures, long long* replays);
+
 /* Autotuner: renders the context's camera once per candidate launch shape (threads per
  * block {64, 128}; blocks per SM of the ray kernels {max, 2, 3, 4}; for RAPTOR_MIXED also
  * blocks per SM of the FP64 passes {1, 2, 3, 4}), times each with CUDA events on `stream`

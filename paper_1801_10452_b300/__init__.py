@@ -31,7 +31,7 @@ EXPORTS = [
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
-    "raptor_mixed_config",
+    "raptor_mixed_config", "raptor_graph_config", "raptor_graph_stats",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp"]
@@ -111,6 +111,8 @@ def lib():
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
             "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
+            "raptor_graph_config": (st, [vp, C.c_int]),
+            "raptor_graph_stats": (st, [vp, C.c_void_p, C.c_void_p]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -357,6 +359,16 @@ class Context:
             b = (C.c_int * max(1, len(budgets)))(*[int(v) for v in budgets])
             self._check(lib().raptor_mixed_config(self._h, float(crit_band), len(budgets) + 1, b, int(c_split)),
                         "raptor_mixed_config")
+
+    def graph_config(self, enable=True):
+        """Replay repeated identical renders from a captured CUDA graph (default on)."""
+        self._check(lib().raptor_graph_config(self._h, 1 if enable else 0), "raptor_graph_config")
+
+    def graph_stats(self):
+        """(captures, replays) of the context's render graphs."""
+        c, r = C.c_longlong(0), C.c_longlong(0)
+        self._check(lib().raptor_graph_stats(self._h, C.byref(c), C.byref(r)), "raptor_graph_stats")
+        return int(c.value), int(r.value)
 
     def surrogate_kernel(self, kind):
         """Inference kernel: MLP_TCGEN05 (default) or MLP_MMA_SYNC."""

@@ -52,6 +52,13 @@ struct raptor_ctx {
     cudaStream_t s_c1 = nullptr;    // third stream (phase C1)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork_c = nullptr, ev_join_c = nullptr;
     int c_split = 0;              // phase C1 starts after this many FP64 passes (0: no split)
+    // CUDA graph of the last repeated render (raptor_graph_config)
+    bool graphs = true;
+    cudaStream_t s_cap = nullptr;     // capture stream
+    cudaGraphExec_t g_exec = nullptr;
+    std::vector<unsigned char> g_key, g_seen;
+    long long g_captures = 0, g_replays = 0;
+    unsigned long long epoch = 0;     // device-buffer epoch (see ensure)
     double crit_band = 0.5;       // M: near-critical band of the mixed path's B-long
     int n_passes = 8;             // FP64 passes of the other rays and their step budgets
     int pass_budget[8] = {16, 32, 48, 64, 96, 128, 256, 1 << 30};
@@ -144,9 +151,13 @@ raptor_status fail(raptor_ctx* c, raptor_status s, const std::string& msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                        \
     } while (0)
 
+// The context's device-buffer epoch (raptor_ctx::epoch) is bumped whenever the library
+// frees or (re)allocates a buffer that a render's kernels reference, so that a captured
+// render graph is never replayed with stale pointers.
 template <typename T>
-cudaError_t ensure(T** p, size_t* cap, size_t n) {
+cudaError_t ensure(raptor_ctx* c, T** p, size_t* cap, size_t n) {
     if (*cap >= n && *p) return cudaSuccess;
+    c->epoch += 1;
     if (*p) cudaFree(*p);
     *p = nullptr;
     *cap = 0;
@@ -333,6 +344,7 @@ int ew_blocks(long long n);
 // staged before cudaMemcpyAsync returns.
 cudaError_t upload_curve(raptor_ctx* c, const Params& p, cudaStream_t s) {
     if (!c->d_curve) {
+        c->epoch += 1;
         cudaError_t e = cudaMalloc((void**)&c->d_curve, kMaxCurve * sizeof(float2));
         if (e != cudaSuccess) return e;
     }
@@ -543,6 +555,7 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
             const size_t need = (size_t)p.n_rays;
             if (p.n_rays > 0x7fffffffLL) return fail(ctx, RAPTOR_EINVAL, "the mixed path takes at most 2^31 - 1 rays per call");
             if (ctx->mq_cap < need || ctx->mq.nf_cap < p.nf) {
+                ctx->epoch += 1;
                 free_mixed_queues(ctx->mq);
                 cudaFree(ctx->d_crit);
                 cudaFree(ctx->d_rest);
@@ -560,8 +573,8 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
     const long long len = (long long)p.n_rows * p.nx;
     const int planes = n_frames * n_freq;
     const int chunks = (int)std::min<long long>(256, std::max<long long>(1, len / 4096));
-    RCK(ensure(&ctx->d_partial, &ctx->partial_cap, (size_t)planes * chunks));
-    RCK(ensure(&ctx->d_flux, &ctx->flux_cap, (size_t)planes));
+    RCK(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, (size_t)planes * chunks));
+    RCK(ensure(ctx, &ctx->d_flux, &ctx->flux_cap, (size_t)planes));
     dim3 g1(chunks, planes);
     {
         ProfScope ps(ctx, kProfReduce, s);
@@ -574,6 +587,68 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
     }
     RCK(cudaGetLastError());
     (void)planes_per_frame;
+    return RAPTOR_OK;
+}
+
+// run_rays through a CUDA graph: the second identical call (same parameters, frequencies,
+// context settings and device buffers) captures the whole launch sequence, both streams
+// included, on the context's capture stream; later identical calls replay it with one
+// cudaGraphLaunch.  Calls with profiling on, or whose capture fails, run directly.
+raptor_status run_rays_graph(raptor_ctx* ctx, const Params& p, const double* freqs, int n_freq, long long planes_per_frame,
+                             int n_frames, cudaStream_t s) {
+    if (!ctx->graphs || ctx->prof) return run_rays(ctx, p, freqs, n_freq, planes_per_frame, n_frames, s);
+    std::vector<unsigned char> key;
+    auto put = [&key](const void* v, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(v);
+        key.insert(key.end(), b, b + n);
+    };
+    const unsigned long long epoch = ctx->epoch;
+    put(&p, sizeof(p));
+    put(&n_freq, sizeof(n_freq));
+    put(freqs, sizeof(double) * n_freq);
+    put(&planes_per_frame, sizeof(planes_per_frame));
+    put(&n_frames, sizeof(n_frames));
+    put(&ctx->cam, sizeof(ctx->cam));
+    int cfg[] = {ctx->launch_block, ctx->launch_bps, ctx->launch_bps64, ctx->n_passes, ctx->c_split, ctx->s_kernel,
+                 ctx->sur_ready ? 1 : 0};
+    put(cfg, sizeof(cfg));
+    put(ctx->pass_budget, sizeof(ctx->pass_budget));
+    double dcfg[] = {ctx->crit_band, ctx->s_band, ctx->s_r_exit};
+    put(dcfg, sizeof(dcfg));
+    put(&epoch, sizeof(epoch));
+    put(&s, sizeof(s));
+    if (ctx->g_exec && key == ctx->g_key) {
+        RCK(cudaGraphLaunch(ctx->g_exec, s));
+        ctx->g_replays += 1;
+        return RAPTOR_OK;
+    }
+    if (key != ctx->g_seen) {
+        ctx->g_seen = key;
+        return run_rays(ctx, p, freqs, n_freq, planes_per_frame, n_frames, s);
+    }
+    // second identical call: capture
+    if (!ctx->s_cap) RCK(cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    RCK(cudaStreamBeginCapture(ctx->s_cap, cudaStreamCaptureModeThreadLocal));
+    const raptor_status st = run_rays(ctx, p, freqs, n_freq, planes_per_frame, n_frames, ctx->s_cap);
+    const cudaError_t ec = cudaStreamEndCapture(ctx->s_cap, &g);
+    cudaGraphExec_t ex = nullptr;
+    const bool ok = st == RAPTOR_OK && ec == cudaSuccess && g && ctx->epoch == epoch &&
+                    cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        if (ex) cudaGraphExecDestroy(ex);
+        cudaGetLastError();  // clear a capture error; run the call directly
+        ctx->g_seen.clear();
+        ctx->err.clear();
+        return run_rays(ctx, p, freqs, n_freq, planes_per_frame, n_frames, s);
+    }
+    if (ctx->g_exec) cudaGraphExecDestroy(ctx->g_exec);
+    ctx->g_exec = ex;
+    ctx->g_key = key;
+    ctx->g_captures += 1;
+    RCK(cudaGraphLaunch(ctx->g_exec, s));
+    ctx->g_replays += 1;
     return RAPTOR_OK;
 }
 
@@ -685,7 +760,7 @@ raptor_status raptor_load_plasma(raptor_ctx* ctx, const raptor_plasma_desc* desc
     if (desc->kind == RAPTOR_PLASMA_GRID_MKS2D) {
         const size_t cells = (size_t)desc->n1 * desc->n2;
         const size_t n = cells * desc->n_snap * 8;
-        RCK(ensure(&ctx->d_grid, &ctx->grid_cap, n));
+        RCK(ensure(ctx, &ctx->d_grid, &ctx->grid_cap, n));
         float* staging = nullptr;
         RCK(cudaMallocAsync((void**)&staging, n * sizeof(float), s));
         cudaError_t e = cudaMemcpyAsync(staging, desc->fields, n * sizeof(float),
@@ -732,7 +807,7 @@ raptor_status raptor_render_ex(raptor_ctx* ctx, const double* freqs_hz, int n_fr
     p.image = image_dev;
     p.steps_out = steps_dev;
     p.status_out = status_dev;
-    st = run_rays(ctx, p, freqs_hz, n_freq, n_freq, 1, s);
+    st = run_rays_graph(ctx, p, freqs_hz, n_freq, n_freq, 1, s);
     if (st != RAPTOR_OK) return st;
     if (flux_jy_host) {
         RCK(cudaMemcpyAsync(flux_jy_host, ctx->d_flux, n_freq * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -755,7 +830,7 @@ raptor_status raptor_render_host(raptor_ctx* ctx, const double* freqs_hz, int n_
     raptor_status st = check_freqs(ctx, freqs_hz, n_freq);
     if (st != RAPTOR_OK) return st;
     const size_t n = (size_t)n_freq * ctx->cam.nx * ctx->cam.ny;
-    RCK(ensure(&ctx->d_img, &ctx->img_cap, n));
+    RCK(ensure(ctx, &ctx->d_img, &ctx->img_cap, n));
     double flux[64];
     st = raptor_render(ctx, freqs_hz, n_freq, t_obs, ctx->d_img, flux, stream);
     if (st != RAPTOR_OK) return st;
@@ -787,13 +862,13 @@ raptor_status raptor_lightcurve(raptor_ctx* ctx, const double* freqs_hz, int n_f
     if (npix * n_frames > (1LL << 40)) return fail(ctx, RAPTOR_EINVAL, "too many rays");
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
-    RCK(ensure(&ctx->d_tframes, &ctx->tframes_cap, (size_t)n_frames));
+    RCK(ensure(ctx, &ctx->d_tframes, &ctx->tframes_cap, (size_t)n_frames));
     std::vector<double> tf(n_frames);
     for (int f = 0; f < n_frames; ++f) tf[f] = t_obs_host[f] + ctx->cam.t_delay;
     RCK(cudaMemcpyAsync(ctx->d_tframes, tf.data(), n_frames * sizeof(double), cudaMemcpyHostToDevice, s));
     double* img = images_dev;
     if (!img) {
-        RCK(ensure(&ctx->d_img, &ctx->img_cap, (size_t)npix * n_freq * n_frames));
+        RCK(ensure(ctx, &ctx->d_img, &ctx->img_cap, (size_t)npix * n_freq * n_frames));
         img = ctx->d_img;
     }
     Params p = base_params(ctx);
@@ -805,7 +880,7 @@ raptor_status raptor_lightcurve(raptor_ctx* ctx, const double* freqs_hz, int n_f
     p.lc_fast = fast ? 1 : 0;
     p.frame_snap0 = first_frame;
     p.image = img;
-    st = run_rays(ctx, p, freqs_hz, n_freq, n_freq, n_frames, s);
+    st = run_rays_graph(ctx, p, freqs_hz, n_freq, n_freq, n_frames, s);
     if (st != RAPTOR_OK) return st;
     RCK(cudaMemcpyAsync(flux_jy_host, ctx->d_flux, (size_t)n_frames * n_freq * sizeof(double), cudaMemcpyDeviceToHost, s));
     RCK(cudaStreamSynchronize(s));
@@ -825,7 +900,7 @@ raptor_status raptor_trace_ray(raptor_ctx* ctx, double alpha, double beta, doubl
     if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(t_obs)) return fail(ctx, RAPTOR_EINVAL, "non-finite ray");
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
-    RCK(ensure(&ctx->d_rec, &ctx->rec_cap, (size_t)std::max(max_rec, 1) * 12));
+    RCK(ensure(ctx, &ctx->d_rec, &ctx->rec_cap, (size_t)std::max(max_rec, 1) * 12));
     Params p = base_params(ctx);
     p.i_unscale = 1.0;
     p.nf = n_freq;
@@ -897,6 +972,8 @@ void raptor_destroy(raptor_ctx* ctx) {
     cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_fork_c, ctx->ev_join_c};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
+    if (ctx->g_exec) cudaGraphExecDestroy(ctx->g_exec);
+    if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
     if (ctx->s_long) cudaStreamDestroy(ctx->s_long);
     if (ctx->s_c1) cudaStreamDestroy(ctx->s_c1);
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
@@ -932,6 +1009,7 @@ uint64_t splitmix(uint64_t& s) {
 
 cudaError_t sur_alloc(raptor_ctx* c) {
     cudaError_t e = cudaSuccess;
+    if (!c->s_P || c->s_rows < kSurRows) c->epoch += 1;
     if (!c->s_P) {
         const size_t n = MlpLayout::SIZE;
         e = cudaMalloc((void**)&c->s_P, n * sizeof(float));
@@ -940,6 +1018,9 @@ cudaError_t sur_alloc(raptor_ctx* c) {
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_m2, n * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_w, 6 * kHid * kHid * sizeof(__nv_bfloat16));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_err, sizeof(int));
+        // the tcgen05 kernels' shared-memory plans (set once, outside any stream capture)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc12, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc12Smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc34, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc34Smem);
         if (e == cudaSuccess) e = cudaMemset(c->s_err, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->s_G, 0, n * sizeof(float));
         if (e != cudaSuccess) return e;
@@ -1031,6 +1112,7 @@ cudaError_t sur_eval_rows(raptor_ctx* c, const float* inputs, long long n, float
     const long long tiles = (n + kTcRows - 1) / kTcRows;
     cudaError_t e = cudaSuccess;
     if ((size_t)tiles > c->s_h2tc_tiles) {
+        c->epoch += 1;
         e = cudaFree(c->s_h2tc);
         c->s_h2tc = nullptr;
         c->s_h2tc_tiles = 0;
@@ -1038,9 +1120,6 @@ cudaError_t sur_eval_rows(raptor_ctx* c, const float* inputs, long long n, float
         if (e != cudaSuccess) return e;
         c->s_h2tc_tiles = (size_t)tiles;
     }
-    e = cudaFuncSetAttribute(k_mlp_tc12, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc12Smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc34, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc34Smem);
-    if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<long long>(tiles, c->num_sms);
     k_mlp_tc12<<<grid, kTcThreads, kTc12Smem, s>>>(c->s_P, wtc(c), inputs, n, c->s_h2tc, c->s_err);
     k_mlp_tc34<<<grid, kTcThreads, kTc34Smem, s>>>(c->s_P, wtc(c) + kHid * kHid, c->s_h2tc, n, out_dev, c->s_err);
@@ -1312,6 +1391,25 @@ raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passe
     return RAPTOR_OK;
 }
 
+raptor_status raptor_graph_config(raptor_ctx* ctx, int enable) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->graphs = enable != 0;
+    if (!ctx->graphs && ctx->g_exec) {
+        cudaGraphExecDestroy(ctx->g_exec);
+        ctx->g_exec = nullptr;
+        ctx->g_key.clear();
+    }
+    ctx->g_seen.clear();
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_graph_stats(raptor_ctx* ctx, long long* captures, long long* replays) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (captures) *captures = ctx->g_captures;
+    if (replays) *replays = ctx->g_replays;
+    return RAPTOR_OK;
+}
+
 raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind) {
     if (!ctx) return RAPTOR_EINVAL;
     if (kind != RAPTOR_MLP_TCGEN05 && kind != RAPTOR_MLP_MMA_SYNC) return fail(ctx, RAPTOR_EINVAL, "unknown surrogate kernel");
@@ -1338,6 +1436,7 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
     RCK(sur_alloc(ctx));
     const size_t rays = (size_t)p.n_rays;
     if (ctx->s_ray_cap < rays) {
+        ctx->epoch += 1;
         cudaFree(ctx->s_in);
         cudaFree(ctx->s_fb);
         cudaFree(ctx->s_start);
@@ -1504,7 +1603,7 @@ raptor_status raptor_autotune(raptor_ctx* ctx, const double* freqs_hz, int n_fre
     if (st != RAPTOR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)n_freq * ctx->cam.nx * ctx->cam.ny;
-    RCK(ensure(&ctx->d_img, &ctx->img_cap, n));
+    RCK(ensure(ctx, &ctx->d_img, &ctx->img_cap, n));
     const bool mixed = ctx->cam.precision == RAPTOR_MIXED;
     const int blocks[2] = {64, 128};
     const int bpss[4] = {0, 2, 3, 4};
