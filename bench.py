@@ -35,6 +35,22 @@ def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def max_over_ranks(value, dist, device="cuda"):
+    """The maximum of a per-rank number over all ranks: a replicated job takes as long as its
+    slowest rank."""
+    import torch
+
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, units_per_step_per_rank, ms_per_step):
+    """Whole-job throughput of `world` replicas, each processing units_per_step_per_rank per
+    step, timed by the slowest rank's ms per step (weak scaling)."""
+    return world * units_per_step_per_rank / (ms_per_step * 1e-3)
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -224,9 +240,7 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
     ctx.profile(False)
     st = ctx.stats()
     if world > 1:
-        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
+        dev_ms = max_over_ranks(dev_ms, dist)
     _, flux = ctx.render(freqs, image=image, stream=stream)
     torch.cuda.synchronize()
     return dict(ctx=ctx, image=image, ms=dev_ms / args.steps, wall=wall, clocks=clocks, prof=prof, stats=st, flux=flux,
@@ -274,7 +288,7 @@ def run_native(args):
                                params=params if pth.startswith("mlp") else None, flags=flags)
     main = res[paths[0]]
     ms_step = main["ms"]
-    value = world * rays_step / (ms_step * 1e-3)
+    value = aggregate_rate(world, rays_step, ms_step)
     st = main["stats"]
     steps_per_s = world * (st["steps"] / args.steps) / (ms_step * 1e-3)
     launches = sum(v[1] for v in main["prof"].values())
