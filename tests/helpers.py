@@ -36,6 +36,14 @@ def ring_mask(alpha, beta, a, incl_deg, width):
     return (d < width).reshape(A.shape)
 
 
+def near_ring(alpha, beta, a, incl_deg, width):
+    """True for the points (alpha[n], beta[n]) within `width` M of the critical curve."""
+    cc = bardeen_critical_curve(a, incl_deg)
+    P = np.stack([np.asarray(alpha, float), np.asarray(beta, float)], 1)
+    d = np.sqrt(((P[:, None, :] - cc[None, :, :]) ** 2).sum(-1)).min(1)
+    return d < width
+
+
 def rel_err(gpu, ref, floor_frac=1e-12):
     """|gpu - ref| / max(|ref|, floor_frac * max|ref|) element-wise."""
     ref = np.asarray(ref)

@@ -4,7 +4,7 @@ Lyapunov amplification makes any arithmetic difference grow).  Needs a GPU."""
 import numpy as np
 import pytest
 
-from helpers import oracle_kwargs, rel_err, ring_mask
+from helpers import near_ring, oracle_kwargs, rel_err, ring_mask
 from paper_1801_10452_b300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -128,3 +128,37 @@ def test_inner_region_in_double_float(R, ora):
     _check(R, cam, img_df, fl_df, oimg, "df64")
     assert np.all(np.abs(fl_df / fl_64 - 1) < 1e-5)
     assert (st_df == ost).mean() > 0.99
+
+
+@pytest.mark.parametrize("spin,flags", [(0.0, "df64"), (0.5, "df64"), (0.9375, "df64"), (0.9375, "fp64")])
+def test_spectral_scene_full_size(R, ora, spin, flags):
+    """The spectral workload at its full size (512^2, 8 frequencies 1e10-1e13 Hz) in the
+    mixed path: the flux of every band against the FP64 GPU path (itself pinned to the
+    oracle at 1e-10), and seeded sample pixels outside the photon-ring band against the
+    oracle tracing them one by one."""
+    import torch
+
+    cam = dict(scenes.SPECTRAL, spin=spin)
+    freqs = scenes.SPECTRAL_FREQS
+    fl_flags = R.FLAG_INNER_DF64 if flags == "df64" else 0
+    ctx, img, fl, st, stat = _mixed(R, cam, freqs, flags=fl_flags)
+    c64 = R.Context(R.camera_desc(**cam, precision=R.FP64))
+    c64.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    _, f64 = c64.render(freqs)
+    torch.cuda.synchronize()
+    for f in range(len(freqs)):
+        if f64[f] >= MIN_FLUX_JY:
+            assert abs(fl[f] / f64[f] - 1) <= FLUX_TOL, (f, fl[f] / f64[f] - 1)
+    s = ora.scene(**oracle_kwargs(cam))
+    al, be = R.pixel_centres(ctx.cam)
+    Lcm = ora.length_unit_cm(cam["mass_msun"])
+    D = cam["distance_pc"] * 3.0856775814913673e18
+    pix_jy = (al[1] - al[0]) * (be[1] - be[0]) * Lcm**2 / D**2 / 1e-23
+    pix = scenes.sample_pixels(cam["nx"], cam["ny"], 40, seed=512)
+    keep = ~near_ring(al[pix[:, 1]], be[pix[:, 0]], spin, cam["incl_deg"], RING_BAND)
+    peak = img.reshape(len(freqs), -1).max(1)
+    for (i, j) in pix[keep]:
+        o = ora.trace_ray(s, al[j], be[i], freqs)
+        for f in range(len(freqs)):
+            ov = o["I"][f] * pix_jy
+            assert abs(img[f, i, j] - ov) <= PIX_TOL * max(abs(ov), 1e-6 * peak[f]), (i, j, f)

@@ -7,7 +7,7 @@ import time
 import numpy as np
 import pytest
 
-from helpers import oracle_kwargs, rel_err, ring_mask
+from helpers import near_ring, oracle_kwargs, rel_err, ring_mask
 from oracle import mlp
 from paper_1801_10452_b300 import scenes
 
@@ -202,3 +202,36 @@ def test_surrogate_gain_over_the_method_without_it(R, trained):
           f"(network {s1['surrogate_mlp']:.2f} ms); frame {gain:.3f}x (mixed {res[R.MIXED] * 1e3:.2f} ms, "
           f"mixed+MLP {res[R.MIXED_MLP] * 1e3:.2f} ms)")
     assert fp32_saved > s1["surrogate"]
+
+
+@pytest.mark.parametrize("size", [1024, 2048])
+def test_learned_path_full_size(R, ora, trained, size):
+    """The headline image (1024^2) and the learned-surrogate workload's render (2048^2),
+    a = 0.9375, 230 GHz, through RAPTOR_MIXED_MLP with double-float inner steps, as the
+    benchmark runs it: flux against the FP64 GPU path, seeded sample pixels outside the
+    photon-ring band against the oracle tracing them one by one."""
+    import torch
+
+    cam = dict(scenes.HEADLINE, nx=size, ny=size)
+    freqs = [230e9]
+    ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED_MLP, flags=R.FLAG_INNER_DF64))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    ctx.surrogate_set(trained)
+    img, fl = ctx.render(freqs)
+    c64 = R.Context(R.camera_desc(**cam, precision=R.FP64))
+    c64.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    _, f64 = c64.render(freqs)
+    torch.cuda.synchronize()
+    assert abs(fl[0] / f64[0] - 1) <= FLUX_TOL
+    img = img.cpu().numpy()
+    s = ora.scene(**oracle_kwargs(cam))
+    al, be = R.pixel_centres(ctx.cam)
+    Lcm = ora.length_unit_cm(cam["mass_msun"])
+    D = cam["distance_pc"] * 3.0856775814913673e18
+    pix_jy = (al[1] - al[0]) * (be[1] - be[0]) * Lcm**2 / D**2 / 1e-23
+    pix = scenes.sample_pixels(size, size, 48, seed=size)
+    keep = ~near_ring(al[pix[:, 1]], be[pix[:, 0]], cam["spin"], cam["incl_deg"], 0.5)
+    peak = img[0].max()
+    for (i, j) in pix[keep]:
+        ov = ora.trace_ray(s, al[j], be[i], freqs)["I"][0] * pix_jy
+        assert abs(img[0, i, j] - ov) <= PIX_TOL * max(abs(ov), 1e-6 * peak), (i, j)
