@@ -210,10 +210,16 @@ def train_surrogate(R, torch, cam, steps, n_train):
     return ctx.surrogate_get(), summ
 
 
-def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks, params=None, flags=0):
-    """Warm up, then time args.steps renders of one path; returns measurements."""
+def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks, params=None, flags=0,
+                plasma=None, fields=None, steps=None):
+    """Warm up, then time `steps` (default args.steps) renders of one path; returns
+    measurements.  plasma/fields: a grid scene (default: the analytic plasma)."""
     ctx = R.Context(R.camera_desc(**cam, precision=prec, flags=flags))
-    ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
+    if plasma is None:
+        ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
+    else:
+        ctx.load_plasma(R.plasma_desc(**plasma), fields=fields)
+    n_steps = args.steps if steps is None else steps
     if params is not None:
         ctx.surrogate_set(params)
     image = torch.empty((len(freqs), cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
@@ -230,7 +236,7 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
     ctx.stats_reset()
     ctx.profile(True)
     wall0 = time.perf_counter()
-    dev_ms = _time_render(ctx, torch, freqs, image, flush, args.steps, stream)
+    dev_ms = _time_render(ctx, torch, freqs, image, flush, n_steps, stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
@@ -243,7 +249,7 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
         dev_ms = max_over_ranks(dev_ms, dist)
     _, flux = ctx.render(freqs, image=image, stream=stream)
     torch.cuda.synchronize()
-    return dict(ctx=ctx, image=image, ms=dev_ms / args.steps, wall=wall, clocks=clocks, prof=prof, stats=st, flux=flux,
+    return dict(ctx=ctx, image=image, ms=dev_ms / n_steps, wall=wall, clocks=clocks, prof=prof, stats=st, flux=flux,
                 tuned=tuned)
 
 
@@ -286,6 +292,36 @@ def run_native(args):
         res[pth] = _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist,
                                sample_clocks=(rank == 0 and pth == paths[0]),
                                params=params if pth.startswith("mlp") else None, flags=flags)
+    # ---- the grid workload (synthetic FM torus snapshot, 256^2 MKS cells) at the same size ----
+    grid = None
+    if not args.no_grid:
+        fields, meta = scenes.torus_snapshots(1)
+        gplasma = scenes.grid_plasma(meta, scenes.DISK_MODEL)
+        gres = {}
+        for pth in ("mlp_df", "mixed_df", "fp64"):
+            prec = {"mlp_df": R.MIXED_MLP, "mixed_df": R.MIXED, "fp64": R.FP64}[pth]
+            if prec == R.MIXED_MLP and params is None:
+                continue
+            gres[pth] = _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks=False,
+                                    params=params if prec == R.MIXED_MLP else None,
+                                    flags=R.FLAG_INNER_DF64 if pth.endswith("_df") else 0, plasma=gplasma,
+                                    fields=fields, steps=2 if pth == "fp64" else None)
+        grid = {"workload": workload.replace("kerr_analytic", "grid_torus"),
+                "snapshot": "Fishbone-Moncrief torus x lognormal noise, 256 x 256 MKS cells, 2 MiB (L2-resident)"}
+        for pth, r in gres.items():
+            st = r["stats"]
+            n_r = args.steps if pth != "fp64" else 2
+            samples_s = (st["steps"] / n_r) / (r["ms"] * 1e-3)
+            grid[pth] = {"ms_per_step": r["ms"], "rays_per_s": aggregate_rate(world, rays_step, r["ms"]),
+                         "geodesic_steps_per_s": world * samples_s, "flux_jy": float(r["flux"][0]),
+                         "grid_sample_GBps": samples_s * 128 / 1e9,
+                         "grid_sample_note": "128 B of FP32 fields per plasma sample (4 corners x 8 fields), "
+                                             "served from L2: the snapshot is 2 MiB"}
+            r["ctx"].close()
+        if "fp64" in gres:
+            for pth in gres:
+                if pth != "fp64":
+                    grid[pth]["flux_rel_err_vs_fp64"] = float(abs(gres[pth]["flux"][0] / gres["fp64"]["flux"][0] - 1))
     main = res[paths[0]]
     ms_step = main["ms"]
     value = aggregate_rate(world, rays_step, ms_step)
@@ -404,6 +440,7 @@ def run_native(args):
         "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64},
         "launch": main["tuned"],
         "surrogate": sur,
+        "grid_workload": grid,
     }
     for pth, r in res.items():
         if pth == paths[0]:
@@ -453,6 +490,7 @@ def main():
     ap.add_argument("--size", type=int, default=1024, help="image side (profiling runs use a smaller case)")
     ap.add_argument("--paths", default="mlp_df,mlp,mixed_df,mixed,fp64",
                     help="comma list of paths to time (first = value): mlp, mixed, fp64, mlp_df, mixed_df")
+    ap.add_argument("--no-grid", action="store_true", help="skip the grid (torus snapshot) workload")
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-rays", type=int, default=1_000_000)
     args = ap.parse_args()

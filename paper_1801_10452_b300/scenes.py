@@ -177,3 +177,10 @@ def torus_snapshots(n_snap=1, dt_snap=10.0, **over):
     meta = dict(x1_min=G["x1_min"], x1_max=G["x1_max"], h_mks=h, n1=c["n1"], n2=c["n2"], n_snap=n_snap,
                 dt_snap=dt_snap, gamma_ad=gam, spin=a, l=l)
     return out, meta
+
+
+def grid_plasma(meta: dict, model: dict, slow: int = 0, t0: float = 0.0) -> dict:
+    """raptor_plasma_desc fields of a grid snapshot series made by torus_snapshots."""
+    return dict(slow_light=slow, x1_min=meta["x1_min"], x1_max=meta["x1_max"], h_mks=meta["h_mks"], t0=t0,
+                dt_snap=meta["dt_snap"], mass_unit_g=model["mass_unit_g"], r_high=model["r_high"],
+                r_low=model["r_low"], gamma_ad=meta["gamma_ad"])

@@ -85,6 +85,6 @@ def grid_oracle_scene(ora, cam, fields, meta, model, slow=0, t0=0.0, snap=0):
 
 
 def grid_plasma_kwargs(meta, model, slow=0, t0=0.0):
-    return dict(slow_light=slow, x1_min=meta["x1_min"], x1_max=meta["x1_max"], h_mks=meta["h_mks"], t0=t0,
-                dt_snap=meta["dt_snap"], mass_unit_g=model["mass_unit_g"], r_high=model["r_high"],
-                r_low=model["r_low"], gamma_ad=meta["gamma_ad"])
+    from paper_1801_10452_b300 import scenes
+
+    return scenes.grid_plasma(meta, model, slow, t0)
