@@ -253,6 +253,65 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
                 tuned=tuned)
 
 
+def _lightcurve_extra(R, torch, args, stream, params, n=100, size=256):
+    """Slow-light light curve: n snapshots of the torus 10 M apart (noise advected at the
+    Keplerian rate), n frames of size^2 at 230 GHz in one persistent launch sequence per
+    path, against n per-frame fast-light renders (frame f on snapshot f)."""
+    from paper_1801_10452_b300 import scenes
+
+    fields, meta = scenes.torus_snapshots(n, dt_snap=10.0, device="cuda", seed=scenes.SLOW["seed"])
+    cam = dict(scenes.HEADLINE, nx=size, ny=size)
+    freqs = [230e9]
+    t_obs = 10.0 * np.arange(n)
+    out = {"workload": f"grid_torus_lightcurve_{n}x{size}x{size}_230GHz",
+           "frames": n, "rays_per_lightcurve": n * size * size,
+           "snapshots": f"{n} x 2 MiB, 10 M apart, noise rotated at the local Keplerian rate"}
+
+    def make(prec, flags, slow):
+        ctx = R.Context(R.camera_desc(**cam, precision=prec, flags=flags))
+        ctx.load_plasma(R.plasma_desc(**scenes.grid_plasma(meta, scenes.DISK_MODEL, slow, -50.0)), fields=fields)
+        if prec == R.MIXED_MLP:
+            ctx.surrogate_set(params)
+        return ctx
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    paths = [("mlp_df", R.MIXED_MLP, R.FLAG_INNER_DF64)] if params is not None else []
+    paths += [("mixed_df", R.MIXED, R.FLAG_INNER_DF64), ("fp64", R.FP64, 0)]
+    for name, prec, flags in paths:
+        slow = make(prec, flags, 1)
+        reps = 1 if prec == R.FP64 else 2
+        ms_lc = timed(lambda: slow.lightcurve(freqs, t_obs, stream=stream), reps)
+        fl = slow.lightcurve(freqs, t_obs, stream=stream)
+        entry = {"ms_per_lightcurve": ms_lc, "rays_per_s": n * size * size / (ms_lc * 1e-3),
+                 "flux_jy_min_max": [float(fl.min()), float(fl.max())]}
+        slow.close()
+        if prec != R.FP64:
+            fast = make(prec, flags, 0)
+            img = torch.empty((1, size, size), dtype=torch.float64, device="cuda")
+
+            def frames():
+                for f in range(n):
+                    fast.render(freqs, image=img, flux=False, snap=f, stream=stream)
+
+            ms_pf = timed(frames, 1)
+            entry["per_frame_fast_light_ms"] = ms_pf
+            entry["per_frame_rays_per_s"] = n * size * size / (ms_pf * 1e-3)
+            fast.close()
+        out[name] = entry
+    return out
+
+
 def scenes_mod():
     from paper_1801_10452_b300 import scenes
 
@@ -322,6 +381,10 @@ def run_native(args):
             for pth in gres:
                 if pth != "fp64":
                     grid[pth]["flux_rel_err_vs_fp64"] = float(abs(gres[pth]["flux"][0] / gres["fp64"]["flux"][0] - 1))
+    # ---- the slow-light light curve (100 snapshots 10 M apart, 100 frames of 256^2) ----
+    lcurve = None
+    if not args.no_lightcurve:
+        lcurve = _lightcurve_extra(R, torch, args, stream, params)
     main = res[paths[0]]
     ms_step = main["ms"]
     value = aggregate_rate(world, rays_step, ms_step)
@@ -441,6 +504,7 @@ def run_native(args):
         "launch": main["tuned"],
         "surrogate": sur,
         "grid_workload": grid,
+        "lightcurve_workload": lcurve,
     }
     for pth, r in res.items():
         if pth == paths[0]:
@@ -491,6 +555,7 @@ def main():
     ap.add_argument("--paths", default="mlp_df,mlp,mixed_df,mixed,fp64",
                     help="comma list of paths to time (first = value): mlp, mixed, fp64, mlp_df, mixed_df")
     ap.add_argument("--no-grid", action="store_true", help="skip the grid (torus snapshot) workload")
+    ap.add_argument("--no-lightcurve", action="store_true", help="skip the slow-light light-curve workload")
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-rays", type=int, default=1_000_000)
     args = ap.parse_args()

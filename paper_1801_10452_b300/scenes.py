@@ -100,9 +100,18 @@ def _noise(rng, n_modes, ell):
     return k.astype(np.float64), ph
 
 
-def _sample_noise(k, ph, X):
-    """G at points X [..., 3]: sqrt(2/N) sum cos(k.x + phi)."""
+def _sample_noise(k, ph, X, device=None):
+    """G at points X [..., 3]: sqrt(2/N) sum cos(k.x + phi).  With a torch `device` the sum
+    runs there in float64 (same formula; rounding differs in the last bits)."""
     shp = X.shape[:-1]
+    if device is not None:
+        import torch
+
+        kt = torch.as_tensor(k, dtype=torch.float64, device=device)
+        pt = torch.as_tensor(ph, dtype=torch.float64, device=device)
+        P = torch.as_tensor(X.reshape(-1, 3), dtype=torch.float64, device=device)
+        g = torch.cos(P @ kt.T + pt).sum(1) * np.sqrt(2.0 / k.shape[0])
+        return g.cpu().numpy().reshape(shp)
     P = X.reshape(-1, 3)
     out = np.empty(P.shape[0])
     for i in range(0, P.shape[0], 16384):
@@ -111,8 +120,9 @@ def _sample_noise(k, ph, X):
     return (np.sqrt(2.0 / k.shape[0]) * out).reshape(shp)
 
 
-def torus_snapshots(n_snap=1, dt_snap=10.0, **over):
-    """Seeded synthetic snapshot series.  Returns (fields float32 [n_snap][8][n2][n1], meta)."""
+def torus_snapshots(n_snap=1, dt_snap=10.0, device=None, **over):
+    """Seeded synthetic snapshot series.  Returns (fields float32 [n_snap][8][n2][n1], meta).
+    device: a torch device for the noise sums (long series; default numpy)."""
     c = dict(TORUS)
     c.update(over)
     a, h, gam = c["spin"], c["h_mks"], c["gamma_ad"]
@@ -169,7 +179,7 @@ def torus_snapshots(n_snap=1, dt_snap=10.0, **over):
     for s in range(n_snap):
         ang = -Om_k * dt_snap * s
         X = np.stack([varpi * np.cos(ang), varpi * np.sin(ang), r * np.cos(th)], -1)
-        Gn = _sample_noise(k, ph, X)
+        Gn = _sample_noise(k, ph, X, device)
         ln = np.exp(c["sigma"] * Gn - 0.5 * c["sigma"] ** 2)
         rho = np.maximum(rho_t * ln, rho_fl)
         u = np.maximum(u_t * ln, u_fl)
