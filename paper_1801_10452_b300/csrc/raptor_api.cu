@@ -379,9 +379,9 @@ cudaError_t upload_curve(raptor_ctx* c, const Params& p, cudaStream_t s) {
 constexpr int kPassBudget[kMaxPasses] = {16, 32, 48, 64, 96, 128, 256, 1 << 30};
 
 template <int NF, typename S>
-cudaError_t launch_fp64_phase(raptor_ctx* c, const Params& p, const PhaseIO& io, int blocks, cudaStream_t s) {
+cudaError_t launch_fp64_phase(raptor_ctx* c, const Params& p, const PhaseIO& io, int blocks, int threads, cudaStream_t s) {
     ProfScope ps(c, kProfMixedB, s);
-    k_mixed_fp64<NF, S><<<std::max(1, blocks), c->launch_block, 0, s>>>(p, io, c->mq.cap, c->d_counters, c->d_stats);
+    k_mixed_fp64<NF, S><<<std::max(1, blocks), threads, 0, s>>>(p, io, c->mq.cap, c->d_counters, c->d_stats);
     return cudaGetLastError();
 }
 
@@ -408,9 +408,14 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     const int bA = (int)std::max<long long>(1, std::min<long long>(b32, need));
     const MixedQueues& mq = c->mq;
     unsigned long long* cnt = c->d_counters;
-    auto fp64_phase = [&](const PhaseIO& io, int blocks, cudaStream_t st) {
-        return df ? launch_fp64_phase<NF, df64>(c, p, io, blocks, st) : launch_fp64_phase<NF, double>(c, p, io, blocks, st);
+    auto fp64_phase = [&](const PhaseIO& io, int blocks, int threads, cudaStream_t st) {
+        return df ? launch_fp64_phase<NF, df64>(c, p, io, blocks, threads, st)
+                  : launch_fp64_phase<NF, double>(c, p, io, blocks, threads, st);
     };
+    // B-long uses the launch shape of the passes (one-warp blocks, which return their
+    // registers to the SM as soon as their warp is done, measured slower)
+    const int long_threads = c->launch_block;
+    const int b_long = b64;
     // near-critical / other split
     const float grow = (float)c->crit_band + 1e-3f;
     const float4 box = make_float4(c->curve_box.x - grow, c->curve_box.y + grow, c->curve_box.z - grow, c->curve_box.w + grow);
@@ -446,7 +451,7 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     bl.push_cnt = kCntPush32L;
     bl.requeue_cnt = -1;
     bl.budget = 1 << 30;
-    e = fp64_phase(bl, b64, c->s_long);
+    e = fp64_phase(bl, b_long, long_threads, c->s_long);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->s_long);
     if (e != cudaSuccess) return e;
     // phase A2
@@ -496,7 +501,7 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
         b.push_cnt = kCntPush32;
         b.requeue_cnt = pass + 1 < c->n_passes ? kCntPassOut + pass : -1;
         b.budget = pass + 1 < c->n_passes ? c->pass_budget[pass] : (1 << 30);
-        e = fp64_phase(b, b64, s);
+        e = fp64_phase(b, b64, c->launch_block, s);
         if (e != cudaSuccess) return e;
     }
     // phase C (C2 after a split: the leavers from the snapshot on), then, after the joins,
