@@ -317,6 +317,12 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 raptor_status raptor_profile(raptor_ctx* ctx, int enable);
 raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches);
 
+/* Self-check of the FP32 reciprocal the FP32 code paths use (the hardware's approximate
+ * reciprocal refined by one Newton-Raphson step): *max_ulp receives the largest distance in
+ * ulps from the correctly rounded 1/v over n values spanning 2^-100 .. 2^101 of both signs.
+ * Synchronises the device.  The paper has no counterpart. */
+raptor_status raptor_check_fp32_reciprocal(long long n, unsigned int* max_ulp);
+
 /* FMA-chain microbenchmark on the current device: dependent FP64 (fp64 = 1) or FP32
  * (fp64 = 0) fused multiply-adds on every SM; *tflops = achieved rate (2 flops per FMA).
  * Measures the arithmetic ceiling used for the rooflines of the ray kernels. */

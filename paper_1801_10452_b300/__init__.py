@@ -31,7 +31,7 @@ EXPORTS = [
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
-    "raptor_mixed_config", "raptor_graph_config", "raptor_graph_stats",
+    "raptor_mixed_config", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_reciprocal",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp"]
@@ -112,6 +112,7 @@ def lib():
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
             "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
             "raptor_graph_config": (st, [vp, C.c_int]),
+            "raptor_check_fp32_reciprocal": (st, [C.c_longlong, C.c_void_p]),
             "raptor_graph_stats": (st, [vp, C.c_void_p, C.c_void_p]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
@@ -409,3 +410,12 @@ def pixel_centres(cam: CameraDesc):
     da = (cam.alpha_max - cam.alpha_min) / cam.nx
     db = (cam.beta_max - cam.beta_min) / cam.ny
     return cam.alpha_min + (np.arange(cam.nx) + 0.5) * da, cam.beta_min + (np.arange(cam.ny) + 0.5) * db
+
+
+def check_fp32_reciprocal(n=1 << 24):
+    """Largest ulp distance of the library's FP32 reciprocal from the correctly rounded one."""
+    u = C.c_uint(0)
+    st = lib().raptor_check_fp32_reciprocal(int(n), C.byref(u))
+    if st != OK:
+        raise RaptorError(st, "raptor_check_fp32_reciprocal")
+    return int(u.value)

@@ -34,7 +34,7 @@ RAPTOR_HD T newton_x2(T theta, T h) {
         if (fabs(fp) < T(1e-12)) {
             xn = T(0.05);
         } else {
-            xn = xv - f / fp;
+            xn = xv - dv(f, fp);
             if (xn < T(0) || xn > T(1)) xn = T(0.05);
         }
         const T d = fabs(xn - xv);
@@ -84,8 +84,8 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     if (x1 < RAPTOR_P(T, x1_min) || x1 > RAPTOR_P(T, x1_max)) return 0;
     const T h = RAPTOR_P(T, h_mks);
     const T x2 = newton_x2<T>(x[2], h);
-    T fi = (x1 - RAPTOR_P(T, x1_min)) / RAPTOR_P(T, dx1) - T(0.5);
-    T fj = x2 / RAPTOR_P(T, dx2) - T(0.5);
+    T fi = dv(x1 - RAPTOR_P(T, x1_min), RAPTOR_P(T, dx1)) - T(0.5);
+    T fj = dv(x2, RAPTOR_P(T, dx2)) - T(0.5);
     int i0 = (int)floor(fi), j0 = (int)floor(fj);
     T wi = fi - T(i0), wj = fj - T(j0);
     if (i0 < 0) { i0 = 0; wi = T(0); }
@@ -94,7 +94,7 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     if (j0 > p.n2 - 2) { j0 = p.n2 - 2; wj = T(1); }
     T q[8];
     if (p.slow && p.n_snap > 1) {
-        T fs = (x[0] - RAPTOR_P(T, t0)) / RAPTOR_P(T, dt_snap);
+        T fs = dv(x[0] - RAPTOR_P(T, t0), RAPTOR_P(T, dt_snap));
         fs = fmin(fmax(fs, T(0)), T(p.n_snap - 1));
         int s0 = (int)floor(fs);
         if (s0 > p.n_snap - 2) s0 = p.n_snap - 2;
@@ -120,8 +120,8 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     const T gam = Real<T>::sqrt_(T(1) + qq);
     const T opz = T(1) + P.z;
     const T alp = rsq(opz);                 // lapse, g^tt = -(1 + z)
-    const T gti1 = P.z / J1;                // g^{t x1} in MKS; g^{t x2} = g^{t x3} = 0
-    const T ut = gam / alp;
+    const T gti1 = dv(P.z, J1);                // g^{t x1} in MKS; g^{t x2} = g^{t x3} = 0
+    const T ut = dv(gam, alp);
     const T u1 = U1 - gam * alp * gti1, u2 = U2, u3 = U3;
     // covariant spatial u_i (MKS)
     const T uc1 = J1 * (P.gtr * ut + P.grr * J1 * u1 + P.grp * u3);
@@ -129,7 +129,7 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     const T uc3 = P.gtp * ut + P.grp * J1 * u1 + P.gpp * u3;
     const T B1 = q[5], B2 = q[6], B3 = q[7];
     const T bt = B1 * uc1 + B2 * uc2 + B3 * uc3;
-    const T iut = T(1) / ut;
+    const T iut = dv(T(1), ut);
     const T b1 = (B1 + bt * u1) * iut, b2 = (B2 + bt * u2) * iut, b3 = (B3 + bt * u3) * iut;
     // KS components
     u[0] = ut; u[1] = J1 * u1; u[2] = J2 * u2; u[3] = u3;
@@ -141,10 +141,10 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     const T gm1 = RAPTOR_P(T, gam) - T(1);
     ne = rho * RAPTOR_P(T, rho0_ne);
     B = Real<T>::sqrt_(bsq) * RAPTOR_P(T, B_unit);
-    const T betap = gm1 * uu / (T(0.5) * bsq);
+    const T betap = dv(gm1 * uu, T(0.5) * bsq);
     const T b2p = betap * betap;
-    const T R = RAPTOR_P(T, r_low) / (T(1) + b2p) + RAPTOR_P(T, r_high) * b2p / (T(1) + b2p);
-    the = T(kMp / kMe) * gm1 * (uu / rho) / (T(1) + R);
+    const T R = dv(RAPTOR_P(T, r_low), T(1) + b2p) + dv(RAPTOR_P(T, r_high) * b2p, T(1) + b2p);
+    the = dv(T(kMp / kMe) * gm1 * dv(uu, rho), T(1) + R);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = bk[i] * RAPTOR_P(T, B_unit);
     return 1;
@@ -185,11 +185,11 @@ RAPTOR_HD int plasma_sample(const Params& p, const T x[4], const T k[4], int sna
         if (ok <= 0) return ok;
         ks_lower(P, k, kc);
         g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];
-        kb = (kc[0] * b[0] + kc[1] * b[1] + kc[2] * b[2] + kc[3] * b[3]) / B;
+        kb = dv(kc[0] * b[0] + kc[1] * b[1] + kc[2] * b[2] + kc[3] * b[3], B);
     }
     if (!(g > T(0))) return -1;
     // cos theta_B = (k_phys . b) / (g |b|) with k_phys = -k
-    T cb = -kb / g;
+    T cb = dv(-kb, g);
     cb = fmin(fmax(cb, T(-1)), T(1));
     sinb = Real<T>::sqrt_(T(1) - cb * cb);
     return 1;

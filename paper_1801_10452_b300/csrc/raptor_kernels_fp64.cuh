@@ -236,6 +236,22 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double* __re
 }
 
 // FMA-chain microbenchmark: 16 independent dependent chains per thread.
+// Self-check of rcp_nr against the correctly rounded reciprocal: the largest distance in
+// ulps over n values v = +-m 2^e (m from a Weyl sequence in [1, 2), e in [-100, 100]).
+__global__ void k_check_rcp(long long n, unsigned int* max_ulp) {
+    unsigned int worst = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float m = 1.0f + (float)((i * 0x9E3779B9ull) & 0xFFFFFF) * (1.0f / 16777216.0f);
+        const int e = (int)(i % 201) - 100;
+        float v = ldexpf(m, e);
+        if (i & 1) v = -v;
+        const float r1 = rcp_nr(v), r0 = 1.0f / v;
+        const int d = __float_as_int(r1) - __float_as_int(r0);
+        worst = max(worst, (unsigned int)(d < 0 ? -d : d));
+    }
+    atomicMax(max_ulp, worst);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fma_peak(T* out, int iters, T seed) {
     T a[16];

@@ -176,7 +176,7 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
     if (ok <= 0) return ok;
     const float dlcm = dl * p.f.Lcm;
     const float gdl_unscaled = g * dlcm * float(kIUnscale);
-    const float ig2 = 1.f / (g * g);
+    const float ig2 = rcp_nr(g * g);
     const bool k2x = (p.flags & kFlagK2Exact) != 0;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -184,8 +184,8 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
             float j, S;
             synchrotron<float>(g * p.f.nu[f], ne, the, B, sinb, k2x, j, S, kIScale);
             if (j > 0.f && S > 0.f) {
-                const float dtau = j / S * gdl_unscaled;
-                const float F = dtau > 1e-4f ? -expm1f(-dtau) / dtau : 1.f - 0.5f * dtau;
+                const float dtau = j * rcp_nr(S) * gdl_unscaled;
+                const float F = dtau > 1e-4f ? -expm1f(-dtau) * rcp_nr(dtau) : 1.f - 0.5f * dtau;
                 const float tau_now = tau[f] + tau_hi[f].hi;
                 I[f] += TI(expf(-tau_now) * j * dlcm * F * ig2);
                 if (tau_hi[f].hi > 0.f || tau[f] + dtau > 10.f) tau_hi[f] = tau_hi[f] + df64(dtau, 0.f);

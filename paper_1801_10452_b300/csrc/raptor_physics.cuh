@@ -194,9 +194,9 @@ RAPTOR_HD int analytic_velocity(T a, T r_isco, const KSPoint<T>& P, T u[4]) {
         const T a2 = a * a;
         const T Pp = r * r + a2;
         const T s = Real<T>::sqrt_(T(2) * r * Pp);
-        u[0] = (Pp * (Pp * Pp + T(2) * r * Pp + T(4) * r * r) / (Pp * Pp + T(2) * r * s) - a2 * P.s2) * P.iSig;
+        u[0] = (dv(Pp * (Pp * Pp + T(2) * r * Pp + T(4) * r * r), Pp * Pp + T(2) * r * s) - a2 * P.s2) * P.iSig;
         u[1] = -s * P.iSig;
-        u[3] = -T(2) * a * r * P.iSig / (T(2) * r + s);
+        u[3] = dv(-T(2) * a * r * P.iSig, T(2) * r + s);
     }
     return 1;
 }
@@ -227,12 +227,12 @@ RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, 
     const T nu_c_per_G = T(kQe / (2.0 * kPi * kMe * kC));
     const T cj = T(1.4142135623730951 * kPi * kQe * kQe / (3.0 * kC)) * jscale;
     const T hme = T(kH / (kMe * kC * kC));
-    const T x = hme * nu / the;
-    S = T(2.0 * kMe) * nu * nu * the * (x / Real<T>::expm1_(x));
+    const T x = dv(hme * nu, the);
+    S = T(2.0 * kMe) * nu * nu * the * dv(x, Real<T>::expm1_(x));
     j = T(0);
     const T nu_s = T(2.0 / 9.0) * nu_c_per_G * B * the * the * sinb;
     if (!(nu_s > T(0))) return;
-    const T X = nu / nu_s;
+    const T X = dv(nu, nu_s);
     const T X13 = Real<T>::cbrt_(X);
     if (X13 > Real<T>::exp_cut) return;
     const T X16 = Real<T>::sqrt_(X13);
@@ -240,7 +240,7 @@ RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, 
     const T fac = X12 + T(1.8877486253633870) * X16;  // 2^(11/12)
     T K2 = T(2) * the * the;
     if (k2_exact) K2 = T(bessel_k2_exact(1.0 / double(the)));
-    j = cj * ne * nu_s / K2 * fac * fac * Real<T>::exp_(-X13);
+    j = dv(cj * ne * nu_s, K2) * fac * fac * Real<T>::exp_(-X13);
 }
 
 // Backward transfer (Eqs. 35-36, per-step solution of Eq. 34):

@@ -162,3 +162,9 @@ def test_spectral_scene_full_size(R, ora, spin, flags):
         for f in range(len(freqs)):
             ov = o["I"][f] * pix_jy
             assert abs(img[f, i, j] - ov) <= PIX_TOL * max(abs(ov), 1e-6 * peak[f]), (i, j, f)
+
+
+def test_fp32_reciprocal_within_one_ulp(R):
+    """The FP32 paths' reciprocal (approximate reciprocal + one Newton-Raphson step) stays
+    within one ulp of the correctly rounded 1/v over 2^24 values spanning 2^-100 .. 2^101."""
+    assert R.check_fp32_reciprocal(1 << 24) <= 1
