@@ -203,19 +203,22 @@ raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int bloc
  * concurrently with the other rays' phases A2, B and C [0.5].  The other rays' FP64 phase
  * runs in n_passes passes (1..8): pass k continues each ray for at most budgets[k] steps
  * and re-queues the unfinished ones for pass k + 1; the last pass has no limit (budgets may
- * be NULL: the default schedule).  After c_split passes (0: never) the leavers so far go
- * through phase C on a third stream while the later passes run [0].  Only the schedule
- * changes: every ray's arithmetic, and so every result, is the same for any setting.
- * RAPTOR_EINVAL for a negative or non-finite band, n_passes outside 1..8, a budget < 1 or
- * a negative c_split. */
-raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int c_split);
+ * be NULL: the default schedule).  With tail_split = K in 1 .. n_passes - 1, the rays still
+ * in the FP64 region after K passes finish their FP64 phase on the second stream (after the
+ * near-critical rays), while the first stream goes on with phase C [0: no split].  Only the
+ * schedule changes: every ray's arithmetic, and so every result, is the same for any
+ * setting.  RAPTOR_EINVAL for a negative or non-finite band, n_passes outside 1..8, a
+ * budget < 1 or a negative tail_split. */
+raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int tail_split);
 
 /* CUDA graphs (enable != 0, the default): the second raptor_render / raptor_render_ex /
  * raptor_lightcurve call with the same arguments, context settings and device buffers
  * captures its whole launch sequence (both streams of the mixed path) into a graph, and
  * later identical calls replay it with one launch; light curves keep their frame times in a
- * context buffer, so a batch of frames with new times replays the same graph.  Calls made
- * while profiling is on run directly.  raptor_graph_stats returns the number of captures and
+ * context buffer, so a batch of frames with new times replays the same graph.  Calls of more
+ * than 2^19 rays (pixels x frames) and calls made while profiling is on run directly (at that
+ * size the launch latencies are negligible and direct launches overlap the two streams
+ * better).  raptor_graph_stats returns the number of captures and
  * replays so far (outputs may be NULL). */
 raptor_status raptor_graph_config(raptor_ctx* ctx, int enable);
 raptor_status raptor_graph_stats(raptor_ctx* ctx, long long* captures, long long* replays);

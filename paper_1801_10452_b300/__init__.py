@@ -349,16 +349,17 @@ class Context:
         P = np.ascontiguousarray(P, dtype=np.float32)
         self._check(lib().raptor_surrogate_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size), "raptor_surrogate_set")
 
-    def mixed_config(self, crit_band=0.5, budgets=None, c_split=0):
+    def mixed_config(self, crit_band=0.5, budgets=None, tail_split=0):
         """Schedule of the mixed path: the near-critical band (M) whose rays run their FP64
         phase on the second stream, the step budgets of the other rays' FP64 passes (None:
-        the default; the last pass is unlimited), and the pass after which phase C starts on
-        a third stream (0: never)."""
+        the default; the last pass is unlimited), and the number of passes after which the
+        remaining FP64 work moves to the second stream (0: never)."""
         if budgets is None:
-            self._check(lib().raptor_mixed_config(self._h, float(crit_band), 8, None, int(c_split)), "raptor_mixed_config")
+            self._check(lib().raptor_mixed_config(self._h, float(crit_band), 8, None, int(tail_split)),
+                        "raptor_mixed_config")
         else:
             b = (C.c_int * max(1, len(budgets)))(*[int(v) for v in budgets])
-            self._check(lib().raptor_mixed_config(self._h, float(crit_band), len(budgets) + 1, b, int(c_split)),
+            self._check(lib().raptor_mixed_config(self._h, float(crit_band), len(budgets) + 1, b, int(tail_split)),
                         "raptor_mixed_config")
 
     def graph_config(self, enable=True):

@@ -49,9 +49,8 @@ struct raptor_ctx {
     int* d_crit = nullptr;        // mixed path: near-critical ray ids (phase A1)
     int* d_rest = nullptr;        // mixed path: the other ray ids (phase A2)
     cudaStream_t s_long = nullptr;  // second stream of the mixed path (B-long)
-    cudaStream_t s_c1 = nullptr;    // third stream (phase C1)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork_c = nullptr, ev_join_c = nullptr;
-    int c_split = 0;              // phase C1 starts after this many FP64 passes (0: no split)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr;
+    int tail_split = 0;           // after this many FP64 passes the rest moves to B-tail (0: never)
     // CUDA graph of the last repeated render (raptor_graph_config)
     bool graphs = true;
     cudaStream_t s_cap = nullptr;     // capture stream
@@ -377,6 +376,7 @@ cudaError_t upload_curve(raptor_ctx* c, const Params& p, cudaStream_t s) {
 // stream phase A2, the FP64 passes of growing step budget on the other queued rays, phase C
 // on their leavers; join; phase C on B-long's leavers.
 constexpr int kPassBudget[kMaxPasses] = {16, 32, 48, 64, 96, 128, 256, 1 << 30};
+constexpr long long kGraphMaxRays = 1LL << 19;  // largest call replayed from a graph
 
 template <int NF, typename S>
 cudaError_t launch_fp64_phase(raptor_ctx* c, const Params& p, const PhaseIO& io, int blocks, int threads, cudaStream_t s) {
@@ -389,9 +389,15 @@ template <int NF>
 cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s);
     if (e == cudaSuccess) e = upload_curve(c, p, s);
-    if (e == cudaSuccess && !c->s_long) e = cudaStreamCreateWithFlags(&c->s_long, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !c->s_c1) e = cudaStreamCreateWithFlags(&c->s_c1, cudaStreamNonBlocking);
-    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join, &c->ev_fork_c, &c->ev_join_c};
+    if (e == cudaSuccess && !c->s_long) {
+        // the near-critical rays' chain of steps bounds the frame: their stream gets the
+        // highest priority, so its blocks are placed first whenever an SM frees resources
+        // (kernel nodes captured into a graph keep the priority)
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_long, cudaStreamNonBlocking, hi);
+    }
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join, &c->ev_tail};
     for (cudaEvent_t* ev : evs)
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
@@ -452,7 +458,6 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     bl.requeue_cnt = -1;
     bl.budget = 1 << 30;
     e = fp64_phase(bl, b_long, long_threads, c->s_long);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->s_long);
     if (e != cudaSuccess) return e;
     // phase A2
     PhaseIO a2 = a1;
@@ -472,26 +477,12 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     cc.total = kCntPush32;
     cc.push_cnt = -1;
     cc.requeue_cnt = -1;
-    const bool split_c = c->c_split > 0 && c->c_split < c->n_passes;
-    // FP64 passes on the other rays: q64 [snapshot, end) -> q64b -> q64c -> q64b ...
-    for (int pass = 0; pass < c->n_passes; ++pass) {
-        if (split_c && pass == c->c_split) {
-            // fork: phase C1 on the leavers so far, concurrently with the later passes
-            k_snapshot32<<<1, 1, 0, s>>>(cnt);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork_c, s);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_c1, c->ev_fork_c, 0);
-            if (e != cudaSuccess) return e;
-            PhaseIO c1 = cc;
-            c1.total = kCntSnap32;
-            {
-                ProfScope ps(c, kProfMixedC, c->s_c1);
-                k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, c->s_c1>>>(p, c1, mq.cap, cnt, c->d_stats);
-            }
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_c, c->s_c1);
-            if (e != cudaSuccess) return e;
-        }
+    // FP64 passes on the other rays: q64 [snapshot, end) -> q64b -> q64c -> q64b ...; with a
+    // tail split after K passes, pass K - 1 still re-queues, and B-tail (second stream, after
+    // B-long and after pass K - 1) takes those rays to the end of their FP64 phase
+    const int K = (c->tail_split > 0 && c->tail_split < c->n_passes) ? c->tail_split : c->n_passes;
+    const bool tail = K < c->n_passes;
+    for (int pass = 0; pass < K; ++pass) {
         PhaseIO b{};
         b.in = pass == 0 ? mq.q64 : ((pass & 1) ? mq.q64b : mq.q64c);
         b.requeue = (pass & 1) ? mq.q64c : mq.q64b;
@@ -499,21 +490,36 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
         b.fetch = kCntPassFetch + pass;
         b.total = pass == 0 ? kCntPush64 : kCntPassOut + pass - 1;
         b.push_cnt = kCntPush32;
-        b.requeue_cnt = pass + 1 < c->n_passes ? kCntPassOut + pass : -1;
+        b.requeue_cnt = (pass + 1 < c->n_passes) ? kCntPassOut + pass : -1;
         b.budget = pass + 1 < c->n_passes ? c->pass_budget[pass] : (1 << 30);
+        b.in_exact = pass > 0;
         e = fp64_phase(b, b64, c->launch_block, s);
         if (e != cudaSuccess) return e;
     }
-    // phase C (C2 after a split: the leavers from the snapshot on), then, after the joins,
-    // on B-long's leavers
-    PhaseIO c2 = cc;
-    if (split_c) c2.fetch = kCntFetch32b;
+    if (tail) {
+        e = cudaEventRecord(c->ev_tail, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_tail, 0);
+        if (e != cudaSuccess) return e;
+        PhaseIO bt{};
+        bt.in = ((K - 1) & 1) ? mq.q64c : mq.q64b;
+        bt.push = mq.q32l;
+        bt.fetch = kCntTailFetch;
+        bt.total = kCntPassOut + K - 1;
+        bt.push_cnt = kCntPush32L;
+        bt.requeue_cnt = -1;
+        bt.budget = 1 << 30;
+        bt.in_exact = 1;
+        e = fp64_phase(bt, b64, c->launch_block, c->s_long);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaEventRecord(c->ev_join, c->s_long);
+    if (e != cudaSuccess) return e;
+    // phase C on the passes' leavers, then, after the join, on B-long's (and B-tail's)
     {
         ProfScope ps(c, kProfMixedC, s);
-        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, c2, mq.cap, cnt, c->d_stats);
+        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, cc, mq.cap, cnt, c->d_stats);
     }
     e = cudaGetLastError();
-    if (e == cudaSuccess && split_c) e = cudaStreamWaitEvent(s, c->ev_join_c, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
     if (e != cudaSuccess) return e;
     PhaseIO cl = cc;
@@ -601,7 +607,10 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
 // cudaGraphLaunch.  Calls with profiling on, or whose capture fails, run directly.
 raptor_status run_rays_graph(raptor_ctx* ctx, const Params& p, const double* freqs, int n_freq, long long planes_per_frame,
                              int n_frames, cudaStream_t s) {
-    if (!ctx->graphs || ctx->prof) return run_rays(ctx, p, freqs, n_freq, planes_per_frame, n_frames, s);
+    // Graph replay saves the launch latencies, which matter up to ~2^19 rays per call
+    // (measured 3-5 % at 64^2 .. 512^2); beyond, the graph's own ordering of the two streams'
+    // kernels overlaps them worse than direct launches do (measured 7-10 % slower at 1024^2).
+    if (!ctx->graphs || ctx->prof || p.n_rays > kGraphMaxRays) return run_rays(ctx, p, freqs, n_freq, planes_per_frame, n_frames, s);
     std::vector<unsigned char> key;
     auto put = [&key](const void* v, size_t n) {
         const unsigned char* b = static_cast<const unsigned char*>(v);
@@ -614,7 +623,7 @@ raptor_status run_rays_graph(raptor_ctx* ctx, const Params& p, const double* fre
     put(&planes_per_frame, sizeof(planes_per_frame));
     put(&n_frames, sizeof(n_frames));
     put(&ctx->cam, sizeof(ctx->cam));
-    int cfg[] = {ctx->launch_block, ctx->launch_bps, ctx->launch_bps64, ctx->n_passes, ctx->c_split, ctx->s_kernel,
+    int cfg[] = {ctx->launch_block, ctx->launch_bps, ctx->launch_bps64, ctx->n_passes, ctx->tail_split, ctx->s_kernel,
                  ctx->sur_ready ? 1 : 0};
     put(cfg, sizeof(cfg));
     put(ctx->pass_budget, sizeof(ctx->pass_budget));
@@ -974,13 +983,12 @@ void raptor_destroy(raptor_ctx* ctx) {
     cudaFree(ctx->d_trace_I);
     cudaFree(ctx->d_rec);
     free_mixed_queues(ctx->mq);
-    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_fork_c, ctx->ev_join_c};
+    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_tail};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
     if (ctx->g_exec) cudaGraphExecDestroy(ctx->g_exec);
     if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
     if (ctx->s_long) cudaStreamDestroy(ctx->s_long);
-    if (ctx->s_c1) cudaStreamDestroy(ctx->s_c1);
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
                   ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
@@ -1381,16 +1389,16 @@ raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, in
     return RAPTOR_OK;
 }
 
-raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int c_split) {
+raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int tail_split) {
     if (!ctx) return RAPTOR_EINVAL;
     if (!(crit_band >= 0.0) || !std::isfinite(crit_band)) return fail(ctx, RAPTOR_EINVAL, "crit_band must be finite and >= 0");
     if (n_passes < 1 || n_passes > kMaxPasses) return fail(ctx, RAPTOR_EINVAL, "n_passes must lie in [1, 8]");
     if (budgets)
         for (int k = 0; k + 1 < n_passes; ++k)
             if (budgets[k] < 1) return fail(ctx, RAPTOR_EINVAL, "pass budgets must be >= 1");
-    if (c_split < 0) return fail(ctx, RAPTOR_EINVAL, "c_split must be >= 0");
+    if (tail_split < 0) return fail(ctx, RAPTOR_EINVAL, "tail_split must be >= 0");
     ctx->crit_band = crit_band;
-    ctx->c_split = c_split;
+    ctx->tail_split = tail_split;
     ctx->n_passes = budgets ? n_passes : kMaxPasses;
     for (int k = 0; k < kMaxPasses; ++k) ctx->pass_budget[k] = budgets ? (k + 1 < n_passes ? budgets[k] : (1 << 30)) : kPassBudget[k];
     return RAPTOR_OK;

@@ -14,10 +14,11 @@
 // Rays near the critical curve orbit the photon sphere and need ~10^3 sequential FP64
 // steps: their chain of steps, not the total work, bounds the frame.  They are selected
 // first (phase A1), and their FP64 phase runs on a second stream (B-long) while the other
-// rays go through phases A2, B and C on the first; the leavers of the early FP64 passes go
-// through phase C on a third stream (C1) while the later passes, whose ends are mostly
-// idle, run.  Every launch works on a range of a queue fixed before it starts (a snapshot
-// of the push counter, taken in stream order), so no kernel waits on another.
+// rays go through phases A2, B and C on the first.  The other rays' FP64 passes end in a
+// ragged tail each; after the first few passes, the rays still in the FP64 region move to
+// the second stream (B-tail, after B-long) and the first stream goes on with phase C.
+// Every launch works on a range of a queue fixed before it starts (a snapshot of the push
+// counter, or a queue completed earlier in stream order), so no kernel waits on another.
 // The optical depth of a frequency beyond 10 is accumulated with a 48-bit significand
 // (compensated float pair), so the per-step loops of all phases issue no FP64 instruction
 // for the transfer: on B300 one FP64 compare or conversion occupies the FP64 pipe for as
@@ -60,8 +61,7 @@ enum : int {
     kCntPush32 = 8,      // q32 push counter
     kCntFetch32 = 9,
     kCntFetch32L = 10,
-    kCntSnap32 = 11,     // q32 length after the early passes: phase C1's range is [0, kCntSnap32)
-    kCntFetch32b = 12,   // phase C2's fetch counter (starts at kCntSnap32)
+    kCntTailFetch = 11,  // B-tail's fetch counter
     kCntPassFetch = 16,  // per pass: fetch counters (pass 0 starts at kCntSnap64)
     kCntPassOut = 24,    // per pass: re-queue push counters
     kMaxPasses = 8,
@@ -78,6 +78,7 @@ struct PhaseIO {
     int push_cnt;         // push counter slot of `push` (phase C: -1, re-entries are counted)
     int requeue_cnt;      // push counter slot of `requeue` (-1: no re-queue)
     int budget;           // FP64 launches: steps per ray in this launch
+    int in_exact;         // FP64 launches: `in` holds re-queued states in the exact format
 };
 
 inline cudaError_t alloc_queue(RayQueue& q, size_t cap, int nf) {
@@ -229,6 +230,10 @@ __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
 // depth beyond 10 in the compensated accumulator).
 template <typename S>
 struct StateT;
+// Queue slots hold float pairs.  A state handed from the FP64 phase to another FP64 pass is
+// stored exactly: the double's bits in the slot (from_exact / to_exact), so re-queueing
+// never rounds and the result of a ray does not depend on how often it is re-queued; a
+// double-float state is exact as a pair anyway.
 template <>
 struct StateT<double> {
     static __device__ __forceinline__ double from(double d) { return d; }
@@ -236,6 +241,12 @@ struct StateT<double> {
     static __device__ __forceinline__ float2 to2(double v) {
         const float hi = float(v);
         return make_float2(hi, float(v - double(hi)));
+    }
+    static __device__ __forceinline__ double from_exact(float2 v) {
+        return __hiloint2double(__float_as_int(v.y), __float_as_int(v.x));
+    }
+    static __device__ __forceinline__ float2 to_exact(double v) {
+        return make_float2(__int_as_float(__double2loint(v)), __int_as_float(__double2hiint(v)));
     }
     static __device__ __forceinline__ float f(double v) { return (float)v; }
     static __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
@@ -245,6 +256,8 @@ struct StateT<df64> {
     static __device__ __forceinline__ df64 from(double d) { return df64(d); }
     static __device__ __forceinline__ df64 from2(float2 v) { return df64(v.x, v.y); }
     static __device__ __forceinline__ float2 to2(df64 v) { return make_float2(v.hi, v.lo); }
+    static __device__ __forceinline__ df64 from_exact(float2 v) { return df64(v.x, v.y); }
+    static __device__ __forceinline__ float2 to_exact(df64 v) { return make_float2(v.hi, v.lo); }
     static __device__ __forceinline__ float f(df64 v) { return v.hi + v.lo; }
     static __device__ __forceinline__ bool finite(df64 v) { return isfinite(v.hi) && isfinite(v.lo); }
 };
@@ -485,8 +498,9 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
             pix = (int)(id - (long long)frame * p.n_pix);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                R.x[i] = StateT<S>::from2(q.xk[(size_t)i * cap + nid]);
-                R.k[i] = StateT<S>::from2(q.xk[(size_t)(4 + i) * cap + nid]);
+                const float2 xv = q.xk[(size_t)i * cap + nid], kv = q.xk[(size_t)(4 + i) * cap + nid];
+                R.x[i] = io.in_exact ? StateT<S>::from_exact(xv) : StateT<S>::from2(xv);
+                R.k[i] = io.in_exact ? StateT<S>::from_exact(kv) : StateT<S>::from2(kv);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -518,7 +532,10 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { xd[i] = StateT<S>::to2(R.x[i]); kd[i] = StateT<S>::to2(R.k[i]); }
+            for (int i = 0; i < 4; ++i) {
+                xd[i] = push ? StateT<S>::to2(R.x[i]) : StateT<S>::to_exact(R.x[i]);
+                kd[i] = push ? StateT<S>::to2(R.k[i]) : StateT<S>::to_exact(R.k[i]);
+            }
             store_ray<NF>(push ? io.push : io.requeue, cap, push ? slot : rslot, id, xd, kd, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
@@ -584,13 +601,6 @@ __global__ void __launch_bounds__(256) k_select_critical(const Params p, const f
 __global__ void k_snapshot64(unsigned long long* cnt) {
     cnt[kCntSnap64] = cnt[kCntPush64];
     cnt[kCntPassFetch] = cnt[kCntPush64];
-}
-
-// Stream-ordered snapshot after the early FP64 passes: phase C1 (third stream) takes q32
-// entries [0, n) while the later passes run; phase C2 fetches from n on.
-__global__ void k_snapshot32(unsigned long long* cnt) {
-    cnt[kCntSnap32] = cnt[kCntPush32];
-    cnt[kCntFetch32b] = cnt[kCntPush32];
 }
 
 }  // namespace raptor

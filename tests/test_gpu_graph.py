@@ -70,7 +70,7 @@ def test_lightcurve_batch_replays_with_new_frame_times(R):
     """Slow light: the frame times live in a context buffer, so the second batch's graph is
     replayed by the third batch with other times; every batch equals a direct light curve."""
     fields, meta = scenes.torus_snapshots(6, dt_snap=10.0, n1=32, n2=32, n_modes=64, seed=scenes.SLOW["seed"])
-    cam = dict(scenes.SMALL, spin=scenes.TORUS["spin"], nx=20, ny=16)
+    cam = dict(scenes.SMALL, spin=scenes.TORUS["spin"], nx=20, ny=16)  # 3 frames: under the graph size limit
 
     def make(graphs):
         ctx = R.Context(R.camera_desc(**cam))
@@ -86,3 +86,17 @@ def test_lightcurve_batch_replays_with_new_frame_times(R):
         fl_d = direct.lightcurve(freqs, np.array(t))
         assert np.array_equal(fl_g, fl_d), batch
     assert graph.graph_stats() == (1, 2)
+
+
+def test_large_calls_run_directly(R):
+    """Calls beyond 2^19 rays launch directly (no capture)."""
+    import torch
+
+    cam = dict(scenes.SMALL, nx=1024, ny=520, precision=R.MIXED, flags=R.FLAG_INNER_DF64)
+    ctx = R.Context(R.camera_desc(**cam))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    out = torch.empty((1, 520, 1024), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.render([230e9], image=out, flux=False)
+    torch.cuda.synchronize()
+    assert ctx.graph_stats() == (0, 0)

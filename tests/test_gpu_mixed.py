@@ -168,3 +168,26 @@ def test_fp32_reciprocal_within_one_ulp(R):
     """The FP32 paths' reciprocal (approximate reciprocal + one Newton-Raphson step) stays
     within one ulp of the correctly rounded 1/v over 2^24 values spanning 2^-100 .. 2^101."""
     assert R.check_fp32_reciprocal(1 << 24) <= 1
+
+
+@pytest.mark.parametrize("flags", [0, "df64"])
+def test_results_independent_of_schedule(R, flags):
+    """The near-critical band, the FP64 passes' step budgets and the tail split move work
+    between launches and streams, never a ray's arithmetic: images and fluxes are bit-identical
+    (re-queued FP64 states are stored exactly)."""
+    import torch
+
+    cam = dict(scenes.SMALL, nx=56, ny=48, precision=R.MIXED, flags=R.FLAG_INNER_DF64 if flags else 0)
+    ctx = R.Context(R.camera_desc(**cam))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    ctx.graph_config(False)
+    freqs = scenes.SPECTRAL_FREQS[:2]
+    ref, fref = ctx.render(freqs)
+    ref = ref.cpu().numpy()
+    for band, budgets, tail in [(0.0, None, 0), (1.0, None, 0), (0.5, [64], 0), (0.5, None, 2), (0.5, None, 5),
+                                (2.0, [8, 8, 8], 1)]:
+        ctx.mixed_config(band, budgets, tail)
+        img, fl = ctx.render(freqs)
+        torch.cuda.synchronize()
+        assert np.array_equal(img.cpu().numpy(), ref), (band, budgets, tail)
+        assert np.array_equal(fl, fref), (band, budgets, tail)
