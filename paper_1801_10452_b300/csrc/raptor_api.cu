@@ -1724,7 +1724,6 @@ raptor_status raptor_check_fp32_reciprocal(long long n, unsigned int* max_ulp) {
 }
 
 raptor_status raptor_measure_fma_peak(int fp64, double* tflops) {
-    raptor_ctx* ctx = nullptr;
     if (!tflops) return RAPTOR_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1753,7 +1752,6 @@ raptor_status raptor_measure_fma_peak(int fp64, double* tflops) {
     cudaFree(out);
     if (e != cudaSuccess) return RAPTOR_ECUDA;
     *tflops = 2.0 * 16.0 * iters * (double)threads * blocks / (best * 1e-3) / 1e12;
-    (void)ctx;
     return RAPTOR_OK;
 }
 
