@@ -57,16 +57,21 @@ RAPTOR_HD df64 operator+(df64 a, df64 b) {
 }
 RAPTOR_HD df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 RAPTOR_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
+// Products are left unrenormalised: (p, e + cross terms) has |lo| <= ~1.5 ulp(p) (a product
+// has no cancellation), so the pair is nearly normalised and every operation that consumes
+// it keeps its error bound within a small factor; the value is the one fast-two-sum would
+// give (that transformation is exact).  Sums, where cancellation can leave a large low
+// part, are renormalised.
 RAPTOR_HD df64 operator*(df64 a, df64 b) {
     df64 p = df_two_prod(a.hi, b.hi);
     p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
-    return df_fast_two_sum(p.hi, p.lo);
+    return p;
 }
 // b * q for a float q: the leading product exact, the low part's product rounded.
 RAPTOR_HD df64 df_mul_f(df64 b, float q) {
     df64 p = df_two_prod(b.hi, q);
     p.lo = fmaf(b.lo, q, p.lo);
-    return df_fast_two_sum(p.hi, p.lo);
+    return p;
 }
 // Approximate float reciprocal (a few ulp): it only seeds quotients that the df64
 // residuals below correct.
