@@ -14,7 +14,7 @@ static df64 mk(double d) { return df64(d); }
 int main() {
     std::mt19937_64 g(1801104520ull);
     std::uniform_real_distribution<double> u(-1.0, 1.0);
-    double e_add = 0, e_mul = 0, e_div = 0, e_sqrt = 0, e_sin = 0, e_cos = 0;
+    double e_add = 0, e_mul = 0, e_div = 0, e_sqrt = 0, e_sin = 0, e_cos = 0, e_tab = 0;
     for (int i = 0; i < 200000; ++i) {
         const double a = u(g) * std::pow(10.0, 3 * u(g)), b = u(g) * std::pow(10.0, 3 * u(g));
         const df64 A = mk(a), B = mk(b);
@@ -32,8 +32,13 @@ int main() {
         df_sincos(T, &s, &c);
         e_sin = std::fmax(e_sin, (double)fabsl(LD(s) - sinl(LD(T))));
         e_cos = std::fmax(e_cos, (double)fabsl(LD(c) - cosl(LD(T))));
+        // the table-based form used by the geodesic steps (theta in [0, pi]) and its fallback
+        const df64 T2 = mk(3.14159265358979 * 0.5 * (1.0 + 1.04 * u(g)));
+        df64 s2, c2;
+        df_sincos_tab(T2, &s2, &c2);
+        e_tab = std::fmax(e_tab, (double)std::fmax(fabsl(LD(s2) - sinl(LD(T2))), fabsl(LD(c2) - cosl(LD(T2)))));
     }
-    std::printf("{\"add\": %.3e, \"mul\": %.3e, \"div\": %.3e, \"sqrt\": %.3e, \"sin_abs\": %.3e, \"cos_abs\": %.3e}\n", e_add,
-                e_mul, e_div, e_sqrt, e_sin, e_cos);
+    std::printf("{\"add\": %.3e, \"mul\": %.3e, \"div\": %.3e, \"sqrt\": %.3e, \"sin_abs\": %.3e, \"cos_abs\": %.3e, "
+                "\"sincos_table_abs\": %.3e}\n", e_add, e_mul, e_div, e_sqrt, e_sin, e_cos, e_tab);
     return 0;
 }

@@ -155,7 +155,69 @@ RAPTOR_HD void df_sincos(df64 x, df64* s_out, df64* c_out) {
     else { *s_out = -cr; *c_out = sr; }
 }
 
-RAPTOR_HD void sc(df64 v, df64* s, df64* c) { df_sincos(v, s, c); }
+// sin and cos of theta in [0, pi] (the range of the geodesic's polar angle) from a table of
+// the 65 nodes theta_i = i pi / 64 (float pairs, filled by df_sincos_table_fill) and the
+// Taylor series of the offset d = theta - theta_i, |d| <= pi / 128: sin d to d^7 and cos d
+// to d^6 (first omitted terms < 1e-20), the terms below ~2^-24 of the leading one summed in
+// float; then the angle-addition formulas.  Outside [0, pi]: df_sincos.
+constexpr int kSinTabN = 64;
+#ifdef __CUDACC__
+__device__ float4 g_df_sincos_tab[kSinTabN + 1];
+#endif
+// Host fill of the table (sin hi, sin lo, cos hi, cos lo) from long-double sin and cos.
+inline void df_sincos_table_fill(float4* t) {
+    const long double pi_l = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i <= kSinTabN; ++i) {
+        const long double th = pi_l * i / kSinTabN;
+        const long double sv = sinl(th), cv = cosl(th);
+        const float sh = (float)sv, ch = (float)cv;
+        t[i] = float4{sh, (float)(sv - (long double)sh), ch, (float)(cv - (long double)ch)};
+    }
+}
+RAPTOR_HD float4 df_sincos_node(int i) {
+#ifdef __CUDA_ARCH__
+    return __ldg(&g_df_sincos_tab[i]);
+#else
+    static float4 tab[kSinTabN + 1];
+    static bool init = false;
+    if (!init) {
+        df_sincos_table_fill(tab);
+        init = true;
+    }
+    return tab[i];
+#endif
+}
+RAPTOR_HD void df_sincos_tab(df64 x, df64* s_out, df64* c_out) {
+    const float xf = x.hi + x.lo;
+    if (!(xf >= 0.f && xf <= 3.14159265f)) {
+        df_sincos(x, s_out, c_out);
+        return;
+    }
+    // pi / 64 = Q1 + Q2 + Q3 (three floats)
+    const float Q1 = 0.0490873866f, Q2 = -1.36598088e-09f, Q3 = -5.35976409e-17f;
+    const int i = (int)rintf(xf * (kSinTabN / 3.14159265358979f));
+    const float fi = (float)i;
+    df64 d = x - df_two_prod(fi, Q1);
+    d = d - df_two_prod(fi, Q2);
+    d = d - df64(fi * Q3, 0.f);
+    const df64 d2 = d * d;
+    const float d2f = d2.hi;
+    // sin d = d (1 + d2 (-1/6 + d2 (1/120 + d2 (-1/5040)))): the last two terms in float
+    const float ts = fmaf(-0.000198412701f, d2f, 0.00833333377f);
+    df64 ps = df64(ts, 0.f) * d2 + df64(-0.166666672f, 4.96705388e-09f);
+    ps = ps * d2 + df64(1.f, 0.f);
+    const df64 sd = ps * d;
+    // cos d = 1 + d2 (-1/2 + d2 (1/24 + d2 (-1/720))): the last two terms in float
+    const float tc = fmaf(-0.00138888892f, d2f, 0.0416666679f);
+    df64 pc = df64(tc, 0.f) * d2 + df64(-0.5f, 0.f);
+    pc = pc * d2 + df64(1.f, 0.f);
+    const float4 t = df_sincos_node(i);
+    const df64 s0(t.x, t.y), c0(t.z, t.w);
+    *s_out = s0 * pc + c0 * sd;
+    *c_out = c0 * pc - s0 * sd;
+}
+
+RAPTOR_HD void sc(df64 v, df64* s, df64* c) { df_sincos_tab(v, s, c); }
 // exact scalings by powers of two: two FP32 multiplies instead of a double-float product
 RAPTOR_HD df64 twice(df64 v) { return df64(2.f * v.hi, 2.f * v.lo); }
 RAPTOR_HD df64 halve(df64 v) { return df64(0.5f * v.hi, 0.5f * v.lo); }
@@ -165,6 +227,12 @@ RAPTOR_HD df64 rsq(df64 v) { return df64(1.0) / df_sqrt(v); }
 using dfns::df64;
 using dfns::df_fast_two_sum;
 using dfns::df_sincos;
+using dfns::df_sincos_tab;
+using dfns::df_sincos_table_fill;
+using dfns::kSinTabN;
+#ifdef __CUDACC__
+using dfns::g_df_sincos_tab;
+#endif
 using dfns::df_sqrt;
 using dfns::df_two_prod;
 using dfns::df_two_sum;

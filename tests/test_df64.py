@@ -1,5 +1,7 @@
 """Double-float (df64) arithmetic used by the optional inner-region path: compiled for the
-host with nvcc and checked against long double on seeded random operands.  CPU only."""
+host with nvcc and checked against long double on seeded random operands (sin and cos both
+by argument reduction and by the node table the geodesic steps use, over [0, 1.02 pi] so
+that the fallback is exercised too).  CPU only."""
 import json
 import os
 import subprocess
@@ -18,5 +20,5 @@ def test_df64_accuracy(tmp_path):
     subprocess.run([nvcc, "-O2", "-std=c++17", "-o", exe, SRC], check=True, capture_output=True)
     r = json.loads(subprocess.run([exe], check=True, capture_output=True, text=True).stdout)
     # a 48-bit significand: a few units of 2^-48 = 3.6e-15 per operation
-    for k in ("add", "mul", "div", "sqrt", "sin_abs", "cos_abs"):
+    for k in ("add", "mul", "div", "sqrt", "sin_abs", "cos_abs", "sincos_table_abs"):
         assert r[k] < 3e-14, (k, r[k])
