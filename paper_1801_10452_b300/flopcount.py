@@ -52,11 +52,13 @@ def flops_per_step(n_freq: int = 1, plasma: str = "analytic") -> dict:
 
 
 # FP32 instructions of one double-float operation, counted from raptor_df64.cuh: add
-# (two-sum 6, two adds, fast-two-sum 3) 11; multiply (product, error FMA, two cross FMAs,
-# fast-two-sum 3) 7; division (approximate reciprocal, two residual products and
-# subtractions, three quotient products, renormalisation) ~45; sincos (argument reduction,
-# two Horner chains in double-float with float tails, quadrant selection) ~300.
-DF64_FP32_INSTR = {"add": 11, "mul": 7, "div": 45, "sincos": 300}
+# (two-sum 6, two adds, fast-two-sum 3) 11; multiply (product, error FMA, two cross FMAs; the
+# pair is left unrenormalised) 4; division (approximate reciprocal, two residual products and
+# subtractions, three quotient products, renormalisation) ~40; sincos of the polar angle
+# (node index, offset in double-float, two short series with float tails, table load,
+# angle addition) ~150.  The model gives ~5,400 instructions per step with its FP32
+# transfer sample; ncu counts 5,281 executed per step of the FP64 phase (256^2 render).
+DF64_FP32_INSTR = {"add": 11, "mul": 4, "div": 40, "sincos": 150}
 
 
 def df64_instructions_per_step(n_freq: int = 1, plasma: str = "analytic") -> dict:
