@@ -153,10 +153,10 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
 // Plasma + frequency ratio at state (x, k) in type T.  Returns 1 emitting, 0 no plasma,
 // -1 error.  On success fills ne, the, B, g = nu_fluid/nu_obs and sinb.
 template <typename T>
-RAPTOR_HD int plasma_sample(const Params& p, const T x[4], const T k[4], int snap, T& ne, T& the,
-                                             T& B, T& g, T& sinb) {
+RAPTOR_HD int plasma_sample_sc(const Params& p, const T x[4], const T k[4], T sn, T cs, int snap, T& ne, T& the,
+                               T& B, T& g, T& sinb) {
     KSPoint<T> P;
-    ks_point(RAPTOR_P(T, a), x[1], x[2], P);
+    ks_point_sc(RAPTOR_P(T, a), x[1], sn, cs, P);
     T u[4], kc[4];
     T kb;  // k . b_hat
     if (p.kind == 0) {
@@ -195,4 +195,14 @@ RAPTOR_HD int plasma_sample(const Params& p, const T x[4], const T k[4], int sna
     return 1;
 }
 
+}  // namespace raptor
+
+namespace raptor {
+// plasma_sample_sc with sin and cos of the polar angle computed here.
+template <typename T>
+RAPTOR_HD int plasma_sample(const Params& p, const T x[4], const T k[4], int snap, T& ne, T& the, T& B, T& g, T& sinb) {
+    T sn, cs;
+    sc(x[2], &sn, &cs);
+    return plasma_sample_sc<T>(p, x, k, sn, cs, snap, ne, the, B, g, sinb);
+}
 }  // namespace raptor

@@ -169,11 +169,13 @@ __device__ __forceinline__ void tau_split(double t, float& lo, df64& hi) {
 constexpr float kIScale = 1.2676506002282294e30f;      // 2^100
 constexpr double kIUnscale = 7.888609052210118e-31;    // 2^-100
 
+// (sn, cs): sin and cos of x[2], when the caller has them (sn > 1: compute them here).
 template <int NF, typename TI>
 __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4], const float k[4], float dl, int snap,
-                                              TI* I, float* tau, df64* tau_hi) {
+                                              TI* I, float* tau, df64* tau_hi, float sn = 2.f, float cs = 0.f) {
     float ne, the, B, g, sinb;
-    const int ok = plasma_sample<float>(p, x, k, snap, ne, the, B, g, sinb);
+    if (sn > 1.f) sc(x[2], &sn, &cs);
+    const int ok = plasma_sample_sc<float>(p, x, k, sn, cs, snap, ne, the, B, g, sinb);
     if (ok <= 0) return ok;
     const float dlcm = dl * p.f.Lcm;
     const float gdl_unscaled = g * dlcm * float(kIUnscale);
@@ -212,7 +214,8 @@ __device__ __forceinline__ int thick_or_capped(const Params& p, const float* tau
 template <int NF>
 __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     const float dl = step_size<float>(p.f.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
-    rk4_step_comp(p.f.a, R.x, R.xl, R.k, R.kl, dl);
+    float sn, cs;
+    rk4_step_comp(p.f.a, R.x, R.xl, R.k, R.kl, dl, &sn, &cs);
     R.n += 1;
     bool fin = true;
 #pragma unroll
@@ -221,7 +224,7 @@ __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     if (R.x[1] < p.f.r_stop) return kCaptured;
     if (R.x[1] > p.f.r_esc) return kEscaped;
     if (p.r_exit_f > 0.f && R.x[1] > p.r_exit_f && R.k[1] > 0.f) return kEscaped;  // surrogate path only
-    if (rt_sample_fp32<NF, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+    if (rt_sample_fp32<NF, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi, sn, cs) < 0) return kError;
     return thick_or_capped<NF>(p, R.tau, R.tau_hi, R.n);
 }
 
