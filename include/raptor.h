@@ -211,6 +211,15 @@ raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int bloc
  * budget < 1 or a negative tail_split. */
 raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int tail_split);
 
+/* Schedule of the near-critical rays' FP64 phase on the mixed path's second stream:
+ * threads_per_block in {32, 64, 96, 128} (0: the block size of the other launches) and
+ * n_passes (1..8) passes, pass k continuing each ray for at most budgets[k] steps and
+ * re-queueing the unfinished ones, packed into full warps, for pass k + 1; the last pass has
+ * no limit (budgets may be NULL for n_passes = 1) [0, 1].  The grid keeps the thread count of
+ * the other FP64 passes.  Only the schedule changes, never a result.  RAPTOR_EINVAL for a
+ * block size or pass count out of range, or a budget < 1. */
+raptor_status raptor_long_config(raptor_ctx* ctx, int threads_per_block, int n_passes, const int* budgets);
+
 /* CUDA graphs (enable != 0, the default): the second raptor_render / raptor_render_ex /
  * raptor_lightcurve call with the same arguments, context settings and device buffers
  * captures its whole launch sequence (both streams of the mixed path) into a graph, and
@@ -319,6 +328,17 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 #define RAPTOR_KERNEL_SURROGATE_MLP 10 /* the network inside RAPTOR_KERNEL_SURROGATE        */
 raptor_status raptor_profile(raptor_ctx* ctx, int enable);
 raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches);
+
+/* Per-launch timeline of the recorded scopes since the last raptor_profile(ctx, 1), in
+ * launch order: kernel slot (RAPTOR_KERNEL_*), lane (0: the call's stream, 1: the mixed
+ * path's second stream), start relative to the first recorded scope and duration, both in
+ * ms from CUDA events on the launch's stream.  Waits for the recorded events (as
+ * raptor_profile_read, whose sums include the same scopes).  Writes min(cap, count) records
+ * into the caller's host arrays slot[cap], lane[cap], start_ms[cap], dur_ms[cap] (may be
+ * NULL when cap = 0) and the number of records held in *count (at most 65,536 are kept).
+ * RAPTOR_EINVAL for a NULL count, a negative cap or NULL arrays with cap > 0. */
+raptor_status raptor_profile_timeline(raptor_ctx* ctx, int cap, int* slot, int* lane, double* start_ms,
+                                      double* dur_ms, int* count);
 
 /* Self-check of the FP32 reciprocal the FP32 code paths use (the hardware's approximate
  * reciprocal refined by one Newton-Raphson step): *max_ulp receives the largest distance in

@@ -31,7 +31,7 @@ EXPORTS = [
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
-    "raptor_mixed_config", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_reciprocal",
+    "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_reciprocal",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp"]
@@ -111,6 +111,9 @@ def lib():
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
             "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
+            "raptor_long_config": (st, [vp, C.c_int, C.c_int, C.c_void_p]),
+            "raptor_profile_timeline": (st, [vp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.POINTER(C.c_int)]),
             "raptor_graph_config": (st, [vp, C.c_int]),
             "raptor_check_fp32_reciprocal": (st, [C.c_longlong, C.c_void_p]),
             "raptor_graph_stats": (st, [vp, C.c_void_p, C.c_void_p]),
@@ -148,6 +151,10 @@ def plasma_desc(**kw) -> PlasmaDesc:
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
 
 
 def _freqs(freqs):
@@ -295,6 +302,22 @@ class Context:
         self._check(lib().raptor_profile_read(self._h, _dp(ms), n), "raptor_profile_read")
         return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(k)}
 
+    def profile_timeline(self):
+        """Recorded launches since the last profile(True), in launch order: a list of
+        (kernel name, lane, start ms, duration ms); lane 1 is the mixed path's second stream."""
+        n = C.c_int(0)
+        self._check(lib().raptor_profile_timeline(self._h, 0, None, None, None, None, C.byref(n)),
+                    "raptor_profile_timeline")
+        k = n.value
+        slot = np.zeros(k, dtype=np.int32)
+        lane = np.zeros(k, dtype=np.int32)
+        t0 = np.zeros(k)
+        dt = np.zeros(k)
+        if k:
+            self._check(lib().raptor_profile_timeline(self._h, k, _ip(slot), _ip(lane), _dp(t0), _dp(dt), C.byref(n)),
+                        "raptor_profile_timeline")
+        return [(KERNEL_NAMES[slot[i]], int(lane[i]), float(t0[i]), float(dt[i])) for i in range(k)]
+
     # ---- learned surrogate -------------------------------------------------------------
     def surrogate_generate(self, n, seed=0x1801104520000005, spin=(0.0, 0.99), incl=(5.0, 85.0), states=False,
                            stream=None):
@@ -348,6 +371,14 @@ class Context:
     def surrogate_set(self, P):
         P = np.ascontiguousarray(P, dtype=np.float32)
         self._check(lib().raptor_surrogate_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size), "raptor_surrogate_set")
+
+    def long_config(self, threads_per_block=0, budgets=None):
+        """Schedule of the near-critical rays' FP64 phase on the second stream: block size
+        (0: the other launches') and the step budgets of its passes (None: one unlimited
+        pass; the last pass is unlimited)."""
+        b = (C.c_int * max(1, len(budgets or [])))(*[int(v) for v in (budgets or [])])
+        self._check(lib().raptor_long_config(self._h, int(threads_per_block), len(budgets or []) + 1, b),
+                    "raptor_long_config")
 
     def mixed_config(self, crit_band=0.5, budgets=None, tail_split=0):
         """Schedule of the mixed path: the near-critical band (M) whose rays run their FP64

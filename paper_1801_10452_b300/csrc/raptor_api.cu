@@ -51,6 +51,9 @@ struct raptor_ctx {
     cudaStream_t s_long = nullptr;  // second stream of the mixed path (B-long)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr;
     int tail_split = 0;           // after this many FP64 passes the rest moves to B-tail (0: never)
+    int long_block = 0;           // threads per block of the second stream's FP64 passes (0: launch_block)
+    int long_passes = 1;          // near-critical rays' FP64 passes and their step budgets
+    int long_budget[8] = {1 << 30, 1 << 30, 1 << 30, 1 << 30, 1 << 30, 1 << 30, 1 << 30, 1 << 30};
     // CUDA graph of the last repeated render (raptor_graph_config)
     bool graphs = true;
     cudaStream_t s_cap = nullptr;     // capture stream
@@ -96,7 +99,18 @@ struct raptor_ctx {
     // per-kernel CUDA-event timing (raptor_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
+    struct OpenRec {
+        int slot, lane;
+        cudaEvent_t a, b;
+    };
+    struct TimeRec {
+        int slot, lane;
+        double start_ms, dur_ms;
+    };
+    std::vector<OpenRec> ev_open;
+    std::vector<TimeRec> timeline;   // per-launch records since the last clear (capped)
+    cudaEvent_t ev_t0 = nullptr;     // timeline origin: recorded before the first scope
+    bool t0_pending = false;
     double prof_ms[kProfSlots] = {0};
     long long prof_launches[kProfSlots] = {0};
 };
@@ -124,6 +138,11 @@ struct ProfScope {
     ProfScope(raptor_ctx* c_, int slot_, cudaStream_t s_, int kernels = 1) : c(c_), slot(slot_), s(s_) {
         c->prof_launches[slot] += kernels;
         if (c->prof) {
+            if (c->t0_pending) {
+                if (!c->ev_t0) cudaEventCreate(&c->ev_t0);
+                cudaEventRecord(c->ev_t0, s);
+                c->t0_pending = false;
+            }
             a = take_event(c);
             b = take_event(c);
             cudaEventRecord(a, s);
@@ -132,7 +151,7 @@ struct ProfScope {
     ~ProfScope() {
         if (c->prof && a && b) {
             cudaEventRecord(b, s);
-            c->ev_open.push_back({slot, {a, b}});
+            c->ev_open.push_back({slot, (c->s_long && s == c->s_long) ? 1 : 0, a, b});
         }
     }
 };
@@ -385,8 +404,12 @@ cudaError_t launch_fp64_phase(raptor_ctx* c, const Params& p, const PhaseIO& io,
     return cudaGetLastError();
 }
 
+cudaError_t surrogate_stage(raptor_ctx* ctx, const Params& p, cudaStream_t s);
+
+// One frequency chunk of a mixed render.  sur_stage: run the surrogate's inference first
+// (the first chunk of a learned render).
 template <int NF>
-cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
+cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool sur_stage) {
     cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s);
     if (e == cudaSuccess) e = upload_curve(c, p, s);
     if (e == cudaSuccess && !c->s_long) {
@@ -418,10 +441,15 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
         return df ? launch_fp64_phase<NF, df64>(c, p, io, blocks, threads, st)
                   : launch_fp64_phase<NF, double>(c, p, io, blocks, threads, st);
     };
-    // B-long uses the launch shape of the passes (one-warp blocks, which return their
-    // registers to the SM as soon as their warp is done, measured slower)
-    const int long_threads = c->launch_block;
-    const int b_long = b64;
+    // the second stream's launches keep the thread count of the first's FP64 passes; smaller
+    // blocks return their registers to the SM as soon as their warps are done
+    const int long_threads = c->long_block > 0 ? c->long_block : c->launch_block;
+    const int b_long = (int)(((long long)b64 * c->launch_block + long_threads - 1) / long_threads);
+    // the surrogate's inference (first frequency chunk of a learned render)
+    if (sur_stage) {
+        e = surrogate_stage(c, p, s);
+        if (e != cudaSuccess) return e;
+    }
     // near-critical / other split
     const float grow = (float)c->crit_band + 1e-3f;
     const float4 box = make_float4(c->curve_box.x - grow, c->curve_box.y + grow, c->curve_box.z - grow, c->curve_box.w + grow);
@@ -429,41 +457,52 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
                                                           c->d_rest, cnt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // phase A1
+    // phase A1: near-critical rays.  Their entries fill the top of q64 (from cap - number of
+    // near-critical rays up) and of the re-queue targets, the other rays' the bottom: each
+    // ray has at most one entry per queue, so the ranges never meet.
     PhaseIO a1{};
     a1.fresh = c->d_crit;
     a1.push = mq.q64;
     a1.fetch = kCntFreshCrit;
     a1.total = kCntListCrit;
-    a1.push_cnt = kCntPush64;
+    a1.push_cnt = kCntPush64C;
+    a1.push_top = kCntListCrit;
     a1.requeue_cnt = -1;
     {
         ProfScope ps(c, kProfMixedA, s);
         k_mixed_fp32<NF><<<bA, c->launch_block, 0, s>>>(p, a1, mq.cap, cnt, c->d_stats);
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_snapshot64<<<1, 1, 0, s>>>(cnt);
-    e = cudaGetLastError();
-    // fork: B-long on the second stream
+    // fork: the near-critical rays' FP64 phase on the second stream, in passes like the
+    // other rays' (each pass re-packs the unfinished rays into full warps)
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_fork, 0);
     if (e != cudaSuccess) return e;
-    PhaseIO bl{};
-    bl.in = mq.q64;
-    bl.push = mq.q32l;
-    bl.fetch = kCntLongFetch;
-    bl.total = kCntSnap64;
-    bl.push_cnt = kCntPush32L;
-    bl.requeue_cnt = -1;
-    bl.budget = 1 << 30;
-    e = fp64_phase(bl, b_long, long_threads, c->s_long);
-    if (e != cudaSuccess) return e;
+    const int LK = c->long_passes;
+    for (int pass = 0; pass < LK; ++pass) {
+        PhaseIO bl{};
+        bl.in = pass == 0 ? mq.q64 : ((pass & 1) ? mq.q64b : mq.q64c);
+        bl.in_top = kCntListCrit;
+        bl.requeue = (pass & 1) ? mq.q64c : mq.q64b;
+        bl.requeue_top = kCntListCrit;
+        bl.push = mq.q32l;
+        bl.fetch = kCntLPassFetch + pass;
+        bl.total = pass == 0 ? kCntPush64C : kCntLPassOut + pass - 1;
+        bl.push_cnt = kCntPush32L;
+        bl.requeue_cnt = pass + 1 < LK ? kCntLPassOut + pass : -1;
+        bl.budget = pass + 1 < LK ? c->long_budget[pass] : (1 << 30);
+        bl.in_exact = pass > 0;
+        e = fp64_phase(bl, b_long, long_threads, c->s_long);
+        if (e != cudaSuccess) return e;
+    }
     // phase A2
-    PhaseIO a2 = a1;
+    PhaseIO a2{};
     a2.fresh = c->d_rest;
+    a2.push = mq.q64;
     a2.fetch = kCntFreshRest;
     a2.total = kCntListRest;
+    a2.push_cnt = kCntPush64;
+    a2.requeue_cnt = -1;
     {
         ProfScope ps(c, kProfMixedA, s);
         k_mixed_fp32<NF><<<bA, c->launch_block, 0, s>>>(p, a2, mq.cap, cnt, c->d_stats);
@@ -509,7 +548,7 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
         bt.requeue_cnt = -1;
         bt.budget = 1 << 30;
         bt.in_exact = 1;
-        e = fp64_phase(bt, b64, c->launch_block, c->s_long);
+        e = fp64_phase(bt, b_long, long_threads, c->s_long);
         if (e != cudaSuccess) return e;
     }
     e = cudaEventRecord(c->ev_join, c->s_long);
@@ -533,12 +572,12 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_mixed(raptor_ctx* c, const Params& p, cudaStream_t s) {
-    if (p.nf <= 1) return launch_mixed_nf<1>(c, p, s);
-    if (p.nf <= 2) return launch_mixed_nf<2>(c, p, s);
-    if (p.nf <= 4) return launch_mixed_nf<4>(c, p, s);
-    if (p.nf <= 8) return launch_mixed_nf<8>(c, p, s);
-    return launch_mixed_nf<16>(c, p, s);
+cudaError_t launch_mixed(raptor_ctx* c, const Params& p, cudaStream_t s, bool sur_stage) {
+    if (p.nf <= 1) return launch_mixed_nf<1>(c, p, s, sur_stage);
+    if (p.nf <= 2) return launch_mixed_nf<2>(c, p, s, sur_stage);
+    if (p.nf <= 4) return launch_mixed_nf<4>(c, p, s, sur_stage);
+    if (p.nf <= 8) return launch_mixed_nf<8>(c, p, s, sur_stage);
+    return launch_mixed_nf<16>(c, p, s, sur_stage);
 }
 
 raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t s);
@@ -577,7 +616,7 @@ raptor_status run_rays(raptor_ctx* ctx, Params p, const double* freqs, int n_fre
                 RCK(cudaMalloc((void**)&ctx->d_rest, need * sizeof(int)));
                 ctx->mq_cap = need;
             }
-            RCK(launch_mixed(ctx, p, s));
+            RCK(launch_mixed(ctx, p, s, ctx->cam.precision == RAPTOR_MIXED_MLP && f0 == 0));
         }
     }
     // flux: planes = n_frames * n_freq, each n_rows * nx
@@ -624,9 +663,10 @@ raptor_status run_rays_graph(raptor_ctx* ctx, const Params& p, const double* fre
     put(&n_frames, sizeof(n_frames));
     put(&ctx->cam, sizeof(ctx->cam));
     int cfg[] = {ctx->launch_block, ctx->launch_bps, ctx->launch_bps64, ctx->n_passes, ctx->tail_split, ctx->s_kernel,
-                 ctx->sur_ready ? 1 : 0};
+                 ctx->sur_ready ? 1 : 0, ctx->long_block, ctx->long_passes};
     put(cfg, sizeof(cfg));
     put(ctx->pass_budget, sizeof(ctx->pass_budget));
+    put(ctx->long_budget, sizeof(ctx->long_budget));
     double dcfg[] = {ctx->crit_band, ctx->s_band, ctx->s_r_exit};
     put(dcfg, sizeof(dcfg));
     put(&epoch, sizeof(epoch));
@@ -1001,10 +1041,11 @@ void raptor_destroy(raptor_ctx* ctx) {
                   ctx->d_crit, ctx->d_rest};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
-        cudaEventDestroy(e.second.first);
-        cudaEventDestroy(e.second.second);
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
     }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->ev_t0) cudaEventDestroy(ctx->ev_t0);
     delete ctx;
 }
 
@@ -1410,6 +1451,20 @@ raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passe
     return RAPTOR_OK;
 }
 
+raptor_status raptor_long_config(raptor_ctx* ctx, int threads_per_block, int n_passes, const int* budgets) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (threads_per_block < 0 || threads_per_block > 128 || threads_per_block % 32)
+        return fail(ctx, RAPTOR_EINVAL, "threads_per_block must be 0, 32, 64, 96 or 128");
+    if (n_passes < 1 || n_passes > kMaxPasses) return fail(ctx, RAPTOR_EINVAL, "n_passes must lie in [1, 8]");
+    if (n_passes > 1 && !budgets) return fail(ctx, RAPTOR_EINVAL, "budgets must be given for n_passes > 1");
+    for (int k = 0; k + 1 < n_passes; ++k)
+        if (budgets[k] < 1) return fail(ctx, RAPTOR_EINVAL, "pass budgets must be >= 1");
+    ctx->long_block = threads_per_block;
+    ctx->long_passes = n_passes;
+    for (int k = 0; k < kMaxPasses; ++k) ctx->long_budget[k] = k + 1 < n_passes ? budgets[k] : (1 << 30);
+    return RAPTOR_OK;
+}
+
 raptor_status raptor_graph_config(raptor_ctx* ctx, int enable) {
     if (!ctx) return RAPTOR_EINVAL;
     ctx->graphs = enable != 0;
@@ -1450,6 +1505,7 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 namespace {
 
 // RAPTOR_MIXED_MLP: predicted start states for every non-fallback ray, then the mixed path.
+// Buffers and launch parameters of a learned render (the kernels run in surrogate_stage).
 raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t s) {
     if (!ctx->sur_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "RAPTOR_MIXED_MLP needs a trained or loaded surrogate");
     RCK(sur_alloc(ctx));
@@ -1469,17 +1525,30 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
         ctx->s_ray_cap = rays;
     }
     RCK(upload_curve(ctx, p, s));
+    p.start_xk = ctx->s_start;
+    p.fallback = ctx->s_fb;
+    p.start_n = kSurrogateSteps;
+    p.r_exit = ctx->s_r_exit;
+    p.r_exit_f = (float)ctx->s_r_exit;
+    return RAPTOR_OK;
+}
+
+// The surrogate's part of a learned render on stream s: network inputs and fallback flags,
+// inference, start states.
+cudaError_t surrogate_stage(raptor_ctx* ctx, const Params& p, cudaStream_t s) {
+    const size_t rays = (size_t)p.n_rays;
     const int nc = ctx->n_curve;
     const float grow = (float)ctx->s_band + 1e-3f;
     const float4 box = make_float4(ctx->curve_box.x - grow, ctx->curve_box.y + grow, ctx->curve_box.z - grow,
                                    ctx->curve_box.w + grow);
     float* out = nullptr;
-    RCK(cudaMallocAsync((void**)&out, rays * kOut * sizeof(float), s));
+    cudaError_t e = cudaMallocAsync((void**)&out, rays * kOut * sizeof(float), s);
+    if (e != cudaSuccess) return e;
     {
         ProfScope ps(ctx, kProfSurrogate, s, 2);  // inputs and start states; the network nests below
         k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->d_curve, nc, (float)ctx->s_band, box,
                                                                        ctx->s_in, ctx->s_fb);
-        cudaError_t e = cudaGetLastError();
+        e = cudaGetLastError();
         if (e == cudaSuccess) {
             ProfScope pm(ctx, kProfSurrogateMlp, s, ctx->s_kernel == RAPTOR_MLP_MMA_SYNC ? 1 : 2);
             e = sur_eval_rows(ctx, ctx->s_in, (long long)rays, out, s);
@@ -1488,15 +1557,9 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
             k_surrogate_states<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_P, out, ctx->s_start);
             e = cudaGetLastError();
         }
-        cudaFreeAsync(out, s);
-        if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, std::string("surrogate: ") + cudaGetErrorString(e));
     }
-    p.start_xk = ctx->s_start;
-    p.fallback = ctx->s_fb;
-    p.start_n = kSurrogateSteps;
-    p.r_exit = ctx->s_r_exit;
-    p.r_exit_f = (float)ctx->s_r_exit;
-    return RAPTOR_OK;
+    const cudaError_t ef = cudaFreeAsync(out, s);
+    return e != cudaSuccess ? e : ef;
 }
 
 }  // namespace
@@ -1684,10 +1747,12 @@ raptor_status raptor_profile(raptor_ctx* ctx, int enable) {
     if (enable) {
         RCK(cudaStreamSynchronize(ctx->last_stream));
         for (auto& e : ctx->ev_open) {
-            ctx->ev_pool.push_back(e.second.first);
-            ctx->ev_pool.push_back(e.second.second);
+            ctx->ev_pool.push_back(e.a);
+            ctx->ev_pool.push_back(e.b);
         }
         ctx->ev_open.clear();
+        ctx->timeline.clear();
+        ctx->t0_pending = true;
         for (int i = 0; i < kProfSlots; ++i) {
             ctx->prof_ms[i] = 0.0;
             ctx->prof_launches[i] = 0;
@@ -1697,17 +1762,44 @@ raptor_status raptor_profile(raptor_ctx* ctx, int enable) {
     return RAPTOR_OK;
 }
 
-raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches) {
-    if (!ctx) return RAPTOR_EINVAL;
+// Wait for the recorded scopes, add their durations to the slots and append them to the
+// timeline (start relative to the origin event).
+static raptor_status drain_profile(raptor_ctx* ctx) {
+    constexpr size_t kTimelineCap = 1 << 16;
     for (auto& e : ctx->ev_open) {
-        RCK(cudaEventSynchronize(e.second.second));
-        float t = 0.f;
-        RCK(cudaEventElapsedTime(&t, e.second.first, e.second.second));
-        ctx->prof_ms[e.first] += t;
-        ctx->ev_pool.push_back(e.second.first);
-        ctx->ev_pool.push_back(e.second.second);
+        RCK(cudaEventSynchronize(e.b));
+        float t = 0.f, t0 = 0.f;
+        RCK(cudaEventElapsedTime(&t, e.a, e.b));
+        if (ctx->ev_t0) RCK(cudaEventElapsedTime(&t0, ctx->ev_t0, e.a));
+        ctx->prof_ms[e.slot] += t;
+        if (ctx->timeline.size() < kTimelineCap) ctx->timeline.push_back({e.slot, e.lane, (double)t0, (double)t});
+        ctx->ev_pool.push_back(e.a);
+        ctx->ev_pool.push_back(e.b);
     }
     ctx->ev_open.clear();
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_profile_timeline(raptor_ctx* ctx, int cap, int* slot, int* lane, double* start_ms, double* dur_ms,
+                                      int* count) {
+    if (!ctx || cap < 0 || !count || (cap > 0 && (!slot || !lane || !start_ms || !dur_ms))) return RAPTOR_EINVAL;
+    raptor_status st = drain_profile(ctx);
+    if (st != RAPTOR_OK) return st;
+    const int n = (int)ctx->timeline.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        slot[i] = ctx->timeline[i].slot;
+        lane[i] = ctx->timeline[i].lane;
+        start_ms[i] = ctx->timeline[i].start_ms;
+        dur_ms[i] = ctx->timeline[i].dur_ms;
+    }
+    *count = n;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches) {
+    if (!ctx) return RAPTOR_EINVAL;
+    raptor_status st = drain_profile(ctx);
+    if (st != RAPTOR_OK) return st;
     for (int i = 0; i < kProfSlots; ++i) {
         if (ms) ms[i] = ctx->prof_ms[i];
         if (launches) launches[i] = ctx->prof_launches[i];

@@ -54,18 +54,19 @@ enum : int {
     kCntListRest = 1,    // length of the other id list (phase A2)
     kCntFreshCrit = 2,   // fetch counters of the two lists
     kCntFreshRest = 3,
-    kCntPush64 = 4,      // q64 push counter
-    kCntSnap64 = 5,      // q64 length after A1: B-long's range is [0, kCntSnap64)
-    kCntLongFetch = 6,
+    kCntPush64 = 4,      // q64 push counter of A2 (entries from the bottom of q64)
+    kCntPush64C = 5,     // q64 push counter of A1 (entries from cap - cnt[kCntListCrit] up)
     kCntPush32L = 7,     // q32l push counter
     kCntPush32 = 8,      // q32 push counter
     kCntFetch32 = 9,
     kCntFetch32L = 10,
     kCntTailFetch = 11,  // B-tail's fetch counter
-    kCntPassFetch = 16,  // per pass: fetch counters (pass 0 starts at kCntSnap64)
-    kCntPassOut = 24,    // per pass: re-queue push counters
+    kCntPassFetch = 16,  // per pass of the first stream: fetch counters
+    kCntPassOut = 24,    // per pass of the first stream: re-queue push counters
+    kCntLPassFetch = 32, // per pass of the second stream (near-critical rays): fetch counters
+    kCntLPassOut = 40,   // per pass of the second stream: re-queue push counters
     kMaxPasses = 8,
-    kNumCounters = 32
+    kNumCounters = 48
 };
 
 // Input, outputs and counter slots of one launch of the mixed kernels.
@@ -79,6 +80,9 @@ struct PhaseIO {
     int requeue_cnt;      // push counter slot of `requeue` (-1: no re-queue)
     int budget;           // FP64 launches: steps per ray in this launch
     int in_exact;         // FP64 launches: `in` holds re-queued states in the exact format
+    int push_top = -1;    // counter slot c: `push` entries start at cap - cnt[c] (-1: at 0)
+    int in_top = -1;      // the same for `in`
+    int requeue_top = -1; // and for `requeue`
 };
 
 inline cudaError_t alloc_queue(RayQueue& q, size_t cap, int nf) {
@@ -403,6 +407,7 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, 
     bool drained = false;
     const bool fresh = io.fresh != nullptr;
     const long long n_total = (long long)cnt[io.total];
+    const long long push_off = io.push_top >= 0 ? (long long)cap - (long long)cnt[io.push_top] : 0;
     unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0, c_re = 0;
     for (;;) {
         const long long nid = warp_fetch(&cnt[io.fetch], n_total, id < 0, drained);
@@ -454,7 +459,7 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, 
             for (int i = 0; i < 4; ++i) { x[i] = make_float2(R.x[i], R.xl[i]); k[i] = make_float2(R.k[i], R.kl[i]); }
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
-            store_ray<NF>(io.push, cap, slot, id, x, k, R.I, tau, R.n, p.nf);
+            store_ray<NF>(io.push, cap, slot + push_off, id, x, k, R.I, tau, R.n, p.nf);
             id = -1;
         } else if (id >= 0 && st >= 0) {
             double I[NF];
@@ -490,27 +495,30 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
     int frame = 0, pix = 0, n_in = 0;
     bool drained = false;
     const long long n_total = (long long)cnt[io.total];
+    const long long in_off = io.in_top >= 0 ? (long long)cap - (long long)cnt[io.in_top] : 0;
+    const long long rq_off = io.requeue_top >= 0 ? (long long)cap - (long long)cnt[io.requeue_top] : 0;
     const bool can_requeue = io.requeue_cnt >= 0;
     unsigned long long c_rays = 0, c_steps = 0, c_64 = 0, c_trunc = 0, c_err = 0;
     for (;;) {
         const long long nid = warp_fetch(&cnt[io.fetch], n_total, id < 0, drained);
         if (id < 0 && nid >= 0) {
             const RayQueue& q = io.in;
-            id = q.id[nid];
+            const long long e = nid + in_off;
+            id = q.id[e];
             frame = (int)(id / p.n_pix);
             pix = (int)(id - (long long)frame * p.n_pix);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float2 xv = q.xk[(size_t)i * cap + nid], kv = q.xk[(size_t)(4 + i) * cap + nid];
+                const float2 xv = q.xk[(size_t)i * cap + e], kv = q.xk[(size_t)(4 + i) * cap + e];
                 R.x[i] = io.in_exact ? StateT<S>::from_exact(xv) : StateT<S>::from2(xv);
                 R.k[i] = io.in_exact ? StateT<S>::from_exact(kv) : StateT<S>::from2(kv);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                R.I[f] = f < p.nf ? AccI<S>(q.I[(size_t)f * cap + nid]) : AccI<S>(0);
-                tau_split(f < p.nf ? q.tau[(size_t)f * cap + nid] : 0.0, R.tau[f], R.tau_hi[f]);
+                R.I[f] = f < p.nf ? AccI<S>(q.I[(size_t)f * cap + e]) : AccI<S>(0);
+                tau_split(f < p.nf ? q.tau[(size_t)f * cap + e] : 0.0, R.tau[f], R.tau_hi[f]);
             }
-            R.n = q.n[nid];
+            R.n = q.n[e];
             n_in = R.n;
             R.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
         }
@@ -539,7 +547,7 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
                 xd[i] = push ? StateT<S>::to2(R.x[i]) : StateT<S>::to_exact(R.x[i]);
                 kd[i] = push ? StateT<S>::to2(R.k[i]) : StateT<S>::to_exact(R.k[i]);
             }
-            store_ray<NF>(push ? io.push : io.requeue, cap, push ? slot : rslot, id, xd, kd, R.I, tau, R.n, p.nf);
+            store_ray<NF>(push ? io.push : io.requeue, cap, push ? slot : rslot + rq_off, id, xd, kd, R.I, tau, R.n, p.nf);
             c_64 += (unsigned long long)(R.n - n_in);
             id = -1;
         } else if (id >= 0 && st >= 0) {
@@ -582,11 +590,9 @@ __global__ void __launch_bounds__(256) k_select_critical(const Params p, const f
             const int row = p.row0 + pix / p.nx, col = pix % p.nx;
             const float alf = (float)(p.amin + (col + 0.5) * p.da), bef = (float)(p.bmin + (row + 0.5) * p.db);
             if (alf >= box.x && alf <= box.y && bef >= box.z && bef <= box.w) {
-                float d2 = 3.0e38f;
-                for (int c = 0; c < n_curve; ++c) {
-                    const float dx = alf - sc[c].x, dy = bef - sc[c].y;
-                    d2 = fminf(d2, dx * dx + dy * dy);
-                }
+                float d2;
+                bool inside;
+                curve_relation(alf, bef, sc, n_curve, false, d2, inside);
                 is_crit = d2 < band2;
             }
         }
@@ -597,13 +603,6 @@ __global__ void __launch_bounds__(256) k_select_critical(const Params p, const f
             else rest[sr_slot] = (int)id;
         }
     }
-}
-
-// Stream-ordered snapshot after phase A1: B-long takes q64 entries [0, n), the first FP64
-// pass starts fetching at n.
-__global__ void k_snapshot64(unsigned long long* cnt) {
-    cnt[kCntSnap64] = cnt[kCntPush64];
-    cnt[kCntPassFetch] = cnt[kCntPush64];
 }
 
 }  // namespace raptor

@@ -611,6 +611,28 @@ RAPTOR_HD void surrogate_state(float a, float sn_i, float cs_i, float alpha, flo
     k[3] = grp * kcr + gpp * kcp;
 }
 
+// Squared distance from a pixel centre to the nearest vertex of the critical-curve polygon
+// (sc[n], in order around the closed curve) and, with `want_inside`, the even-odd test for
+// the centre lying inside it.  FP32 with every rounding explicit (no contraction), so that
+// the kernels taking decisions on the same pixel (fallback flag, near-critical list) take
+// them identically.
+__device__ __forceinline__ void curve_relation(float alf, float bef, const float2* sc, int n, bool want_inside,
+                                               float& d2, bool& inside) {
+    d2 = 3.0e38f;
+    inside = false;
+    for (int c = 0; c < n; ++c) {
+        const float2 v1 = sc[c];
+        const float dx = __fsub_rn(alf, v1.x), dy = __fsub_rn(bef, v1.y);
+        d2 = fminf(d2, __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+        if (want_inside) {
+            const float2 v2 = sc[c + 1 < n ? c + 1 : 0];
+            if ((v1.y > bef) != (v2.y > bef) &&
+                alf < __fadd_rn(v1.x, __fdiv_rn(__fmul_rn(dy, __fsub_rn(v2.x, v1.x)), __fsub_rn(v2.y, v1.y))))
+                inside = !inside;
+        }
+    }
+}
+
 // Per ray of a render: network inputs (alpha, beta, a, i in degrees) and the fallback flag:
 // pixel centre within `band` M of the critical curve (n_curve <= kMaxCurve points in order
 // around the closed curve, FP32) or inside it (captured rays, whose near-horizon emission is
@@ -635,16 +657,10 @@ __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const
         reinterpret_cast<float4*>(inputs)[id] = make_float4(alf, bef, a_f, inc_deg);
         unsigned char fb = 0;
         if (alf >= box.x && alf <= box.y && bef >= box.z && bef <= box.w) {
-            // distance to the curve's vertices and even-odd inside test, in FP32 (the band
-            // edge needs no more precision)
-            float d2 = 3.0e38f;
-            bool inside = false;
-            for (int c = 0; c < n_curve; ++c) {
-                const float2 v1 = sc[c], v2 = sc[c + 1 < n_curve ? c + 1 : 0];
-                const float dx = alf - v1.x, dy = bef - v1.y;
-                d2 = fminf(d2, dx * dx + dy * dy);
-                if ((v1.y > bef) != (v2.y > bef) && alf < v1.x + (bef - v1.y) * (v2.x - v1.x) / (v2.y - v1.y)) inside = !inside;
-            }
+            // FP32 suffices: the band edge needs no more precision
+            float d2;
+            bool inside;
+            curve_relation(alf, bef, sc, n_curve, true, d2, inside);
             fb = (inside || d2 < band2) ? 1 : 0;
         }
         fallback[id] = fb;

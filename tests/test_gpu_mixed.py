@@ -172,9 +172,10 @@ def test_fp32_reciprocal_within_one_ulp(R):
 
 @pytest.mark.parametrize("flags", [0, "df64"])
 def test_results_independent_of_schedule(R, flags):
-    """The near-critical band, the FP64 passes' step budgets and the tail split move work
-    between launches and streams, never a ray's arithmetic: images and fluxes are bit-identical
-    (re-queued FP64 states are stored exactly)."""
+    """The near-critical band, the FP64 passes' step budgets on both streams, the second
+    stream's block size and the tail split move work between launches and streams, never a
+    ray's arithmetic: images and fluxes are bit-identical (re-queued FP64 states are stored
+    exactly)."""
     import torch
 
     cam = dict(scenes.SMALL, nx=56, ny=48, precision=R.MIXED, flags=R.FLAG_INNER_DF64 if flags else 0)
@@ -184,10 +185,12 @@ def test_results_independent_of_schedule(R, flags):
     freqs = scenes.SPECTRAL_FREQS[:2]
     ref, fref = ctx.render(freqs)
     ref = ref.cpu().numpy()
-    for band, budgets, tail in [(0.0, None, 0), (1.0, None, 0), (0.5, [64], 0), (0.5, None, 2), (0.5, None, 5),
-                                (2.0, [8, 8, 8], 1)]:
+    for band, budgets, tail, long in [(0.0, None, 0, None), (1.0, None, 0, None), (0.5, [64], 0, None),
+                                      (0.5, None, 2, None), (0.5, None, 5, [16]), (2.0, [8, 8, 8], 1, [4, 8, 16]),
+                                      (2.0, None, 0, [1, 2, 3, 4, 5, 6, 7]), (1.0, None, 3, [32])]:
         ctx.mixed_config(band, budgets, tail)
+        ctx.long_config(32 if long and len(long) > 2 else 0, long)
         img, fl = ctx.render(freqs)
         torch.cuda.synchronize()
-        assert np.array_equal(img.cpu().numpy(), ref), (band, budgets, tail)
-        assert np.array_equal(fl, fref), (band, budgets, tail)
+        assert np.array_equal(img.cpu().numpy(), ref), (band, budgets, tail, long)
+        assert np.array_equal(fl, fref), (band, budgets, tail, long)

@@ -235,3 +235,28 @@ def test_learned_path_full_size(R, ora, trained, size):
     for (i, j) in pix[keep]:
         ov = ora.trace_ray(s, al[j], be[i], freqs)["I"][0] * pix_jy
         assert abs(img[0, i, j] - ov) <= PIX_TOL * max(abs(ov), 1e-6 * peak), (i, j)
+
+
+@pytest.mark.parametrize("fb_band", [0.5, 0.2])
+def test_learned_results_independent_of_schedule(R, trained, fb_band):
+    """The near-critical band only moves rays between the streams: near-critical rays are
+    fallback rays (same FP32 predicate in both kernels), so whatever the band, the rays the
+    network serves and every ray's arithmetic stay the same: bit-identical images and fluxes,
+    also for bands wider than the fallback band."""
+    import torch
+
+    cam = dict(scenes.SMALL, nx=64, ny=56, precision=R.MIXED_MLP, flags=R.FLAG_INNER_DF64)
+    ctx = R.Context(R.camera_desc(**cam))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    ctx.surrogate_set(trained)
+    ctx.surrogate_config(fb_band, 50.0)
+    ctx.graph_config(False)
+    freqs = [1e10, 230e9]
+    ref, fref = ctx.render(freqs)
+    ref = ref.cpu().numpy()
+    for band in (0.0, 0.3, 0.5, 1.0, 2.0):
+        ctx.mixed_config(band)
+        img, fl = ctx.render(freqs)
+        torch.cuda.synchronize()
+        assert np.array_equal(img.cpu().numpy(), ref), band
+        assert np.array_equal(fl, fref), band
