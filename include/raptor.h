@@ -340,11 +340,14 @@ raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launch
 raptor_status raptor_profile_timeline(raptor_ctx* ctx, int cap, int* slot, int* lane, double* start_ms,
                                       double* dur_ms, int* count);
 
-/* Self-check of the FP32 reciprocal the FP32 code paths use (the hardware's approximate
- * reciprocal refined by one Newton-Raphson step): *max_ulp receives the largest distance in
- * ulps from the correctly rounded 1/v over n values spanning 2^-100 .. 2^101 of both signs.
- * Synchronises the device.  The paper has no counterpart. */
-raptor_status raptor_check_fp32_reciprocal(long long n, unsigned int* max_ulp);
+/* Self-check of the FP32 code paths' own arithmetic primitives over n inputs each:
+ * max_ulp[5] (caller's host array) receives the largest distance in ulps from the reference
+ * rounded to float of (0) the reciprocal (approximate reciprocal + one Newton-Raphson step)
+ * against 1/v over +-2^-100 .. 2^101, (1) the square root against sqrtf and (2) the cube root
+ * against the FP64 cube root over 2^-100 .. 2^101, (3) x / (e^x - 1) and (4) (1 - e^-x) / x
+ * (series below 1, quotients above) against FP64 over 2^-40 .. 36.  Synchronises the
+ * device.  RAPTOR_EINVAL for n < 1 or a NULL max_ulp.  The paper has no counterpart. */
+raptor_status raptor_check_fp32_math(long long n, unsigned int* max_ulp);
 
 /* FMA-chain microbenchmark on the current device: dependent FP64 (fp64 = 1) or FP32
  * (fp64 = 0) fused multiply-adds on every SM; *tflops = achieved rate (2 flops per FMA).

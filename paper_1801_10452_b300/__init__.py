@@ -31,7 +31,7 @@ EXPORTS = [
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
-    "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_reciprocal",
+    "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp"]
@@ -115,7 +115,7 @@ def lib():
             "raptor_profile_timeline": (st, [vp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.POINTER(C.c_int)]),
             "raptor_graph_config": (st, [vp, C.c_int]),
-            "raptor_check_fp32_reciprocal": (st, [C.c_longlong, C.c_void_p]),
+            "raptor_check_fp32_math": (st, [C.c_longlong, C.c_void_p]),
             "raptor_graph_stats": (st, [vp, C.c_void_p, C.c_void_p]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
         }
@@ -444,10 +444,11 @@ def pixel_centres(cam: CameraDesc):
     return cam.alpha_min + (np.arange(cam.nx) + 0.5) * da, cam.beta_min + (np.arange(cam.ny) + 0.5) * db
 
 
-def check_fp32_reciprocal(n=1 << 24):
-    """Largest ulp distance of the library's FP32 reciprocal from the correctly rounded one."""
-    u = C.c_uint(0)
-    st = lib().raptor_check_fp32_reciprocal(int(n), C.byref(u))
+def check_fp32_math(n=1 << 24):
+    """Largest ulp distances of the library's FP32 primitives from their references:
+    {"rcp", "sqrt", "cbrt", "x_over_expm1", "one_minus_exp_over"}."""
+    u = (C.c_uint * 5)()
+    st = lib().raptor_check_fp32_math(int(n), u)
     if st != OK:
-        raise RaptorError(st, "raptor_check_fp32_reciprocal")
-    return int(u.value)
+        raise RaptorError(st, "raptor_check_fp32_math")
+    return dict(zip(["rcp", "sqrt", "cbrt", "x_over_expm1", "one_minus_exp_over"], [int(v) for v in u]))

@@ -1807,16 +1807,16 @@ raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launch
     return RAPTOR_OK;
 }
 
-raptor_status raptor_check_fp32_reciprocal(long long n, unsigned int* max_ulp) {
+raptor_status raptor_check_fp32_math(long long n, unsigned int* max_ulp) {
     if (n < 1 || !max_ulp) return RAPTOR_EINVAL;
     unsigned int* d = nullptr;
-    if (cudaMalloc(&d, sizeof(unsigned int)) != cudaSuccess) return RAPTOR_ENOMEM;
-    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned int));
+    if (cudaMalloc(&d, 5 * sizeof(unsigned int)) != cudaSuccess) return RAPTOR_ENOMEM;
+    cudaError_t e = cudaMemset(d, 0, 5 * sizeof(unsigned int));
     if (e == cudaSuccess) {
-        k_check_rcp<<<256, 256>>>(n, d);
+        k_check_fp32_math<<<256, 256>>>(n, d);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpy(max_ulp, d, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(max_ulp, d, 5 * sizeof(unsigned int), cudaMemcpyDeviceToHost);
     cudaFree(d);
     return e == cudaSuccess ? RAPTOR_OK : RAPTOR_ECUDA;
 }

@@ -236,20 +236,32 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double* __re
 }
 
 // FMA-chain microbenchmark: 16 independent dependent chains per thread.
-// Self-check of rcp_nr against the correctly rounded reciprocal: the largest distance in
-// ulps over n values v = +-m 2^e (m from a Weyl sequence in [1, 2), e in [-100, 100]).
-__global__ void k_check_rcp(long long n, unsigned int* max_ulp) {
-    unsigned int worst = 0;
+// Self-check of the FP32 code paths' own primitives.  Per primitive, the largest distance in
+// ulps (of the float bit patterns) from a reference rounded to float: rcp_nr and sqrt_nr
+// against the correctly rounded 1/v and sqrtf, cbrt_nr against the FP64 cube root rounded
+// to float, x_over_expm1f and one_minus_exp_over_f against FP64 x / expm1(x) and
+// -expm1(-d) / d rounded to float.  Inputs: m 2^e, m from a Weyl sequence in [1, 2), e in
+// [-100, 100] (both signs for the reciprocal); x and d = m 2^e with e in [-40, 4], and
+// 1 + 35 m for the series' other branch.
+__global__ void k_check_fp32_math(long long n, unsigned int* max_ulp) {
+    unsigned int worst[5] = {0, 0, 0, 0, 0};
+    auto ulps = [](float a, float b) {
+        const int d = __float_as_int(a) - __float_as_int(b);
+        return (unsigned int)(d < 0 ? -d : d);
+    };
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float m = 1.0f + (float)((i * 0x9E3779B9ull) & 0xFFFFFF) * (1.0f / 16777216.0f);
         const int e = (int)(i % 201) - 100;
-        float v = ldexpf(m, e);
-        if (i & 1) v = -v;
-        const float r1 = rcp_nr(v), r0 = 1.0f / v;
-        const int d = __float_as_int(r1) - __float_as_int(r0);
-        worst = max(worst, (unsigned int)(d < 0 ? -d : d));
+        const float v = ldexpf(m, e);
+        const float vs = (i & 1) ? -v : v;
+        worst[0] = max(worst[0], ulps(rcp_nr(vs), 1.0f / vs));
+        worst[1] = max(worst[1], ulps(sqrt_nr(v), sqrtf(v)));
+        worst[2] = max(worst[2], ulps(cbrt_nr(v), (float)cbrt((double)v)));
+        const float x = (i % 3 == 0) ? 1.0f + 35.0f * (m - 1.0f) : ldexpf(m, (int)(i % 45) - 40);
+        worst[3] = max(worst[3], ulps(x_over_expm1f(x), (float)((double)x / expm1((double)x))));
+        worst[4] = max(worst[4], ulps(one_minus_exp_over_f(x), (float)(-expm1(-(double)x) / (double)x)));
     }
-    atomicMax(max_ulp, worst);
+    for (int k = 0; k < 5; ++k) atomicMax(&max_ulp[k], worst[k]);
 }
 
 template <typename T>

@@ -192,7 +192,7 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
             synchrotron<float>(g * p.f.nu[f], ne, the, B, sinb, k2x, j, S, kIScale);
             if (j > 0.f && S > 0.f) {
                 const float dtau = j * rcp_nr(S) * gdl_unscaled;
-                const float F = dtau > 1e-4f ? -expm1f(-dtau) * rcp_nr(dtau) : 1.f - 0.5f * dtau;
+                const float F = one_minus_exp_over_f(dtau);
                 const float tau_now = tau[f] + tau_hi[f].hi;
                 I[f] += TI(expf(-tau_now) * j * dlcm * F * ig2);
                 if (tau_hi[f].hi > 0.f || tau[f] + dtau > 10.f) tau_hi[f] = tau_hi[f] + df64(dtau, 0.f);

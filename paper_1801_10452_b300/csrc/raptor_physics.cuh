@@ -228,7 +228,8 @@ RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, 
     const T cj = T(1.4142135623730951 * kPi * kQe * kQe / (3.0 * kC)) * jscale;
     const T hme = T(kH / (kMe * kC * kC));
     const T x = dv(hme * nu, the);
-    S = T(2.0 * kMe) * nu * nu * the * dv(x, Real<T>::expm1_(x));
+    if constexpr (std::is_same<T, float>::value) S = T(2.0 * kMe) * nu * nu * the * x_over_expm1f(x);
+    else S = T(2.0 * kMe) * nu * nu * the * dv(x, Real<T>::expm1_(x));
     j = T(0);
     const T nu_s = T(2.0 / 9.0) * nu_c_per_G * B * the * the * sinb;
     if (!(nu_s > T(0))) return;
@@ -236,7 +237,9 @@ RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, 
     const T X13 = Real<T>::cbrt_(X);
     if (X13 > Real<T>::exp_cut) return;
     const T X16 = Real<T>::sqrt_(X13);
-    const T X12 = Real<T>::sqrt_(X);
+    T X12;
+    if constexpr (std::is_same<T, float>::value) X12 = X13 * X16;  // X^(1/2) = X^(1/3) X^(1/6)
+    else X12 = Real<T>::sqrt_(X);
     const T fac = X12 + T(1.8877486253633870) * X16;  // 2^(11/12)
     T K2 = T(2) * the * the;
     if (k2_exact) K2 = T(bessel_k2_exact(1.0 / double(the)));

@@ -164,10 +164,19 @@ def test_spectral_scene_full_size(R, ora, spin, flags):
             assert abs(img[f, i, j] - ov) <= PIX_TOL * max(abs(ov), 1e-6 * peak[f]), (i, j, f)
 
 
-def test_fp32_reciprocal_within_one_ulp(R):
-    """The FP32 paths' reciprocal (approximate reciprocal + one Newton-Raphson step) stays
-    within one ulp of the correctly rounded 1/v over 2^24 values spanning 2^-100 .. 2^101."""
-    assert R.check_fp32_reciprocal(1 << 24) <= 1
+def test_fp32_primitives_within_their_bounds(R):
+    """The FP32 paths' own primitives over 2^24 inputs each: reciprocal and square root
+    (approximate hardware value + one Newton-Raphson step) within one ulp of the correctly
+    rounded result; cube root (approximate 2^(log2 x / 3) + one Newton step) within two ulp
+    of the FP64 cube root; the Bernoulli series of x / (e^x - 1) and the Taylor series of
+    (1 - e^-x) / x within two ulp of FP64.  Beyond x = 1, x / (e^x - 1) is the quotient of
+    expf (two ulp), whose error the subtraction of 1 amplifies by e^x / (e^x - 1) <= 1.6,
+    and the reciprocal: four ulp."""
+    u = R.check_fp32_math(1 << 24)
+    print(u)
+    assert u["rcp"] <= 1 and u["sqrt"] <= 1
+    assert u["cbrt"] <= 2
+    assert u["x_over_expm1"] <= 4 and u["one_minus_exp_over"] <= 2
 
 
 @pytest.mark.parametrize("flags", [0, "df64"])
