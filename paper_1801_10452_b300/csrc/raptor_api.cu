@@ -776,10 +776,10 @@ raptor_status raptor_camera_init(const raptor_camera_desc* desc, raptor_ctx** ou
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_trace_int, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_trace_I, 64 * sizeof(double));
     if (e == cudaSuccess) {
-        // the double-float sin/cos table of this device
+        // the sin/cos node table of this device (double-float polar-angle sin/cos)
         float4 tab[kSinTabN + 1];
-        df_sincos_table_fill(tab);
-        e = cudaMemcpyToSymbol(g_df_sincos_tab, tab, sizeof(tab));
+        sincos_table_fill(tab);
+        e = cudaMemcpyToSymbol(g_sincos_tab, tab, sizeof(tab));
     }
     if (e != cudaSuccess) {
         const raptor_status s = e == cudaErrorMemoryAllocation ? RAPTOR_ENOMEM : RAPTOR_ECUDA;

@@ -77,7 +77,9 @@ RAPTOR_HD df64 df_mul_f(df64 b, float q) {
 // residuals below correct.
 RAPTOR_HD float df_rcp_approx(float v) {
 #ifdef __CUDA_ARCH__
-    return __fdividef(1.f, v);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
 #else
     return 1.f / v;
 #endif
@@ -156,37 +158,10 @@ RAPTOR_HD void df_sincos(df64 x, df64* s_out, df64* c_out) {
 }
 
 // sin and cos of theta in [0, pi] (the range of the geodesic's polar angle) from a table of
-// the 65 nodes theta_i = i pi / 64 (float pairs, filled by df_sincos_table_fill) and the
+// the 65 nodes theta_i = i pi / 64 (float pairs, raptor::sincos_node) and the
 // Taylor series of the offset d = theta - theta_i, |d| <= pi / 128: sin d to d^7 and cos d
 // to d^6 (first omitted terms < 1e-20), the terms below ~2^-24 of the leading one summed in
 // float; then the angle-addition formulas.  Outside [0, pi]: df_sincos.
-constexpr int kSinTabN = 64;
-#ifdef __CUDACC__
-__device__ float4 g_df_sincos_tab[kSinTabN + 1];
-#endif
-// Host fill of the table (sin hi, sin lo, cos hi, cos lo) from long-double sin and cos.
-inline void df_sincos_table_fill(float4* t) {
-    const long double pi_l = 3.141592653589793238462643383279502884L;
-    for (int i = 0; i <= kSinTabN; ++i) {
-        const long double th = pi_l * i / kSinTabN;
-        const long double sv = sinl(th), cv = cosl(th);
-        const float sh = (float)sv, ch = (float)cv;
-        t[i] = float4{sh, (float)(sv - (long double)sh), ch, (float)(cv - (long double)ch)};
-    }
-}
-RAPTOR_HD float4 df_sincos_node(int i) {
-#ifdef __CUDA_ARCH__
-    return __ldg(&g_df_sincos_tab[i]);
-#else
-    static float4 tab[kSinTabN + 1];
-    static bool init = false;
-    if (!init) {
-        df_sincos_table_fill(tab);
-        init = true;
-    }
-    return tab[i];
-#endif
-}
 RAPTOR_HD void df_sincos_tab(df64 x, df64* s_out, df64* c_out) {
     const float xf = x.hi + x.lo;
     if (!(xf >= 0.f && xf <= 3.14159265f)) {
@@ -195,7 +170,7 @@ RAPTOR_HD void df_sincos_tab(df64 x, df64* s_out, df64* c_out) {
     }
     // pi / 64 = Q1 + Q2 + Q3 (three floats)
     const float Q1 = 0.0490873866f, Q2 = -1.36598088e-09f, Q3 = -5.35976409e-17f;
-    const int i = (int)rintf(xf * (kSinTabN / 3.14159265358979f));
+    const int i = (int)rintf(xf * (::raptor::kSinTabN / 3.14159265358979f));
     const float fi = (float)i;
     df64 d = x - df_two_prod(fi, Q1);
     d = d - df_two_prod(fi, Q2);
@@ -211,7 +186,7 @@ RAPTOR_HD void df_sincos_tab(df64 x, df64* s_out, df64* c_out) {
     const float tc = fmaf(-0.00138888892f, d2f, 0.0416666679f);
     df64 pc = df64(tc, 0.f) * d2 + df64(-0.5f, 0.f);
     pc = pc * d2 + df64(1.f, 0.f);
-    const float4 t = df_sincos_node(i);
+    const float4 t = ::raptor::sincos_node(i);
     const df64 s0(t.x, t.y), c0(t.z, t.w);
     *s_out = s0 * pc + c0 * sd;
     *c_out = c0 * pc - s0 * sd;
@@ -228,11 +203,6 @@ using dfns::df64;
 using dfns::df_fast_two_sum;
 using dfns::df_sincos;
 using dfns::df_sincos_tab;
-using dfns::df_sincos_table_fill;
-using dfns::kSinTabN;
-#ifdef __CUDACC__
-using dfns::g_df_sincos_tab;
-#endif
 using dfns::df_sqrt;
 using dfns::df_two_prod;
 using dfns::df_two_sum;
