@@ -27,6 +27,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 KIND_ANALYTIC, KIND_GRID, KIND_STATIC_ISO, KIND_BALL = 0, 1, 2, 3
 ESCAPED, CAPTURED, THICK, TRUNCATED, ERROR = 0, 1, 2, 3, 4
+DISK_HIT, DISK_NO_HIT = 5, 6
 
 
 class OraScene(C.Structure):
@@ -88,6 +89,8 @@ def lib():
             "ora_trace_ray": (I, [sp, D, D, D, dp, I, dp, dp, ip, dp, I]),
             "ora_geodesic": (I, [sp, D, D, I, dp, dp, ip]),
             "ora_render": (I, [sp, dp, I, D, I, I, dp, ip, ip, I]),
+            "ora_disk_ray": (I, [sp, D, D, D, D, D, I, dp]),
+            "ora_disk_render": (I, [sp, D, D, D, I, dp, dp, ip, ip, ip, I]),
             "ora_length_unit_cm": (D, [D]),
             "ora_num_threads": (I, []),
         }
@@ -260,6 +263,39 @@ def render(s, freqs, t_cam=0.0, row0=0, nrows=0, nthreads=0):
     status = np.zeros((rows, s.nx), np.int32)
     lib().ora_render(C.byref(s), _dp(nus), nf, t_cam, row0, nrows, _dp(img), _ip(steps), _ip(status), nthreads)
     return img, steps, status
+
+
+def disk_ray(s, alpha, beta, r_in=0.0, r_out=15.0, q=2.0, max_cross=10):
+    """One ray against the thin disk of sec. 4.2.1 (r_in <= 0: the ISCO).  Returns dict(status,
+    ratio = E_obs/E_em, I, order, r, theta, g, steps)."""
+    out = np.zeros(7)
+    st = lib().ora_disk_ray(C.byref(s), alpha, beta, r_in, r_out, q, max_cross, _dp(out))
+    return dict(status=st, ratio=out[0], I=out[1], order=int(out[2]), r=out[3], theta=out[4], g=out[5],
+                steps=int(out[6]))
+
+
+def disk_render(s, r_in=0.0, r_out=15.0, q=2.0, max_cross=10, nthreads=0):
+    """Thin-disk image: (ratio, I, order, status, steps), each [ny][nx]."""
+    shape = (s.ny, s.nx)
+    ratio = np.zeros(shape); inten = np.zeros(shape)
+    order = np.zeros(shape, np.int32); status = np.zeros(shape, np.int32); steps = np.zeros(shape, np.int32)
+    lib().ora_disk_render(C.byref(s), r_in, r_out, q, max_cross, _dp(ratio), _dp(inten), _ip(order), _ip(status),
+                          _ip(steps), nthreads)
+    return ratio, inten, order, status, steps
+
+
+def line_profile(ratio, inten, order, x_min, x_max, n_bins, pix_area, profile_order=1):
+    """Line spectrum of sec. 4.2.1: the sum of I * pixel area over pixels whose hit has
+    crossing number profile_order (0: any order), in n_bins bins of E_obs/E_em over
+    [x_min, x_max): bin floor((x - x_min) / dx), dx = (x_max - x_min) / n_bins."""
+    sel = (order == profile_order) if profile_order > 0 else (order > 0)
+    dx = (x_max - x_min) / n_bins
+    hist = np.zeros(n_bins)
+    for x, w in zip(ratio[sel].ravel(), inten[sel].ravel()):
+        b = int(np.floor((x - x_min) / dx))
+        if 0 <= b < n_bins:
+            hist[b] += w * pix_area
+    return hist
 
 
 def length_unit_cm(mass_msun):
