@@ -160,6 +160,40 @@ raptor_status raptor_render_ex(raptor_ctx* ctx, const double* freqs_hz, int n_fr
                                int row0, int n_rows, int snap, double* image_dev, double* flux_jy_host,
                                int* steps_dev, int* status_dev, void* stream);
 
+/* Thin-disk line emitter (sec. 4.2.1): an opaque disk in the equatorial plane between r_in
+ * and r_out on circular Keplerian orbits (Omega = 1/(r^{3/2} + a): prograde for a > 0,
+ * retrograde relative to the hole for a < 0), emitting one line with emission ~ r^-q and no
+ * absorption. */
+typedef struct {
+    double r_in;        /* inner radius in M; <= 0: the ISCO of the camera's spin [0] */
+    double r_out;       /* outer radius in M [15] */
+    double q;           /* emission ~ r^-q [2] */
+    int max_cross;      /* crossings of the equatorial plane after which a ray gives up [10] */
+    int profile_order;  /* crossing number of the hits that form the spectrum; 0: all [1] */
+    int n_bins;         /* spectrum bins of E_obs/E_em over [x_min, x_max) [64] */
+    double x_min, x_max; /* [0.2, 1.6] */
+} raptor_disk_desc;
+
+raptor_status raptor_disk_desc_default(raptor_disk_desc* d);
+
+/* Render the thin disk with the context's camera (spin, inclination, field of view, step
+ * rule, r_stop, r_escape, max_steps), always in FP64 (no plasma needed).  Each pixel's ray
+ * is integrated until it crosses theta = pi/2 inside the disk (a hit: crossing point refined
+ * by Newton's iteration on the length of the last RK4 step), is captured or escapes, or has
+ * crossed the plane max_cross times.  Outputs (caller-owned device arrays [ny][nx], row-major
+ * as the images): ratio_dev = E_obs/E_em = 1 / (k.u) at the hit, intensity_dev = the line's
+ * frequency-integrated intensity (E_obs/E_em)^4 r^-q, order_dev = crossing number of the hit
+ * (0 and zeros elsewhere for rays without a hit); optional status_dev (0 escaped, 1 captured,
+ * 3 truncated, 4 error, 5 hit, 6 max_cross crossings without a hit) and steps_dev (may be
+ * NULL).  profile_host (host, [n_bins], may be NULL): the line spectrum, the sum of
+ * intensity x pixel area (d alpha d beta in M^2) over the hits of crossing number
+ * profile_order in bins floor((ratio - x_min) / dx), dx = (x_max - x_min) / n_bins, summed
+ * in 64-bit fixed point (order-independent); with a spectrum the call synchronises the
+ * stream.  RAPTOR_EINVAL for NULL required buffers, r_in >= r_out, max_cross < 1 or a bad
+ * bin range. */
+raptor_status raptor_disk_render(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev, double* intensity_dev,
+                                 int* order_dev, int* status_dev, int* steps_dev, double* profile_host, void* stream);
+
 /* Render an image from host buffers: copies nothing in but the frequencies, renders, copies
  * the image to image_host (double [n_freq][ny][nx], may be NULL) and the flux to
  * flux_jy_host (may be NULL), and synchronises `stream`.  Device scratch is context-owned. */
@@ -310,8 +344,8 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 /* Per-kernel device time, measured with CUDA events recorded around every kernel launch on
  * the launch's own stream.  raptor_profile(ctx, 1) clears the accumulators and starts
  * recording; raptor_profile(ctx, 0) stops.  raptor_profile_read waits for the recorded
- * events and returns, per kernel slot RAPTOR_KERNEL_* (11 slots), the summed milliseconds
- * (ms[11], may be NULL) and the number of launches since the last clear (launches[11],
+ * events and returns, per kernel slot RAPTOR_KERNEL_* (12 slots), the summed milliseconds
+ * (ms[12], may be NULL) and the number of launches since the last clear (launches[12],
  * may be NULL; counted whether or not recording is on).  A slot covers all the kernels of
  * one stage (e.g. the surrogate slot times its inference as one interval). */
 #define RAPTOR_KERNEL_RENDER_FP64 0  /* persistent FP64 ray kernel                         */
@@ -326,6 +360,7 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
                                      /* network; launches count its own two kernels)       */
 #define RAPTOR_KERNEL_TRAIN 9        /* surrogate data generation and training             */
 #define RAPTOR_KERNEL_SURROGATE_MLP 10 /* the network inside RAPTOR_KERNEL_SURROGATE        */
+#define RAPTOR_KERNEL_DISK 11        /* thin-disk rays and their spectrum                  */
 raptor_status raptor_profile(raptor_ctx* ctx, int enable);
 raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches);
 

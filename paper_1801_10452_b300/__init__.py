@@ -31,10 +31,10 @@ EXPORTS = [
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
-    "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
+    "raptor_disk_desc_default", "raptor_disk_render", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
-                "surrogate", "train", "surrogate_mlp"]
+                "surrogate", "train", "surrogate_mlp", "disk"]
 
 
 class RaptorError(RuntimeError):
@@ -51,6 +51,13 @@ class CameraDesc(C.Structure):
         ("eps", C.c_double), ("r_stop_factor", C.c_double), ("r_escape", C.c_double), ("tau_cut", C.c_double),
         ("max_steps", C.c_int), ("precision", C.c_int), ("flags", C.c_uint), ("reserved0", C.c_int),
         ("r_fp64", C.c_double), ("turn_kr", C.c_double), ("t_delay", C.c_double),
+    ]
+
+
+class DiskDesc(C.Structure):
+    _fields_ = [
+        ("r_in", C.c_double), ("r_out", C.c_double), ("q", C.c_double), ("max_cross", C.c_int),
+        ("profile_order", C.c_int), ("n_bins", C.c_int), ("x_min", C.c_double), ("x_max", C.c_double),
     ]
 
 
@@ -118,6 +125,8 @@ def lib():
             "raptor_check_fp32_math": (st, [C.c_longlong, C.c_void_p]),
             "raptor_graph_stats": (st, [vp, C.c_void_p, C.c_void_p]),
             "raptor_render_noalloc": (st, [C.POINTER(CameraDesc), C.POINTER(PlasmaDesc), dp, C.c_int, C.c_double, vp, vp, vp]),
+            "raptor_disk_desc_default": (st, [C.POINTER(DiskDesc)]),
+            "raptor_disk_render": (st, [vp, C.POINTER(DiskDesc), vp, vp, vp, vp, vp, dp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -301,6 +310,33 @@ class Context:
         n = (C.c_longlong * k)()
         self._check(lib().raptor_profile_read(self._h, _dp(ms), n), "raptor_profile_read")
         return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(k)}
+
+    def disk_render(self, r_in=0.0, r_out=15.0, q=2.0, max_cross=10, profile_order=1, n_bins=64, x_range=(0.2, 1.6),
+                    spectrum=True, stream=None):
+        """Thin-disk line emitter (sec. 4.2.1) with this context's camera, in FP64: per pixel
+        E_obs/E_em, line intensity and hit order (device tensors [ny][nx]), status and steps,
+        and the line spectrum (host array [n_bins], None without `spectrum`) with its bin
+        edges."""
+        import torch
+
+        d = DiskDesc()
+        lib().raptor_disk_desc_default(C.byref(d))
+        d.r_in, d.r_out, d.q, d.max_cross = float(r_in), float(r_out), float(q), int(max_cross)
+        d.profile_order, d.n_bins, d.x_min, d.x_max = int(profile_order), int(n_bins), float(x_range[0]), float(x_range[1])
+        shape = (self.cam.ny, self.cam.nx)
+        ratio = torch.empty(shape, dtype=torch.float64, device="cuda")
+        inten = torch.empty_like(ratio)
+        order = torch.empty(shape, dtype=torch.int32, device="cuda")
+        status = torch.empty_like(order)
+        steps = torch.empty_like(order)
+        prof = np.zeros(max(1, n_bins)) if spectrum else None
+        self._check(lib().raptor_disk_render(self._h, C.byref(d), C.c_void_p(ratio.data_ptr()),
+                                             C.c_void_p(inten.data_ptr()), C.c_void_p(order.data_ptr()),
+                                             C.c_void_p(status.data_ptr()), C.c_void_p(steps.data_ptr()),
+                                             _dp(prof) if spectrum else None, _stream(stream)), "raptor_disk_render")
+        edges = np.linspace(x_range[0], x_range[1], n_bins + 1)
+        return dict(ratio=ratio, intensity=inten, order=order, status=status, steps=steps,
+                    spectrum=prof[:n_bins] if spectrum else None, edges=edges)
 
     def profile_timeline(self):
         """Recorded launches since the last profile(True), in launch order: a list of

@@ -33,6 +33,8 @@ struct raptor_ctx {
     unsigned long long* d_counters = nullptr;  // [8] work counters
     unsigned long long* d_stats = nullptr;     // [8]
     double* d_partial = nullptr;
+    unsigned long long* d_hist = nullptr;  // thin-disk spectrum (fixed point)
+    size_t hist_cap = 0;
     size_t partial_cap = 0;
     double* d_flux = nullptr;
     size_t flux_cap = 0;
@@ -884,6 +886,83 @@ raptor_status raptor_render(raptor_ctx* ctx, const double* freqs_hz, int n_freq,
                             stream);
 }
 
+raptor_status raptor_disk_desc_default(raptor_disk_desc* d) {
+    if (!d) return RAPTOR_EINVAL;
+    d->r_in = 0.0;
+    d->r_out = 15.0;
+    d->q = 2.0;
+    d->max_cross = 10;
+    d->profile_order = 1;
+    d->n_bins = 64;
+    d->x_min = 0.2;
+    d->x_max = 1.6;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_disk_render(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev, double* intensity_dev,
+                                 int* order_dev, int* status_dev, int* steps_dev, double* profile_host, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!d) return fail(ctx, RAPTOR_EINVAL, "disk descriptor is NULL");
+    if (!ratio_dev || !intensity_dev || !order_dev) return fail(ctx, RAPTOR_EINVAL, "ratio, intensity and order buffers are required");
+    const double r_in = d->r_in > 0.0 ? d->r_in : r_isco_prograde(ctx->cam.spin);
+    if (!std::isfinite(d->r_in) || !(d->r_out > r_in) || !std::isfinite(d->r_out))
+        return fail(ctx, RAPTOR_EINVAL, "need finite 0 < r_in < r_out (r_in <= 0: the ISCO)");
+    if (!std::isfinite(d->q) || d->max_cross < 1 || d->profile_order < 0)
+        return fail(ctx, RAPTOR_EINVAL, "need finite q, max_cross >= 1, profile_order >= 0");
+    if (profile_host && (d->n_bins < 1 || d->n_bins > (1 << 20) || !(d->x_max > d->x_min) || !(d->x_min >= 0.0) ||
+                         !std::isfinite(d->x_max)))
+        return fail(ctx, RAPTOR_EINVAL, "need 1 <= n_bins <= 2^20 and 0 <= x_min < x_max");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    Params p = base_params(ctx);
+    p.row0 = 0;
+    p.n_rows = ctx->cam.ny;
+    p.n_pix = ctx->cam.ny * ctx->cam.nx;
+    p.n_rays = p.n_pix;
+    p.t_cam = 0.0;
+    DiskArgs a{};
+    a.r_in = r_in;
+    a.r_out = d->r_out;
+    a.q = d->q;
+    a.max_cross = d->max_cross;
+    a.ratio = ratio_dev;
+    a.inten = intensity_dev;
+    a.order = order_dev;
+    a.status = status_dev;
+    a.steps = steps_dev;
+    RCK(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s));
+    int occ = 0;
+    RCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disk_fp64, ctx->launch_block, 0));
+    const long long need = (p.n_rays + ctx->launch_block - 1) / ctx->launch_block;
+    const long long blocks = std::max<long long>(1, std::min<long long>(grid_blocks(ctx, std::max(occ, 1)), need));
+    {
+        ProfScope ps(ctx, kProfDisk, s);
+        k_disk_fp64<<<(int)blocks, ctx->launch_block, 0, s>>>(p, a, ctx->d_counters, ctx->d_stats);
+    }
+    RCK(cudaGetLastError());
+    if (!profile_host) return RAPTOR_OK;
+    // fixed-point scale: the largest possible total (every pixel at the top bin edge and the
+    // inner radius, times the field of view) stays below 2^62
+    const double pix_area = p.da * p.db;
+    const double w_max = std::pow(d->x_max, 4.0) * std::pow(r_in, -d->q) * pix_area * (double)p.n_pix;
+    const double scale = std::ldexp(1.0, 62 - (int)std::ceil(std::log2(std::max(w_max, 1e-290))));
+    RCK(ensure(ctx, &ctx->d_hist, &ctx->hist_cap, (size_t)d->n_bins));
+    RCK(cudaMemsetAsync(ctx->d_hist, 0, sizeof(unsigned long long) * d->n_bins, s));
+    const double dx = (d->x_max - d->x_min) / d->n_bins;
+    {
+        ProfScope ps(ctx, kProfDisk, s);
+        k_disk_profile<<<ew_blocks(p.n_pix), 256, 0, s>>>(ratio_dev, intensity_dev, order_dev, p.n_pix, d->profile_order,
+                                                          d->x_min, dx, d->n_bins, pix_area, scale, ctx->d_hist);
+    }
+    RCK(cudaGetLastError());
+    std::vector<unsigned long long> h(d->n_bins);
+    RCK(cudaMemcpyAsync(h.data(), ctx->d_hist, sizeof(unsigned long long) * d->n_bins, cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    for (int b = 0; b < d->n_bins; ++b) profile_host[b] = (double)h[b] / scale;
+    return RAPTOR_OK;
+}
+
 raptor_status raptor_render_host(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, double* image_host,
                                  double* flux_jy_host, void* stream) {
     if (!ctx) return RAPTOR_EINVAL;
@@ -1038,7 +1117,7 @@ void raptor_destroy(raptor_ctx* ctx) {
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
                   ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
-                  ctx->d_crit, ctx->d_rest};
+                  ctx->d_crit, ctx->d_rest, ctx->d_hist};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.a);

@@ -11,12 +11,12 @@ constexpr unsigned kFlagK2Exact = 0x1u;
 constexpr unsigned kFlagLinearR = 0x2u;
 constexpr unsigned kFlagInnerDf64 = 0x4u;
 
-enum : int { kEscaped = 0, kCaptured = 1, kThick = 2, kTruncated = 3, kError = 4 };
+enum : int { kEscaped = 0, kCaptured = 1, kThick = 2, kTruncated = 3, kError = 4, kDiskHit = 5, kDiskNone = 6 };
 
 // Per-kernel profiling slots (raptor_profile_read).
 enum : int { kProfRenderFp64 = 0, kProfMixedA = 1, kProfMixedB = 2, kProfMixedC = 3, kProfReduce = 4, kProfTrace = 5,
              kProfLoad = 6, kProfPeak = 7, kProfSurrogate = 8, kProfTrain = 9, kProfSurrogateMlp = 10,
-             kProfSlots = 11 };
+             kProfDisk = 11, kProfSlots = 12 };
 
 // Stats slots (device unsigned long long[8]).
 enum : int { kStatRays = 0, kStatSteps = 1, kStatFp64Steps = 2, kStatTrunc = 3, kStatErr = 4, kStatFallback = 5,
@@ -166,6 +166,140 @@ __global__ void __launch_bounds__(128) k_render_fp64(const Params p, unsigned lo
         }
     }
     warp_add_stats(stats, c_rays, c_steps, c_steps, c_trunc, c_err);
+}
+
+// ------------------------------------------------------------------------------------
+// Thin-disk line emitter (sec. 4.2.1): an opaque equatorial disk between r_in and r_out on
+// circular Keplerian orbits (Omega = 1/(r^{3/2} + a)), emission ~ r^{-q}, no absorption.  Each
+// ray is integrated with the FP64 step of k_render_fp64 until it crosses theta = pi/2 inside
+// the disk (a hit), is captured or escapes, or has crossed the plane max_cross times.  The
+// crossing point: Newton's iteration on the length h of one RK4 step from the state before
+// the crossing step, h <- h - (theta(h) - pi/2) / k^theta(h), from the linear estimate, a
+// fixed four iterations, then the step of the final length.  At a hit: E_obs/E_em = 1 / g,
+// g = k.u (Eq. 30), and the line intensity I = (E_obs/E_em)^4 r^{-q}.
+// ------------------------------------------------------------------------------------
+struct DiskArgs {
+    double r_in, r_out, q;
+    int max_cross;
+    double* ratio;    // [n_pix] E_obs/E_em (0: no hit)
+    double* inten;    // [n_pix] line intensity (0: no hit)
+    int* order;       // [n_pix] crossing number of the hit (0: no hit)
+    int* status;      // [n_pix] or nullptr
+    int* steps;       // [n_pix] or nullptr
+};
+
+__device__ __forceinline__ void disk_crossing(double a, const double x0[4], const double k0[4], double dl, double th1,
+                                              double xc[4], double kc[4]) {
+    const double half_pi = 0.5 * kPi;
+    double h = dl * (half_pi - x0[2]) / (th1 - x0[2]);
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { xc[i] = x0[i]; kc[i] = k0[i]; }
+        rk4_step<double>(a, xc, kc, h);
+        if (!(fabs(kc[2]) > 0.0)) break;
+        h -= (xc[2] - half_pi) / kc[2];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { xc[i] = x0[i]; kc[i] = k0[i]; }
+    rk4_step<double>(a, xc, kc, h);
+}
+
+// One step of a disk ray: returns the termination code or -1; on a hit fills ratio, I.
+__device__ __forceinline__ int disk_step(const Params& p, const DiskArgs& d, double x[4], double k[4], int& n,
+                                         int& crossings, double& ratio, double& inten) {
+    const double half_pi = 0.5 * kPi;
+    const double dl = step_size<double>(p.eps, (p.flags & kFlagLinearR) != 0, x, k);
+    double xo[4], ko[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { xo[i] = x[i]; ko[i] = k[i]; }
+    rk4_step<double>(p.a, x, k, dl);
+    n += 1;
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fin = fin && isfinite(x[i]) && isfinite(k[i]);
+    if (!fin) return kError;
+    if ((xo[2] - half_pi) * (x[2] - half_pi) <= 0.0 && xo[2] != half_pi) {
+        crossings += 1;
+        double xc[4], kc[4];
+        disk_crossing(p.a, xo, ko, dl, x[2], xc, kc);
+        const double rc = xc[1];
+        if (rc >= d.r_in && rc <= d.r_out) {
+            KSPoint<double> P;
+            ks_point<double>(p.a, rc, xc[2], P);
+            double u[4], kcov[4];
+            if (analytic_velocity<double>(p.a, 0.0, P, u) < 0) return kError;  // Keplerian at every r
+            ks_lower(P, kc, kcov);
+            const double g = kcov[0] * u[0] + kcov[1] * u[1] + kcov[2] * u[2] + kcov[3] * u[3];
+            if (!(g > 0.0)) return kError;
+            ratio = 1.0 / g;
+            inten = ratio * ratio * ratio * ratio * pow(rc, -d.q);
+            return kDiskHit;
+        }
+        if (crossings >= d.max_cross) return kDiskNone;
+    }
+    if (x[1] < p.r_stop) return kCaptured;
+    if (x[1] > p.r_esc) return kEscaped;
+    if (n >= p.max_steps) return kTruncated;
+    return -1;
+}
+
+// Persistent: each warp keeps 32 rays in flight and refills lanes from the counter.
+__global__ void __launch_bounds__(128) k_disk_fp64(const Params p, const DiskArgs d, unsigned long long* counter,
+                                                   unsigned long long* stats) {
+    double x[4], k[4], ratio = 0.0, inten = 0.0;
+    int n = 0, crossings = 0, pix = 0;
+    long long id = -1;
+    bool drained = false;
+    unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0;
+    for (;;) {
+        const long long nid = warp_fetch(counter, p.n_rays, id < 0, drained);
+        if (id < 0 && nid >= 0) {
+            id = nid;
+            pix = (int)id;
+            const int row = pix / p.nx, col = pix % p.nx;
+            camera_ray(p, p.amin + (col + 0.5) * p.da, p.bmin + (row + 0.5) * p.db, p.t_cam, x, k);
+            n = 0;
+            crossings = 0;
+            ratio = 0.0;
+            inten = 0.0;
+        }
+        if (!__any_sync(0xffffffffu, id >= 0)) break;
+        if (id >= 0) {
+            const int st = disk_step(p, d, x, k, n, crossings, ratio, inten);
+            if (st >= 0) {
+                const bool hit = st == kDiskHit;
+                d.ratio[pix] = hit ? ratio : 0.0;
+                d.inten[pix] = hit ? inten : 0.0;
+                d.order[pix] = hit ? crossings : 0;
+                if (d.status) d.status[pix] = st;
+                if (d.steps) d.steps[pix] = n;
+                c_rays += 1;
+                c_steps += (unsigned long long)n;
+                c_trunc += (st == kTruncated);
+                c_err += (st == kError);
+                id = -1;
+            }
+        }
+    }
+    warp_add_stats(stats, c_rays, c_steps, c_steps, c_trunc, c_err);
+}
+
+// Line spectrum of the disk image: pixels whose hit has crossing number `sel_order` (0: any)
+// add I * pixel area to bin floor((ratio - x_min) / dx) when it lies in [0, n_bins).  The
+// weights are summed as 64-bit fixed-point integers (w * 2^scale_log2, rounded), so the
+// spectrum does not depend on the order of the atomic additions.
+__global__ void __launch_bounds__(256) k_disk_profile(const double* __restrict__ ratio, const double* __restrict__ inten,
+                                                      const int* __restrict__ order, long long n, int sel_order,
+                                                      double x_min, double dx, int n_bins, double pix_area,
+                                                      double scale, unsigned long long* __restrict__ hist) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int o = order[i];
+        if (o == 0 || (sel_order > 0 && o != sel_order)) continue;
+        const double b = floor((ratio[i] - x_min) / dx);
+        if (!(b >= 0.0 && b < (double)n_bins)) continue;
+        atomicAdd(&hist[(int)b], (unsigned long long)llrint(inten[i] * pix_area * scale));
+    }
 }
 
 // Single-ray trace with per-step records (same arithmetic as k_render_fp64).

@@ -28,6 +28,13 @@ SPECTRAL = dict(SMALL, nx=512, ny=512)
 
 # Headline image: 1024 x 1024, a = 0.9375, i = 60 deg, 230 GHz.
 HEADLINE = dict(SMALL, spin=0.9375, nx=1024, ny=1024)
+
+# Thin-disk line emitter (sec. 4.2.1): disk from the ISCO to 15 M, emission ~ r^-2, the
+# paper's five spins; 1024^2 over +-16 M at i = 30 deg (the paper does not state i).
+THIN_DISK = dict(SMALL, spin=0.99, incl_deg=30.0, nx=1024, ny=1024, alpha_min=-16.0, alpha_max=16.0,
+                 beta_min=-16.0, beta_max=16.0)
+THIN_DISK_GEOM = dict(r_out=15.0, q=2.0, max_cross=10)
+THIN_DISK_SPINS = [-0.99, -0.5, 0.0, 0.5, 0.99]
 HEADLINE_FREQS = [230e9]
 
 
