@@ -312,6 +312,57 @@ def _lightcurve_extra(R, torch, args, stream, params, n=100, size=256):
     return out
 
 
+def _disk_extra(R, torch, stream, fma64, reps=2):
+    """Thin-disk line emitter (sec. 4.2.1): the paper's five spins at 1024^2, i = 30 deg,
+    FP64 rays with Newton-refined equatorial crossings and the first-order line spectrum.
+    Roofline: the geodesic step's algorithmic flops (step size + RK4; counted from the
+    source) x steps / kernel time against the FP64 FMA-chain peak."""
+    from paper_1801_10452_b300 import flopcount, scenes
+
+    geo = flopcount.flops_per_step(1, "analytic")["geodesic_only"]
+    cam0 = scenes.THIN_DISK
+    out = {"workload": f"thin_disk_{cam0['nx']}x{cam0['ny']}_i{cam0['incl_deg']:g}_rin_isco_rout15_q2",
+           "spins": scenes.THIN_DISK_SPINS, "per_spin": {}}
+    tot_ms = tot_rays = 0.0
+    for a in scenes.THIN_DISK_SPINS:
+        ctx = R.Context(R.camera_desc(**dict(cam0, spin=a)))
+        res = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream)
+        torch.cuda.synchronize()
+        ctx.stats_reset()
+        ctx.profile(True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            res = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream)
+        t1.record(stream)
+        t1.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        st = ctx.stats()
+        order = res["order"].cpu().numpy()
+        spec = res["spectrum"]
+        edges = res["edges"]
+        centres = 0.5 * (edges[1:] + edges[:-1])
+        rays = cam0["nx"] * cam0["ny"]
+        steps = st["steps"] / reps
+        k_ms = prof["disk"][0] / reps
+        ach = geo * steps / (k_ms * 1e-3) / 1e12
+        out["per_spin"][f"{a:g}"] = {
+            "ms": ms, "rays_per_s": rays / (ms * 1e-3), "steps_per_ray": steps / rays,
+            "hit_fraction_first_order": float((order == 1).mean()), "hit_fraction_any": float((order > 0).mean()),
+            "line_peak_E_ratio": float(centres[int(np.argmax(spec))]),
+            "line_mean_E_ratio": float((spec * centres).sum() / spec.sum()),
+            "roofline": {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": fma64, "unit": "TFLOP/s",
+                         "frac": ach / fma64, "flops_per_step": geo}}
+        tot_ms += ms
+        tot_rays += rays
+        ctx.close()
+    out["rays_per_s_all_spins"] = tot_rays / (tot_ms * 1e-3)
+    return out
+
+
 def scenes_mod():
     from paper_1801_10452_b300 import scenes
 
@@ -385,6 +436,10 @@ def run_native(args):
     lcurve = None
     if not args.no_lightcurve:
         lcurve = _lightcurve_extra(R, torch, args, stream, params)
+    # ---- the thin-disk line emitter (sec. 4.2.1), five spins ----
+    disk = None
+    if not args.no_disk and rank == 0:
+        disk = _disk_extra(R, torch, stream, R.measure_fma_peak(True))
     main = res[paths[0]]
     ms_step = main["ms"]
     value = aggregate_rate(world, rays_step, ms_step)
@@ -505,6 +560,7 @@ def run_native(args):
         "surrogate": sur,
         "grid_workload": grid,
         "lightcurve_workload": lcurve,
+        "thin_disk_workload": disk,
     }
     for pth, r in res.items():
         if pth == paths[0]:
@@ -556,6 +612,7 @@ def main():
                     help="comma list of paths to time (first = value): mlp, mixed, fp64, mlp_df, mixed_df")
     ap.add_argument("--no-grid", action="store_true", help="skip the grid (torus snapshot) workload")
     ap.add_argument("--no-lightcurve", action="store_true", help="skip the slow-light light-curve workload")
+    ap.add_argument("--no-disk", action="store_true", help="skip the thin-disk line-emitter workload")
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-rays", type=int, default=1_000_000)
     args = ap.parse_args()
