@@ -28,6 +28,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 KIND_ANALYTIC, KIND_GRID, KIND_STATIC_ISO, KIND_BALL = 0, 1, 2, 3
 ESCAPED, CAPTURED, THICK, TRUNCATED, ERROR = 0, 1, 2, 3, 4
 DISK_HIT, DISK_NO_HIT = 5, 6
+RK4, VERLET, VERLET_REEVAL = 0, 1, 2
 
 
 class OraScene(C.Structure):
@@ -46,6 +47,7 @@ class OraScene(C.Structure):
         ("x1_min", C.c_double), ("x1_max", C.c_double), ("h_mks", C.c_double),
         ("t0", C.c_double), ("dt_snap", C.c_double),
         ("mass_unit_g", C.c_double), ("r_high", C.c_double), ("r_low", C.c_double), ("gamma_ad", C.c_double),
+        ("integrator", C.c_int),
     ]
 
 
@@ -75,6 +77,7 @@ def lib():
             "ora_connection": (None, [sp, D, D, dp]),
             "ora_step_size": (D, [sp, dp, dp]),
             "ora_rk4_step": (None, [sp, dp, dp, D]),
+            "ora_verlet_step": (None, [sp, dp, dp, dp, D, I]),
             "ora_horizon": (D, [sp]),
             "ora_vec_bl_to_ks": (None, [sp, D, dp, dp]),
             "ora_pos_bl_to_ks": (None, [sp, dp, dp]),
@@ -121,7 +124,7 @@ def scene(**kw) -> OraScene:
              n0=1.0e6, n_pow=-1.5, the0=10.0, the_pow=-1.0, B0=20.0, B_pow=-1.0,
              ball_R=0.0, ball_j=0.0, ball_alpha=0.0, grid=None, n1=0, n2=0, n_snap=0, snap=0,
              x1_min=0.0, x1_max=0.0, h_mks=1.0, t0=0.0, dt_snap=1.0,
-             mass_unit_g=0.0, r_high=1.0, r_low=1.0, gamma_ad=4.0 / 3.0)
+             mass_unit_g=0.0, r_high=1.0, r_low=1.0, gamma_ad=4.0 / 3.0, integrator=RK4)
     d.update(kw)
     keep = d.pop("_grid_ref", None)
     for k, v in d.items():
@@ -180,6 +183,13 @@ def rk4_step(s, x, k, dl):
     x = np.array(x, float); k = np.array(k, float)
     lib().ora_rk4_step(C.byref(s), _dp(x), _dp(k), dl)
     return x, k
+
+
+def verlet_step(s, x, k, f, dl, reeval=False):
+    """One velocity-Verlet step (sec. 2.2.2); f is the carried derivative.  Returns (x, k, f)."""
+    x = np.array(x, float); k = np.array(k, float); f = np.array(f, float)
+    lib().ora_verlet_step(C.byref(s), _dp(x), _dp(k), _dp(f), dl, int(reeval))
+    return x, k, f
 
 
 def horizon(s):

@@ -10,7 +10,8 @@
 //   * metric g_{mu nu} of Kerr in Kerr-Schild (KS) or Boyer-Lindquist (BL) coordinates,
 //     its analytic first derivatives, a numerically inverted g^{mu nu};
 //   * the connection from the metric, Eq. 2 (sec. 2.1), generic 4x4x4 contraction;
-//   * the first-order geodesic system, Eqs. 5-6, integrated by classical RK4, Eqs. 7-15;
+//   * the first-order geodesic system, Eqs. 5-6, integrated by classical RK4, Eqs. 7-15, or
+//     by the velocity Verlet scheme of sec. 2.2.2 (Eqs. 16-19, optionally re-evaluated);
 //   * the adaptive step of Eqs. 20-23 read in log-radius coordinates;
 //   * the Bardeen camera, Eqs. 24-28 (sec. 2.3), plus k^r from the null condition Eq. 4;
 //   * the BL -> KS transforms of App. A.1;
@@ -77,6 +78,7 @@ typedef struct {
     double x1_min, x1_max, h_mks;
     double t0, dt_snap;
     double mass_unit_g, r_high, r_low, gamma_ad;
+    int integrator;      // 0 = RK4 (Eqs. 7-15), 1 = velocity Verlet (Eqs. 16-19), 2 = Verlet with re-evaluation
 } OraScene;
 
 }  // extern "C"
@@ -229,6 +231,49 @@ static void rk4_step(const OraScene* s, double x[4], double k[4], double dl) {
     }
 }
 
+// Sec. 2.2.2, velocity Verlet (Eqs. 16-19).  f holds (dk/dl)_n on entry and the derivative
+// at the new point on return, so each step evaluates the connection once (twice with the
+// re-evaluation):
+//   x_{n+1} = x_n + k_n dl + f_n dl^2 / 2                          (Eq. 16)
+//   k_p = k_n + f_n dl                                             (Eq. 17)
+//   f_{n+1} = -Gamma(x_{n+1}) k_p k_p                              (Eq. 18)
+//   k_{n+1} = k_n + (f_n + f_{n+1}) dl / 2                         (Eq. 19)
+// Re-evaluation (reeval): Eq. 18 again with k_p = k_{n+1} from Eq. 19, then Eq. 19 again;
+// the derivative carried to the next step is the last one evaluated (reading: the paper
+// does not say which derivative the next step starts from; the last is the only one at the
+// new point that needs no further evaluation).
+static void verlet_step(const OraScene* s, double x[4], double k[4], double f[4], double dl, int reeval) {
+    double xn[4], kp[4], kn[4], fn[4], dx[4];
+    for (int i = 0; i < 4; ++i) {
+        xn[i] = x[i] + k[i] * dl + 0.5 * f[i] * dl * dl;
+        kp[i] = k[i] + f[i] * dl;
+    }
+    rhs(s, xn, kp, dx, fn);
+    for (int i = 0; i < 4; ++i) kn[i] = k[i] + 0.5 * (f[i] + fn[i]) * dl;
+    if (reeval) {
+        rhs(s, xn, kn, dx, fn);
+        for (int i = 0; i < 4; ++i) kn[i] = k[i] + 0.5 * (f[i] + fn[i]) * dl;
+    }
+    for (int i = 0; i < 4; ++i) { x[i] = xn[i]; k[i] = kn[i]; f[i] = fn[i]; }
+}
+
+// One step of the scene's integrator; f is the carried derivative of the Verlet schemes
+// (unused by RK4).
+static void advance(const OraScene* s, double x[4], double k[4], double f[4], double dl) {
+    if (s->integrator == 0) rk4_step(s, x, k, dl);
+    else verlet_step(s, x, k, f, dl, s->integrator == 2);
+}
+
+// The carried derivative at the start of a ray: (dk/dl)_0 = -Gamma(x_0) k_0 k_0.
+static void start_derivative(const OraScene* s, const double x[4], const double k[4], double f[4]) {
+    double dx[4];
+    if (s->integrator == 0) {
+        for (int i = 0; i < 4; ++i) f[i] = 0.0;
+        return;
+    }
+    rhs(s, x, k, dx, f);
+}
+
 // Eqs. 20-23 evaluated in coordinates x1 = ln r, x2 = theta/pi, x3 = phi, i.e.
 //   dl1 = eps / (|k^r|/r + delta), dl2 = eps min(x2, 1-x2) / (|k^theta|/pi + delta),
 //   dl3 = eps / (|k^phi| + delta),  dl = 1 / (1/dl1 + 1/dl2 + 1/dl3).
@@ -309,6 +354,10 @@ void ora_connection(const OraScene* s, double r, double th, double* G64) {
 double ora_step_size(const OraScene* s, const double* x, const double* k) { return step_size(s, x, k); }
 
 void ora_rk4_step(const OraScene* s, double* x, double* k, double dl) { rk4_step(s, x, k, dl); }
+
+void ora_verlet_step(const OraScene* s, double* x, double* k, double* f, double dl, int reeval) {
+    verlet_step(s, x, k, f, dl, reeval);
+}
 
 double ora_horizon(const OraScene* s) { return horizon(s); }
 
@@ -699,14 +748,15 @@ static int rt_sample(const OraScene* s, const double x[4], const double k[4], do
 // g = 0 on the terminating step, which takes no transfer sample.
 int ora_trace_ray(const OraScene* s, double alpha, double beta, double t_cam, const double* nus, int nf,
                   double* I, double* tau, int* steps, double* trace, int max_trace) {
-    double x[4], k[4];
+    double x[4], k[4], fd[4];
     ora_camera(s, alpha, beta, t_cam, x, k);
+    start_derivative(s, x, k, fd);
     for (int f = 0; f < nf; ++f) { I[f] = 0.0; tau[f] = 0.0; }
     const double r_stop = s->r_stop_factor * horizon(s);
     int n = 0, status = 3;
     while (n < s->max_steps) {
         const double dl = step_size(s, x, k);
-        rk4_step(s, x, k, dl);
+        advance(s, x, k, fd, dl);
         ++n;
         bool finite = true;
         for (int i = 0; i < 4; ++i) finite = finite && std::isfinite(x[i]) && std::isfinite(k[i]);
@@ -736,17 +786,19 @@ int ora_trace_ray(const OraScene* s, double alpha, double beta, double t_cam, co
 // status (0 escaped, 1 captured, 3 truncated, 4 error) and the final state.
 int ora_geodesic(const OraScene* s, double alpha, double beta, int max_steps, double* x, double* k, int* steps) {
     ora_camera(s, alpha, beta, 0.0, x, k);
+    double fd[4];
+    start_derivative(s, x, k, fd);
     const double r_stop = s->r_stop_factor * horizon(s);
     int n = 0, status = 3;
     while (n < max_steps) {
         const double dl = step_size(s, x, k);
-        double xn[4], kn[4];
-        for (int i = 0; i < 4; ++i) { xn[i] = x[i]; kn[i] = k[i]; }
-        rk4_step(s, xn, kn, dl);
+        double xn[4], kn[4], fn[4];
+        for (int i = 0; i < 4; ++i) { xn[i] = x[i]; kn[i] = k[i]; fn[i] = fd[i]; }
+        advance(s, xn, kn, fn, dl);
         bool finite = true;
         for (int i = 0; i < 4; ++i) finite = finite && std::isfinite(xn[i]) && std::isfinite(kn[i]);
         if (!finite) { status = 4; break; }
-        for (int i = 0; i < 4; ++i) { x[i] = xn[i]; k[i] = kn[i]; }
+        for (int i = 0; i < 4; ++i) { x[i] = xn[i]; k[i] = kn[i]; fd[i] = fn[i]; }
         ++n;
         if (x[1] < r_stop) { status = 1; break; }
         if (x[1] > s->r_esc) { status = 0; break; }
