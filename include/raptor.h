@@ -76,6 +76,11 @@ typedef enum {
 #define RAPTOR_FLAG_INNER_DF64 0x4u    /* MIXED/MIXED_MLP: inner-region geodesic steps in double-
                                           float arithmetic on the FP32 pipe (48-bit significand,
                                           ~1e-14 relative) instead of native FP64              */
+#define RAPTOR_FLAG_VERLET 0x8u        /* RAPTOR_FP64: velocity Verlet (sec. 2.2.2, Eqs. 16-19,
+                                          one connection evaluation per step) instead of RK4  */
+#define RAPTOR_FLAG_VERLET_REEVAL 0x10u /* RAPTOR_FP64: velocity Verlet with the re-evaluation
+                                          of Eqs. 18-19 (two evaluations per step); the
+                                          derivative carried on is the last one evaluated    */
 
 /* Ray termination codes written to status_dev (render_ex) and trace calls. */
 #define RAPTOR_RAY_ESCAPED 0   /* r > r_escape                       */

@@ -205,7 +205,11 @@ std::string validate_camera(const raptor_camera_desc* d) {
     if (!(d->tau_cut > 0.0)) return "tau_cut must be > 0 (may be +inf)";
     if (d->max_steps < 1) return "max_steps must be >= 1";
     if (d->precision < RAPTOR_FP64 || d->precision > RAPTOR_MIXED_MLP) return "unknown precision";
-    if (d->flags & ~(RAPTOR_FLAG_K2_EXACT | RAPTOR_FLAG_STEP_LINEAR_R | RAPTOR_FLAG_INNER_DF64)) return "unknown flag bits";
+    if (d->flags & ~(RAPTOR_FLAG_K2_EXACT | RAPTOR_FLAG_STEP_LINEAR_R | RAPTOR_FLAG_INNER_DF64 | RAPTOR_FLAG_VERLET |
+                     RAPTOR_FLAG_VERLET_REEVAL))
+        return "unknown flag bits";
+    if ((d->flags & (RAPTOR_FLAG_VERLET | RAPTOR_FLAG_VERLET_REEVAL)) && d->precision != RAPTOR_FP64)
+        return "the Verlet integrator is built for RAPTOR_FP64 only";
     if (!(d->r_fp64 >= 0.0) || !std::isfinite(d->r_fp64)) return "r_fp64 must be finite and >= 0";
     if (!(d->turn_kr >= 0.0) || !std::isfinite(d->turn_kr)) return "turn_kr must be finite and >= 0";
     if (!std::isfinite(d->t_delay)) return "t_delay must be finite";
@@ -339,12 +343,15 @@ int grid_blocks(const raptor_ctx* c, int per_sm_occ) {
 template <int NF>
 cudaError_t launch_fp64_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fp64<NF>, c->launch_block, 0);
+    const bool verlet = (p.flags & (kFlagVerlet | kFlagVerletReeval)) != 0;
+    cudaError_t e = verlet ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fp64<NF, true>, c->launch_block, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fp64<NF, false>, c->launch_block, 0);
     if (e != cudaSuccess) return e;
     const long long need = (p.n_rays + c->launch_block - 1) / c->launch_block;
-    const long long blocks = std::min<long long>(grid_blocks(c, std::max(occ, 1)), need);
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(grid_blocks(c, std::max(occ, 1)), need));
     ProfScope ps(c, kProfRenderFp64, s);
-    k_render_fp64<NF><<<(int)std::max<long long>(blocks, 1), c->launch_block, 0, s>>>(p, c->d_counters, c->d_stats);
+    if (verlet) k_render_fp64<NF, true><<<blocks, c->launch_block, 0, s>>>(p, c->d_counters, c->d_stats);
+    else k_render_fp64<NF, false><<<blocks, c->launch_block, 0, s>>>(p, c->d_counters, c->d_stats);
     return cudaGetLastError();
 }
 
@@ -905,6 +912,8 @@ raptor_status raptor_disk_render(raptor_ctx* ctx, const raptor_disk_desc* d, dou
     ctx->err.clear();
     if (!d) return fail(ctx, RAPTOR_EINVAL, "disk descriptor is NULL");
     if (!ratio_dev || !intensity_dev || !order_dev) return fail(ctx, RAPTOR_EINVAL, "ratio, intensity and order buffers are required");
+    if (ctx->cam.flags & (RAPTOR_FLAG_VERLET | RAPTOR_FLAG_VERLET_REEVAL))
+        return fail(ctx, RAPTOR_EUNSUPPORTED, "the thin disk is integrated with RK4 only");
     const double r_in = d->r_in > 0.0 ? d->r_in : r_isco_prograde(ctx->cam.spin);
     if (!std::isfinite(d->r_in) || !(d->r_out > r_in) || !std::isfinite(d->r_out))
         return fail(ctx, RAPTOR_EINVAL, "need finite 0 < r_in < r_out (r_in <= 0: the ISCO)");
@@ -1048,10 +1057,16 @@ raptor_status raptor_trace_ray(raptor_ctx* ctx, double alpha, double beta, doubl
     p.snap = 0;
     const double tc = t_obs + ctx->cam.t_delay;
     ProfScope ps(ctx, kProfTrace, s);
-    if (n_freq <= 1)
-        k_trace_fp64<1><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ctx->d_trace_int, ctx->d_trace_int + 1, ctx->d_trace_I);
+    const bool verlet = (p.flags & (kFlagVerlet | kFlagVerletReeval)) != 0;
+    int* ti = ctx->d_trace_int;
+    if (n_freq <= 1 && !verlet)
+        k_trace_fp64<1, false><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ti, ti + 1, ctx->d_trace_I);
+    else if (n_freq <= 1)
+        k_trace_fp64<1, true><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ti, ti + 1, ctx->d_trace_I);
+    else if (!verlet)
+        k_trace_fp64<16, false><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ti, ti + 1, ctx->d_trace_I);
     else
-        k_trace_fp64<16><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ctx->d_trace_int, ctx->d_trace_int + 1, ctx->d_trace_I);
+        k_trace_fp64<16, true><<<1, 32, 0, s>>>(p, alpha, beta, tc, max_rec, ctx->d_rec, ti, ti + 1, ctx->d_trace_I);
     RCK(cudaGetLastError());
     int hi[2] = {0, 0};
     RCK(cudaMemcpyAsync(hi, ctx->d_trace_int, sizeof(hi), cudaMemcpyDeviceToHost, s));

@@ -10,6 +10,8 @@ namespace raptor {
 constexpr unsigned kFlagK2Exact = 0x1u;
 constexpr unsigned kFlagLinearR = 0x2u;
 constexpr unsigned kFlagInnerDf64 = 0x4u;
+constexpr unsigned kFlagVerlet = 0x8u;         // velocity Verlet (sec. 2.2.2) instead of RK4
+constexpr unsigned kFlagVerletReeval = 0x10u;  // ... with the re-evaluation of Eqs. 18-19
 
 enum : int { kEscaped = 0, kCaptured = 1, kThick = 2, kTruncated = 3, kError = 4, kDiskHit = 5, kDiskNone = 6 };
 
@@ -25,17 +27,20 @@ enum : int { kStatRays = 0, kStatSteps = 1, kStatFp64Steps = 2, kStatTrunc = 3, 
 template <int NF>
 struct RayD {
     double x[4], k[4];
+    double f[4];  // carried derivative of the Verlet integrator (unused by RK4)
     double I[NF], tau[NF];
     int n;
     int snap;
 };
 
-// One FP64 step of a ray: adaptive step, RK4, termination, transfer sample.  Returns the
-// termination code or -1 to continue.  dl_out / g_out feed the trace recorder.
-template <int NF>
+// One FP64 step of a ray: adaptive step, RK4 (VERLET = false) or velocity Verlet,
+// termination, transfer sample.  Returns the termination code or -1 to continue.
+// dl_out / g_out feed the trace recorder.
+template <int NF, bool VERLET = false>
 __device__ __forceinline__ int step_fp64(const Params& p, RayD<NF>& R, double& dl_out, double& g_out) {
     const double dl = step_size<double>(p.eps, (p.flags & kFlagLinearR) != 0, R.x, R.k);
-    rk4_step<double>(p.a, R.x, R.k, dl);
+    if constexpr (VERLET) verlet_step<double>(p.a, R.x, R.k, R.f, dl, (p.flags & kFlagVerletReeval) != 0);
+    else rk4_step<double>(p.a, R.x, R.k, dl);
     R.n += 1;
     dl_out = dl;
     g_out = 0.0;
@@ -70,8 +75,8 @@ __device__ __forceinline__ int step_fp64(const Params& p, RayD<NF>& R, double& d
     return -1;
 }
 
-// Ray id -> (frame, pixel, row, col); initial state.
-template <int NF>
+// Ray id -> (frame, pixel, row, col); initial state (and, for Verlet, the derivative there).
+template <int NF, bool VERLET = false>
 __device__ __forceinline__ void init_ray(const Params& p, long long id, RayD<NF>& R, int& frame, int& pix) {
     frame = (int)(id / p.n_pix);
     pix = (int)(id - (long long)frame * p.n_pix);
@@ -80,6 +85,7 @@ __device__ __forceinline__ void init_ray(const Params& p, long long id, RayD<NF>
     const double beta = p.bmin + (row + 0.5) * p.db;
     const double tc = p.t_frames ? p.t_frames[frame] : p.t_cam;
     camera_ray(p, alpha, beta, tc, R.x, R.k);
+    if constexpr (VERLET) geodesic_force<double>(p.a, R.x[1], R.x[2], R.k, R.f);
 #pragma unroll
     for (int f = 0; f < NF; ++f) { R.I[f] = 0.0; R.tau[f] = 0.0; }
     R.n = 0;
@@ -137,8 +143,8 @@ __device__ __forceinline__ long long warp_fetch(unsigned long long* counter, lon
 
 // Persistent FP64 kernel: each warp keeps 32 rays in flight and refills a lane from the
 // global work counter as soon as its ray terminates (per-warp compaction of uneven ray
-// lengths).  Blocks must be a multiple of 32 threads.
-template <int NF>
+// lengths).  Blocks must be a multiple of 32 threads.  VERLET: the velocity-Verlet integrator.
+template <int NF, bool VERLET = false>
 __global__ void __launch_bounds__(128) k_render_fp64(const Params p, unsigned long long* counter, unsigned long long* stats) {
     RayD<NF> R;
     long long id = -1;
@@ -149,12 +155,12 @@ __global__ void __launch_bounds__(128) k_render_fp64(const Params p, unsigned lo
         const long long nid = warp_fetch(counter, p.n_rays, id < 0, drained);
         if (id < 0 && nid >= 0) {
             id = nid;
-            init_ray<NF>(p, id, R, frame, pix);
+            init_ray<NF, VERLET>(p, id, R, frame, pix);
         }
         if (!__any_sync(0xffffffffu, id >= 0)) break;
         if (id >= 0) {
             double dl, g;
-            const int st = step_fp64<NF>(p, R, dl, g);
+            const int st = step_fp64<NF, VERLET>(p, R, dl, g);
             if (st >= 0) {
                 write_ray<NF>(p, frame, pix, R.I, R.n, st);
                 c_rays += 1;
@@ -303,12 +309,13 @@ __global__ void __launch_bounds__(256) k_disk_profile(const double* __restrict__
 }
 
 // Single-ray trace with per-step records (same arithmetic as k_render_fp64).
-template <int NF>
+template <int NF, bool VERLET = false>
 __global__ void k_trace_fp64(const Params p, double alpha, double beta, double t_cam, int max_rec, double* rec, int* out_n,
                              int* out_status, double* out_I) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     RayD<NF> R;
     camera_ray(p, alpha, beta, t_cam, R.x, R.k);
+    if constexpr (VERLET) geodesic_force<double>(p.a, R.x[1], R.x[2], R.k, R.f);
 #pragma unroll
     for (int f = 0; f < NF; ++f) { R.I[f] = 0.0; R.tau[f] = 0.0; }
     R.n = 0;
@@ -316,7 +323,7 @@ __global__ void k_trace_fp64(const Params p, double alpha, double beta, double t
     int st = -1;
     while (st < 0) {
         double dl, g;
-        st = step_fp64<NF>(p, R, dl, g);
+        st = step_fp64<NF, VERLET>(p, R, dl, g);
         if (R.n <= max_rec) {
             double* T = rec + (long long)(R.n - 1) * 12;
             for (int i = 0; i < 4; ++i) { T[i] = R.x[i]; T[4 + i] = R.k[i]; }
