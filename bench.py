@@ -363,6 +363,54 @@ def _disk_extra(R, torch, stream, fma64, reps=2):
     return out
 
 
+def _verlet_extra(R, torch, stream, fma64, flush, reps=2):
+    """The FP64 path with the velocity-Verlet integrator (sec. 2.2.2) on the headline image,
+    with and without the re-evaluation, beside RK4: time per render, rays/s, steps/s, flux
+    against RK4, and the FP64 roofline (algorithmic flops per Verlet step, counted from the
+    source, x steps / kernel time against the FP64 FMA-chain peak)."""
+    from paper_1801_10452_b300 import flopcount, scenes
+
+    fl = flopcount.flops_per_step(1, "analytic")
+    cam = scenes.HEADLINE
+    freqs = scenes.HEADLINE_FREQS
+    out = {"workload": "kerr_analytic_1024x1024_a0.9375_i60_230GHz_fp64", "per_integrator": {}}
+    flux_rk4 = None
+    for name, flags, fps in (("rk4", 0, fl["fp64_step"]), ("verlet", R.FLAG_VERLET, fl["verlet_step"]),
+                             ("verlet_reeval", R.FLAG_VERLET_REEVAL, fl["verlet_reeval_step"])):
+        ctx = R.Context(R.camera_desc(**cam, flags=flags))
+        ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+        img = torch.empty((1, cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
+        _, flux = ctx.render(freqs, image=img, stream=stream)
+        ctx.stats_reset()
+        ctx.profile(True)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.render(freqs, image=img, flux=False, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        st = ctx.stats()
+        t = float(np.mean(ms))
+        steps = st["steps"] / reps
+        k_ms = prof["render_fp64"][0] / reps
+        ach = fps * steps / (k_ms * 1e-3) / 1e12
+        if flux_rk4 is None:
+            flux_rk4 = flux[0]
+        out["per_integrator"][name] = {
+            "ms": t, "rays_per_s": cam["nx"] * cam["ny"] / (t * 1e-3), "geodesic_steps_per_s": steps / (t * 1e-3),
+            "steps_per_ray": steps / (cam["nx"] * cam["ny"]), "flux_rel_vs_rk4": float(flux[0] / flux_rk4 - 1),
+            "roofline": {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": fma64, "unit": "TFLOP/s",
+                         "frac": ach / fma64, "flops_per_step": fps}}
+        ctx.close()
+    return out
+
+
 def scenes_mod():
     from paper_1801_10452_b300 import scenes
 
@@ -436,6 +484,10 @@ def run_native(args):
     lcurve = None
     if not args.no_lightcurve:
         lcurve = _lightcurve_extra(R, torch, args, stream, params)
+    # ---- the FP64 path with the velocity-Verlet integrator (sec. 2.2.2) ----
+    verlet = None
+    if not args.no_verlet and rank == 0:
+        verlet = _verlet_extra(R, torch, stream, R.measure_fma_peak(True), flush)
     # ---- the thin-disk line emitter (sec. 4.2.1), five spins ----
     disk = None
     if not args.no_disk and rank == 0:
@@ -561,6 +613,7 @@ def run_native(args):
         "grid_workload": grid,
         "lightcurve_workload": lcurve,
         "thin_disk_workload": disk,
+        "verlet_workload": verlet,
     }
     for pth, r in res.items():
         if pth == paths[0]:
@@ -613,6 +666,7 @@ def main():
     ap.add_argument("--no-grid", action="store_true", help="skip the grid (torus snapshot) workload")
     ap.add_argument("--no-lightcurve", action="store_true", help="skip the slow-light light-curve workload")
     ap.add_argument("--no-disk", action="store_true", help="skip the thin-disk line-emitter workload")
+    ap.add_argument("--no-verlet", action="store_true", help="skip the FP64 velocity-Verlet workload")
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-rays", type=int, default=1_000_000)
     args = ap.parse_args()

@@ -110,6 +110,20 @@ int main() {
     Cnt f[4];
     geodesic_force<Cnt>(Cnt(p.a), x[1], x[2], k, f);
     print_ops("geodesic_rhs", g_ops, false);
+    // velocity Verlet (sec. 2.2.2): step size + one step, without and with the re-evaluation
+    {
+        Cnt xv[4], kv[4], fv[4];
+        for (int i = 0; i < 4; ++i) { xv[i] = x[i]; kv[i] = k[i]; fv[i] = f[i]; }
+        g_ops = Ops();
+        Cnt dv = step_size<Cnt>(Cnt(p.eps), false, xv, kv);
+        verlet_step<Cnt>(Cnt(p.a), xv, kv, fv, dv, false);
+        print_ops("verlet_step", g_ops, false);
+        for (int i = 0; i < 4; ++i) { xv[i] = x[i]; kv[i] = k[i]; fv[i] = f[i]; }
+        g_ops = Ops();
+        dv = step_size<Cnt>(Cnt(p.eps), false, xv, kv);
+        verlet_step<Cnt>(Cnt(p.a), xv, kv, fv, dv, true);
+        print_ops("verlet_reeval_step", g_ops, false);
+    }
     // analytic plasma sample (Keplerian branch) and the free-fall branch
     Cnt ne, the, B, g, sinb;
     g_ops = Ops();

@@ -48,7 +48,9 @@ def flops_per_step(n_freq: int = 1, plasma: str = "analytic") -> dict:
     sample = c["sample_analytic"]["flops"] if plasma == "analytic" else c["sample_grid_" + plasma]["flops"]
     total = c["geodesic_step"]["flops"] + sample + n_freq * c["per_frequency"]["flops"]
     return {"fp64_step": total, "fp32_step": total, "geodesic_only": c["geodesic_step"]["flops"],
-            "sample": sample, "per_frequency": c["per_frequency"]["flops"]}
+            "sample": sample, "per_frequency": c["per_frequency"]["flops"],
+            "verlet_step": c["verlet_step"]["flops"] + sample + n_freq * c["per_frequency"]["flops"],
+            "verlet_reeval_step": c["verlet_reeval_step"]["flops"] + sample + n_freq * c["per_frequency"]["flops"]}
 
 
 # FP32 instructions of one double-float operation, counted from raptor_df64.cuh: add
