@@ -411,6 +411,37 @@ def _verlet_extra(R, torch, stream, fma64, flush, reps=2):
     return out
 
 
+def _emissivity_extra(R, torch, stream, size=256):
+    """Emissivity options on the spectral scene (a = 0.9375, i = 60 deg, eight frequencies
+    1e10-1e13 Hz) through the FP64 path: the flux change from the exact K2 (sec. 4.2.2 expects
+    a few per cent at most) and from the Theta_e fit-validity mask at 0.5 (the fit's stated
+    limit) and 2, per frequency, with the render times."""
+    from paper_1801_10452_b300 import scenes
+
+    cam = dict(scenes.SPECTRAL, spin=0.9375, nx=size, ny=size)
+    freqs = scenes.SPECTRAL_FREQS
+    out = {"workload": f"kerr_analytic_{size}x{size}_a0.9375_i60_8freq_fp64", "freqs_hz": freqs}
+    base = None
+    for name, flags, mask in (("k2_fit", 0, 0.0), ("k2_exact", R.FLAG_K2_EXACT, 0.0), ("mask_0.5", 0, 0.5),
+                              ("mask_2", 0, 2.0)):
+        ctx = R.Context(R.camera_desc(**cam, flags=flags))
+        ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA, theta_e_min=mask))
+        img = torch.empty((len(freqs), size, size), dtype=torch.float64, device="cuda")
+        ctx.render(freqs, image=img, stream=stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, fl = ctx.render(freqs, image=img, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        if base is None:
+            base = fl
+        out[name] = {"ms": a.elapsed_time(b), "flux_jy": [float(v) for v in fl],
+                     "flux_rel_vs_fit": [float(v / w - 1) if w > 0 else 0.0 for v, w in zip(fl, base)]}
+        ctx.close()
+    return out
+
+
 def scenes_mod():
     from paper_1801_10452_b300 import scenes
 
@@ -488,6 +519,10 @@ def run_native(args):
     verlet = None
     if not args.no_verlet and rank == 0:
         verlet = _verlet_extra(R, torch, stream, R.measure_fma_peak(True), flush)
+    # ---- emissivity options: exact K2 and the Theta_e validity mask ----
+    emis = None
+    if not args.no_emissivity and rank == 0:
+        emis = _emissivity_extra(R, torch, stream)
     # ---- the thin-disk line emitter (sec. 4.2.1), five spins ----
     disk = None
     if not args.no_disk and rank == 0:
@@ -614,6 +649,7 @@ def run_native(args):
         "lightcurve_workload": lcurve,
         "thin_disk_workload": disk,
         "verlet_workload": verlet,
+        "emissivity_options": emis,
     }
     for pth, r in res.items():
         if pth == paths[0]:
@@ -667,6 +703,7 @@ def main():
     ap.add_argument("--no-lightcurve", action="store_true", help="skip the slow-light light-curve workload")
     ap.add_argument("--no-disk", action="store_true", help="skip the thin-disk line-emitter workload")
     ap.add_argument("--no-verlet", action="store_true", help="skip the FP64 velocity-Verlet workload")
+    ap.add_argument("--no-emissivity", action="store_true", help="skip the exact-K2 / Theta_e-mask comparison")
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-rays", type=int, default=1_000_000)
     args = ap.parse_args()

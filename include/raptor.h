@@ -132,6 +132,9 @@ typedef struct {
     double mass_unit_g;   /* GRID: mass unit (Eq. 45), grams                             */
     double r_high, r_low; /* GRID: R-beta parameters (Eq. 46)                             */
     double gamma_ad;      /* GRID: adiabatic index                                 [4/3]  */
+    double theta_e_min;   /* emission (and absorption) only where Theta_e >= theta_e_min: the
+                             validity mask of the emissivity fit (the paper quotes < 1 %
+                             error for Theta_e > 0.5, sec. 4.2.2); 0 = no mask          [0]    */
 } raptor_plasma_desc;
 
 /* Fill descriptors with the defaults shown in brackets above. */

@@ -79,6 +79,7 @@ typedef struct {
     double t0, dt_snap;
     double mass_unit_g, r_high, r_low, gamma_ad;
     int integrator;      // 0 = RK4 (Eqs. 7-15), 1 = velocity Verlet (Eqs. 16-19), 2 = Verlet with re-evaluation
+    double theta_e_min;  // no emission (nor absorption) where Theta_e < theta_e_min; 0 = no mask
 } OraScene;
 
 }  // extern "C"
@@ -734,6 +735,9 @@ static int rt_sample(const OraScene* s, const double x[4], const double k[4], do
             ora_rt_update(&I[f], &tau[f], P.jfix, S, gr, dl * L);
             continue;
         }
+        // sec. 4.2.2: the fit holds for Theta_e above ~0.5; below theta_e_min the sample
+        // emits and absorbs nothing (validity mask, off by default)
+        if (P.thetae < s->theta_e_min) continue;
         ora_emissivity(nuf, P.ne, P.thetae, P.B, sinb, s->k2_exact, jS);
         ora_rt_update(&I[f], &tau[f], jS[0], jS[1], gr, dl * L);
     }

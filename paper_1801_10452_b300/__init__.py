@@ -69,7 +69,7 @@ class PlasmaDesc(C.Structure):
         ("fields", C.c_void_p), ("n1", C.c_int), ("n2", C.c_int), ("n_snap", C.c_int), ("fields_on_device", C.c_int),
         ("x1_min", C.c_double), ("x1_max", C.c_double), ("h_mks", C.c_double),
         ("t0", C.c_double), ("dt_snap", C.c_double), ("mass_unit_g", C.c_double),
-        ("r_high", C.c_double), ("r_low", C.c_double), ("gamma_ad", C.c_double),
+        ("r_high", C.c_double), ("r_low", C.c_double), ("gamma_ad", C.c_double), ("theta_e_min", C.c_double),
     ]
 
 

@@ -218,6 +218,7 @@ std::string validate_camera(const raptor_camera_desc* d) {
 
 std::string validate_plasma(const raptor_plasma_desc* d) {
     if (!d) return "plasma descriptor is NULL";
+    if (!(d->theta_e_min >= 0.0) || !std::isfinite(d->theta_e_min)) return "theta_e_min must be finite and >= 0";
     if (d->kind == RAPTOR_PLASMA_ANALYTIC) {
         const double v[6] = {d->n0, d->n_pow, d->the0, d->the_pow, d->B0_gauss, d->B_pow};
         for (double x : v)
@@ -252,7 +253,7 @@ void fill_float_params(Params& p) {
     f.a = (float)p.a; f.eps = (float)p.eps; f.r_stop = (float)p.r_stop; f.r_esc = (float)p.r_esc;
     f.Lcm = (float)p.Lcm; f.tau_cut = (float)p.tau_cut;
     f.n0 = (float)p.n0; f.n_pow = (float)p.n_pow; f.the0 = (float)p.the0; f.the_pow = (float)p.the_pow;
-    f.B0 = (float)p.B0; f.B_pow = (float)p.B_pow; f.r_isco = (float)p.r_isco;
+    f.B0 = (float)p.B0; f.B_pow = (float)p.B_pow; f.r_isco = (float)p.r_isco; f.the_min = (float)p.the_min;
     f.x1_min = (float)p.x1_min; f.x1_max = (float)p.x1_max; f.dx1 = (float)p.dx1; f.dx2 = (float)p.dx2;
     f.h_mks = (float)p.h_mks; f.t0 = (float)p.t0; f.dt_snap = (float)p.dt_snap; f.rho0_ne = (float)p.rho0_ne;
     f.B_unit = (float)p.B_unit; f.r_high = (float)p.r_high; f.r_low = (float)p.r_low; f.gam = (float)p.gam;
@@ -312,6 +313,7 @@ Params base_params(const raptor_ctx* c) {
     p.B0 = q.B0_gauss;
     p.B_pow = q.B_pow;
     p.r_isco = r_isco_prograde(d.spin);
+    p.the_min = q.theta_e_min;
     if (q.kind == RAPTOR_PLASMA_GRID_MKS2D) {
         p.grid = c->d_grid;
         p.n1 = q.n1;

@@ -61,7 +61,7 @@ __device__ __forceinline__ int step_fp64(const Params& p, RayD<NF>& R, double& d
         for (int f = 0; f < NF; ++f) {
             if (f < p.nf) {
                 double j, S;
-                synchrotron<double>(g * p.nu[f], ne, the, B, sinb, k2x, j, S);
+                synchrotron<double>(g * p.nu[f], ne, the, B, sinb, k2x, j, S, 1.0, p.the_min);
                 rt_update<double, double>(j, S, g, dlcm, R.I[f], R.tau[f]);
             }
         }

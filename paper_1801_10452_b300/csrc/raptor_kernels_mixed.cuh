@@ -189,7 +189,7 @@ __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4],
     for (int f = 0; f < NF; ++f) {
         if (f < p.nf) {
             float j, S;
-            synchrotron<float>(g * p.f.nu[f], ne, the, B, sinb, k2x, j, S, kIScale);
+            synchrotron<float>(g * p.f.nu[f], ne, the, B, sinb, k2x, j, S, kIScale, p.f.the_min);
             if (j > 0.f && S > 0.f) {
                 const float dtau = j * rcp_nr(S) * gdl_unscaled;
                 const float F = one_minus_exp_over_f(dtau);

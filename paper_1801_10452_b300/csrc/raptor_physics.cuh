@@ -9,7 +9,7 @@ namespace raptor {
 // paths run no double -> float conversion (B300 executes FP64 conversions slowly).
 struct ParamsF {
     float a, eps, r_stop, r_esc, Lcm, tau_cut;
-    float n0, n_pow, the0, the_pow, B0, B_pow, r_isco;
+    float n0, n_pow, the0, the_pow, B0, B_pow, r_isco, the_min;
     float x1_min, x1_max, dx1, dx2, h_mks, t0, dt_snap, rho0_ne, B_unit, r_high, r_low, gam;
     float r_fp64, turn_kr;
     float nu[16];
@@ -33,6 +33,7 @@ struct Params {
     // analytic plasma
     int kind, slow;
     double n0, n_pow, the0, the_pow, B0, B_pow, r_isco;
+    double the_min;  // emission only where Theta_e >= the_min (fit-validity mask; 0 = none)
     // grid plasma (MKS, r0 = 0)
     const float* grid;  // [n_snap][8][n2][n1]
     int n1, n2, n_snap, snap;
@@ -221,9 +222,11 @@ RAPTOR_HD double bessel_k2_exact(double x) {
 }
 
 // `jscale` multiplies j (the FP32 transfer carries emissivities scaled by 2^100 so that the
-// exponential tail of Eq. 41 stays inside FP32 range; the FP64 path passes 1).
+// exponential tail of Eq. 41 stays inside FP32 range; the FP64 path passes 1).  j = 0 where
+// Theta_e < the_min (the fit-validity mask; j = 0 also means no absorption there).
 template <typename T>
-RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, T& S, T jscale = T(1)) {
+RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, T& S, T jscale = T(1),
+                           T the_min = T(0)) {
     const T nu_c_per_G = T(kQe / (2.0 * kPi * kMe * kC));
     const T cj = T(1.4142135623730951 * kPi * kQe * kQe / (3.0 * kC)) * jscale;
     const T hme = T(kH / (kMe * kC * kC));
@@ -231,6 +234,7 @@ RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, 
     if constexpr (std::is_same<T, float>::value) S = T(2.0 * kMe) * nu * nu * the * x_over_expm1f(x);
     else S = T(2.0 * kMe) * nu * nu * the * dv(x, Real<T>::expm1_(x));
     j = T(0);
+    if (the < the_min) return;  // outside the fit's validity mask: no emission
     const T nu_s = T(2.0 / 9.0) * nu_c_per_G * B * the * the * sinb;
     if (!(nu_s > T(0))) return;
     const T X = dv(nu, nu_s);

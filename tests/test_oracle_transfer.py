@@ -187,3 +187,33 @@ def test_flux_converges_with_resolution(ora):
     d = np.abs(np.diff(fl))
     assert d[2] < d[1] < d[0]
     assert d[2] / fl[-1] < 0.02
+
+
+def test_theta_e_validity_mask(ora):
+    """Fit-validity mask (sec. 4.2.2: the fit holds for Theta_e > 0.5): along a traced ray the
+    masked run adds nothing (I and tau) at steps where Theta_e < theta_e_min, adds the
+    unmasked run's d tau exactly elsewhere, and its intensity increments are the unmasked ones
+    times exp(-(tau_masked - tau_unmasked)) before the step; a mask of 0 changes nothing and
+    an unreachable one empties the image."""
+    base = dict(a=0.9, incl_deg=60.0)
+    s0, s1 = ora.scene(**base), ora.scene(**base, theta_e_min=0.5)
+    for al, be in [(5.0, 3.0), (-9.0, 1.5), (2.0, -12.0)]:
+        t0 = ora.trace_ray(s0, al, be, [230e9], max_trace=5000)["trace"]
+        t1 = ora.trace_ray(s1, al, be, [230e9], max_trace=5000)["trace"]
+        assert np.array_equal(t0[:, :9], t1[:, :9])  # the geometry is untouched
+        I0, tau0 = np.concatenate([[0.0], t0[:, 10]]), np.concatenate([[0.0], t0[:, 11]])
+        I1, tau1 = np.concatenate([[0.0], t1[:, 10]]), np.concatenate([[0.0], t1[:, 11]])
+        the = 10.0 / t0[:, 1]  # the analytic scene's Theta_e = 10 / r
+        masked = the < 0.5
+        assert masked.any() and (~masked).any()
+        dI0, dI1 = np.diff(I0), np.diff(I1)
+        dt0, dt1 = np.diff(tau0), np.diff(tau1)
+        assert (dI1[masked] == 0).all() and (dt1[masked] == 0).all()
+        assert np.allclose(dt1[~masked], dt0[~masked], rtol=1e-12, atol=0)
+        w = np.exp(-(tau1[:-1] - tau0[:-1]))
+        assert np.allclose(dI1[~masked], dI0[~masked] * w[~masked], rtol=1e-9, atol=1e-300)
+    sm = dict(base, nx=8, ny=8)
+    a0, _, _ = ora.render(ora.scene(**sm), [230e9])
+    az, _, _ = ora.render(ora.scene(**sm, theta_e_min=0.0), [230e9])
+    ah, _, _ = ora.render(ora.scene(**sm, theta_e_min=1e9), [230e9])
+    assert np.array_equal(a0, az) and (ah == 0).all() and a0.sum() > 0
