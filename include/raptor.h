@@ -235,6 +235,14 @@ raptor_status raptor_stats(raptor_ctx* ctx, unsigned long long* rays, unsigned l
 /* Reset the counters of raptor_stats. */
 raptor_status raptor_stats_reset(raptor_ctx* ctx);
 
+/* All counters behind raptor_stats (synchronises the context's last stream): values[count]
+ * (caller's host array, 1 <= count <= 16) receives, in order, rays, accepted steps, FP64
+ * steps, truncated rays, rays with an error status, surrogate fallbacks, re-entries of the
+ * FP64 region during the outbound FP32 phase (counted, not moved), clamped slow-light
+ * samples, and the FP64 steps taken on the mixed path's second stream (near-critical rays);
+ * later slots are zero.  RAPTOR_EINVAL for a count outside 1..16. */
+raptor_status raptor_stats_ex(raptor_ctx* ctx, unsigned long long* values, int count);
+
 /* Launch shape of the persistent kernels (used by the autotuner): threads per block in
  * {32, 64, 96, 128}, resident blocks per SM of the FP64 and FP32 ray kernels, and of the
  * mixed path's FP64 passes (0 = the occupancy maximum). */
@@ -352,13 +360,14 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 /* Per-kernel device time, measured with CUDA events recorded around every kernel launch on
  * the launch's own stream.  raptor_profile(ctx, 1) clears the accumulators and starts
  * recording; raptor_profile(ctx, 0) stops.  raptor_profile_read waits for the recorded
- * events and returns, per kernel slot RAPTOR_KERNEL_* (12 slots), the summed milliseconds
- * (ms[12], may be NULL) and the number of launches since the last clear (launches[12],
+ * events and returns, per kernel slot RAPTOR_KERNEL_* (13 slots), the summed milliseconds
+ * (ms[13], may be NULL) and the number of launches since the last clear (launches[13],
  * may be NULL; counted whether or not recording is on).  A slot covers all the kernels of
  * one stage (e.g. the surrogate slot times its inference as one interval). */
 #define RAPTOR_KERNEL_RENDER_FP64 0  /* persistent FP64 ray kernel                         */
 #define RAPTOR_KERNEL_MIXED_A 1      /* mixed: FP32 phase on camera rays                   */
-#define RAPTOR_KERNEL_MIXED_B 2      /* mixed: FP64 phase (inner region, turning points)   */
+#define RAPTOR_KERNEL_MIXED_B 2      /* mixed: FP64 phase (inner region, turning points) of
+                                        the first stream                                    */
 #define RAPTOR_KERNEL_MIXED_C 3      /* mixed: FP32 phase on outbound rays                 */
 #define RAPTOR_KERNEL_REDUCE 4       /* flux reduction (two launches per render)          */
 #define RAPTOR_KERNEL_TRACE 5        /* single-ray trace                                   */
@@ -369,6 +378,8 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 #define RAPTOR_KERNEL_TRAIN 9        /* surrogate data generation and training             */
 #define RAPTOR_KERNEL_SURROGATE_MLP 10 /* the network inside RAPTOR_KERNEL_SURROGATE        */
 #define RAPTOR_KERNEL_DISK 11        /* thin-disk rays and their spectrum                  */
+#define RAPTOR_KERNEL_MIXED_B_LONG 12 /* mixed: FP64 phase of the near-critical rays (second
+                                        stream); RAPTOR_KERNEL_MIXED_B has the other rays'  */
 raptor_status raptor_profile(raptor_ctx* ctx, int enable);
 raptor_status raptor_profile_read(raptor_ctx* ctx, double* ms, long long* launches);
 

@@ -26,7 +26,7 @@ RAY_ESCAPED, RAY_CAPTURED, RAY_THICK, RAY_TRUNCATED, RAY_ERROR = range(5)
 EXPORTS = [
     "raptor_version", "raptor_camera_desc_default", "raptor_plasma_desc_default", "raptor_camera_init",
     "raptor_camera_set", "raptor_load_plasma", "raptor_render", "raptor_render_ex", "raptor_render_host",
-    "raptor_lightcurve", "raptor_trace_ray", "raptor_stats", "raptor_stats_reset", "raptor_set_launch",
+    "raptor_lightcurve", "raptor_trace_ray", "raptor_stats", "raptor_stats_reset", "raptor_stats_ex", "raptor_set_launch",
     "raptor_last_error", "raptor_destroy", "raptor_profile", "raptor_profile_read", "raptor_measure_fma_peak",
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
@@ -34,7 +34,7 @@ EXPORTS = [
     "raptor_disk_desc_default", "raptor_disk_render", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
-                "surrogate", "train", "surrogate_mlp", "disk"]
+                "surrogate", "train", "surrogate_mlp", "disk", "mixed_fp64_long"]
 
 
 class RaptorError(RuntimeError):
@@ -99,6 +99,7 @@ def lib():
             "raptor_trace_ray": (st, [vp, C.c_double, C.c_double, C.c_double, dp, C.c_int, C.c_int, dp, ip, ip, dp, vp]),
             "raptor_stats": (st, [vp, u64p, u64p, u64p, u64p, u64p, u64p]),
             "raptor_stats_reset": (st, [vp]),
+            "raptor_stats_ex": (st, [vp, vp, C.c_int]),
             "raptor_set_launch": (st, [vp, C.c_int, C.c_int, C.c_int]),
             "raptor_last_error": (C.c_char_p, [vp]),
             "raptor_destroy": (None, [vp]),
@@ -283,6 +284,14 @@ class Context:
         v = [C.c_ulonglong(0) for _ in range(6)]
         self._check(lib().raptor_stats(self._h, *[C.byref(x) for x in v]), "raptor_stats")
         return dict(zip(["rays", "steps", "fp64_steps", "truncated", "errors", "fallback"], [x.value for x in v]))
+
+    def stats_ex(self):
+        """All counters: rays, steps, fp64_steps, truncated, errors, fallback, reentries,
+        clamped, fp64_steps_long (second stream)."""
+        v = (C.c_ulonglong * 9)()
+        self._check(lib().raptor_stats_ex(self._h, v, 9), "raptor_stats_ex")
+        return dict(zip(["rays", "steps", "fp64_steps", "truncated", "errors", "fallback", "reentries", "clamped",
+                         "fp64_steps_long"], [int(x) for x in v]))
 
     def stats_reset(self):
         self._check(lib().raptor_stats_reset(self._h), "raptor_stats_reset")

@@ -31,7 +31,7 @@ struct raptor_ctx {
     float* d_grid = nullptr;      // interleaved [snap][n2][n1][8]
     size_t grid_cap = 0;
     unsigned long long* d_counters = nullptr;  // [8] work counters
-    unsigned long long* d_stats = nullptr;     // [8]
+    unsigned long long* d_stats = nullptr;     // [kNumStats]
     double* d_partial = nullptr;
     unsigned long long* d_hist = nullptr;  // thin-disk spectrum (fixed point)
     size_t hist_cap = 0;
@@ -410,7 +410,7 @@ constexpr long long kGraphMaxRays = 1LL << 19;  // largest call replayed from a 
 
 template <int NF, typename S>
 cudaError_t launch_fp64_phase(raptor_ctx* c, const Params& p, const PhaseIO& io, int blocks, int threads, cudaStream_t s) {
-    ProfScope ps(c, kProfMixedB, s);
+    ProfScope ps(c, io.long_lane ? kProfMixedBLong : kProfMixedB, s);
     k_mixed_fp64<NF, S><<<std::max(1, blocks), threads, 0, s>>>(p, io, c->mq.cap, c->d_counters, c->d_stats);
     return cudaGetLastError();
 }
@@ -503,6 +503,7 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool
         bl.requeue_cnt = pass + 1 < LK ? kCntLPassOut + pass : -1;
         bl.budget = pass + 1 < LK ? c->long_budget[pass] : (1 << 30);
         bl.in_exact = pass > 0;
+        bl.long_lane = 1;
         e = fp64_phase(bl, b_long, long_threads, c->s_long);
         if (e != cudaSuccess) return e;
     }
@@ -559,6 +560,7 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool
         bt.requeue_cnt = -1;
         bt.budget = 1 << 30;
         bt.in_exact = 1;
+        bt.long_lane = 1;
         e = fp64_phase(bt, b_long, long_threads, c->s_long);
         if (e != cudaSuccess) return e;
     }
@@ -782,8 +784,8 @@ raptor_status raptor_camera_init(const raptor_camera_desc* desc, raptor_ctx** ou
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_counters, kNumCounters * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_stats, 8 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_stats, kNumStats * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, kNumStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_trace_int, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_trace_I, 64 * sizeof(double));
     if (e == cudaSuccess) {
@@ -1105,7 +1107,14 @@ raptor_status raptor_stats(raptor_ctx* ctx, unsigned long long* rays, unsigned l
 raptor_status raptor_stats_reset(raptor_ctx* ctx) {
     if (!ctx) return RAPTOR_EINVAL;
     RCK(cudaStreamSynchronize(ctx->last_stream));
-    RCK(cudaMemset(ctx->d_stats, 0, 8 * sizeof(unsigned long long)));
+    RCK(cudaMemset(ctx->d_stats, 0, kNumStats * sizeof(unsigned long long)));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_stats_ex(raptor_ctx* ctx, unsigned long long* values, int count) {
+    if (!ctx || !values || count < 1 || count > kNumStats) return RAPTOR_EINVAL;
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemcpy(values, ctx->d_stats, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return RAPTOR_OK;
 }
 

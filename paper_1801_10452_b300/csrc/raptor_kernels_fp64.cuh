@@ -18,11 +18,11 @@ enum : int { kEscaped = 0, kCaptured = 1, kThick = 2, kTruncated = 3, kError = 4
 // Per-kernel profiling slots (raptor_profile_read).
 enum : int { kProfRenderFp64 = 0, kProfMixedA = 1, kProfMixedB = 2, kProfMixedC = 3, kProfReduce = 4, kProfTrace = 5,
              kProfLoad = 6, kProfPeak = 7, kProfSurrogate = 8, kProfTrain = 9, kProfSurrogateMlp = 10,
-             kProfDisk = 11, kProfSlots = 12 };
+             kProfDisk = 11, kProfMixedBLong = 12, kProfSlots = 13 };
 
-// Stats slots (device unsigned long long[8]).
+// Stats slots (device unsigned long long[kNumStats]).
 enum : int { kStatRays = 0, kStatSteps = 1, kStatFp64Steps = 2, kStatTrunc = 3, kStatErr = 4, kStatFallback = 5,
-             kStatReentry = 6, kStatClamp = 7 };
+             kStatReentry = 6, kStatClamp = 7, kStatFp64Long = 8, kNumStats = 16 };
 
 template <int NF>
 struct RayD {

@@ -83,6 +83,7 @@ struct PhaseIO {
     int push_top = -1;    // counter slot c: `push` entries start at cap - cnt[c] (-1: at 0)
     int in_top = -1;      // the same for `in`
     int requeue_top = -1; // and for `requeue`
+    int long_lane = 0;    // FP64 launches on the second stream: their FP64 steps also go to kStatFp64Long
 };
 
 inline cudaError_t alloc_queue(RayQueue& q, size_t cap, int nf) {
@@ -564,6 +565,11 @@ __global__ void __launch_bounds__(128, kMixed64MinBlocks<S>) k_mixed_fp64(const 
         }
     }
     warp_add_stats(stats, c_rays, c_steps, c_64, c_trunc, c_err);
+    if (io.long_lane) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c_64 += __shfl_down_sync(0xffffffffu, c_64, o);
+        if ((threadIdx.x & 31) == 0 && c_64) atomicAdd(&stats[kStatFp64Long], c_64);
+    }
 }
 
 // Split the rays of a render into the near-critical list (pixel centre within `band` M of

@@ -33,11 +33,15 @@ def test_timeline_matches_slot_sums_and_shows_both_streams(R):
     sums = ctx.profile_read()
     ctx.profile(False)
     names = [t[0] for t in tl]
-    # A1, A2, C, C-long; one FP64 launch on the second stream and eight passes; two reductions
+    # A1, A2, C, C-long; one FP64 launch on the second stream (its own slot) and eight passes;
+    # two reductions
     assert names.count("mixed_fp32_in") == 2 and names.count("mixed_fp32_out") == 2
     assert names.count("reduce") == 2
-    lanes = {t[1] for t in tl if t[0] == "mixed_fp64"}
-    assert lanes == {0, 1}
+    assert {t[1] for t in tl if t[0] == "mixed_fp64"} == {0}
+    assert {t[1] for t in tl if t[0] == "mixed_fp64_long"} == {1}
+    # the second stream's FP64 steps are counted apart, and are part of the FP64 steps
+    st = ctx.stats_ex()
+    assert 0 < st["fp64_steps_long"] < st["fp64_steps"]
     assert all(t[2] >= -0.05 and t[3] >= 0.0 for t in tl)
     for k, (ms, _) in sums.items():
         tot = sum(t[3] for t in tl if t[0] == k)
