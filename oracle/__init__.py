@@ -47,7 +47,7 @@ class OraScene(C.Structure):
         ("x1_min", C.c_double), ("x1_max", C.c_double), ("h_mks", C.c_double),
         ("t0", C.c_double), ("dt_snap", C.c_double),
         ("mass_unit_g", C.c_double), ("r_high", C.c_double), ("r_low", C.c_double), ("gamma_ad", C.c_double),
-        ("integrator", C.c_int), ("theta_e_min", C.c_double),
+        ("integrator", C.c_int), ("theta_e_min", C.c_double), ("rt_scheme", C.c_int),
     ]
 
 
@@ -124,7 +124,7 @@ def scene(**kw) -> OraScene:
              n0=1.0e6, n_pow=-1.5, the0=10.0, the_pow=-1.0, B0=20.0, B_pow=-1.0,
              ball_R=0.0, ball_j=0.0, ball_alpha=0.0, grid=None, n1=0, n2=0, n_snap=0, snap=0,
              x1_min=0.0, x1_max=0.0, h_mks=1.0, t0=0.0, dt_snap=1.0,
-             mass_unit_g=0.0, r_high=1.0, r_low=1.0, gamma_ad=4.0 / 3.0, integrator=RK4, theta_e_min=0.0)
+             mass_unit_g=0.0, r_high=1.0, r_low=1.0, gamma_ad=4.0 / 3.0, integrator=RK4, theta_e_min=0.0, rt_scheme=0)
     d.update(kw)
     keep = d.pop("_grid_ref", None)
     for k, v in d.items():

@@ -32,6 +32,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <cstdint>
+#include <vector>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -80,6 +81,7 @@ typedef struct {
     double mass_unit_g, r_high, r_low, gamma_ad;
     int integrator;      // 0 = RK4 (Eqs. 7-15), 1 = velocity Verlet (Eqs. 16-19), 2 = Verlet with re-evaluation
     double theta_e_min;  // no emission (nor absorption) where Theta_e < theta_e_min; 0 = no mask
+    int rt_scheme;       // 0 = backward accumulation (Eqs. 35-36), 1 = forward formal solution (Eq. 34)
 } OraScene;
 
 }  // extern "C"
@@ -697,10 +699,27 @@ void ora_rt_update(double* I, double* tau, double j, double S, double g, double 
     *tau += dtau;
 }
 
+// Forward formal solution (sec. 3, Eq. 34 over one step, constant coefficients): the step's
+// optical depth and its own invariant contribution S (1 - e^{-dtau}) / g^3 are recorded (in
+// `fwd`, pairs in step order) and the optical depth from the camera is still accumulated
+// for the cut-off; the intensity is formed once the ray has ended, from its far end:
+// I <- I e^{-dtau} + S (1 - e^{-dtau}) / g^3 towards the camera.
+static void rt_record(std::vector<double>* fwd, double* tau, double j, double S, double g, double dl_cm) {
+    double dtau = 0.0, c = 0.0;
+    if (j > 0.0 && S > 0.0) {
+        dtau = j / S * g * dl_cm;
+        c = S * (-std::expm1(-dtau)) / (g * g * g);
+    }
+    fwd->push_back(dtau);
+    fwd->push_back(c);
+    *tau += dtau;
+}
+
 // One transfer sample at state (x, k) for all frequencies.  Returns 0 on success, 1 if
 // the frequency ratio g <= 0 (not possible for a timelike u: reported as an error).
 static int rt_sample(const OraScene* s, const double x[4], const double k[4], double dl,
-                     const double* nus, int nf, double* I, double* tau, double* g_out) {
+                     const double* nus, int nf, double* I, double* tau, double* g_out,
+                     std::vector<double>* fwd = nullptr) {
     Plasma P;
     const int ok = plasma_at(s, x, &P);
     if (g_out) *g_out = 0.0;
@@ -731,15 +750,17 @@ static int rt_sample(const OraScene* s, const double x[4], const double k[4], do
         double jS[2];
         if (P.iso == 2) {
             // constant j, alpha in the fluid frame
-            const double S = P.jfix / P.afix;
-            ora_rt_update(&I[f], &tau[f], P.jfix, S, gr, dl * L);
-            continue;
+            jS[0] = P.jfix;
+            jS[1] = P.jfix / P.afix;
+        } else if (P.thetae < s->theta_e_min) {
+            // sec. 4.2.2: the fit holds for Theta_e above ~0.5; below theta_e_min the
+            // sample emits and absorbs nothing (validity mask, off by default)
+            jS[0] = jS[1] = 0.0;
+        } else {
+            ora_emissivity(nuf, P.ne, P.thetae, P.B, sinb, s->k2_exact, jS);
         }
-        // sec. 4.2.2: the fit holds for Theta_e above ~0.5; below theta_e_min the sample
-        // emits and absorbs nothing (validity mask, off by default)
-        if (P.thetae < s->theta_e_min) continue;
-        ora_emissivity(nuf, P.ne, P.thetae, P.B, sinb, s->k2_exact, jS);
-        ora_rt_update(&I[f], &tau[f], jS[0], jS[1], gr, dl * L);
+        if (fwd) rt_record(&fwd[f], &tau[f], jS[0], jS[1], gr, dl * L);
+        else ora_rt_update(&I[f], &tau[f], jS[0], jS[1], gr, dl * L);
     }
     return 0;
 }
@@ -749,13 +770,15 @@ static int rt_sample(const OraScene* s, const double x[4], const double k[4], do
 // r_h), escaped (r > r_esc), truncated (max_steps); thick (min tau > tau_cut) is tested
 // after the sample.  Status: 0 escaped, 1 captured, 2 thick, 3 truncated, 4 error.
 // trace (optional) receives per step: x[4], k[4], dl, g, I[0], tau[0]  (12 doubles);
-// g = 0 on the terminating step, which takes no transfer sample.
+// g = 0 on the terminating step, which takes no transfer sample.  With the forward scheme
+// (rt_scheme = 1) the intensity exists only once the ray has ended: the trace's I stays 0.
 int ora_trace_ray(const OraScene* s, double alpha, double beta, double t_cam, const double* nus, int nf,
                   double* I, double* tau, int* steps, double* trace, int max_trace) {
     double x[4], k[4], fd[4];
     ora_camera(s, alpha, beta, t_cam, x, k);
     start_derivative(s, x, k, fd);
     for (int f = 0; f < nf; ++f) { I[f] = 0.0; tau[f] = 0.0; }
+    std::vector<std::vector<double>> fwd(s->rt_scheme == 1 ? nf : 0);
     const double r_stop = s->r_stop_factor * horizon(s);
     int n = 0, status = 3;
     while (n < s->max_steps) {
@@ -769,7 +792,7 @@ int ora_trace_ray(const OraScene* s, double alpha, double beta, double t_cam, co
         if (!finite) done = 4;
         else if (x[1] < r_stop) done = 1;
         else if (x[1] > s->r_esc) done = 0;
-        else if (rt_sample(s, x, k, dl, nus, nf, I, tau, &gr)) done = 4;
+        else if (rt_sample(s, x, k, dl, nus, nf, I, tau, &gr, fwd.empty() ? nullptr : fwd.data())) done = 4;
         if (trace && n <= max_trace) {
             double* T = trace + (size_t)(n - 1) * 12;
             for (int i = 0; i < 4; ++i) { T[i] = x[i]; T[4 + i] = k[i]; }
@@ -781,6 +804,11 @@ int ora_trace_ray(const OraScene* s, double alpha, double beta, double t_cam, co
             for (int f = 1; f < nf; ++f) tmin = std::fmin(tmin, tau[f]);
             if (tmin > s->tau_cut) { status = 2; break; }
         }
+    }
+    for (size_t f = 0; f < fwd.size(); ++f) {
+        double Iinv = 0.0;
+        for (size_t q = fwd[f].size(); q >= 2; q -= 2) Iinv = Iinv * std::exp(-fwd[f][q - 2]) + fwd[f][q - 1];
+        I[f] = Iinv;
     }
     if (steps) *steps = n;
     return status;

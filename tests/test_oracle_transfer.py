@@ -217,3 +217,27 @@ def test_theta_e_validity_mask(ora):
     az, _, _ = ora.render(ora.scene(**sm, theta_e_min=0.0), [230e9])
     ah, _, _ = ora.render(ora.scene(**sm, theta_e_min=1e9), [230e9])
     assert np.array_equal(a0, az) and (ah == 0).all() and a0.sum() > 0
+
+
+def test_forward_scheme_on_whole_rays(ora):
+    """The forward formal solution over each ray's recorded steps (rt_scheme = 1, Eq. 34
+    from the far end) gives the backward scheme's image to rounding, with the same
+    terminations, also with the optical-depth cut-off; and the flat-space uniform ball's
+    chord closed form holds for it as for the backward scheme."""
+    freqs = [1e10, 230e9, 1e12]
+    for extra in ({}, {"tau_cut": math.log(1000.0)}):
+        s0 = ora.scene(a=0.9, nx=12, ny=12, **extra)
+        s1 = ora.scene(a=0.9, nx=12, ny=12, rt_scheme=1, **extra)
+        a, n0, st0 = ora.render(s0, freqs)
+        b, n1, st1 = ora.render(s1, freqs)
+        assert np.array_equal(st0, st1) and np.array_equal(n0, n1)
+        assert np.all(np.abs(b - a) <= 1e-12 * np.abs(a) + 1e-300)
+        assert a.sum() > 0
+    R, jv, av, b_ = 10.0, 1e-20, 1e-14, 3.0
+    Lcm = ora.length_unit_cm(4e6)
+    exact = jv / av * (-math.expm1(-av * 2 * math.sqrt(R * R - b_ * b_) * Lcm))
+    for scheme in (0, 1):
+        s = ora.scene(m=0.0, a=0.0, plasma_kind=ora.KIND_BALL, ball_R=R, ball_j=jv, ball_alpha=av, eps=0.01,
+                      r_cam=200.0, r_esc=200.0, incl_deg=45.0, rt_scheme=scheme)
+        out = ora.trace_ray(s, b_ * 0.6, b_ * 0.8, [1e11])
+        assert abs(out["I"][0] / exact - 1) < 2.5 * 0.01 * R / (2 * math.sqrt(R * R - b_ * b_))
