@@ -81,6 +81,15 @@ typedef enum {
 #define RAPTOR_FLAG_VERLET_REEVAL 0x10u /* RAPTOR_FP64: velocity Verlet with the re-evaluation
                                           of Eqs. 18-19 (two evaluations per step); the
                                           derivative carried on is the last one evaluated    */
+#define RAPTOR_FLAG_FORWARD_RT 0x20u   /* RAPTOR_FP64: forward formal-solution transfer (sec. 3,
+                                          Eq. 34 from the far end) instead of the backward
+                                          accumulation: each ray records its steps' optical
+                                          depth and contribution (at most 2048 emitting steps:
+                                          beyond, status RAPTOR_RAY_ERROR) in a context buffer
+                                          of (launched threads x 2048 x n_freq) pairs; at most
+                                          4 frequencies per call (EINVAL); the same results to
+                                          rounding; not with raptor_render_noalloc
+                                          (EUNSUPPORTED)                                     */
 
 /* Ray termination codes written to status_dev (render_ex) and trace calls. */
 #define RAPTOR_RAY_ESCAPED 0   /* r > r_escape                       */

@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOPLASMA, EUNSUPPORTED = range(7)
 FP64, MIXED, MIXED_MLP = 0, 1, 2
 PLASMA_ANALYTIC, PLASMA_GRID = 0, 1
 FLAG_K2_EXACT, FLAG_STEP_LINEAR_R, FLAG_INNER_DF64, FLAG_VERLET, FLAG_VERLET_REEVAL = 0x1, 0x2, 0x4, 0x8, 0x10
+FLAG_FORWARD_RT = 0x20
 MLP_TCGEN05, MLP_MMA_SYNC = 0, 1
 RAY_ESCAPED, RAY_CAPTURED, RAY_THICK, RAY_TRUNCATED, RAY_ERROR = range(5)
 

@@ -35,6 +35,8 @@ struct raptor_ctx {
     double* d_partial = nullptr;
     unsigned long long* d_hist = nullptr;  // thin-disk spectrum (fixed point)
     size_t hist_cap = 0;
+    double2* d_fwd = nullptr;              // forward-scheme transfer records
+    size_t fwd_cap_elems = 0;
     size_t partial_cap = 0;
     double* d_flux = nullptr;
     size_t flux_cap = 0;
@@ -206,10 +208,12 @@ std::string validate_camera(const raptor_camera_desc* d) {
     if (d->max_steps < 1) return "max_steps must be >= 1";
     if (d->precision < RAPTOR_FP64 || d->precision > RAPTOR_MIXED_MLP) return "unknown precision";
     if (d->flags & ~(RAPTOR_FLAG_K2_EXACT | RAPTOR_FLAG_STEP_LINEAR_R | RAPTOR_FLAG_INNER_DF64 | RAPTOR_FLAG_VERLET |
-                     RAPTOR_FLAG_VERLET_REEVAL))
+                     RAPTOR_FLAG_VERLET_REEVAL | RAPTOR_FLAG_FORWARD_RT))
         return "unknown flag bits";
     if ((d->flags & (RAPTOR_FLAG_VERLET | RAPTOR_FLAG_VERLET_REEVAL)) && d->precision != RAPTOR_FP64)
         return "the Verlet integrator is built for RAPTOR_FP64 only";
+    if ((d->flags & RAPTOR_FLAG_FORWARD_RT) && d->precision != RAPTOR_FP64)
+        return "the forward transfer scheme is built for RAPTOR_FP64 only";
     if (!(d->r_fp64 >= 0.0) || !std::isfinite(d->r_fp64)) return "r_fp64 must be finite and >= 0";
     if (!(d->turn_kr >= 0.0) || !std::isfinite(d->turn_kr)) return "turn_kr must be finite and >= 0";
     if (!std::isfinite(d->t_delay)) return "t_delay must be finite";
@@ -351,9 +355,18 @@ cudaError_t launch_fp64_nf(raptor_ctx* c, const Params& p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const long long need = (p.n_rays + c->launch_block - 1) / c->launch_block;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(grid_blocks(c, std::max(occ, 1)), need));
+    Params q = p;
+    if (p.flags & kFlagForwardRT) {
+        // forward scheme: each thread's transfer records, [record][frequency][thread]
+        q.fwd_stride = (long long)blocks * c->launch_block;
+        q.fwd_cap = kForwardCap;
+        e = ensure(c, &c->d_fwd, &c->fwd_cap_elems, (size_t)q.fwd_stride * kForwardCap * p.nf);
+        if (e != cudaSuccess) return e;
+        q.fwd = c->d_fwd;
+    }
     ProfScope ps(c, kProfRenderFp64, s);
-    if (verlet) k_render_fp64<NF, true><<<blocks, c->launch_block, 0, s>>>(p, c->d_counters, c->d_stats);
-    else k_render_fp64<NF, false><<<blocks, c->launch_block, 0, s>>>(p, c->d_counters, c->d_stats);
+    if (verlet) k_render_fp64<NF, true><<<blocks, c->launch_block, 0, s>>>(q, c->d_counters, c->d_stats);
+    else k_render_fp64<NF, false><<<blocks, c->launch_block, 0, s>>>(q, c->d_counters, c->d_stats);
     return cudaGetLastError();
 }
 
@@ -724,6 +737,8 @@ raptor_status check_freqs(raptor_ctx* ctx, const double* freqs, int n_freq) {
     if (n_freq < 1 || n_freq > 64) return fail(ctx, RAPTOR_EINVAL, "n_freq must lie in [1, 64]");
     for (int f = 0; f < n_freq; ++f)
         if (!finite_pos(freqs[f])) return fail(ctx, RAPTOR_EINVAL, "frequencies must be finite and positive");
+    if ((ctx->cam.flags & RAPTOR_FLAG_FORWARD_RT) && n_freq > kForwardMaxFreq)
+        return fail(ctx, RAPTOR_EINVAL, "the forward scheme takes at most 4 frequencies");
     return RAPTOR_OK;
 }
 
@@ -1061,6 +1076,13 @@ raptor_status raptor_trace_ray(raptor_ctx* ctx, double alpha, double beta, doubl
     p.snap = 0;
     const double tc = t_obs + ctx->cam.t_delay;
     ProfScope ps(ctx, kProfTrace, s);
+    if (p.flags & kFlagForwardRT) {
+        if (n_freq > kForwardMaxFreq) return fail(ctx, RAPTOR_EINVAL, "the forward scheme takes at most 4 frequencies");
+        RCK(ensure(ctx, &ctx->d_fwd, &ctx->fwd_cap_elems, (size_t)kForwardCap * n_freq));
+        p.fwd = ctx->d_fwd;
+        p.fwd_cap = kForwardCap;
+        p.fwd_stride = 1;
+    }
     const bool verlet = (p.flags & (kFlagVerlet | kFlagVerletReeval)) != 0;
     int* ti = ctx->d_trace_int;
     if (n_freq <= 1 && !verlet)
@@ -1143,7 +1165,7 @@ void raptor_destroy(raptor_ctx* ctx) {
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
                   ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
-                  ctx->d_crit, ctx->d_rest, ctx->d_hist};
+                  ctx->d_crit, ctx->d_rest, ctx->d_hist, ctx->d_fwd};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.a);
@@ -1726,6 +1748,7 @@ raptor_status raptor_render_noalloc(const raptor_camera_desc* cam, const raptor_
                                     int n_freq, double t_obs, double* image_dev, double* flux_dev, void* stream) {
     if (!validate_camera(cam).empty() || !validate_plasma(plasma).empty()) return RAPTOR_EINVAL;
     if (cam->precision != RAPTOR_FP64) return RAPTOR_EINVAL;
+    if (cam->flags & RAPTOR_FLAG_FORWARD_RT) return RAPTOR_EUNSUPPORTED;  // needs a record buffer
     if (plasma->kind != RAPTOR_PLASMA_ANALYTIC) return RAPTOR_EUNSUPPORTED;
     if (!freqs_hz || n_freq < 1 || n_freq > RAPTOR_NOALLOC_MAX_FREQ || !image_dev || !std::isfinite(t_obs))
         return RAPTOR_EINVAL;

@@ -12,6 +12,9 @@ constexpr unsigned kFlagLinearR = 0x2u;
 constexpr unsigned kFlagInnerDf64 = 0x4u;
 constexpr unsigned kFlagVerlet = 0x8u;         // velocity Verlet (sec. 2.2.2) instead of RK4
 constexpr unsigned kFlagVerletReeval = 0x10u;  // ... with the re-evaluation of Eqs. 18-19
+constexpr unsigned kFlagForwardRT = 0x20u;     // forward formal-solution transfer (FP64 path)
+constexpr int kForwardCap = 2048;              // forward scheme: transfer records per ray
+constexpr int kForwardMaxFreq = 4;             // forward scheme: frequencies per call
 
 enum : int { kEscaped = 0, kCaptured = 1, kThick = 2, kTruncated = 3, kError = 4, kDiskHit = 5, kDiskNone = 6 };
 
@@ -31,7 +34,20 @@ struct RayD {
     double I[NF], tau[NF];
     int n;
     int snap;
+    int ns;       // forward scheme: transfer records of this ray
 };
+
+// Forward formal solution (sec. 3, Eq. 34 with constant coefficients over each step): the
+// thread's records of this ray, (dtau, S (1 - e^{-dtau}) / g^3) in step order, combined from
+// the far end: I <- I e^{-dtau} + contribution, towards the camera.
+__device__ __forceinline__ double forward_intensity(const Params& p, long long tid, int ns, int f) {
+    double I = 0.0;
+    for (int q = ns - 1; q >= 0; --q) {
+        const double2 rec = p.fwd[((long long)q * p.nf + f) * p.fwd_stride + tid];
+        I = I * exp(-rec.x) + rec.y;
+    }
+    return I;
+}
 
 // One FP64 step of a ray: adaptive step, RK4 (VERLET = false) or velocity Verlet,
 // termination, transfer sample.  Returns the termination code or -1 to continue.
@@ -57,14 +73,28 @@ __device__ __forceinline__ int step_fp64(const Params& p, RayD<NF>& R, double& d
         g_out = g;
         const double dlcm = dl * p.Lcm;
         const bool k2x = (p.flags & kFlagK2Exact) != 0;
+        const bool fwd = (p.flags & kFlagForwardRT) != 0;
+        if (fwd && R.ns >= p.fwd_cap) return kError;  // this ray's records are full
+        const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             if (f < p.nf) {
                 double j, S;
                 synchrotron<double>(g * p.nu[f], ne, the, B, sinb, k2x, j, S, 1.0, p.the_min);
-                rt_update<double, double>(j, S, g, dlcm, R.I[f], R.tau[f]);
+                if (fwd) {
+                    double dtau = 0.0, c = 0.0;
+                    if (j > 0.0 && S > 0.0) {
+                        dtau = j / S * g * dlcm;
+                        c = S * (-expm1(-dtau)) / (g * g * g);
+                    }
+                    p.fwd[((long long)R.ns * p.nf + f) * p.fwd_stride + tid] = make_double2(dtau, c);
+                    R.tau[f] += dtau;
+                } else {
+                    rt_update<double, double>(j, S, g, dlcm, R.I[f], R.tau[f]);
+                }
             }
         }
+        if (fwd) R.ns += 1;
     }
     double tmin = R.tau[0];
 #pragma unroll
@@ -89,6 +119,7 @@ __device__ __forceinline__ void init_ray(const Params& p, long long id, RayD<NF>
 #pragma unroll
     for (int f = 0; f < NF; ++f) { R.I[f] = 0.0; R.tau[f] = 0.0; }
     R.n = 0;
+    R.ns = 0;
     R.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
 }
 
@@ -162,6 +193,12 @@ __global__ void __launch_bounds__(128) k_render_fp64(const Params p, unsigned lo
             double dl, g;
             const int st = step_fp64<NF, VERLET>(p, R, dl, g);
             if (st >= 0) {
+                if (p.flags & kFlagForwardRT) {
+                    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        if (f < p.nf) R.I[f] = forward_intensity(p, tid, R.ns, f);
+                }
                 write_ray<NF>(p, frame, pix, R.I, R.n, st);
                 c_rays += 1;
                 c_steps += (unsigned long long)R.n;
@@ -319,6 +356,7 @@ __global__ void k_trace_fp64(const Params p, double alpha, double beta, double t
 #pragma unroll
     for (int f = 0; f < NF; ++f) { R.I[f] = 0.0; R.tau[f] = 0.0; }
     R.n = 0;
+    R.ns = 0;
     R.snap = p.snap;
     int st = -1;
     while (st < 0) {
@@ -333,6 +371,9 @@ __global__ void k_trace_fp64(const Params p, double alpha, double beta, double t
             T[11] = R.tau[0];
         }
     }
+    if (p.flags & kFlagForwardRT)
+        for (int f = 0; f < NF; ++f)
+            if (f < p.nf) R.I[f] = forward_intensity(p, 0, R.ns, f);
     *out_n = R.n;
     *out_status = st;
     for (int f = 0; f < NF; ++f)

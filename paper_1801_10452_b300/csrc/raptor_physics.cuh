@@ -55,6 +55,9 @@ struct Params {
     int lc_fast;             // 1: frame f samples snapshot frame_snap0 + f
     // outputs
     double* image;           // [frame][nf_total][n_rows][nx]
+    double2* fwd;            // forward scheme: per thread, (dtau, contribution) [record][freq][thread]
+    int fwd_cap;             // records per ray
+    long long fwd_stride;    // threads of the launch
     double i_unscale;        // stored intensity = I * i_unscale (1 for FP64; 2^-100 for the FP32 scaling)
     int nf_total, f_off;     // frequency chunking: this launch covers [f_off, f_off + nf)
     int* steps_out;          // optional [n_rows][nx]
