@@ -365,9 +365,10 @@ def _disk_extra(R, torch, stream, fma64, reps=2):
 
 def _verlet_extra(R, torch, stream, fma64, flush, reps=2):
     """The FP64 path with the velocity-Verlet integrator (sec. 2.2.2) on the headline image,
-    with and without the re-evaluation, beside RK4: time per render, rays/s, steps/s, flux
-    against RK4, and the FP64 roofline (algorithmic flops per Verlet step, counted from the
-    source, x steps / kernel time against the FP64 FMA-chain peak)."""
+    with and without the re-evaluation, beside RK4, and RK4 with the forward formal-solution
+    transfer (sec. 3): time per render, rays/s, steps/s, flux against RK4, and the FP64
+    roofline (algorithmic flops per step, counted from the source, x steps / kernel time
+    against the FP64 FMA-chain peak)."""
     from paper_1801_10452_b300 import flopcount, scenes
 
     fl = flopcount.flops_per_step(1, "analytic")
@@ -376,7 +377,8 @@ def _verlet_extra(R, torch, stream, fma64, flush, reps=2):
     out = {"workload": "kerr_analytic_1024x1024_a0.9375_i60_230GHz_fp64", "per_integrator": {}}
     flux_rk4 = None
     for name, flags, fps in (("rk4", 0, fl["fp64_step"]), ("verlet", R.FLAG_VERLET, fl["verlet_step"]),
-                             ("verlet_reeval", R.FLAG_VERLET_REEVAL, fl["verlet_reeval_step"])):
+                             ("verlet_reeval", R.FLAG_VERLET_REEVAL, fl["verlet_reeval_step"]),
+                             ("rk4_forward_transfer", R.FLAG_FORWARD_RT, fl["fp64_step"])):
         ctx = R.Context(R.camera_desc(**cam, flags=flags))
         ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
         img = torch.empty((1, cam["ny"], cam["nx"]), dtype=torch.float64, device="cuda")
