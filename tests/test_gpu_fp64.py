@@ -193,3 +193,38 @@ def test_step_cap_counts_truncated_rays(R):
     assert np.all(steps.cpu().numpy() == 20)
     assert np.all(status.cpu().numpy() == R.RAY_TRUNCATED)
     assert st["truncated"] == 64 and st["rays"] == 64 and st["steps"] == 64 * 20
+
+
+def test_invalid_arguments_of_the_options(R):
+    """Argument checks of the schedule, profiling, disk and emissivity entry points (EINVAL,
+    nothing launched) and that a context stays usable after them."""
+    import torch
+
+    ctx = R.Context(R.camera_desc(nx=8, ny=8))
+    ctx.load_plasma(R.plasma_desc())
+    bad_calls = [
+        lambda: ctx.mixed_config(-1.0),
+        lambda: ctx.mixed_config(0.5, [0]),
+        lambda: ctx.mixed_config(0.5, None, -1),
+        lambda: ctx.long_config(48),
+        lambda: ctx.long_config(0, [0]),
+        lambda: ctx.long_config(0, [1] * 8),
+        lambda: ctx.disk_render(r_in=20.0, r_out=15.0),
+        lambda: ctx.disk_render(max_cross=0),
+        lambda: ctx.disk_render(n_bins=0),
+        lambda: ctx.disk_render(x_range=(1.0, 0.5)),
+        lambda: ctx.load_plasma(R.plasma_desc(theta_e_min=-1.0)),
+        lambda: ctx.load_plasma(R.plasma_desc(theta_e_min=float("nan"))),
+    ]
+    for call in bad_calls:
+        with pytest.raises(R.RaptorError) as e:
+            call()
+        assert e.value.status == R.EINVAL
+    with pytest.raises(R.RaptorError) as e:
+        R.Context(R.camera_desc(flags=0x40))
+    assert e.value.status == R.EINVAL
+    img, fl = ctx.render([1e11])
+    torch.cuda.synchronize()
+    assert np.isfinite(fl[0])
+    d = ctx.disk_render()
+    assert d["spectrum"].shape == (64,) and d["edges"].shape == (65,)
