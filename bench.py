@@ -200,7 +200,7 @@ def train_surrogate(R, torch, cam, steps, n_train):
     ctx.surrogate_train(x, y, steps, lr=2e-3, lr_final=2e-5, seed=11)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    xh, yh = ctx.surrogate_generate(50_000, seed=0x1801104520000006)
+    xh, yh = ctx.surrogate_generate(100_000, seed=0x1801104520000006)
     err = np.abs(ctx.surrogate_eval(xh).cpu().numpy() - yh.cpu().numpy())
     names = ["dt", "ln_r", "theta", "phi", "k_theta", "k_r"]
     summ = {"rays": n_train, "steps": steps, "batch": 4096, "generate_s": t_gen, "train_s": t_train,
@@ -728,7 +728,7 @@ def main():
     ap.add_argument("--no-verlet", action="store_true", help="skip the FP64 velocity-Verlet workload")
     ap.add_argument("--no-emissivity", action="store_true", help="skip the exact-K2 / Theta_e-mask comparison")
     ap.add_argument("--train-steps", type=int, default=16000)
-    ap.add_argument("--train-rays", type=int, default=1_000_000)
+    ap.add_argument("--train-rays", type=int, default=10_000_000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
