@@ -639,6 +639,10 @@ def run_native(args):
         cpu = {"value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"], "kind": "oracle",
                "sample": f"{int(r['rays'])} rays: every {CPU_SAMPLE_STRIDE}th pixel per axis of the {args.size}^2 image",
                "steps_per_s": r["steps"] / r["seconds"]}
+        # and on one core (a sparser sample of the same image)
+        r1 = oracle_sample(cam, freqs, CPU_SAMPLE_STRIDE * 4, threads=1)
+        cpu["single_thread"] = {"value": r1["rays"] / r1["seconds"], "steps_per_s": r1["steps"] / r1["seconds"],
+                                "sample": f"{int(r1['rays'])} rays: every {CPU_SAMPLE_STRIDE * 4}th pixel per axis"}
         o = r["img"]
         h = CPU_SAMPLE_STRIDE // 2
         sl = (slice(None), slice(h, None, CPU_SAMPLE_STRIDE), slice(h, None, CPU_SAMPLE_STRIDE))
