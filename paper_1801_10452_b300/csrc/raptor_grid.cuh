@@ -170,9 +170,11 @@ RAPTOR_HD int plasma_sample_sc(const Params& p, const T x[4], const T k[4], T sn
             the = p.f.the0 * exp2f(p.f.the_pow * l2r);
             B = p.f.B0 * exp2f(p.f.B_pow * l2r);
         } else {
-            ne = RAPTOR_P(T, n0) * Real<T>::pow_(r, RAPTOR_P(T, n_pow));
-            the = RAPTOR_P(T, the0) * Real<T>::pow_(r, RAPTOR_P(T, the_pow));
-            B = RAPTOR_P(T, B0) * Real<T>::pow_(r, RAPTOR_P(T, B_pow));
+            // one logarithm, three exponentials (r^n = e^{n ln r})
+            const T lr = Real<T>::log_(r);
+            ne = RAPTOR_P(T, n0) * Real<T>::exp_(RAPTOR_P(T, n_pow) * lr);
+            the = RAPTOR_P(T, the0) * Real<T>::exp_(RAPTOR_P(T, the_pow) * lr);
+            B = RAPTOR_P(T, B0) * Real<T>::exp_(RAPTOR_P(T, B_pow) * lr);
         }
         ks_lower(P, k, kc);
         g = kc[0] * u[0] + kc[1] * u[1] + kc[2] * u[2] + kc[3] * u[3];

@@ -235,6 +235,7 @@ RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, 
     const T hme = T(kH / (kMe * kC * kC));
     const T x = dv(hme * nu, the);
     if constexpr (std::is_same<T, float>::value) S = T(2.0 * kMe) * nu * nu * the * x_over_expm1f(x);
+    else if constexpr (std::is_same<T, double>::value) S = T(2.0 * kMe) * nu * nu * the * x_over_expm1(x);
     else S = T(2.0 * kMe) * nu * nu * the * dv(x, Real<T>::expm1_(x));
     j = T(0);
     if (the < the_min) return;  // outside the fit's validity mask: no emission
@@ -244,9 +245,7 @@ RAPTOR_HD void synchrotron(T nu, T ne, T the, T B, T sinb, bool k2_exact, T& j, 
     const T X13 = Real<T>::cbrt_(X);
     if (X13 > Real<T>::exp_cut) return;
     const T X16 = Real<T>::sqrt_(X13);
-    T X12;
-    if constexpr (std::is_same<T, float>::value) X12 = X13 * X16;  // X^(1/2) = X^(1/3) X^(1/6)
-    else X12 = Real<T>::sqrt_(X);
+    const T X12 = X13 * X16;  // X^(1/2) = X^(1/3) X^(1/6)
     const T fac = X12 + T(1.8877486253633870) * X16;  // 2^(11/12)
     T K2 = T(2) * the * the;
     if (k2_exact) K2 = T(bessel_k2_exact(1.0 / double(the)));
