@@ -19,11 +19,14 @@ template <>
 struct NewtonTol<float> { static constexpr float v = 1e-7f; };
 
 // App. A.2: theta = pi x2 + (1-h)/2 sin(2 pi x2) inverted by Newton-Raphson from
-// x2 = theta/pi, resetting to 0.05 outside [0, 1] or where f' vanishes, stopping when the
-// update is below tolerance or after 20 iterations.
+// x2 = theta/pi (FP64: from the FP32 root), resetting to 0.05 outside [0, 1] or where f'
+// vanishes, stopping when the update is below tolerance or after 20 iterations.
 template <typename T>
 RAPTOR_HD T newton_x2(T theta, T h) {
     T xv = theta * T(1.0 / kPi);
+    // FP64: start from the FP32 root (tolerance 1e-7), so that one or two FP64 iterations
+    // reach the FP64 tolerance; the converged root is the same
+    if constexpr (std::is_same<T, double>::value) xv = (double)newton_x2<float>((float)theta, (float)h);
     const T oh = T(1) - h;
     for (int it = 0; it < 20; ++it) {
         T s, c;
