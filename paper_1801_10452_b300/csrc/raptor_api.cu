@@ -29,6 +29,7 @@ struct raptor_ctx {
     int device = 0;
     int num_sms = 0;
     float* d_grid = nullptr;      // interleaved [snap][n2][n1][8]
+    float* d_x2tab = nullptr;     // MKS inversion table [kX2TabN + 1] of the loaded grid's h
     size_t grid_cap = 0;
     unsigned long long* d_counters = nullptr;  // [8] work counters
     unsigned long long* d_stats = nullptr;     // [kNumStats]
@@ -320,6 +321,7 @@ Params base_params(const raptor_ctx* c) {
     p.the_min = q.theta_e_min;
     if (q.kind == RAPTOR_PLASMA_GRID_MKS2D) {
         p.grid = c->d_grid;
+        p.x2tab = c->d_x2tab;
         p.n1 = q.n1;
         p.n2 = q.n2;
         p.n_snap = q.n_snap;
@@ -861,7 +863,16 @@ raptor_status raptor_load_plasma(raptor_ctx* ctx, const raptor_plasma_desc* desc
         }
         cudaError_t e2 = cudaFreeAsync(staging, s);
         if (e == cudaSuccess) e = e2;
+        // x2(theta) at the table's angles for this grid's h (FP64 Newton roots)
+        if (e == cudaSuccess && !ctx->d_x2tab) e = cudaMalloc((void**)&ctx->d_x2tab, (kX2TabN + 1) * sizeof(float));
+        if (e == cudaSuccess) {
+            std::vector<float> tab(kX2TabN + 1);
+            for (int i = 0; i <= kX2TabN; ++i) tab[i] = (float)newton_x2<double>(kPi * i / kX2TabN, desc->h_mks);
+            e = cudaMemcpyAsync(ctx->d_x2tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host table goes out of scope
+        }
         if (e == cudaSuccess && !desc->fields_on_device) e = cudaStreamSynchronize(s);  // caller may free its host buffer
+        ctx->epoch += 1;  // the kernels read the new table
         if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, std::string("load_plasma: ") + cudaGetErrorString(e));
     }
     ctx->plasma = *desc;
@@ -1165,7 +1176,7 @@ void raptor_destroy(raptor_ctx* ctx) {
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
                   ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
-                  ctx->d_crit, ctx->d_rest, ctx->d_hist, ctx->d_fwd};
+                  ctx->d_crit, ctx->d_rest, ctx->d_hist, ctx->d_fwd, ctx->d_x2tab};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.a);

@@ -47,6 +47,26 @@ RAPTOR_HD T newton_x2(T theta, T h) {
     return xv;
 }
 
+// FP32 inversion from a table: x2 at the kX2TabN + 1 angles theta_i = i pi / kX2TabN
+// (converged FP64 Newton roots, filled on the host when the plasma is loaded), linear
+// interpolation between the two nodes around theta (error ~(pi / kX2TabN)^2 x2'' / 8 < 1e-6),
+// then one Newton step (quadratic: below FP32 rounding).  Outside [0, pi]: newton_x2.
+constexpr int kX2TabN = 1024;
+__device__ __forceinline__ float x2_from_table(const float* tab, float theta, float h) {
+    const float u = theta * (float)(kX2TabN / kPi);
+    if (!(u >= 0.f && u <= (float)kX2TabN)) return newton_x2<float>(theta, h);
+    const int i = min((int)u, kX2TabN - 1);
+    const float w = u - (float)i;
+    const float x0 = __ldg(tab + i), x1 = __ldg(tab + i + 1);
+    const float xv = fmaf(w, x1 - x0, x0);
+    float sn, cs;
+    sc(2.f * (float)kPi * xv, &sn, &cs);
+    const float oh = 1.f - h;
+    const float f = (float)kPi * xv + 0.5f * oh * sn - theta;
+    const float fp = (float)kPi * (1.f + oh * cs);
+    return xv - f * rcp_nr(fp);
+}
+
 // Bilinear cell-centred interpolation of the 8 primitives of snapshot s at fractional
 // index (fi, fj) (clamped to edge cells).  Vector loads of the interleaved cells.
 template <typename T>
@@ -86,7 +106,9 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
     const T x1 = Real<T>::log_(r);
     if (x1 < RAPTOR_P(T, x1_min) || x1 > RAPTOR_P(T, x1_max)) return 0;
     const T h = RAPTOR_P(T, h_mks);
-    const T x2 = newton_x2<T>(x[2], h);
+    T x2;
+    if constexpr (std::is_same<T, float>::value) x2 = p.x2tab ? x2_from_table(p.x2tab, x[2], h) : newton_x2<T>(x[2], h);
+    else x2 = newton_x2<T>(x[2], h);
     T fi = dv(x1 - RAPTOR_P(T, x1_min), RAPTOR_P(T, dx1)) - T(0.5);
     T fj = dv(x2, RAPTOR_P(T, dx2)) - T(0.5);
     int i0 = (int)floor(fi), j0 = (int)floor(fj);

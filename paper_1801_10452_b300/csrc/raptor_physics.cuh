@@ -36,6 +36,7 @@ struct Params {
     double the_min;  // emission only where Theta_e >= the_min (fit-validity mask; 0 = none)
     // grid plasma (MKS, r0 = 0)
     const float* grid;  // [n_snap][8][n2][n1]
+    const float* x2tab; // x2 at theta_i = i pi / kX2TabN, i = 0 .. kX2TabN (FP32 inversion start)
     int n1, n2, n_snap, snap;
     double x1_min, x1_max, dx1, dx2, h_mks, t0, dt_snap;
     double rho0_ne;     // rho0 / (m_e + m_p): n_e = rho * rho0_ne
