@@ -349,6 +349,15 @@ raptor_status raptor_surrogate_eval(raptor_ctx* ctx, const float* inputs_dev, lo
 raptor_status raptor_surrogate_get(raptor_ctx* ctx, float* params_host, int n);
 raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, int n);
 
+/* Save the trained surrogate to a file / load one into this context (checkpoint and reuse
+ * of a trained network; the paper has no counterpart).  Format: the 8 bytes "RAPTMLP1",
+ * u32 format version (1), u32 parameter count, the FP32 parameters in raptor_surrogate_get
+ * order (little-endian), u64 FNV-1a hash of the parameter bytes.  `load` validates magic,
+ * version, count, length and hash before touching the context (RAPTOR_EINVAL otherwise) and
+ * then acts as raptor_surrogate_set.  `save` returns RAPTOR_EUNSUPPORTED without a network. */
+raptor_status raptor_surrogate_save(raptor_ctx* ctx, const char* path);
+raptor_status raptor_surrogate_load(raptor_ctx* ctx, const char* path);
+
 /* Kernel of the surrogate's inference (raptor_surrogate_eval and RAPTOR_MIXED_MLP renders):
  *   RAPTOR_MLP_TCGEN05 (default): hidden layers on the 5th-generation tensor cores
  *     (tcgen05.mma, accumulators in tensor memory, weights resident in shared memory);

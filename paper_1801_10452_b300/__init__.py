@@ -31,7 +31,7 @@ EXPORTS = [
     "raptor_last_error", "raptor_destroy", "raptor_profile", "raptor_profile_read", "raptor_measure_fma_peak",
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
-    "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_config", "raptor_surrogate_kernel",
+    "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_save", "raptor_surrogate_load", "raptor_surrogate_config", "raptor_surrogate_kernel",
     "raptor_disk_desc_default", "raptor_disk_render", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
@@ -117,6 +117,8 @@ def lib():
             "raptor_surrogate_eval": (st, [vp, vp, C.c_longlong, vp, vp]),
             "raptor_surrogate_get": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_surrogate_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
+            "raptor_surrogate_save": (st, [vp, C.c_char_p]),
+            "raptor_surrogate_load": (st, [vp, C.c_char_p]),
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
             "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
@@ -452,6 +454,14 @@ class Context:
     def surrogate_kernel(self, kind):
         """Inference kernel: MLP_TCGEN05 (default) or MLP_MMA_SYNC."""
         self._check(lib().raptor_surrogate_kernel(self._h, int(kind)), "raptor_surrogate_kernel")
+
+    def surrogate_save(self, path):
+        """Write the trained network to `path` (format in raptor_surrogate_save)."""
+        self._check(lib().raptor_surrogate_save(self._h, str(path).encode()), "raptor_surrogate_save")
+
+    def surrogate_load(self, path):
+        """Load a network written by surrogate_save (validated; as surrogate_set)."""
+        self._check(lib().raptor_surrogate_load(self._h, str(path).encode()), "raptor_surrogate_load")
 
     def surrogate_config(self, fallback_band=0.5, r_exit=50.0):
         self._check(lib().raptor_surrogate_config(self._h, float(fallback_band), float(r_exit)), "raptor_surrogate_config")

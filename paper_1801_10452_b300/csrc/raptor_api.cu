@@ -1574,6 +1574,53 @@ raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, in
     return RAPTOR_OK;
 }
 
+// File format of a saved surrogate: 8-byte magic, u32 format version, u32 parameter count,
+// the FP32 parameters (little-endian, MlpLayout order), u64 FNV-1a hash of those bytes.
+constexpr char kSurMagic[8] = {'R', 'A', 'P', 'T', 'M', 'L', 'P', '1'};
+constexpr uint32_t kSurVersion = 1;
+
+static uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+    return h;
+}
+
+raptor_status raptor_surrogate_save(raptor_ctx* ctx, const char* path) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!path) return fail(ctx, RAPTOR_EINVAL, "path is NULL");
+    std::vector<float> P(MlpLayout::SIZE);
+    raptor_status st = raptor_surrogate_get(ctx, P.data(), MlpLayout::SIZE);
+    if (st != RAPTOR_OK) return st;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, RAPTOR_EINVAL, std::string("cannot open for writing: ") + path);
+    const uint32_t hdr[2] = {kSurVersion, (uint32_t)MlpLayout::SIZE};
+    const uint64_t h = fnv1a(reinterpret_cast<const unsigned char*>(P.data()), P.size() * sizeof(float));
+    bool ok = std::fwrite(kSurMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(P.data(), sizeof(float), P.size(), f) == P.size() && std::fwrite(&h, sizeof(h), 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? RAPTOR_OK : fail(ctx, RAPTOR_EINVAL, std::string("write failed: ") + path);
+}
+
+raptor_status raptor_surrogate_load(raptor_ctx* ctx, const char* path) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (!path) return fail(ctx, RAPTOR_EINVAL, "path is NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, RAPTOR_EINVAL, std::string("cannot open: ") + path);
+    char magic[8];
+    uint32_t hdr[2] = {0, 0};
+    std::vector<float> P(MlpLayout::SIZE);
+    uint64_t h = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSurMagic, 8) == 0 &&
+              std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == kSurVersion && hdr[1] == (uint32_t)MlpLayout::SIZE &&
+              std::fread(P.data(), sizeof(float), P.size(), f) == P.size() && std::fread(&h, sizeof(h), 1, f) == 1;
+    char extra;
+    ok = ok && std::fread(&extra, 1, 1, f) == 0;  // nothing after the hash
+    std::fclose(f);
+    if (!ok || h != fnv1a(reinterpret_cast<const unsigned char*>(P.data()), P.size() * sizeof(float)))
+        return fail(ctx, RAPTOR_EINVAL, std::string("not a surrogate file of this version, or damaged: ") + path);
+    return raptor_surrogate_set(ctx, P.data(), MlpLayout::SIZE);
+}
+
 raptor_status raptor_mixed_config(raptor_ctx* ctx, double crit_band, int n_passes, const int* budgets, int tail_split) {
     if (!ctx) return RAPTOR_EINVAL;
     if (!(crit_band >= 0.0) || !std::isfinite(crit_band)) return fail(ctx, RAPTOR_EINVAL, "crit_band must be finite and >= 0");

@@ -260,3 +260,33 @@ def test_learned_results_independent_of_schedule(R, trained, fb_band):
         torch.cuda.synchronize()
         assert np.array_equal(img.cpu().numpy(), ref), band
         assert np.array_equal(fl, fref), band
+
+
+def test_save_and_load_round_trip(R, trained, tmp_path):
+    """A saved network loads into another context with identical parameters and renders
+    identically; damaged or foreign files are refused before the context changes."""
+    import torch
+
+    cam = dict(scenes.SMALL, nx=32, ny=24, precision=R.MIXED_MLP, flags=R.FLAG_INNER_DF64)
+    a = R.Context(R.camera_desc(**cam))
+    a.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    a.surrogate_set(trained)
+    path = tmp_path / "net.bin"
+    a.surrogate_save(path)
+    b = R.Context(R.camera_desc(**cam))
+    b.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    with pytest.raises(R.RaptorError):
+        b.surrogate_save(tmp_path / "none.bin")  # no network yet
+    b.surrogate_load(path)
+    assert np.array_equal(b.surrogate_get(), a.surrogate_get())
+    ia, fa = a.render([230e9])
+    ib, fb = b.render([230e9])
+    torch.cuda.synchronize()
+    assert np.array_equal(ia.cpu().numpy(), ib.cpu().numpy()) and np.array_equal(fa, fb)
+    raw = path.read_bytes()
+    for bad in (raw[:-1], raw + b"x", raw[:20] + bytes([raw[20] ^ 1]) + raw[21:], b"NOTAFILE" + raw[8:]):
+        p = tmp_path / "bad.bin"
+        p.write_bytes(bad)
+        with pytest.raises(R.RaptorError):
+            b.surrogate_load(p)
+    assert np.array_equal(b.surrogate_get(), a.surrogate_get())
