@@ -121,3 +121,39 @@ def test_lightcurve_full_size_all_paths(R, ora, trained):
             peak = imgs[f, 0].max()
             floor = 1e-12 if name == "fp64" else 1e-6
             assert abs(imgs[f, 0, i, j] - ov) <= tol * max(abs(ov), floor * peak), (name, f, i, j)
+
+
+def test_large_image_mixed_and_learned(R, ora, trained):
+    """4096^2 (16.8 M rays, ~35 GB of hand-off queues): no index overflows in the queues,
+    the network's buffers or the reductions.  Fluxes of the mixed and learned paths against
+    the FP64 GPU path, seeded pixels outside the photon-ring band against the oracle."""
+    import torch
+
+    cam = dict(scenes.HEADLINE, nx=4096, ny=4096)
+    freqs = [230e9]
+    ref = R.Context(R.camera_desc(**cam))
+    ref.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    _, fl64 = ref.render(freqs, image=torch.empty((1, 4096, 4096), dtype=torch.float64, device="cuda"))
+    ref.close()
+    s = ora.scene(**__import__("helpers").oracle_kwargs(cam))
+    pix = scenes.sample_pixels(4096, 4096, 32, seed=4096)
+    for prec in ("MIXED", "MIXED_MLP"):
+        ctx = R.Context(R.camera_desc(**cam, precision=getattr(R, prec), flags=R.FLAG_INNER_DF64))
+        ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+        if prec == "MIXED_MLP":
+            ctx.surrogate_set(trained)
+        img, fl = ctx.render(freqs)
+        torch.cuda.synchronize()
+        assert abs(fl[0] / fl64[0] - 1) <= FLUX_TOL, (prec, fl[0] / fl64[0] - 1)
+        st = ctx.stats()
+        assert st["rays"] == 4096 * 4096 and st["errors"] == 0
+        al, be, pj = _pix_jy(R, ora, ctx, cam)
+        keep = ~near_ring(al[pix[:, 1]], be[pix[:, 0]], cam["spin"], cam["incl_deg"], 0.5)
+        peak = float(img.max())
+        for i, j in pix[keep]:
+            ov = ora.trace_ray(s, al[j], be[i], freqs, t_cam=ctx.cam.t_delay)["I"][0] * pj
+            g = float(img[0, i, j])
+            assert abs(g - ov) <= PIX_TOL * max(abs(ov), 1e-6 * peak), (prec, i, j)
+        del img
+        ctx.close()
+        torch.cuda.empty_cache()
