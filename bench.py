@@ -541,11 +541,14 @@ def run_native(args):
     if not args.no_e2e:
         ctx = main["ctx"]
         img_bytes = 8 * rays_step
-        ctx.render_host(freqs, want_image=True)
+        host_img = R.pinned_host_array((len(freqs), cam["ny"], cam["nx"]))
+        ctx.render_host(freqs, out=host_img)
         e2e_t = []
         for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx.render_host(freqs, want_image=True)
+            ctx.render_host(freqs, out=host_img)
             e2e_t.append(time.perf_counter() - t0)
         e2e = {"value": world * rays_step / float(np.mean(e2e_t)), "unit": "rays/s", "h2d_bytes_per_step": 8 * len(freqs),
                "d2h_bytes_per_step": int(img_bytes) + 8 * len(freqs)}

@@ -184,6 +184,14 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def pinned_host_array(shape):
+    """A float64 host array in page-locked memory (for render_host's `out`): device-to-host
+    copies into it run as direct DMA instead of through a staging buffer."""
+    import torch
+
+    return torch.empty(tuple(shape), dtype=torch.float64, pin_memory=True).numpy()
+
+
 class Context:
     """One camera (sec. 2.3) with its device work buffers."""
 
@@ -254,9 +262,18 @@ class Context:
         self._check(st, "raptor_render_ex")
         return image, fl
 
-    def render_host(self, freqs, t_obs=0.0, want_image=True, stream=None):
+    def render_host(self, freqs, t_obs=0.0, want_image=True, stream=None, out=None):
+        """Render into host memory: (image, flux).  `out`, if given, is a C-contiguous float64
+        host array of shape (n_freq, ny, nx) that receives the image (page-locked memory from
+        pinned_host_array makes the copy a direct DMA); otherwise a new array is returned."""
         nu = _freqs(freqs)
-        img = np.zeros((nu.size, self.cam.ny, self.cam.nx)) if want_image else None
+        if out is not None:
+            shape = (nu.size, self.cam.ny, self.cam.nx)
+            if out.dtype != np.float64 or tuple(out.shape) != shape or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a C-contiguous float64 array of shape %s" % (shape,))
+            img = out
+        else:
+            img = np.zeros((nu.size, self.cam.ny, self.cam.nx)) if want_image else None
         fl = np.zeros(nu.size)
         st = lib().raptor_render_host(self._h, _dp(nu), nu.size, float(t_obs), _dp(img) if want_image else None, _dp(fl),
                                       _stream(stream))

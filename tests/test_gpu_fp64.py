@@ -102,6 +102,28 @@ def test_row_window_equals_full_image(R):
     assert np.array_equal(part[0], full[0, 11:18])
 
 
+def test_render_host_equals_device_render(R):
+    """raptor_render_host (the end-to-end entry point: host image and flux) returns the device
+    render's image and flux bit for bit, into a new array or into a given page-locked one;
+    a wrong `out` is refused before anything runs."""
+    import torch
+
+    cam = dict(scenes.SMALL, nx=40, ny=24)
+    freqs = [1e10, 230e9]
+    ctx = _ctx(R, cam)
+    img, fl = ctx.render(freqs)
+    torch.cuda.synchronize()
+    h, hfl = ctx.render_host(freqs)
+    assert np.array_equal(h, img.cpu().numpy()) and np.array_equal(hfl, fl)
+    out = R.pinned_host_array((2, 24, 40))
+    out[:] = np.nan
+    h2, hfl2 = ctx.render_host(freqs, out=out)
+    assert h2 is out and np.array_equal(out, h) and np.array_equal(hfl2, fl)
+    for bad in (np.zeros((2, 24, 41)), np.zeros((2, 24, 40), np.float32), np.zeros((40, 24, 2)).transpose(2, 1, 0)):
+        with pytest.raises(ValueError):
+            ctx.render_host(freqs, out=bad)
+
+
 def test_single_pixel_and_many_frequencies(R, ora):
     """Degenerate sizes: one pixel; 20 frequencies (two frequency chunks of the kernel)."""
     cam = dict(scenes.SMALL, nx=1, ny=1, alpha_min=4.0, alpha_max=4.5, beta_min=1.0, beta_max=1.5)
