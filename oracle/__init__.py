@@ -28,6 +28,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 KIND_ANALYTIC, KIND_GRID, KIND_STATIC_ISO, KIND_BALL = 0, 1, 2, 3
 ESCAPED, CAPTURED, THICK, TRUNCATED, ERROR = 0, 1, 2, 3, 4
 DISK_HIT, DISK_NO_HIT = 5, 6
+CROSSINGS_MAX = 7
 RK4, VERLET, VERLET_REEVAL = 0, 1, 2
 
 
@@ -94,6 +95,7 @@ def lib():
             "ora_render": (I, [sp, dp, I, D, I, I, dp, ip, ip, I]),
             "ora_disk_ray": (I, [sp, D, D, D, D, D, I, dp]),
             "ora_disk_render": (I, [sp, D, D, D, I, dp, dp, ip, ip, ip, I]),
+            "ora_disk_crossings": (I, [sp, D, D, I, dp, dp, dp, ip, ip]),
             "ora_length_unit_cm": (D, [D]),
             "ora_num_threads": (I, []),
         }
@@ -282,6 +284,17 @@ def disk_ray(s, alpha, beta, r_in=0.0, r_out=15.0, q=2.0, max_cross=10):
     st = lib().ora_disk_ray(C.byref(s), alpha, beta, r_in, r_out, q, max_cross, _dp(out))
     return dict(status=st, ratio=out[0], I=out[1], order=int(out[2]), r=out[3], theta=out[4], g=out[5],
                 steps=int(out[6]))
+
+
+def disk_crossings(s, alpha, beta, max_n=4):
+    """Ordered equatorial crossings of one ray (the thin disk's geometry without the disk):
+    dict(r, lam, t: arrays of the crossings found, fate: ESCAPED, CAPTURED, TRUNCATED, ERROR
+    or CROSSINGS_MAX, steps)."""
+    r = np.zeros(max(max_n, 1)); lam = np.zeros_like(r); t = np.zeros_like(r)
+    fate = C.c_int(0); steps = C.c_int(0)
+    n = lib().ora_disk_crossings(C.byref(s), alpha, beta, int(max_n), _dp(r), _dp(lam), _dp(t), C.byref(fate),
+                                 C.byref(steps))
+    return dict(r=r[:n].copy(), lam=lam[:n].copy(), t=t[:n].copy(), fate=fate.value, steps=steps.value)
 
 
 def disk_render(s, r_in=0.0, r_out=15.0, q=2.0, max_cross=10, nthreads=0):

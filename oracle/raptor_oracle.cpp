@@ -969,6 +969,60 @@ int ora_disk_ray(const OraScene* s, double alpha, double beta, double r_in, doub
     return status;
 }
 
+// Ordered equatorial crossings of one ray (the thin disk's geometry, sec. 4.2.1, without the
+// disk): the ray is traced from the camera as in ora_disk_ray, and every crossing of
+// theta = pi/2 is refined by the same Newton iteration on the RK4 step length; its radius,
+// coordinate time and affine length from the camera (the sum of the accepted steps before it
+// plus the refined step) are recorded, up to max_n crossings.  The trace continues from the
+// unrefined step end (crossings change nothing on the ray) until capture, escape, the step
+// cap or the max_n-th crossing.  Returns the number of crossings found; *fate gets 0 escaped,
+// 1 captured, 3 truncated, 4 error, 7 stopped at the max_n-th crossing.
+int ora_disk_crossings(const OraScene* s, double alpha, double beta, int max_n, double* r_out, double* lam_out,
+                       double* t_out, int* fate, int* steps) {
+    const double half_pi = 0.5 * O_PI;
+    double x[4], k[4];
+    ora_camera(s, alpha, beta, 0.0, x, k);
+    const double r_stop = s->r_stop_factor * horizon(s);
+    int n = 0, found = 0, status = 3;
+    double lam = 0.0;
+    while (n < s->max_steps) {
+        const double dl = step_size(s, x, k);
+        double xn[4], kn[4];
+        for (int i = 0; i < 4; ++i) { xn[i] = x[i]; kn[i] = k[i]; }
+        rk4_step(s, xn, kn, dl);
+        ++n;
+        bool finite = true;
+        for (int i = 0; i < 4; ++i) finite = finite && std::isfinite(xn[i]) && std::isfinite(kn[i]);
+        if (!finite) { status = 4; break; }
+        if ((x[2] - half_pi) * (xn[2] - half_pi) <= 0.0 && x[2] != half_pi) {
+            // the refined step length: the Newton iteration of disk_crossing, repeated here
+            // so that the length itself is available
+            double h = dl * (half_pi - x[2]) / (xn[2] - x[2]);
+            double xc[4], kc[4];
+            for (int it = 0; it < 4; ++it) {
+                for (int i = 0; i < 4; ++i) { xc[i] = x[i]; kc[i] = k[i]; }
+                rk4_step(s, xc, kc, h);
+                if (!(std::fabs(kc[2]) > 0.0)) break;
+                h -= (xc[2] - half_pi) / kc[2];
+            }
+            for (int i = 0; i < 4; ++i) { xc[i] = x[i]; kc[i] = k[i]; }
+            rk4_step(s, xc, kc, h);
+            r_out[found] = xc[1];
+            lam_out[found] = lam + h;
+            t_out[found] = xc[0];
+            found += 1;
+            if (found >= max_n) { status = 7; break; }
+        }
+        lam += dl;
+        for (int i = 0; i < 4; ++i) { x[i] = xn[i]; k[i] = kn[i]; }
+        if (x[1] < r_stop) { status = 1; break; }
+        if (x[1] > s->r_esc) { status = 0; break; }
+    }
+    *fate = status;
+    *steps = n;
+    return found;
+}
+
 // Disk image: per pixel (centres as in ora_render) E_obs/E_em, I, hit order, status and
 // steps (0 where the ray does not hit the disk), OpenMP over pixels.
 int ora_disk_render(const OraScene* s, double r_in, double r_out, double q, int max_cross, double* ratio,
