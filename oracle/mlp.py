@@ -89,3 +89,97 @@ def predict(P, x):
     p = unpack(P)
     out, _ = forward(P, x)
     return out[:, :USED] * p["sd"][:USED] + p["mu"][:USED]
+
+
+# ---------------------------------------------------------------------------------------
+# Crossing network: the same hidden layers with 16 outputs, four per equatorial crossing
+# n = 0..3 of the ray (sec. 4.2.1's plane theta = pi/2): a presence logit, ln r_n, the affine
+# length since the previous crossing (the first one against the straight line's length to
+# the plane) and E_obs/E_em of a Keplerian emitter there.  Flat layout as above with OUT = 16
+# and 40 normalisation constants (input scale[4], shift[4], output mean[16], std[16]).
+# Loss per row and output, averaged over rows x 16: presence entries (o % 4 == 0, target 0
+# or 1) the logistic loss log(1 + e^z) - y z; the others (z - (y - mu)/sigma)^2, or nothing
+# where the target is NaN (an absent crossing, or a radius inside the ISCO for the ratio).
+# ---------------------------------------------------------------------------------------
+XOUT = 16
+XW4 = B3 + HID
+XB4 = XW4 + XOUT * HID
+XNORM = XB4 + XOUT
+XSIZE = XNORM + 8 + 2 * XOUT
+
+
+def x_unpack(P):
+    P = np.asarray(P, dtype=np.float64)
+    return dict(W1=P[W1:B1].reshape(HID, IN), b1=P[B1:W2], W2=P[W2:B2].reshape(HID, HID), b2=P[B2:W3],
+                W3=P[W3:B3].reshape(HID, HID), b3=P[B3:XW4], W4=P[XW4:XB4].reshape(XOUT, HID), b4=P[XB4:XNORM],
+                scale=P[XNORM:XNORM + 4], shift=P[XNORM + 4:XNORM + 8], mu=P[XNORM + 8:XNORM + 8 + XOUT],
+                sd=P[XNORM + 8 + XOUT:XSIZE])
+
+
+def x_forward(P, x):
+    """Normalised outputs [rows][16] and the intermediates of the backward pass."""
+    p = x_unpack(P)
+    xn = (np.asarray(x, np.float64) - p["shift"]) * p["scale"]
+    z1 = xn @ p["W1"].T + p["b1"]
+    h1 = silu(z1)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = silu(z2)
+    z3 = h2 @ p["W3"].T + p["b3"]
+    h3 = silu(z3)
+    out = h3 @ p["W4"].T + p["b4"]
+    return out, dict(xn=xn, z1=z1, h1=h1, z2=z2, h2=h2, z3=z3, h3=h3)
+
+
+def _x_terms(p, out, y):
+    """Per-entry loss and its derivative with respect to the output."""
+    y = np.asarray(y, np.float64)
+    pres = (np.arange(XOUT) % 4 == 0)[None, :]
+    yn = np.where(pres, y, (y - p["mu"]) / p["sd"])
+    valid = ~np.isnan(yn)
+    ys = np.where(valid, yn, 0.0)
+    sig = 1.0 / (1.0 + np.exp(-out))
+    l_pres = np.logaddexp(0.0, out) - ys * out
+    l_reg = (out - ys) ** 2
+    l = np.where(valid, np.where(pres, l_pres, l_reg), 0.0)
+    d = np.where(valid, np.where(pres, sig - ys, 2.0 * (out - ys)), 0.0)
+    return l, d
+
+
+def x_loss(P, x, y):
+    p = x_unpack(P)
+    out, _ = x_forward(P, x)
+    l, _ = _x_terms(p, out, y)
+    return float(l.sum() / l.size)
+
+
+def x_grad(P, x, y):
+    """Gradient of x_loss() with respect to every weight and bias (flat, length XNORM)."""
+    p = x_unpack(P)
+    out, c = x_forward(P, x)
+    _, d = _x_terms(p, out, y)
+    dout = d / d.size
+    g = np.zeros(XNORM)
+    g[XW4:XB4] = (dout.T @ c["h3"]).ravel()
+    g[XB4:XNORM] = dout.sum(0)
+    dz3 = (dout @ p["W4"]) * dsilu(c["z3"])
+    g[W3:B3] = (dz3.T @ c["h2"]).ravel()
+    g[B3:XW4] = dz3.sum(0)
+    dz2 = (dz3 @ p["W3"]) * dsilu(c["z2"])
+    g[W2:B2] = (dz2.T @ c["h1"]).ravel()
+    g[B2:W3] = dz2.sum(0)
+    dz1 = (dz2 @ p["W2"]) * dsilu(c["z1"])
+    g[W1:B1] = (dz1.T @ c["xn"]).ravel()
+    g[B1:W2] = dz1.sum(0)
+    return g
+
+
+def x_predict(P, x):
+    """Decoded predictions [rows][16]: per crossing the presence probability, r, the affine
+    length term and E_obs/E_em (un-normalised; r = exp of the ln r output)."""
+    p = x_unpack(P)
+    out, _ = x_forward(P, x)
+    v = out * p["sd"] + p["mu"]
+    res = v.copy()
+    res[:, 0::4] = 1.0 / (1.0 + np.exp(-out[:, 0::4]))
+    res[:, 1::4] = np.exp(v[:, 1::4])
+    return res
