@@ -363,6 +363,102 @@ def _disk_extra(R, torch, stream, fma64, reps=2):
     return out
 
 
+def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
+    """The surrogate's equatorial outputs: a crossing network (4 -> 256 -> 256 -> 256 -> 16)
+    trained on n_train integrator rays over the learned workload's range, its held-out
+    accuracy, and the learned thin disk against the FP64 disk at 1024^2 (i = 30 deg, +-16 M)
+    for the disk workload's spins inside the training range.  Network roofline: its
+    algorithmic flops (2 x (4 x 256 + 2 x 256^2 + 256 x 16) per ray) over its profiled time
+    against the measured BF16 peak."""
+    from paper_1801_10452_b300 import scenes
+
+    cam_t = dict(scenes.SMALL)
+    ctx = R.Context(R.camera_desc(**cam_t))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, y = ctx.crossings_generate(n_train, seed=0x1801104520000005)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    ctx.crossings_init(y, seed=7)
+    t1 = time.perf_counter()
+    ctx.crossings_train(x, y, steps, lr=2e-3, lr_final=2e-5, seed=11)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    del x, y
+    P = ctx.crossings_get()
+    xh, _, zh = ctx.crossings_generate(100_000, seed=0x1801104520000006, raw=True)
+    ph = ctx.crossings_eval(xh).cpu().numpy()
+    zh = zh.cpu().numpy()
+    pres_t, pres_p = zh[:, 0::4] > 0.5, ph[:, 0::4] > 0.5
+    both = pres_t & pres_p
+    rel_r = np.abs(ph[:, 1::4][both] / zh[:, 1::4][both] - 1)
+    rel_l = np.abs(ph[:, 2::4][both] / zh[:, 2::4][both] - 1)
+    rat = both & np.isfinite(zh[:, 3::4]) & (zh[:, 1::4] >= 6.0)
+    rel_g = np.abs(ph[:, 3::4][rat] / zh[:, 3::4][rat] - 1)
+    out = {"training": {"rays": n_train, "steps": steps, "batch": 4096, "generate_s": t_gen, "train_s": t_train,
+                        "range": "alpha, beta in +-20 M; a in [0, 0.99]; i in [5, 85] deg",
+                        "heldout_rays": 100_000,
+                        "heldout_count_accuracy": float(np.mean(np.all(pres_t == pres_p, axis=1))),
+                        "heldout_r_rel_err_median": float(np.median(rel_r)),
+                        "heldout_r_rel_err_p99": float(np.quantile(rel_r, 0.99)),
+                        "heldout_lambda_rel_err_p99": float(np.quantile(rel_l, 0.99)),
+                        "heldout_ratio_rel_err_median_r_ge_6": float(np.median(rel_g)),
+                        "heldout_ratio_rel_err_p99_r_ge_6": float(np.quantile(rel_g, 0.99)),
+                        "note": "held-out rays over the whole range, critical-curve band included"}}
+    ctx.close()
+    flops_ray = 2 * (4 * 256 + 2 * 256 * 256 + 256 * 16)
+    cam0 = scenes.THIN_DISK
+    out["workload"] = f"learned_thin_disk_{cam0['nx']}x{cam0['ny']}_i{cam0['incl_deg']:g}_rin_isco_rout15_q2"
+    out["per_spin"] = {}
+    for a in [v for v in scenes.THIN_DISK_SPINS if 0.0 <= v <= 0.99]:
+        ctx = R.Context(R.camera_desc(**dict(cam0, spin=a)))
+        ctx.crossings_set(P)
+        res = {}
+        for learned in (False, True):
+            r = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream, learned=learned)
+            torch.cuda.synchronize()
+            ctx.profile(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                r = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream, learned=learned)
+            e1.record(stream)
+            e1.synchronize()
+            prof = ctx.profile_read()
+            ctx.profile(False)
+            res[learned] = (e0.elapsed_time(e1) / reps, {k: v.cpu().numpy() if hasattr(v, "cpu") else v
+                                                         for k, v in r.items()}, prof)
+        (ms_f, f, _), (ms_l, g, prof) = res[False], res[True]
+        fb = g["steps"] > 0
+        nb = ~fb
+        hit = nb & (f["order"] > 0) & (g["order"] == f["order"])
+        rel = np.abs(g["ratio"][hit] / f["ratio"][hit] - 1)
+        sf, sg = f["spectrum"], g["spectrum"]
+        rays = cam0["nx"] * cam0["ny"]
+        mlp_ms = prof["surrogate_mlp"][0] / reps
+        ach = flops_ray * rays / (mlp_ms * 1e-3) / 1e12
+        out["per_spin"][f"{a:g}"] = {
+            "ms_learned": ms_l, "ms_fp64": ms_f, "speedup": ms_f / ms_l, "rays_per_s_learned": rays / (ms_l * 1e-3),
+            "fallback_fraction": float(fb.mean()),
+            "order_agreement_outside_fallback": float((g["order"][nb] == f["order"][nb]).mean()),
+            "ratio_rel_err_max": float(rel.max()), "ratio_rel_err_p99": float(np.quantile(rel, 0.99)),
+            "pixels_compared": int(hit.sum()), "pixels_over_1e-2": int((rel > 1e-2).sum()),
+            "worst_pixel_alpha_beta": [float(cam0["alpha_min"] + (np.nonzero(hit)[1][np.argmax(rel)] + 0.5) *
+                                             (cam0["alpha_max"] - cam0["alpha_min"]) / cam0["nx"]),
+                                       float(cam0["beta_min"] + (np.nonzero(hit)[0][np.argmax(rel)] + 0.5) *
+                                             (cam0["beta_max"] - cam0["beta_min"]) / cam0["ny"])],
+            "spectrum_total_rel_err": float(sg.sum() / sf.sum() - 1),
+            "spectrum_l1_normalised": float(np.abs(sg / sg.sum() - sf / sf.sum()).sum()),
+            "stage_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
+            "network_roofline": {"bound": "tensor", "kernel": "k_mlp_fused<16> (mma.sync)", "achieved": ach,
+                                 "peak": bf16_peak, "unit": "TFLOP/s", "frac": ach / bf16_peak,
+                                 "flops_per_ray": flops_ray}}
+        ctx.close()
+    out["heldout_ratio_note"] = "held-out ratios compared where r >= 6 M (outside every prograde ISCO)"
+    return out
+
+
 def _verlet_extra(R, torch, stream, fma64, flush, reps=2):
     """The FP64 path with the velocity-Verlet integrator (sec. 2.2.2) on the headline image,
     with and without the re-evaluation, beside RK4, and RK4 with the forward formal-solution
@@ -529,6 +625,10 @@ def run_native(args):
     disk = None
     if not args.no_disk and rank == 0:
         disk = _disk_extra(R, torch, stream, R.measure_fma_peak(True))
+    ldisk = None
+    if not args.no_disk and not args.no_learned_disk and rank == 0:
+        ldisk = _learned_disk_extra(R, torch, stream, _peaks().get("bf16_tflops", 1800.0), args.train_steps,
+                                   args.train_rays)
     main = res[paths[0]]
     ms_step = main["ms"]
     value = aggregate_rate(world, rays_step, ms_step)
@@ -678,6 +778,7 @@ def run_native(args):
         "grid_workload": grid,
         "lightcurve_workload": lcurve,
         "thin_disk_workload": disk,
+        "learned_thin_disk_workload": ldisk,
         "verlet_workload": verlet,
         "emissivity_options": emis,
     }
@@ -732,6 +833,7 @@ def main():
     ap.add_argument("--no-grid", action="store_true", help="skip the grid (torus snapshot) workload")
     ap.add_argument("--no-lightcurve", action="store_true", help="skip the slow-light light-curve workload")
     ap.add_argument("--no-disk", action="store_true", help="skip the thin-disk line-emitter workload")
+    ap.add_argument("--no-learned-disk", action="store_true", help="skip the crossing network and the learned thin disk")
     ap.add_argument("--no-verlet", action="store_true", help="skip the FP64 velocity-Verlet workload")
     ap.add_argument("--no-emissivity", action="store_true", help="skip the exact-K2 / Theta_e-mask comparison")
     ap.add_argument("--train-steps", type=int, default=16000)

@@ -375,6 +375,61 @@ raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind);
  * outbound rays stop at r > r_exit in RAPTOR_MIXED_MLP (0 = off) [50]. */
 raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit);
 
+/* Learned equatorial crossings (the learned surrogate's thin-disk outputs; the geometry is
+ * sec. 4.2.1's disk plane theta = pi/2, the network has no counterpart in the paper).  A
+ * second network of the same shape (4 -> 256 -> 256 -> 256 -> 16, SiLU; BF16 hidden layers
+ * with FP32 accumulation, FP32 input and output layers) maps (alpha, beta, a, i in degrees)
+ * to the first four crossings n = 0..3 of the plane by the backward ray, four outputs each:
+ *   presence logit; ln r_n (for n = 0 relative to the straight camera ray's crossing radius,
+ *   flat space, FP32, as ln sqrt(r_flat^2 + 9)); lambda_n - lambda_{n-1}, lambda the affine
+ *   length from the camera (E = 1), lambda_{-1} the straight ray's length to the plane;
+ *   E_obs/E_em of a prograde Keplerian emitter at r_n (Eq. 30), trained for r_n >= r_isco.
+ *
+ * raptor_crossings_generate: n counter-based samples over the camera's field of view and the
+ * given spin and inclination ranges (0 < i < 90), inputs_dev (device float [n][4], rounded
+ * to FP32 before tracing) and targets_dev (device double [n][16]: presence 1/0; NaN for the
+ * regression entries of absent crossings and for ratios inside the ISCO), raw_dev (optional,
+ * device double [n][16]: per crossing presence, r_n, lambda_n, E_obs/E_em, NaN if absent).
+ * The targets come from the FP64 RK4 integrator with the camera's step rule, r_stop, r_escape
+ * and max_steps; every step that ends across the plane is refined by Newton's iteration on
+ * its length (as raptor_disk_render).  Asynchronous on `stream`.
+ * raptor_crossings_init / _train / _grad / _get / _set: as the raptor_surrogate_* calls, for
+ * this network (targets [n][16]; param count raptor_crossings_param_count()).  The loss is the
+ * mean over rows x 16 outputs of the logistic loss log(1 + e^z) - y z on the presence logits
+ * and the squared normalised error on the others, with NaN targets carrying no weight.
+ * raptor_crossings_eval: decoded predictions pred_dev (device double [n][16]) per crossing:
+ * presence probability, r_n, lambda_n, E_obs/E_em.  Asynchronous on `stream`.
+ * RAPTOR_EUNSUPPORTED before init or set; RAPTOR_EINVAL for bad sizes or ranges. */
+int raptor_crossings_param_count(void);
+raptor_status raptor_crossings_generate(raptor_ctx* ctx, long long n, unsigned long long seed, double spin_min,
+                                        double spin_max, double incl_min_deg, double incl_max_deg, float* inputs_dev,
+                                        double* targets_dev, double* raw_dev, void* stream);
+raptor_status raptor_crossings_init(raptor_ctx* ctx, const double* targets_dev, long long n, unsigned long long seed,
+                                    void* stream);
+raptor_status raptor_crossings_train(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                     int steps, double lr, double lr_final, unsigned long long seed, double* loss_host,
+                                     void* stream);
+raptor_status raptor_crossings_grad(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                    float* grad_host, double* loss_host, void* stream);
+raptor_status raptor_crossings_eval(raptor_ctx* ctx, const float* inputs_dev, long long n, double* pred_dev, void* stream);
+raptor_status raptor_crossings_get(raptor_ctx* ctx, float* params_host, int n);
+raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, int n);
+
+/* The thin disk of raptor_disk_render from the learned crossings (sec. 4.2.1): pixels whose
+ * centre lies outside the critical curve and its fallback band (raptor_surrogate_config)
+ * take the first predicted crossing (presence probability > 1/2, in order) with r_in <= r_n
+ * <= r_out: E_obs/E_em of the Keplerian emitter at the predicted r_n (closed form, exact given
+ * the radius: 1 / (u^t (1 - Omega L)), L = -alpha sin i), intensity (E_obs/E_em)^4 r_n^-q,
+ * order n + 1,
+ * status 5 (6 without a hit), steps 0; the other pixels are integrated exactly as in
+ * raptor_disk_render.  The network is valid inside the spin, inclination and field-of-view
+ * range of its training data; the caller keeps the camera there.  Same arguments and
+ * outputs; r_in must not lie inside the ISCO
+ * (RAPTOR_EUNSUPPORTED), nor may the crossing network be missing (RAPTOR_EUNSUPPORTED). */
+raptor_status raptor_disk_render_learned(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev,
+                                         double* intensity_dev, int* order_dev, int* status_dev, int* steps_dev,
+                                         double* profile_host, void* stream);
+
 /* Per-kernel device time, measured with CUDA events recorded around every kernel launch on
  * the launch's own stream.  raptor_profile(ctx, 1) clears the accumulators and starts
  * recording; raptor_profile(ctx, 0) stops.  raptor_profile_read waits for the recorded

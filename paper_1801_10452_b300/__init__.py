@@ -32,7 +32,9 @@ EXPORTS = [
     "raptor_render_noalloc", "raptor_autotune", "raptor_surrogate_param_count", "raptor_surrogate_generate",
     "raptor_surrogate_init", "raptor_surrogate_train", "raptor_surrogate_grad", "raptor_surrogate_eval",
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_save", "raptor_surrogate_load", "raptor_surrogate_config", "raptor_surrogate_kernel",
-    "raptor_disk_desc_default", "raptor_disk_render", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
+    "raptor_disk_desc_default", "raptor_disk_render", "raptor_disk_render_learned", "raptor_crossings_param_count",
+    "raptor_crossings_generate", "raptor_crossings_init", "raptor_crossings_train", "raptor_crossings_grad",
+    "raptor_crossings_eval", "raptor_crossings_get", "raptor_crossings_set", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp", "disk", "mixed_fp64_long"]
@@ -121,6 +123,15 @@ def lib():
             "raptor_surrogate_load": (st, [vp, C.c_char_p]),
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
+            "raptor_crossings_param_count": (C.c_int, []),
+            "raptor_crossings_generate": (st, [vp, C.c_longlong, C.c_ulonglong, C.c_double, C.c_double, C.c_double,
+                                               C.c_double, vp, vp, vp, vp]),
+            "raptor_crossings_init": (st, [vp, vp, C.c_longlong, C.c_ulonglong, vp]),
+            "raptor_crossings_train": (st, [vp, vp, vp, C.c_longlong, C.c_int, C.c_double, C.c_double, C.c_ulonglong, dp, vp]),
+            "raptor_crossings_grad": (st, [vp, vp, vp, C.c_longlong, C.POINTER(C.c_float), dp, vp]),
+            "raptor_crossings_eval": (st, [vp, vp, C.c_longlong, vp, vp]),
+            "raptor_crossings_get": (st, [vp, C.POINTER(C.c_float), C.c_int]),
+            "raptor_crossings_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
             "raptor_long_config": (st, [vp, C.c_int, C.c_int, C.c_void_p]),
             "raptor_profile_timeline": (st, [vp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -341,11 +352,12 @@ class Context:
         return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(k)}
 
     def disk_render(self, r_in=0.0, r_out=15.0, q=2.0, max_cross=10, profile_order=1, n_bins=64, x_range=(0.2, 1.6),
-                    spectrum=True, stream=None):
+                    spectrum=True, stream=None, learned=False):
         """Thin-disk line emitter (sec. 4.2.1) with this context's camera, in FP64: per pixel
         E_obs/E_em, line intensity and hit order (device tensors [ny][nx]), status and steps,
         and the line spectrum (host array [n_bins], None without `spectrum`) with its bin
-        edges."""
+        edges.  `learned`: from the crossing network outside the critical curve's fallback
+        band (raptor_disk_render_learned)."""
         import torch
 
         d = DiskDesc()
@@ -359,10 +371,10 @@ class Context:
         status = torch.empty_like(order)
         steps = torch.empty_like(order)
         prof = np.zeros(max(1, n_bins)) if spectrum else None
-        self._check(lib().raptor_disk_render(self._h, C.byref(d), C.c_void_p(ratio.data_ptr()),
-                                             C.c_void_p(inten.data_ptr()), C.c_void_p(order.data_ptr()),
-                                             C.c_void_p(status.data_ptr()), C.c_void_p(steps.data_ptr()),
-                                             _dp(prof) if spectrum else None, _stream(stream)), "raptor_disk_render")
+        fn = "raptor_disk_render_learned" if learned else "raptor_disk_render"
+        self._check(getattr(lib(), fn)(self._h, C.byref(d), C.c_void_p(ratio.data_ptr()), C.c_void_p(inten.data_ptr()),
+                                       C.c_void_p(order.data_ptr()), C.c_void_p(status.data_ptr()),
+                                       C.c_void_p(steps.data_ptr()), _dp(prof) if spectrum else None, _stream(stream)), fn)
         edges = np.linspace(x_range[0], x_range[1], n_bins + 1)
         return dict(ratio=ratio, intensity=inten, order=order, status=status, steps=steps,
                     spectrum=prof[:n_bins] if spectrum else None, edges=edges)
@@ -436,6 +448,65 @@ class Context:
     def surrogate_set(self, P):
         P = np.ascontiguousarray(P, dtype=np.float32)
         self._check(lib().raptor_surrogate_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size), "raptor_surrogate_set")
+
+    # ---- crossing network (the surrogate's equatorial outputs) ---------------------------
+    def crossings_generate(self, n, seed=0x1801104520000005, spin=(0.0, 0.99), incl=(5.0, 85.0), raw=False,
+                           stream=None):
+        """Integrator-generated crossing set: (inputs float32 [n][4], targets float64 [n][16]
+        [, raw float64 [n][16]: per crossing presence, r, lambda, E_obs/E_em])."""
+        import torch
+
+        x = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        y = torch.empty((n, 16), dtype=torch.float64, device="cuda")
+        z = torch.empty((n, 16), dtype=torch.float64, device="cuda") if raw else None
+        self._check(lib().raptor_crossings_generate(self._h, int(n), int(seed), float(spin[0]), float(spin[1]),
+                                                    float(incl[0]), float(incl[1]), C.c_void_p(x.data_ptr()),
+                                                    C.c_void_p(y.data_ptr()), C.c_void_p(z.data_ptr()) if raw else None,
+                                                    _stream(stream)), "raptor_crossings_generate")
+        return (x, y, z) if raw else (x, y)
+
+    def crossings_init(self, targets, seed=7, stream=None):
+        self._check(lib().raptor_crossings_init(self._h, C.c_void_p(targets.data_ptr()), int(targets.shape[0]), int(seed),
+                                                _stream(stream)), "raptor_crossings_init")
+
+    def crossings_train(self, inputs, targets, steps, lr=2e-3, lr_final=2e-5, seed=11, record_loss=False, stream=None):
+        loss = np.zeros(steps) if record_loss else None
+        self._check(lib().raptor_crossings_train(self._h, C.c_void_p(inputs.data_ptr()), C.c_void_p(targets.data_ptr()),
+                                                 int(inputs.shape[0]), int(steps), float(lr), float(lr_final), int(seed),
+                                                 _dp(loss) if record_loss else None, _stream(stream)),
+                    "raptor_crossings_train")
+        return loss
+
+    def crossings_grad(self, inputs, targets, stream=None):
+        """(gradient float32 [param_count - 40], loss) of one batch (a multiple of 128 rows)."""
+        n = lib().raptor_crossings_param_count() - 40
+        g = np.zeros(n, dtype=np.float32)
+        L = C.c_double(0.0)
+        self._check(lib().raptor_crossings_grad(self._h, C.c_void_p(inputs.data_ptr()), C.c_void_p(targets.data_ptr()),
+                                                int(inputs.shape[0]), g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(L),
+                                                _stream(stream)), "raptor_crossings_grad")
+        return g, L.value
+
+    def crossings_eval(self, inputs, stream=None):
+        """Decoded predictions float64 [n][16]: per crossing presence probability, r, lambda,
+        E_obs/E_em."""
+        import torch
+
+        pred = torch.empty((inputs.shape[0], 16), dtype=torch.float64, device="cuda")
+        self._check(lib().raptor_crossings_eval(self._h, C.c_void_p(inputs.data_ptr()), int(inputs.shape[0]),
+                                                C.c_void_p(pred.data_ptr()), _stream(stream)), "raptor_crossings_eval")
+        return pred
+
+    def crossings_get(self):
+        n = lib().raptor_crossings_param_count()
+        P = np.zeros(n, dtype=np.float32)
+        self._check(lib().raptor_crossings_get(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), n), "raptor_crossings_get")
+        return P
+
+    def crossings_set(self, P):
+        P = np.ascontiguousarray(P, dtype=np.float32)
+        self._check(lib().raptor_crossings_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size),
+                    "raptor_crossings_set")
 
     def long_config(self, threads_per_block=0, budgets=None):
         """Schedule of the near-critical rays' FP64 phase on the second stream: block size

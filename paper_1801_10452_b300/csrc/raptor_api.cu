@@ -19,6 +19,7 @@
 #include "raptor_kernels_mixed.cuh"
 #include "raptor_surrogate.cuh"
 #include "raptor_mlp_tc.cuh"
+#include "raptor_crossings.cuh"
 
 using namespace raptor;
 
@@ -101,6 +102,16 @@ struct raptor_ctx {
     size_t s_ray_cap = 0;
     double s_band = 0.5, s_r_exit = 50.0;
     unsigned long long s_step = 0;   // Adam step counter
+    // crossing network (the surrogate's equatorial outputs); shares the work buffers above
+    bool x_ready = false;
+    float *x_P = nullptr, *x_G = nullptr, *x_m1 = nullptr, *x_m2 = nullptr;  // XLayout::SIZE each
+    __nv_bfloat16* x_w = nullptr;    // w2, w2t, w3, w3t
+    float *x_out = nullptr, *x_dout = nullptr;  // [rows][16]
+    double* x_y = nullptr;           // [rows][16]
+    unsigned long long x_step = 0;
+    int* x_list = nullptr;           // learned disk: fallback pixels
+    unsigned int* x_nlist = nullptr;
+    size_t x_list_cap = 0;
     // per-kernel CUDA-event timing (raptor_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -609,6 +620,7 @@ cudaError_t launch_mixed(raptor_ctx* c, const Params& p, cudaStream_t s, bool su
 }
 
 raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t s);
+raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, cudaStream_t s);
 raptor_status check_tc_err(raptor_ctx* ctx);
 
 // Enqueue every ray of `p` (all frequency chunks), then the flux reduction of `planes`
@@ -936,8 +948,9 @@ raptor_status raptor_disk_desc_default(raptor_disk_desc* d) {
     return RAPTOR_OK;
 }
 
-raptor_status raptor_disk_render(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev, double* intensity_dev,
-                                 int* order_dev, int* status_dev, int* steps_dev, double* profile_host, void* stream) {
+static raptor_status disk_render_impl(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev, double* intensity_dev,
+                                      int* order_dev, int* status_dev, int* steps_dev, double* profile_host, void* stream,
+                                      bool learned) {
     if (!ctx) return RAPTOR_EINVAL;
     ctx->err.clear();
     if (!d) return fail(ctx, RAPTOR_EINVAL, "disk descriptor is NULL");
@@ -970,6 +983,10 @@ raptor_status raptor_disk_render(raptor_ctx* ctx, const raptor_disk_desc* d, dou
     a.order = order_dev;
     a.status = status_dev;
     a.steps = steps_dev;
+    if (learned) {
+        const raptor_status ls = disk_learned_stage(ctx, p, a, s);
+        if (ls != RAPTOR_OK) return ls;
+    }
     RCK(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s));
     int occ = 0;
     RCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disk_fp64, ctx->launch_block, 0));
@@ -1000,6 +1017,17 @@ raptor_status raptor_disk_render(raptor_ctx* ctx, const raptor_disk_desc* d, dou
     RCK(cudaStreamSynchronize(s));
     for (int b = 0; b < d->n_bins; ++b) profile_host[b] = (double)h[b] / scale;
     return RAPTOR_OK;
+}
+
+raptor_status raptor_disk_render(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev, double* intensity_dev,
+                                 int* order_dev, int* status_dev, int* steps_dev, double* profile_host, void* stream) {
+    return disk_render_impl(ctx, d, ratio_dev, intensity_dev, order_dev, status_dev, steps_dev, profile_host, stream, false);
+}
+
+raptor_status raptor_disk_render_learned(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev,
+                                         double* intensity_dev, int* order_dev, int* status_dev, int* steps_dev,
+                                         double* profile_host, void* stream) {
+    return disk_render_impl(ctx, d, ratio_dev, intensity_dev, order_dev, status_dev, steps_dev, profile_host, stream, true);
 }
 
 raptor_status raptor_render_host(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, double* image_host,
@@ -1176,7 +1204,8 @@ void raptor_destroy(raptor_ctx* ctx) {
     void* sp[] = {ctx->s_P, ctx->s_G, ctx->s_m1, ctx->s_m2, ctx->s_w, ctx->s_x, ctx->s_z1, ctx->s_z2, ctx->s_z3,
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
                   ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
-                  ctx->d_crit, ctx->d_rest, ctx->d_hist, ctx->d_fwd, ctx->d_x2tab};
+                  ctx->d_crit, ctx->d_rest, ctx->d_hist, ctx->d_fwd, ctx->d_x2tab, ctx->x_P, ctx->x_G, ctx->x_m1,
+                  ctx->x_m2, ctx->x_w, ctx->x_out, ctx->x_dout, ctx->x_y, ctx->x_list, ctx->x_nlist};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.a);
@@ -2036,6 +2065,353 @@ raptor_status raptor_measure_fma_peak(int fp64, double* tflops) {
     cudaFree(out);
     if (e != cudaSuccess) return RAPTOR_ECUDA;
     *tflops = 2.0 * 16.0 * iters * (double)threads * blocks / (best * 1e-3) / 1e12;
+    return RAPTOR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Crossing network: the learned surrogate's equatorial outputs (raptor_crossings.cuh).  The
+// same hidden layers and kernels as the state network with a 16-wide output layer; it uses
+// the state network's work buffers (sur_alloc) and its own parameters and output buffers.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+cudaError_t x_alloc(raptor_ctx* c) {
+    cudaError_t e = sur_alloc(c);
+    if (e != cudaSuccess) return e;
+    if (!c->x_P) {
+        const size_t n = XLayout::SIZE;
+        float** f[] = {&c->x_P, &c->x_G, &c->x_m1, &c->x_m2};
+        for (float** q : f)
+            if (e == cudaSuccess) e = cudaMalloc((void**)q, n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_w, 4 * kHid * kHid * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_out, kSurRows * kXOut * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_dout, kSurRows * kXOut * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_y, kSurRows * kXOut * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemset(c->x_G, 0, n * sizeof(float));
+    }
+    return e;
+}
+
+__nv_bfloat16* xw(raptor_ctx* c, int i) { return c->x_w + (size_t)i * kHid * kHid; }  // w2, w2t, w3, w3t
+
+cudaError_t x_refresh(raptor_ctx* c, cudaStream_t s) {
+    k_refresh_bf16<<<256, 256, 0, s>>>(c->x_P, xw(c, 0), xw(c, 1), xw(c, 2), xw(c, 3));
+    return cudaGetLastError();
+}
+
+// Forward pass of the crossing network on `rows` rows in c->s_x.
+cudaError_t x_forward(raptor_ctx* c, long long rows, cudaStream_t s) {
+    k_mlp_layer1<kXOut><<<ew_blocks(rows * kHid), 256, 0, s>>>(c->x_P, c->s_x, rows, rows, c->s_z1, c->s_h1);
+    dim3 g(kHid / kGBN, (unsigned)(rows / kGBM));
+    k_gemm_bf16<true, true><<<g, 256, 0, s>>>(c->s_h1, kHid, xw(c, 0), kHid, c->s_z2, kHid, rows, kHid, kHid);
+    k_bias_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_z2, c->x_P + XLayout::B2, rows, c->s_h2);
+    k_gemm_bf16<true, true><<<g, 256, 0, s>>>(c->s_h2, kHid, xw(c, 2), kHid, c->s_z3, kHid, rows, kHid, kHid);
+    k_bias_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_z3, c->x_P + XLayout::B3, rows, c->s_h3);
+    k_mlp_layer4<kXOut><<<ew_blocks(rows * 32), 256, 0, s>>>(c->x_P, c->s_h3, rows, c->x_out);
+    return cudaGetLastError();
+}
+
+// Loss and gradient of the batch in (s_x, x_y) into x_G; loss partials in s_loss[0..nb).
+cudaError_t x_backward(raptor_ctx* c, long long rows, int* nb_out, cudaStream_t s) {
+    const int nb = 64;
+    *nb_out = nb;
+    float* G = c->x_G;
+    k_cross_grad<<<nb, 256, 0, s>>>(c->x_P, c->x_out, c->x_y, rows, c->x_dout, c->s_loss);
+    k_colred<float, __nv_bfloat16><<<kXOut * kHid, 256, 0, s>>>(c->x_dout, kXOut, c->s_h3, kHid, rows, kXOut, kHid,
+                                                                  G + XLayout::W4);
+    k_colred<float, float><<<kXOut, 256, 0, s>>>(nullptr, 0, c->x_dout, kXOut, rows, 1, kXOut, G + XLayout::B4);
+    k_back_layer4<kXOut><<<ew_blocks(rows * kHid), 256, 0, s>>>(c->x_P, c->x_dout, c->s_z3, rows, c->s_dzf, c->s_dzb);
+    dim3 gw(kHid / kGBN, kHid / kGBM), ga(kHid / kGBN, (unsigned)(rows / kGBM));
+    k_gemm_bf16<false, false><<<gw, 256, 0, s>>>(c->s_dzb, kHid, c->s_h2, kHid, G + XLayout::W3, kHid, kHid, kHid, rows);
+    k_colred<float, float><<<kHid, 256, 0, s>>>(nullptr, 0, c->s_dzf, kHid, rows, 1, kHid, G + XLayout::B3);
+    k_gemm_bf16<true, true><<<ga, 256, 0, s>>>(c->s_dzb, kHid, xw(c, 3), kHid, c->s_dh, kHid, rows, kHid, kHid);
+    k_back_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_dh, c->s_z2, rows * kHid, c->s_dzf, c->s_dzb);
+    k_gemm_bf16<false, false><<<gw, 256, 0, s>>>(c->s_dzb, kHid, c->s_h1, kHid, G + XLayout::W2, kHid, kHid, kHid, rows);
+    k_colred<float, float><<<kHid, 256, 0, s>>>(nullptr, 0, c->s_dzf, kHid, rows, 1, kHid, G + XLayout::B2);
+    k_gemm_bf16<true, true><<<ga, 256, 0, s>>>(c->s_dzb, kHid, xw(c, 1), kHid, c->s_dh, kHid, rows, kHid, kHid);
+    k_back_silu<<<ew_blocks(rows * kHid), 256, 0, s>>>(c->s_dh, c->s_z1, rows * kHid, c->s_dzf, nullptr);
+    k_grad_w1<kXOut><<<kHid * kIn, 256, 0, s>>>(c->x_P, c->s_dzf, c->s_x, rows, G);
+    k_colred<float, float><<<kHid, 256, 0, s>>>(nullptr, 0, c->s_dzf, kHid, rows, 1, kHid, G + XLayout::B1);
+    return cudaGetLastError();
+}
+
+// Network outputs [n][16] (normalised) of n raw input rows: the fused mma.sync kernel.
+cudaError_t x_eval_rows(raptor_ctx* c, const float* inputs, long long n, float* out, cudaStream_t s) {
+    const long long blocks = (n + kFRows - 1) / kFRows;
+    k_mlp_fused<kXOut><<<(unsigned)blocks, 256, 0, s>>>(c->x_P, xw(c, 0), xw(c, 2), inputs, n, out);
+    return cudaGetLastError();
+}
+
+double sum_parts(raptor_ctx* c, int nb, cudaStream_t s, cudaError_t* e) {
+    double parts[64];
+    *e = cudaMemcpyAsync(parts, c->s_loss, nb * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (*e == cudaSuccess) *e = cudaStreamSynchronize(s);
+    double L = 0.0;
+    for (int q = 0; q < nb; ++q) L += parts[q];
+    return L;
+}
+
+}  // namespace
+
+namespace {
+
+// The learned part of a thin-disk image (raptor_disk_render_learned): network inputs and
+// fallback flags per pixel (k_surrogate_prepare, the critical curve of the camera's spin and
+// inclination), the crossing network, the decoded hits of the pixels outside the fallback
+// set, and the list of the others, which k_disk_fp64 then integrates (a.list).
+raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, cudaStream_t s) {
+    if (!ctx->x_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "the learned disk needs a trained crossing network");
+    if (a.r_in < r_isco_prograde(ctx->cam.spin) * (1.0 - 1e-12))
+        return fail(ctx, RAPTOR_EUNSUPPORTED, "the learned disk starts at or outside the ISCO (its ratios are trained there)");
+    const size_t n = (size_t)p.n_rays;
+    if (ctx->s_ray_cap < n) {
+        ctx->epoch += 1;
+        cudaFree(ctx->s_in);
+        cudaFree(ctx->s_fb);
+        cudaFree(ctx->s_start);
+        ctx->s_in = nullptr;
+        ctx->s_fb = nullptr;
+        ctx->s_start = nullptr;
+        ctx->s_ray_cap = 0;
+        RCK(cudaMalloc((void**)&ctx->s_in, n * kIn * sizeof(float)));
+        RCK(cudaMalloc((void**)&ctx->s_fb, n));
+        RCK(cudaMalloc((void**)&ctx->s_start, n * 8 * sizeof(float2)));
+        ctx->s_ray_cap = n;
+    }
+    if (ctx->x_list_cap < n) {
+        cudaFree(ctx->x_list);
+        ctx->x_list = nullptr;
+        ctx->x_list_cap = 0;
+        RCK(cudaMalloc((void**)&ctx->x_list, n * sizeof(int)));
+        ctx->x_list_cap = n;
+    }
+    if (!ctx->x_nlist) RCK(cudaMalloc((void**)&ctx->x_nlist, sizeof(unsigned int)));
+    RCK(upload_curve(ctx, p, s));
+    const float grow = (float)ctx->s_band + 1e-3f;
+    const float4 box = make_float4(ctx->curve_box.x - grow, ctx->curve_box.y + grow, ctx->curve_box.z - grow,
+                                   ctx->curve_box.w + grow);
+    float* out = nullptr;
+    RCK(cudaMallocAsync((void**)&out, n * kXOut * sizeof(float), s));
+    cudaError_t e = cudaSuccess;
+    {
+        ProfScope ps(ctx, kProfSurrogate, s, 2);
+        k_surrogate_prepare<<<ew_blocks((long long)n), 256, 0, s>>>(p, ctx->d_curve, ctx->n_curve, (float)ctx->s_band, box,
+                                                                    ctx->s_in, ctx->s_fb);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            ProfScope pm(ctx, kProfSurrogateMlp, s);
+            e = x_eval_rows(ctx, ctx->s_in, (long long)n, out, s);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->x_list, 0xFF, n * sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->x_nlist, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) {
+            k_disk_learned<<<ew_blocks((long long)n), 256, 0, s>>>(p, a, ctx->x_P, out, ctx->s_fb, ctx->x_list, ctx->x_nlist);
+            e = cudaGetLastError();
+        }
+    }
+    const cudaError_t ef = cudaFreeAsync(out, s);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, cudaGetErrorString(e));
+    a.list = ctx->x_list;
+    return RAPTOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int raptor_crossings_param_count(void) { return XLayout::SIZE; }
+
+raptor_status raptor_crossings_generate(raptor_ctx* ctx, long long n, unsigned long long seed, double spin_min,
+                                        double spin_max, double incl_min_deg, double incl_max_deg, float* inputs_dev,
+                                        double* targets_dev, double* raw_dev, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (n < 1 || !inputs_dev || !targets_dev) return fail(ctx, RAPTOR_EINVAL, "need n >= 1 and output buffers");
+    if (!(spin_min >= 0.0 && spin_max >= spin_min && spin_max < 1.0)) return fail(ctx, RAPTOR_EINVAL, "spin range invalid");
+    if (!(incl_min_deg > 0.0 && incl_max_deg >= incl_min_deg && incl_max_deg < 90.0))
+        return fail(ctx, RAPTOR_EINVAL, "inclination range invalid (0 < i < 90 deg: the camera above the plane)");
+    SurrogateRange R{ctx->cam.alpha_min, ctx->cam.alpha_max, ctx->cam.beta_min, ctx->cam.beta_max, spin_min, spin_max,
+                     incl_min_deg, incl_max_deg, ctx->cam.r_cam, ctx->cam.eps};
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    {
+        ProfScope ps(ctx, kProfTrain, s);
+        k_crossing_data<<<ctx->num_sms * 8, 128, 0, s>>>(R, ctx->cam.r_stop_factor, ctx->cam.r_escape, ctx->cam.max_steps,
+                                                          seed, n, inputs_dev, targets_dev, raw_dev);
+    }
+    RCK(cudaGetLastError());
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_init(raptor_ctx* ctx, const double* targets_dev, long long n, unsigned long long seed,
+                                    void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!targets_dev || n < 2) return fail(ctx, RAPTOR_EINVAL, "need targets and n >= 2");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(x_alloc(ctx));
+    const long long m = std::min<long long>(n, 65536);
+    std::vector<double> y((size_t)m * kXOut);
+    RCK(cudaMemcpyAsync(y.data(), targets_dev, y.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RCK(cudaStreamSynchronize(s));
+    std::vector<float> P(XLayout::SIZE, 0.f);
+    uint64_t st = seed ^ 0xC505ull;
+    auto uni = [&](double lim) { return (float)(lim * (2.0 * ((splitmix(st) >> 11) * (1.0 / 9007199254740992.0)) - 1.0)); };
+    for (int i = 0; i < kHid * kIn; ++i) P[XLayout::W1 + i] = uni(std::sqrt(6.0 / kIn));
+    for (int i = 0; i < kHid * kHid; ++i) P[XLayout::W2 + i] = uni(std::sqrt(6.0 / kHid));
+    for (int i = 0; i < kHid * kHid; ++i) P[XLayout::W3 + i] = uni(std::sqrt(6.0 / kHid));
+    for (int i = 0; i < kXOut * kHid; ++i) P[XLayout::W4 + i] = uni(std::sqrt(3.0 / kHid));
+    const double ha = 0.5 * (ctx->cam.alpha_max - ctx->cam.alpha_min), hb = 0.5 * (ctx->cam.beta_max - ctx->cam.beta_min);
+    const float scale[4] = {(float)(1.0 / ha), (float)(1.0 / hb), 2.0f, 1.0f / 40.0f};
+    const float shift[4] = {(float)(0.5 * (ctx->cam.alpha_max + ctx->cam.alpha_min)),
+                            (float)(0.5 * (ctx->cam.beta_max + ctx->cam.beta_min)), 0.5f, 45.0f};
+    for (int c = 0; c < 4; ++c) {
+        P[XLayout::NORM + c] = scale[c];
+        P[XLayout::NORM + 4 + c] = shift[c];
+    }
+    // output normalisation over the targets present (presence logits: none)
+    for (int q = 0; q < kXOut; ++q) {
+        double mu = 0.0, var = 0.0;
+        long long cnt = 0;
+        if (q % 4 != 0) {
+            for (long long i = 0; i < m; ++i) {
+                const double v = y[i * kXOut + q];
+                if (std::isnan(v)) continue;
+                mu += v;
+                cnt += 1;
+            }
+            mu = cnt ? mu / cnt : 0.0;
+            for (long long i = 0; i < m; ++i) {
+                const double v = y[i * kXOut + q];
+                if (!std::isnan(v)) var += (v - mu) * (v - mu);
+            }
+            var = cnt > 1 ? var / (cnt - 1) : 1.0;
+        } else {
+            var = 1.0;
+        }
+        P[XLayout::MU + q] = (float)mu;
+        P[XLayout::SD + q] = (float)std::max(std::sqrt(var), 1e-6);
+    }
+    RCK(cudaMemcpyAsync(ctx->x_P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    RCK(cudaMemsetAsync(ctx->x_m1, 0, XLayout::SIZE * sizeof(float), s));
+    RCK(cudaMemsetAsync(ctx->x_m2, 0, XLayout::SIZE * sizeof(float), s));
+    RCK(x_refresh(ctx, s));
+    RCK(cudaStreamSynchronize(s));
+    ctx->x_step = 0;
+    ctx->x_ready = true;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_train(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                     int steps, double lr, double lr_final, unsigned long long seed, double* loss_host,
+                                     void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->x_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "crossing network not initialised");
+    if (!inputs_dev || !targets_dev || n < 1 || steps < 1 || !(lr > 0.0) || !(lr_final > 0.0))
+        return fail(ctx, RAPTOR_EINVAL, "invalid training arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(x_alloc(ctx));
+    const float b1 = 0.9f, b2 = 0.999f;
+    ProfScope ps(ctx, kProfTrain, s);
+    for (int it = 0; it < steps; ++it) {
+        k_gather_batch<kXOut><<<ew_blocks(kSurRows), 256, 0, s>>>(inputs_dev, targets_dev, n, kSurRows, seed,
+                                                                  (long long)ctx->x_step, ctx->s_x, ctx->x_y);
+        RCK(x_forward(ctx, kSurRows, s));
+        int nb = 0;
+        RCK(x_backward(ctx, kSurRows, &nb, s));
+        ctx->x_step += 1;
+        const double frac = steps > 1 ? (double)it / (steps - 1) : 1.0;
+        const double lr_it = lr_final + 0.5 * (lr - lr_final) * (1.0 + std::cos(kPi * frac));
+        const double t = (double)ctx->x_step;
+        const float lr_t = (float)(lr_it * std::sqrt(1.0 - std::pow(b2, t)) / (1.0 - std::pow(b1, t)));
+        k_adam<<<ew_blocks(XLayout::NORM), 256, 0, s>>>(ctx->x_P, ctx->x_G, ctx->x_m1, ctx->x_m2, XLayout::NORM, lr_t, b1, b2,
+                                                       1e-8f);
+        RCK(x_refresh(ctx, s));
+        if (loss_host) {
+            cudaError_t e = cudaSuccess;
+            const double L = sum_parts(ctx, nb, s, &e);
+            RCK(e);
+            loss_host[it] = L / (double)(kSurRows * kXOut);
+        }
+    }
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_grad(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                    float* grad_host, double* loss_host, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->x_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "crossing network not initialised");
+    if (!inputs_dev || !targets_dev || n < 1 || n > kSurRows || n % kGBM != 0)
+        return fail(ctx, RAPTOR_EINVAL, "n must be a multiple of 128 and at most 4096");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    RCK(cudaMemcpyAsync(ctx->s_x, inputs_dev, n * kIn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    RCK(cudaMemcpyAsync(ctx->x_y, targets_dev, n * kXOut * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RCK(x_forward(ctx, n, s));
+    int nb = 0;
+    RCK(x_backward(ctx, n, &nb, s));
+    if (grad_host) RCK(cudaMemcpyAsync(grad_host, ctx->x_G, XLayout::NORM * sizeof(float), cudaMemcpyDeviceToHost, s));
+    cudaError_t e = cudaSuccess;
+    const double L = sum_parts(ctx, nb, s, &e);
+    RCK(e);
+    if (loss_host) *loss_host = L / (double)(n * kXOut);
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_eval(raptor_ctx* ctx, const float* inputs_dev, long long n, double* pred_dev, void* stream) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->x_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "crossing network not initialised");
+    if (!inputs_dev || !pred_dev || n < 1) return fail(ctx, RAPTOR_EINVAL, "invalid arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    float* out = nullptr;
+    RCK(cudaMallocAsync((void**)&out, n * kXOut * sizeof(float), s));
+    cudaError_t e = x_eval_rows(ctx, inputs_dev, n, out, s);
+    if (e == cudaSuccess) {
+        k_crossings_decode<<<ew_blocks(n), 256, 0, s>>>(ctx->x_P, inputs_dev, out, n, (float)ctx->cam.r_cam, pred_dev);
+        e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(out, s);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, cudaGetErrorString(e));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_get(raptor_ctx* ctx, float* params_host, int n) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->x_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "crossing network not initialised");
+    if (!params_host || n != XLayout::SIZE) return fail(ctx, RAPTOR_EINVAL, "n must equal raptor_crossings_param_count()");
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemcpy(params_host, ctx->x_P, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, int n) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!params_host || n != XLayout::SIZE) return fail(ctx, RAPTOR_EINVAL, "n must equal raptor_crossings_param_count()");
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(params_host[i])) return fail(ctx, RAPTOR_EINVAL, "parameters must be finite");
+    for (int q = 0; q < kXOut; ++q)
+        if (!(params_host[XLayout::SD + q] > 0.f)) return fail(ctx, RAPTOR_EINVAL, "output scales must be positive");
+    RCK(x_alloc(ctx));
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemcpy(ctx->x_P, params_host, n * sizeof(float), cudaMemcpyHostToDevice));
+    RCK(cudaMemset(ctx->x_m1, 0, n * sizeof(float)));
+    RCK(cudaMemset(ctx->x_m2, 0, n * sizeof(float)));
+    RCK(x_refresh(ctx, nullptr));
+    RCK(cudaDeviceSynchronize());
+    ctx->x_step = 0;
+    ctx->x_ready = true;
     return RAPTOR_OK;
 }
 

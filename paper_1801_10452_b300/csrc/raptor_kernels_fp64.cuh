@@ -229,10 +229,11 @@ struct DiskArgs {
     int* order;       // [n_pix] crossing number of the hit (0: no hit)
     int* status;      // [n_pix] or nullptr
     int* steps;       // [n_pix] or nullptr
+    const int* list;  // nullptr: ray id = pixel; else the pixel of each ray id (-1: none)
 };
 
 __device__ __forceinline__ void disk_crossing(double a, const double x0[4], const double k0[4], double dl, double th1,
-                                              double xc[4], double kc[4]) {
+                                              double xc[4], double kc[4], double* h_out = nullptr) {
     const double half_pi = 0.5 * kPi;
     double h = dl * (half_pi - x0[2]) / (th1 - x0[2]);
 #pragma unroll 1
@@ -246,6 +247,7 @@ __device__ __forceinline__ void disk_crossing(double a, const double x0[4], cons
 #pragma unroll
     for (int i = 0; i < 4; ++i) { xc[i] = x0[i]; kc[i] = k0[i]; }
     rk4_step<double>(a, xc, kc, h);
+    if (h_out) *h_out = h;
 }
 
 // One step of a disk ray: returns the termination code or -1; on a hit fills ratio, I.
@@ -287,7 +289,8 @@ __device__ __forceinline__ int disk_step(const Params& p, const DiskArgs& d, dou
     return -1;
 }
 
-// Persistent: each warp keeps 32 rays in flight and refills lanes from the counter.
+// Persistent: each warp keeps 32 rays in flight and refills lanes from the counter (a ray
+// id is a pixel, or indexes d.list, whose -1 entries are skipped).
 __global__ void __launch_bounds__(128) k_disk_fp64(const Params p, const DiskArgs d, unsigned long long* counter,
                                                    unsigned long long* stats) {
     double x[4], k[4], ratio = 0.0, inten = 0.0;
@@ -297,9 +300,10 @@ __global__ void __launch_bounds__(128) k_disk_fp64(const Params p, const DiskArg
     unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0;
     for (;;) {
         const long long nid = warp_fetch(counter, p.n_rays, id < 0, drained);
-        if (id < 0 && nid >= 0) {
+        const int npix = nid >= 0 ? (d.list ? d.list[nid] : (int)nid) : -1;
+        if (id < 0 && npix >= 0) {
             id = nid;
-            pix = (int)id;
+            pix = npix;
             const int row = pix / p.nx, col = pix % p.nx;
             camera_ray(p, p.amin + (col + 0.5) * p.da, p.bmin + (row + 0.5) * p.db, p.t_cam, x, k);
             n = 0;

@@ -155,18 +155,22 @@ __global__ void k_surrogate_data(SurrogateRange R, uint64_t seed, long long n, f
 // Parameters: one FP32 buffer holding every tensor, plus BF16 copies of the two hidden
 // weight matrices ([out][in] and transposed [in][out]) for the tensor-core GEMMs.
 // ---------------------------------------------------------------------------------------
-struct MlpLayout {
+template <int NOUT>
+struct MlpLayoutT {
     static constexpr int W1 = 0;                         // [256][4]
     static constexpr int B1 = W1 + kHid * kIn;           // [256]
     static constexpr int W2 = B1 + kHid;                 // [256][256]
     static constexpr int B2 = W2 + kHid * kHid;
     static constexpr int W3 = B2 + kHid;
     static constexpr int B3 = W3 + kHid * kHid;
-    static constexpr int W4 = B3 + kHid;                 // [8][256]
-    static constexpr int B4 = W4 + kOut * kHid;          // [8]
-    static constexpr int NORM = B4 + kOut;               // input scale/shift [8], output mean/std [16]
-    static constexpr int SIZE = NORM + 24;
+    static constexpr int W4 = B3 + kHid;                 // [NOUT][256]
+    static constexpr int B4 = W4 + NOUT * kHid;          // [NOUT]
+    static constexpr int NORM = B4 + NOUT;               // input scale[4], shift[4], output mean[NOUT], std[NOUT]
+    static constexpr int MU = NORM + 8;
+    static constexpr int SD = MU + NOUT;
+    static constexpr int SIZE = SD + NOUT;
 };
+using MlpLayout = MlpLayoutT<kOut>;
 
 // SiLU with the hardware exponential and reciprocal (the argument of exp is capped at 80 so
 // that 1 + e^-z stays inside the approximate division's range; below z = -80, silu is ~0).
@@ -177,18 +181,19 @@ __device__ __forceinline__ float dsilu(float z) {
 }
 
 // Layer 1 (FP32): z1 = W1 x_n + b1, h1 = silu(z1) (BF16), x_n = (x - shift) * scale.
+template <int NOUT = kOut>
 __global__ void k_mlp_layer1(const float* __restrict__ P, const float* __restrict__ x, long long rows, long long rows_valid,
                              float* __restrict__ z1, __nv_bfloat16* __restrict__ h1) {
     const long long total = rows * kHid;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         const long long m = e / kHid;
         const int j = (int)(e - m * kHid);
-        float acc = P[MlpLayout::B1 + j];
+        float acc = P[MlpLayoutT<NOUT>::B1 + j];
         if (m < rows_valid) {
 #pragma unroll
             for (int c = 0; c < kIn; ++c) {
-                const float xn = (x[m * kIn + c] - P[MlpLayout::NORM + 4 + c]) * P[MlpLayout::NORM + c];
-                acc += P[MlpLayout::W1 + j * kIn + c] * xn;
+                const float xn = (x[m * kIn + c] - P[MlpLayoutT<NOUT>::NORM + 4 + c]) * P[MlpLayoutT<NOUT>::NORM + c];
+                acc += P[MlpLayoutT<NOUT>::W1 + j * kIn + c] * xn;
             }
         }
         if (z1) z1[e] = acc;
@@ -208,25 +213,26 @@ __global__ void k_bias_silu(float* __restrict__ z, const float* __restrict__ bia
 
 // Output layer (FP32 weights, BF16 activations): out[m][o] = W4[o] . h3[m] + b4[o].
 // One warp per row.
+template <int NOUT = kOut>
 __global__ void k_mlp_layer4(const float* __restrict__ P, const __nv_bfloat16* __restrict__ h3, long long rows,
                              float* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long m = warp; m < rows; m += nw) {
-        float acc[kOut];
+        float acc[NOUT];
 #pragma unroll
-        for (int o = 0; o < kOut; ++o) acc[o] = 0.f;
+        for (int o = 0; o < NOUT; ++o) acc[o] = 0.f;
         for (int j = lane; j < kHid; j += 32) {
             const float h = __bfloat162float(h3[m * kHid + j]);
 #pragma unroll
-            for (int o = 0; o < kOut; ++o) acc[o] += P[MlpLayout::W4 + o * kHid + j] * h;
+            for (int o = 0; o < NOUT; ++o) acc[o] += P[MlpLayoutT<NOUT>::W4 + o * kHid + j] * h;
         }
 #pragma unroll
-        for (int o = 0; o < kOut; ++o) {
+        for (int o = 0; o < NOUT; ++o) {
             float v = acc[o];
             for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-            if (lane == 0) out[m * kOut + o] = v + P[MlpLayout::B4 + o];
+            if (lane == 0) out[m * NOUT + o] = v + P[MlpLayoutT<NOUT>::B4 + o];
         }
     }
 }
@@ -399,6 +405,7 @@ __device__ __forceinline__ void fused_hidden_layer(const __nv_bfloat16* __restri
     __syncthreads();
 }
 
+template <int NOUT = kOut>
 __global__ void __launch_bounds__(256) k_mlp_fused(const float* __restrict__ P, const __nv_bfloat16* __restrict__ w2,
                                                    const __nv_bfloat16* __restrict__ w3, const float* __restrict__ x,
                                                    long long n, float* __restrict__ out) {
@@ -408,30 +415,34 @@ __global__ void __launch_bounds__(256) k_mlp_fused(const float* __restrict__ P, 
     // layer 1 (FP32): 64 x 256 outputs, 64 per thread
     for (int e = threadIdx.x; e < kFRows * kHid; e += 256) {
         const int m = e / kHid, j = e - m * kHid;
-        float acc = P[MlpLayout::B1 + j];
+        float acc = P[MlpLayoutT<NOUT>::B1 + j];
         if (m0 + m < n) {
 #pragma unroll
             for (int c = 0; c < kIn; ++c) {
-                const float xn = (x[(m0 + m) * kIn + c] - P[MlpLayout::NORM + 4 + c]) * P[MlpLayout::NORM + c];
-                acc += P[MlpLayout::W1 + j * kIn + c] * xn;
+                const float xn = (x[(m0 + m) * kIn + c] - P[MlpLayoutT<NOUT>::NORM + 4 + c]) * P[MlpLayoutT<NOUT>::NORM + c];
+                acc += P[MlpLayoutT<NOUT>::W1 + j * kIn + c] * xn;
             }
         }
         H[m][j] = __float2bfloat16(silu(acc));
     }
     __syncthreads();
-    fused_hidden_layer(w2, P + MlpLayout::B2, H, Wc);
-    fused_hidden_layer(w3, P + MlpLayout::B3, H, Wc);
-    // layer 4 (FP32 weights): thread -> (row, output pair)
-    const int m = threadIdx.x >> 2, o = (threadIdx.x & 3) * 2;
-    float a0 = P[MlpLayout::B4 + o], a1 = P[MlpLayout::B4 + o + 1];
+    fused_hidden_layer(w2, P + MlpLayoutT<NOUT>::B2, H, Wc);
+    fused_hidden_layer(w3, P + MlpLayoutT<NOUT>::B3, H, Wc);
+    // layer 4 (FP32 weights): thread -> (row, NOUT / 4 consecutive outputs)
+    constexpr int PER = NOUT / 4;
+    static_assert(NOUT % 4 == 0, "four threads per row");
+    const int m = threadIdx.x >> 2, o = (threadIdx.x & 3) * PER;
+    float acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = P[MlpLayoutT<NOUT>::B4 + o + q];
     for (int j = 0; j < kHid; ++j) {
         const float h = __bfloat162float(H[m][j]);
-        a0 += P[MlpLayout::W4 + o * kHid + j] * h;
-        a1 += P[MlpLayout::W4 + (o + 1) * kHid + j] * h;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) acc[q] += P[MlpLayoutT<NOUT>::W4 + (o + q) * kHid + j] * h;
     }
     if (m0 + m < n) {
-        out[(m0 + m) * kOut + o] = a0;
-        out[(m0 + m) * kOut + o + 1] = a1;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) out[(m0 + m) * NOUT + o + q] = acc[q];
     }
 }
 
@@ -468,6 +479,7 @@ __global__ void k_mse_grad(const float* __restrict__ P, const float* __restrict_
 
 // dh3 = dout W4 (FP32), then dz3 = dh3 * silu'(z3) stored BF16 (the operand of the next GEMMs)
 // and FP32 for the bias gradient.
+template <int NOUT = kOut>
 __global__ void k_back_layer4(const float* __restrict__ P, const float* __restrict__ dout, const float* __restrict__ z3,
                               long long rows, float* __restrict__ dz3f, __nv_bfloat16* __restrict__ dz3) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * kHid; e += (long long)gridDim.x * blockDim.x) {
@@ -475,7 +487,7 @@ __global__ void k_back_layer4(const float* __restrict__ P, const float* __restri
         const int j = (int)(e - m * kHid);
         float acc = 0.f;
 #pragma unroll
-        for (int o = 0; o < kOut; ++o) acc += dout[m * kOut + o] * P[MlpLayout::W4 + o * kHid + j];
+        for (int o = 0; o < NOUT; ++o) acc += dout[m * NOUT + o] * P[MlpLayoutT<NOUT>::W4 + o * kHid + j];
         const float g = acc * dsilu(z3[e]);
         dz3f[e] = g;
         dz3[e] = __float2bfloat16(g);
@@ -515,6 +527,7 @@ __global__ void __launch_bounds__(256) k_colred(const TX* __restrict__ X, int ld
 }
 
 // Input-layer weight gradient: dW1[j][c] = sum_m dz1[m][j] * x_n[m][c].
+template <int NOUT = kOut>
 __global__ void __launch_bounds__(256) k_grad_w1(const float* __restrict__ P, const float* __restrict__ dz1,
                                                  const float* __restrict__ x, long long rows, float* __restrict__ G) {
     __shared__ float sh[256];
@@ -522,7 +535,7 @@ __global__ void __launch_bounds__(256) k_grad_w1(const float* __restrict__ P, co
     const int j = e / kIn, c = e - j * kIn;
     float acc = 0.f;
     for (long long m = threadIdx.x; m < rows; m += 256) {
-        const float xn = (x[m * kIn + c] - P[MlpLayout::NORM + 4 + c]) * P[MlpLayout::NORM + c];
+        const float xn = (x[m * kIn + c] - P[MlpLayoutT<NOUT>::NORM + 4 + c]) * P[MlpLayoutT<NOUT>::NORM + c];
         acc += dz1[m * kHid + j] * xn;
     }
     sh[threadIdx.x] = acc;
@@ -531,7 +544,7 @@ __global__ void __launch_bounds__(256) k_grad_w1(const float* __restrict__ P, co
         if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) G[MlpLayout::W1 + e] = sh[0];
+    if (threadIdx.x == 0) G[MlpLayoutT<NOUT>::W1 + e] = sh[0];
 }
 
 // Adam (decoupled bias correction folded into the step size) over the first n parameters.
@@ -561,13 +574,14 @@ __global__ void k_refresh_bf16(const float* __restrict__ P, __nv_bfloat16* __res
     }
 }
 
-// Gather a training batch: rows idx = hash(seed, step, r) mod n.
+// Gather a training batch: rows idx = hash(seed, step, r) mod n (NY targets per row).
+template <int NY = kOutUsed>
 __global__ void k_gather_batch(const float* __restrict__ x, const double* __restrict__ y, long long n, long long rows,
                                uint64_t seed, long long step, float* __restrict__ xb, double* __restrict__ yb) {
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
         const long long i = (long long)(u01(seed, (uint64_t)step * (uint64_t)rows + r, 7) * (double)n) % n;
         for (int c = 0; c < kIn; ++c) xb[r * kIn + c] = x[i * kIn + c];
-        for (int q = 0; q < kOutUsed; ++q) yb[r * kOutUsed + q] = y[i * kOutUsed + q];
+        for (int q = 0; q < NY; ++q) yb[r * NY + q] = y[i * NY + q];
     }
 }
 
