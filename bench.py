@@ -349,8 +349,7 @@ def _disk_extra(R, torch, stream, fma64, reps=2):
         steps = st["steps"] / reps
         k_ms = prof["disk"][0] / reps
         ach = geo * steps / (k_ms * 1e-3) / 1e12
-        out["per_spin"][f"{a:g}" + ("" if band == 0.5 else f"_band{band:g}")] = {
-            "fallback_band_M": band,
+        out["per_spin"][f"{a:g}"] = {
             "ms": ms, "rays_per_s": rays / (ms * 1e-3), "steps_per_ray": steps / rays,
             "hit_fraction_first_order": float((order == 1).mean()), "hit_fraction_any": float((order > 0).mean()),
             "line_peak_E_ratio": float(centres[int(np.argmax(spec))]),
@@ -411,10 +410,10 @@ def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
     cam0 = scenes.THIN_DISK
     out["workload"] = f"learned_thin_disk_{cam0['nx']}x{cam0['ny']}_i{cam0['incl_deg']:g}_rin_isco_rout15_q2"
     out["per_spin"] = {}
-    for a, band in [(v, b) for v in scenes.THIN_DISK_SPINS if 0.0 <= v <= 0.99 for b in (0.5, 1.0)]:
+    for a, band in [(v, b) for v in scenes.THIN_DISK_SPINS if 0.0 <= v <= 0.99 for b in (1.0, 0.5)]:
         ctx = R.Context(R.camera_desc(**dict(cam0, spin=a)))
         ctx.crossings_set(P)
-        ctx.surrogate_config(fallback_band=band)
+        ctx.crossings_config(fallback_band=band)
         res = {}
         for learned in (False, True):
             r = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream, learned=learned)
@@ -440,7 +439,7 @@ def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
         rays = cam0["nx"] * cam0["ny"]
         mlp_ms = prof["surrogate_mlp"][0] / reps
         ach = flops_ray * rays / (mlp_ms * 1e-3) / 1e12
-        out["per_spin"][f"{a:g}" + ("" if band == 0.5 else f"_band{band:g}")] = {
+        out["per_spin"][f"{a:g}" + ("" if band == 1.0 else f"_band{band:g}")] = {
             "fallback_band_M": band,
             "ms_learned": ms_l, "ms_fp64": ms_f, "speedup": ms_f / ms_l, "rays_per_s_learned": rays / (ms_l * 1e-3),
             "fallback_fraction": float(fb.mean()),

@@ -413,10 +413,16 @@ raptor_status raptor_crossings_grad(raptor_ctx* ctx, const float* inputs_dev, co
                                     float* grad_host, double* loss_host, void* stream);
 raptor_status raptor_crossings_eval(raptor_ctx* ctx, const float* inputs_dev, long long n, double* pred_dev, void* stream);
 raptor_status raptor_crossings_get(raptor_ctx* ctx, float* params_host, int n);
+/* Fallback band of raptor_disk_render_learned: pixel centres inside the critical curve or
+ * within fallback_band M of it are integrated exactly [1.0].  The learned disk's radius
+ * changes steeply across the image just outside the curve (rays deflected behind the hole),
+ * so its band is wider than the volumetric render's (raptor_surrogate_config).  RAPTOR_EINVAL
+ * for a negative or non-finite band. */
+raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band);
 raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, int n);
 
 /* The thin disk of raptor_disk_render from the learned crossings (sec. 4.2.1): pixels whose
- * centre lies outside the critical curve and its fallback band (raptor_surrogate_config)
+ * centre lies outside the critical curve and its fallback band (raptor_crossings_config)
  * take the first predicted crossing (presence probability > 1/2, in order) with r_in <= r_n
  * <= r_out: E_obs/E_em of the Keplerian emitter at the predicted r_n (closed form, exact given
  * the radius: 1 / (u^t (1 - Omega L)), L = -alpha sin i), intensity (E_obs/E_em)^4 r_n^-q,

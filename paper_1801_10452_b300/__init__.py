@@ -34,7 +34,7 @@ EXPORTS = [
     "raptor_surrogate_get", "raptor_surrogate_set", "raptor_surrogate_save", "raptor_surrogate_load", "raptor_surrogate_config", "raptor_surrogate_kernel",
     "raptor_disk_desc_default", "raptor_disk_render", "raptor_disk_render_learned", "raptor_crossings_param_count",
     "raptor_crossings_generate", "raptor_crossings_init", "raptor_crossings_train", "raptor_crossings_grad",
-    "raptor_crossings_eval", "raptor_crossings_get", "raptor_crossings_set", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
+    "raptor_crossings_eval", "raptor_crossings_get", "raptor_crossings_set", "raptor_crossings_config", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp", "disk", "mixed_fp64_long"]
@@ -132,6 +132,7 @@ def lib():
             "raptor_crossings_eval": (st, [vp, vp, C.c_longlong, vp, vp]),
             "raptor_crossings_get": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_crossings_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
+            "raptor_crossings_config": (st, [vp, C.c_double]),
             "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
             "raptor_long_config": (st, [vp, C.c_int, C.c_int, C.c_void_p]),
             "raptor_profile_timeline": (st, [vp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -507,6 +508,10 @@ class Context:
         P = np.ascontiguousarray(P, dtype=np.float32)
         self._check(lib().raptor_crossings_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size),
                     "raptor_crossings_set")
+
+    def crossings_config(self, fallback_band=1.0):
+        """Fallback band (M) of the learned thin disk around the critical curve."""
+        self._check(lib().raptor_crossings_config(self._h, float(fallback_band)), "raptor_crossings_config")
 
     def long_config(self, threads_per_block=0, budgets=None):
         """Schedule of the near-critical rays' FP64 phase on the second stream: block size

@@ -109,6 +109,7 @@ struct raptor_ctx {
     float *x_out = nullptr, *x_dout = nullptr;  // [rows][16]
     double* x_y = nullptr;           // [rows][16]
     unsigned long long x_step = 0;
+    double x_band = 1.0;             // learned disk: fallback band around the critical curve (M)
     int* x_list = nullptr;           // learned disk: fallback pixels
     unsigned int* x_nlist = nullptr;
     size_t x_list_cap = 0;
@@ -2189,7 +2190,7 @@ raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, 
     }
     if (!ctx->x_nlist) RCK(cudaMalloc((void**)&ctx->x_nlist, sizeof(unsigned int)));
     RCK(upload_curve(ctx, p, s));
-    const float grow = (float)ctx->s_band + 1e-3f;
+    const float grow = (float)ctx->x_band + 1e-3f;
     const float4 box = make_float4(ctx->curve_box.x - grow, ctx->curve_box.y + grow, ctx->curve_box.z - grow,
                                    ctx->curve_box.w + grow);
     float* out = nullptr;
@@ -2197,7 +2198,7 @@ raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, 
     cudaError_t e = cudaSuccess;
     {
         ProfScope ps(ctx, kProfSurrogate, s, 2);
-        k_surrogate_prepare<<<ew_blocks((long long)n), 256, 0, s>>>(p, ctx->d_curve, ctx->n_curve, (float)ctx->s_band, box,
+        k_surrogate_prepare<<<ew_blocks((long long)n), 256, 0, s>>>(p, ctx->d_curve, ctx->n_curve, (float)ctx->x_band, box,
                                                                     ctx->s_in, ctx->s_fb);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
@@ -2382,6 +2383,15 @@ raptor_status raptor_crossings_eval(raptor_ctx* ctx, const float* inputs_dev, lo
     const cudaError_t ef = cudaFreeAsync(out, s);
     if (e == cudaSuccess) e = ef;
     if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, cudaGetErrorString(e));
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!(fallback_band >= 0.0) || !std::isfinite(fallback_band))
+        return fail(ctx, RAPTOR_EINVAL, "fallback_band must be finite and >= 0");
+    ctx->x_band = fallback_band;
     return RAPTOR_OK;
 }
 

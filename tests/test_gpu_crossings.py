@@ -248,4 +248,26 @@ def test_learned_disk_argument_checks(R, trained):
     with pytest.raises(R.RaptorError) as e:
         ctx.disk_render(r_in=4.0, r_out=15.0, learned=True)
     assert e.value.status == R.EUNSUPPORTED
+    for bad in (-0.1, float("nan"), float("inf")):
+        with pytest.raises(R.RaptorError) as e:
+            ctx.crossings_config(bad)
+        assert e.value.status == R.EINVAL
     ctx.disk_render(**DISK, learned=True)
+
+
+def test_learned_disk_band_zero_and_wide(R, trained):
+    """The fallback band sets which pixels are integrated exactly: band 0 leaves only the
+    shadow (inside the critical curve) to the integrator, a wide band more pixels, and every
+    fallback pixel equals the FP64 disk."""
+    cam = dict(scenes.THIN_DISK, spin=0.5, nx=128, ny=128)
+    ctx = R.Context(R.camera_desc(**cam))
+    ctx.crossings_set(trained)
+    f = _disk(R, ctx, False)
+    frac = []
+    for band in (0.0, 1.0, 3.0):
+        ctx.crossings_config(band)
+        g = _disk(R, ctx, True)
+        fb = g["steps"] > 0
+        frac.append(fb.mean())
+        assert np.array_equal(g["ratio"][fb], f["ratio"][fb]) and np.array_equal(g["order"][fb], f["order"][fb])
+    assert 0 < frac[0] < frac[1] < frac[2] < 1, frac
