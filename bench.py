@@ -410,52 +410,60 @@ def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
     cam0 = scenes.THIN_DISK
     out["workload"] = f"learned_thin_disk_{cam0['nx']}x{cam0['ny']}_i{cam0['incl_deg']:g}_rin_isco_rout15_q2"
     out["per_spin"] = {}
-    for a, band in [(v, b) for v in scenes.THIN_DISK_SPINS if 0.0 <= v <= 0.99 for b in (1.0, 0.5)]:
+
+    def timed(ctx, learned):
+        r = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream, learned=learned)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            r = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream, learned=learned)
+        e1.record(stream)
+        e1.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        return e0.elapsed_time(e1) / reps, {k: v.cpu().numpy() if hasattr(v, "cpu") else v for k, v in r.items()}, prof
+
+    variants = [("", 1.0, True), ("_fp64fallback", 1.0, False), ("_band0.5", 0.5, True)]
+    for a in [v for v in scenes.THIN_DISK_SPINS if 0.0 <= v <= 0.99]:
         ctx = R.Context(R.camera_desc(**dict(cam0, spin=a)))
         ctx.crossings_set(P)
-        ctx.crossings_config(fallback_band=band)
-        res = {}
-        for learned in (False, True):
-            r = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream, learned=learned)
-            torch.cuda.synchronize()
-            ctx.profile(True)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                r = ctx.disk_render(**scenes.THIN_DISK_GEOM, stream=stream, learned=learned)
-            e1.record(stream)
-            e1.synchronize()
-            prof = ctx.profile_read()
-            ctx.profile(False)
-            res[learned] = (e0.elapsed_time(e1) / reps, {k: v.cpu().numpy() if hasattr(v, "cpu") else v
-                                                         for k, v in r.items()}, prof)
-        (ms_f, f, _), (ms_l, g, prof) = res[False], res[True]
-        fb = g["steps"] > 0
-        nb = ~fb
-        hit = nb & (f["order"] > 0) & (g["order"] == f["order"])
-        rel = np.abs(g["ratio"][hit] / f["ratio"][hit] - 1)
-        sf, sg = f["spectrum"], g["spectrum"]
-        rays = cam0["nx"] * cam0["ny"]
-        mlp_ms = prof["surrogate_mlp"][0] / reps
-        ach = flops_ray * rays / (mlp_ms * 1e-3) / 1e12
-        out["per_spin"][f"{a:g}" + ("" if band == 1.0 else f"_band{band:g}")] = {
-            "fallback_band_M": band,
-            "ms_learned": ms_l, "ms_fp64": ms_f, "speedup": ms_f / ms_l, "rays_per_s_learned": rays / (ms_l * 1e-3),
-            "fallback_fraction": float(fb.mean()),
-            "order_agreement_outside_fallback": float((g["order"][nb] == f["order"][nb]).mean()),
-            "ratio_rel_err_max": float(rel.max()), "ratio_rel_err_p99": float(np.quantile(rel, 0.99)),
-            "pixels_compared": int(hit.sum()), "pixels_over_1e-2": int((rel > 1e-2).sum()),
-            "worst_pixel_alpha_beta": [float(cam0["alpha_min"] + (np.nonzero(hit)[1][np.argmax(rel)] + 0.5) *
-                                             (cam0["alpha_max"] - cam0["alpha_min"]) / cam0["nx"]),
-                                       float(cam0["beta_min"] + (np.nonzero(hit)[0][np.argmax(rel)] + 0.5) *
-                                             (cam0["beta_max"] - cam0["beta_min"]) / cam0["ny"])],
-            "spectrum_total_rel_err": float(sg.sum() / sf.sum() - 1),
-            "spectrum_l1_normalised": float(np.abs(sg / sg.sum() - sf / sf.sum()).sum()),
-            "stage_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
-            "network_roofline": {"bound": "tensor", "kernel": "k_mlp_fused<16> (mma.sync)", "achieved": ach,
-                                 "peak": bf16_peak, "unit": "TFLOP/s", "frac": ach / bf16_peak,
-                                 "flops_per_ray": flops_ray}}
+        ms_f, f, _ = timed(ctx, False)
+        for suffix, band, df in variants:
+            ctx.crossings_config(fallback_band=band, fallback_df64=df)
+            ms_l, g, prof = timed(ctx, True)
+            fb = g["steps"] > 0
+            nb = ~fb
+            hit = nb & (f["order"] > 0) & (g["order"] == f["order"])
+            rel = np.abs(g["ratio"][hit] / f["ratio"][hit] - 1)
+            fbh = fb & (f["order"] > 0) & (g["order"] == f["order"])
+            rel_fb = np.abs(g["ratio"][fbh] / f["ratio"][fbh] - 1)
+            sf, sg = f["spectrum"], g["spectrum"]
+            rays = cam0["nx"] * cam0["ny"]
+            mlp_ms = prof["surrogate_mlp"][0] / reps
+            ach = flops_ray * rays / (mlp_ms * 1e-3) / 1e12
+            w = np.nonzero(hit)
+            out["per_spin"][f"{a:g}{suffix}"] = {
+                "fallback_band_M": band, "fallback_arithmetic": "double-float" if df else "fp64",
+                "ms_learned": ms_l, "ms_fp64": ms_f, "speedup": ms_f / ms_l, "rays_per_s_learned": rays / (ms_l * 1e-3),
+                "fallback_fraction": float(fb.mean()),
+                "fallback_order_agreement": float((g["order"][fb] == f["order"][fb]).mean()),
+                "fallback_ratio_rel_err_max": float(rel_fb.max()) if rel_fb.size else 0.0,
+                "order_agreement_outside_fallback": float((g["order"][nb] == f["order"][nb]).mean()),
+                "ratio_rel_err_max": float(rel.max()), "ratio_rel_err_p99": float(np.quantile(rel, 0.99)),
+                "pixels_compared": int(hit.sum()), "pixels_over_1e-2": int((rel > 1e-2).sum()),
+                "worst_pixel_alpha_beta": [float(cam0["alpha_min"] + (w[1][np.argmax(rel)] + 0.5) *
+                                                 (cam0["alpha_max"] - cam0["alpha_min"]) / cam0["nx"]),
+                                           float(cam0["beta_min"] + (w[0][np.argmax(rel)] + 0.5) *
+                                                 (cam0["beta_max"] - cam0["beta_min"]) / cam0["ny"])],
+                "spectrum_total_rel_err": float(sg.sum() / sf.sum() - 1),
+                "spectrum_l1_normalised": float(np.abs(sg / sg.sum() - sf / sf.sum()).sum()),
+                "stage_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
+                "network_roofline": {"bound": "tensor", "kernel": "k_mlp_fused<16> (mma.sync)", "achieved": ach,
+                                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": ach / bf16_peak,
+                                     "flops_per_ray": flops_ray}}
         ctx.close()
     out["heldout_ratio_note"] = "held-out ratios compared where r >= 6 M (outside every prograde ISCO)"
     return out

@@ -413,12 +413,16 @@ raptor_status raptor_crossings_grad(raptor_ctx* ctx, const float* inputs_dev, co
                                     float* grad_host, double* loss_host, void* stream);
 raptor_status raptor_crossings_eval(raptor_ctx* ctx, const float* inputs_dev, long long n, double* pred_dev, void* stream);
 raptor_status raptor_crossings_get(raptor_ctx* ctx, float* params_host, int n);
-/* Fallback band of raptor_disk_render_learned: pixel centres inside the critical curve or
- * within fallback_band M of it are integrated exactly [1.0].  The learned disk's radius
- * changes steeply across the image just outside the curve (rays deflected behind the hole),
- * so its band is wider than the volumetric render's (raptor_surrogate_config).  RAPTOR_EINVAL
- * for a negative or non-finite band. */
-raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band);
+/* Fallback of raptor_disk_render_learned: pixel centres inside the critical curve or within
+ * fallback_band M of it are integrated by the disk ray of raptor_disk_render [1.0].  The
+ * learned disk's radius changes steeply across the image just outside the curve (rays
+ * deflected behind the hole), so its band is wider than the volumetric render's
+ * (raptor_surrogate_config).  fallback_df64 = 1 [default]: those rays' state, RK4 steps and
+ * crossing refinement in double-float arithmetic (float pairs, ~48-bit significands, on the
+ * FP32 pipe; the step length from the FP32 view of the state) and E_obs/E_em at the hit in
+ * FP64; 0: in FP64, equal to raptor_disk_render bit for bit.  RAPTOR_EINVAL for a negative
+ * or non-finite band or another flag value. */
+raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band, int fallback_df64);
 raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, int n);
 
 /* The thin disk of raptor_disk_render from the learned crossings (sec. 4.2.1): pixels whose
@@ -427,8 +431,8 @@ raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, in
  * <= r_out: E_obs/E_em of the Keplerian emitter at the predicted r_n (closed form, exact given
  * the radius: 1 / (u^t (1 - Omega L)), L = -alpha sin i), intensity (E_obs/E_em)^4 r_n^-q,
  * order n + 1,
- * status 5 (6 without a hit), steps 0; the other pixels are integrated exactly as in
- * raptor_disk_render.  The network is valid inside the spin, inclination and field-of-view
+ * status 5 (6 without a hit), steps 0; the other pixels are integrated by the disk ray of
+ * raptor_disk_render (in double-float arithmetic by default: raptor_crossings_config).  The network is valid inside the spin, inclination and field-of-view
  * range of its training data; the caller keeps the camera there.  Same arguments and
  * outputs; r_in must not lie inside the ISCO
  * (RAPTOR_EUNSUPPORTED), nor may the crossing network be missing (RAPTOR_EUNSUPPORTED). */

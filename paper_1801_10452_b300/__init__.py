@@ -132,7 +132,7 @@ def lib():
             "raptor_crossings_eval": (st, [vp, vp, C.c_longlong, vp, vp]),
             "raptor_crossings_get": (st, [vp, C.POINTER(C.c_float), C.c_int]),
             "raptor_crossings_set": (st, [vp, C.POINTER(C.c_float), C.c_int]),
-            "raptor_crossings_config": (st, [vp, C.c_double]),
+            "raptor_crossings_config": (st, [vp, C.c_double, C.c_int]),
             "raptor_mixed_config": (st, [vp, C.c_double, C.c_int, C.c_void_p, C.c_int]),
             "raptor_long_config": (st, [vp, C.c_int, C.c_int, C.c_void_p]),
             "raptor_profile_timeline": (st, [vp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -509,9 +509,11 @@ class Context:
         self._check(lib().raptor_crossings_set(self._h, P.ctypes.data_as(C.POINTER(C.c_float)), P.size),
                     "raptor_crossings_set")
 
-    def crossings_config(self, fallback_band=1.0):
-        """Fallback band (M) of the learned thin disk around the critical curve."""
-        self._check(lib().raptor_crossings_config(self._h, float(fallback_band)), "raptor_crossings_config")
+    def crossings_config(self, fallback_band=1.0, fallback_df64=True):
+        """Fallback of the learned thin disk: band (M) around the critical curve, and whether
+        its rays run in double-float arithmetic (else FP64, equal to the FP64 disk)."""
+        self._check(lib().raptor_crossings_config(self._h, float(fallback_band), int(bool(fallback_df64))),
+                    "raptor_crossings_config")
 
     def long_config(self, threads_per_block=0, budgets=None):
         """Schedule of the near-critical rays' FP64 phase on the second stream: block size

@@ -110,6 +110,7 @@ struct raptor_ctx {
     double* x_y = nullptr;           // [rows][16]
     unsigned long long x_step = 0;
     double x_band = 1.0;             // learned disk: fallback band around the critical curve (M)
+    bool x_df = true;                // learned disk: fallback pixels in double-float arithmetic
     int* x_list = nullptr;           // learned disk: fallback pixels
     unsigned int* x_nlist = nullptr;
     size_t x_list_cap = 0;
@@ -989,13 +990,18 @@ static raptor_status disk_render_impl(raptor_ctx* ctx, const raptor_disk_desc* d
         if (ls != RAPTOR_OK) return ls;
     }
     RCK(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s));
+    // the learned disk's fallback pixels in double-float arithmetic unless FP64 is asked for
+    const bool df = learned && ctx->x_df;
+    const int blk = df ? 128 : ctx->launch_block;
     int occ = 0;
-    RCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disk_fp64, ctx->launch_block, 0));
-    const long long need = (p.n_rays + ctx->launch_block - 1) / ctx->launch_block;
+    if (df) RCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disk_df, blk, 0));
+    else RCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disk_fp64, blk, 0));
+    const long long need = (p.n_rays + blk - 1) / blk;
     const long long blocks = std::max<long long>(1, std::min<long long>(grid_blocks(ctx, std::max(occ, 1)), need));
     {
         ProfScope ps(ctx, kProfDisk, s);
-        k_disk_fp64<<<(int)blocks, ctx->launch_block, 0, s>>>(p, a, ctx->d_counters, ctx->d_stats);
+        if (df) k_disk_df<<<(int)blocks, blk, 0, s>>>(p, a, ctx->d_counters, ctx->d_stats);
+        else k_disk_fp64<<<(int)blocks, blk, 0, s>>>(p, a, ctx->d_counters, ctx->d_stats);
     }
     RCK(cudaGetLastError());
     if (!profile_host) return RAPTOR_OK;
@@ -2386,12 +2392,14 @@ raptor_status raptor_crossings_eval(raptor_ctx* ctx, const float* inputs_dev, lo
     return RAPTOR_OK;
 }
 
-raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band) {
+raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band, int fallback_df64) {
     if (!ctx) return RAPTOR_EINVAL;
     ctx->err.clear();
     if (!(fallback_band >= 0.0) || !std::isfinite(fallback_band))
         return fail(ctx, RAPTOR_EINVAL, "fallback_band must be finite and >= 0");
+    if (fallback_df64 != 0 && fallback_df64 != 1) return fail(ctx, RAPTOR_EINVAL, "fallback_df64 must be 0 or 1");
     ctx->x_band = fallback_band;
+    ctx->x_df = fallback_df64 != 0;
     return RAPTOR_OK;
 }
 

@@ -7,6 +7,7 @@
 // pixels near the critical curve.
 #pragma once
 
+#include "raptor_df64.cuh"
 #include "raptor_kernels_fp64.cuh"
 #include "raptor_surrogate.cuh"
 
@@ -264,6 +265,127 @@ __global__ void __launch_bounds__(256) k_disk_learned(const Params p, const Disk
         if (d.status) d.status[pix] = order ? kDiskHit : kDiskNone;
         if (d.steps) d.steps[pix] = 0;
     }
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Fallback pixels of the learned disk in double-float arithmetic (float pairs on the FP32
+// pipe, ~48-bit significands): the disk ray of k_disk_fp64 with the state, the RK4 steps and
+// the Newton refinement of a crossing in df64, the step length from the FP32 view of the
+// state (as the mixed path's double-float phase takes it), and E_obs/E_em at a hit in FP64
+// (once per ray).  FP64 issues at a small fraction of the FP32 rate on this GPU, so the
+// exact fallback integration, the learned disk's largest cost, moves to the FP32 pipe.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void disk_crossing_df(df64 a, const df64 x0[4], const df64 k0[4], df64 dl, df64 th1,
+                                                 df64 xc[4], df64 kc[4]) {
+    const df64 hp(0.5 * kPi);
+    df64 h = dl * (hp - x0[2]) / (th1 - x0[2]);
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { xc[i] = x0[i]; kc[i] = k0[i]; }
+        rk4_step_rolled<df64>(a, xc, kc, h);
+        if (!(fabsf(kc[2].hi) > 0.f)) break;
+        h = h - (xc[2] - hp) / kc[2];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { xc[i] = x0[i]; kc[i] = k0[i]; }
+    rk4_step_rolled<df64>(a, xc, kc, h);
+}
+
+__device__ __forceinline__ int disk_step_df(const Params& p, const DiskArgs& d, df64 a, df64 x[4], df64 k[4], int& n,
+                                            int& crossings, double& ratio, double& inten) {
+    const df64 hp(0.5 * kPi);
+    float xf[4], kf[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { xf[i] = x[i].hi + x[i].lo; kf[i] = k[i].hi + k[i].lo; }
+    const df64 dl(step_size<float>(p.f.eps, (p.flags & kFlagLinearR) != 0, xf, kf), 0.f);
+    df64 xo[4], ko[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { xo[i] = x[i]; ko[i] = k[i]; }
+    rk4_step_rolled<df64>(a, x, k, dl);
+    n += 1;
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fin = fin && isfinite(x[i].hi) && isfinite(x[i].lo) && isfinite(k[i].hi) && isfinite(k[i].lo);
+    if (!fin) return kError;
+    const df64 s0 = xo[2] - hp, s1 = x[2] - hp;
+    // the plane is crossed when theta - pi/2 changes sign (or reaches 0), not starting on it
+    if (s0.hi != 0.f && ((s0.hi > 0.f) != (s1.hi > 0.f) || s1.hi == 0.f)) {
+        crossings += 1;
+        df64 xc[4], kc[4];
+        disk_crossing_df(a, xo, ko, dl, x[2], xc, kc);
+        const double rc = (double)xc[1];
+        if (rc >= d.r_in && rc <= d.r_out) {
+            double xd[4], kd[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { xd[i] = (double)xc[i]; kd[i] = (double)kc[i]; }
+            KSPoint<double> P;
+            ks_point<double>(p.a, rc, xd[2], P);
+            double u[4], kcov[4];
+            if (analytic_velocity<double>(p.a, 0.0, P, u) < 0) return kError;
+            ks_lower(P, kd, kcov);
+            const double g = kcov[0] * u[0] + kcov[1] * u[1] + kcov[2] * u[2] + kcov[3] * u[3];
+            if (!(g > 0.0)) return kError;
+            ratio = 1.0 / g;
+            inten = ratio * ratio * ratio * ratio * pow(rc, -d.q);
+            return kDiskHit;
+        }
+        if (crossings >= d.max_cross) return kDiskNone;
+    }
+    const float r = x[1].hi + x[1].lo;
+    if (r < p.f.r_stop) return kCaptured;
+    if (r > p.f.r_esc) return kEscaped;
+    if (n >= p.max_steps) return kTruncated;
+    return -1;
+}
+
+// Persistent over the fallback list (ray id -> d.list[id], -1 entries skipped), one ray per
+// lane, refilled from the counter; outputs and statistics as k_disk_fp64.
+__global__ void __launch_bounds__(128, 4) k_disk_df(const Params p, const DiskArgs d, unsigned long long* counter,
+                                                    unsigned long long* stats) {
+    const df64 a(p.f.a_p.x, p.f.a_p.y);
+    df64 x[4], k[4];
+    double ratio = 0.0, inten = 0.0;
+    int n = 0, crossings = 0, pix = 0;
+    long long id = -1;
+    bool drained = false;
+    unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0;
+    for (;;) {
+        const long long nid = warp_fetch(counter, p.n_rays, id < 0, drained);
+        const int npix = nid >= 0 ? (d.list ? d.list[nid] : (int)nid) : -1;
+        if (id < 0 && npix >= 0) {
+            id = nid;
+            pix = npix;
+            const int row = pix / p.nx, col = pix % p.nx;
+            double xd[4], kd[4];
+            camera_ray(p, p.amin + (col + 0.5) * p.da, p.bmin + (row + 0.5) * p.db, p.t_cam, xd, kd);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { x[i] = df64(xd[i]); k[i] = df64(kd[i]); }
+            n = 0;
+            crossings = 0;
+            ratio = 0.0;
+            inten = 0.0;
+        }
+        if (!__any_sync(0xffffffffu, id >= 0)) break;
+        if (id >= 0) {
+            const int st = disk_step_df(p, d, a, x, k, n, crossings, ratio, inten);
+            if (st >= 0) {
+                const bool hit = st == kDiskHit;
+                d.ratio[pix] = hit ? ratio : 0.0;
+                d.inten[pix] = hit ? inten : 0.0;
+                d.order[pix] = hit ? crossings : 0;
+                if (d.status) d.status[pix] = st;
+                if (d.steps) d.steps[pix] = n;
+                c_rays += 1;
+                c_steps += (unsigned long long)n;
+                c_trunc += (st == kTruncated);
+                c_err += (st == kError);
+                id = -1;
+            }
+        }
+    }
+    warp_add_stats(stats, c_rays, c_steps, c_steps, c_trunc, c_err);
 }
 
 }  // namespace raptor

@@ -171,8 +171,11 @@ def _disk(R, ctx, learned, **kw):
 
 @pytest.mark.parametrize("spin,incl", [(0.9375, 30.0), (0.5, 60.0)])
 def test_learned_disk_matches_fp64_disk_and_oracle(R, ora, trained, spin, incl):
-    """Learned thin disk (256^2, +-16 M) against the exact FP64 disk: fallback pixels equal it
-    bit for bit (the same kernel), the others agree on hit and order for >= 99.5 % of the
+    """Learned thin disk (256^2, +-16 M) against the exact FP64 disk: with the FP64 fallback
+    the fallback pixels equal it bit for bit (the same kernel), with the double-float fallback
+    (the default) they agree on hit and order for >= 99.9 % and on E_obs/E_em within
+    rounding amplified near the photon orbit; the learned pixels agree on hit and order for
+    >= 99.5 % of the
     pixels (the rest lie at the disk's edges, where a radius error moves the crossing across
     r_in or r_out) and on E_obs/E_em within 1e-2; the line spectrum within 1e-2; sampled
     pixels against the oracle one by one."""
@@ -180,11 +183,25 @@ def test_learned_disk_matches_fp64_disk_and_oracle(R, ora, trained, spin, incl):
     ctx = R.Context(R.camera_desc(**cam))
     ctx.crossings_set(trained)
     f = _disk(R, ctx, False)
+    ctx.crossings_config(1.0, fallback_df64=False)
+    g64 = _disk(R, ctx, True)
+    ctx.crossings_config(1.0, fallback_df64=True)
     g = _disk(R, ctx, True)
     fb = g["steps"] > 0
     assert fb.any() and (~fb).sum() > 0.8 * fb.size
+    assert np.array_equal(g64["steps"] > 0, fb)
+    # FP64 fallback: the FP64 disk's own values; double-float fallback: the same hits, ratios
+    # within rounding amplified by the near-critical orbits
     for k in ("ratio", "intensity", "order", "status", "steps"):
-        assert np.array_equal(g[k][fb], f[k][fb]), k
+        assert np.array_equal(g64[k][fb], f[k][fb]), k
+        assert np.array_equal(g64[k][~fb], g[k][~fb]), k
+    same = fb & (g["order"] == f["order"])
+    assert same.sum() >= 0.999 * fb.sum(), (same.sum(), fb.sum())
+    both = same & (f["order"] > 0)
+    d = np.abs(g["ratio"][both] / f["ratio"][both] - 1)
+    print("double-float fallback: %d pixels, order agreement %.5f, ratio diff median %.1e max %.1e"
+          % (fb.sum(), same.sum() / fb.sum(), np.median(d), d.max()))
+    assert np.median(d) <= 1e-9 and d.max() <= RATIO_TOL
     nb = ~fb
     agree = (g["order"][nb] == f["order"][nb])
     assert agree.mean() >= 0.995, agree.mean()
@@ -252,6 +269,8 @@ def test_learned_disk_argument_checks(R, trained):
         with pytest.raises(R.RaptorError) as e:
             ctx.crossings_config(bad)
         assert e.value.status == R.EINVAL
+    from paper_1801_10452_b300 import lib
+    assert lib().raptor_crossings_config(ctx.handle, 1.0, 2) == R.EINVAL
     ctx.disk_render(**DISK, learned=True)
 
 
@@ -265,7 +284,7 @@ def test_learned_disk_band_zero_and_wide(R, trained):
     f = _disk(R, ctx, False)
     frac = []
     for band in (0.0, 1.0, 3.0):
-        ctx.crossings_config(band)
+        ctx.crossings_config(band, fallback_df64=False)
         g = _disk(R, ctx, True)
         fb = g["steps"] > 0
         frac.append(fb.mean())
