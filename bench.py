@@ -461,7 +461,7 @@ def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
                 "spectrum_total_rel_err": float(sg.sum() / sf.sum() - 1),
                 "spectrum_l1_normalised": float(np.abs(sg / sg.sum() - sf / sf.sum()).sum()),
                 "stage_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
-                "network_roofline": {"bound": "tensor", "kernel": "k_mlp_fused<16> (mma.sync)", "achieved": ach,
+                "network_roofline": {"bound": "tensor", "kernel": "k_mlp_tc12<16> + k_mlp_tc34<16> (tcgen05; mma.sync if selected)", "achieved": ach,
                                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": ach / bf16_peak,
                                      "flops_per_ray": flops_ray}}
         ctx.close()

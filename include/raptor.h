@@ -398,7 +398,10 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
  * mean over rows x 16 outputs of the logistic loss log(1 + e^z) - y z on the presence logits
  * and the squared normalised error on the others, with NaN targets carrying no weight.
  * raptor_crossings_eval: decoded predictions pred_dev (device double [n][16]) per crossing:
- * presence probability, r_n, lambda_n, E_obs/E_em.  Asynchronous on `stream`.
+ * presence probability, r_n, lambda_n, E_obs/E_em.  Asynchronous on `stream`.  Inference runs
+ * on the kernel raptor_surrogate_kernel selects (tcgen05 by default, the 16 output sums
+ * reduced in two rounds of 8; or mma.sync); a tensor-core wait that runs out is reported by
+ * the next learned disk render that returns a spectrum (RAPTOR_ECUDA).
  * RAPTOR_EUNSUPPORTED before init or set; RAPTOR_EINVAL for bad sizes or ranges. */
 int raptor_crossings_param_count(void);
 raptor_status raptor_crossings_generate(raptor_ctx* ctx, long long n, unsigned long long seed, double spin_min,

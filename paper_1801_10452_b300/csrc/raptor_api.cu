@@ -111,6 +111,8 @@ struct raptor_ctx {
     unsigned long long x_step = 0;
     double x_band = 1.0;             // learned disk: fallback band around the critical curve (M)
     bool x_df = true;                // learned disk: fallback pixels in double-float arithmetic
+    __nv_bfloat16* x_h2tc = nullptr; // tcgen05 inference: h2 tiles (64 KB each)
+    size_t x_h2tc_tiles = 0;
     int* x_list = nullptr;           // learned disk: fallback pixels
     unsigned int* x_nlist = nullptr;
     size_t x_list_cap = 0;
@@ -1022,6 +1024,10 @@ static raptor_status disk_render_impl(raptor_ctx* ctx, const raptor_disk_desc* d
     std::vector<unsigned long long> h(d->n_bins);
     RCK(cudaMemcpyAsync(h.data(), ctx->d_hist, sizeof(unsigned long long) * d->n_bins, cudaMemcpyDeviceToHost, s));
     RCK(cudaStreamSynchronize(s));
+    if (learned) {
+        const raptor_status te = check_tc_err(ctx);
+        if (te != RAPTOR_OK) return te;
+    }
     for (int b = 0; b < d->n_bins; ++b) profile_host[b] = (double)h[b] / scale;
     return RAPTOR_OK;
 }
@@ -1212,7 +1218,8 @@ void raptor_destroy(raptor_ctx* ctx) {
                   ctx->s_out, ctx->s_dout, ctx->s_dzf, ctx->s_dh, ctx->s_h1, ctx->s_h2, ctx->s_h3, ctx->s_dzb, ctx->s_y,
                   ctx->s_loss, ctx->s_in, ctx->s_fb, ctx->s_start, ctx->d_curve, ctx->s_err, ctx->s_h2tc,
                   ctx->d_crit, ctx->d_rest, ctx->d_hist, ctx->d_fwd, ctx->d_x2tab, ctx->x_P, ctx->x_G, ctx->x_m1,
-                  ctx->x_m2, ctx->x_w, ctx->x_out, ctx->x_dout, ctx->x_y, ctx->x_list, ctx->x_nlist};
+                  ctx->x_m2, ctx->x_w, ctx->x_out, ctx->x_dout, ctx->x_y, ctx->x_list, ctx->x_nlist,
+                  ctx->x_h2tc};
     for (void* q : sp) cudaFree(q);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.a);
@@ -1253,8 +1260,8 @@ cudaError_t sur_alloc(raptor_ctx* c) {
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_w, 6 * kHid * kHid * sizeof(__nv_bfloat16));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_err, sizeof(int));
         // the tcgen05 kernels' shared-memory plans (set once, outside any stream capture)
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc12, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc12Smem);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc34, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc34Smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc12<kOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc12Smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc34<kOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc34Smem);
         if (e == cudaSuccess) e = cudaMemset(c->s_err, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->s_G, 0, n * sizeof(float));
         if (e != cudaSuccess) return e;
@@ -2092,7 +2099,12 @@ cudaError_t x_alloc(raptor_ctx* c) {
         float** f[] = {&c->x_P, &c->x_G, &c->x_m1, &c->x_m2};
         for (float** q : f)
             if (e == cudaSuccess) e = cudaMalloc((void**)q, n * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_w, 4 * kHid * kHid * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_w, 6 * kHid * kHid * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mlp_tc12<kXOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc12Smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mlp_tc34<kXOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc34_smem<kXOut>());
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_out, kSurRows * kXOut * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_dout, kSurRows * kXOut * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_y, kSurRows * kXOut * sizeof(double));
@@ -2101,10 +2113,12 @@ cudaError_t x_alloc(raptor_ctx* c) {
     return e;
 }
 
-__nv_bfloat16* xw(raptor_ctx* c, int i) { return c->x_w + (size_t)i * kHid * kHid; }  // w2, w2t, w3, w3t
+// w2, w2t, w3, w3t, then w2, w3 in the tcgen05 operand layout
+__nv_bfloat16* xw(raptor_ctx* c, int i) { return c->x_w + (size_t)i * kHid * kHid; }
 
 cudaError_t x_refresh(raptor_ctx* c, cudaStream_t s) {
     k_refresh_bf16<<<256, 256, 0, s>>>(c->x_P, xw(c, 0), xw(c, 1), xw(c, 2), xw(c, 3));
+    k_tc_pack<<<256, 256, 0, s>>>(c->x_P, xw(c, 4));
     return cudaGetLastError();
 }
 
@@ -2144,10 +2158,28 @@ cudaError_t x_backward(raptor_ctx* c, long long rows, int* nb_out, cudaStream_t 
     return cudaGetLastError();
 }
 
-// Network outputs [n][16] (normalised) of n raw input rows: the fused mma.sync kernel.
+// Network outputs [n][16] (normalised) of n raw input rows: the two persistent tcgen05
+// kernels (the output layer's 16 sums reduced in two rounds of 8), or the fused mma.sync
+// kernel (raptor_surrogate_kernel chooses for both networks).
 cudaError_t x_eval_rows(raptor_ctx* c, const float* inputs, long long n, float* out, cudaStream_t s) {
-    const long long blocks = (n + kFRows - 1) / kFRows;
-    k_mlp_fused<kXOut><<<(unsigned)blocks, 256, 0, s>>>(c->x_P, xw(c, 0), xw(c, 2), inputs, n, out);
+    if (c->s_kernel == RAPTOR_MLP_MMA_SYNC) {
+        const long long blocks = (n + kFRows - 1) / kFRows;
+        k_mlp_fused<kXOut><<<(unsigned)blocks, 256, 0, s>>>(c->x_P, xw(c, 0), xw(c, 2), inputs, n, out);
+        return cudaGetLastError();
+    }
+    const long long tiles = (n + kTcRows - 1) / kTcRows;
+    cudaError_t e = cudaSuccess;
+    if ((size_t)tiles > c->x_h2tc_tiles) {
+        e = cudaFree(c->x_h2tc);
+        c->x_h2tc = nullptr;
+        c->x_h2tc_tiles = 0;
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->x_h2tc, (size_t)tiles * kTcTileBytes);
+        if (e != cudaSuccess) return e;
+        c->x_h2tc_tiles = (size_t)tiles;
+    }
+    const unsigned grid = (unsigned)std::min<long long>(tiles, c->num_sms);
+    k_mlp_tc12<kXOut><<<grid, kTcThreads, kTc12Smem, s>>>(c->x_P, xw(c, 4), inputs, n, c->x_h2tc, c->s_err);
+    k_mlp_tc34<kXOut><<<grid, kTcThreads, tc34_smem<kXOut>(), s>>>(c->x_P, xw(c, 5), c->x_h2tc, n, out, c->s_err);
     return cudaGetLastError();
 }
 
@@ -2208,7 +2240,7 @@ raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, 
                                                                     ctx->s_in, ctx->s_fb);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
-            ProfScope pm(ctx, kProfSurrogateMlp, s);
+            ProfScope pm(ctx, kProfSurrogateMlp, s, ctx->s_kernel == RAPTOR_MLP_MMA_SYNC ? 1 : 2);
             e = x_eval_rows(ctx, ctx->s_in, (long long)n, out, s);
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->x_list, 0xFF, n * sizeof(int), s);

@@ -182,10 +182,17 @@ __global__ void k_tc_pack(const float* __restrict__ P, __nv_bfloat16* __restrict
 }
 
 // Shared-memory plan of the two kernels (after aligning the dynamic base to 1024 B).
+// Output layer of NOUT outputs: its FP32 weights and biases, and the partial sums of column
+// quarters 1-3 for 8 outputs at a time ([3][128][8]; NOUT / 8 rounds).
 constexpr uint32_t kTc12Params = (kHid * kIn + 2 * kHid + 8) * 4;          // w1, b1, b2, norm
-constexpr uint32_t kTc34Params = (kHid + kOut * kHid + kOut + (kTcQuarters - 1) * kTcRows * kOut) * 4;  // b3, w4, b4, partial sums
+template <int NOUT>
+constexpr uint32_t tc34_params() { return (kHid + NOUT * kHid + NOUT + (kTcQuarters - 1) * kTcRows * 8) * 4; }
+constexpr uint32_t kTc34Params = tc34_params<kOut>();  // b3, w4, b4, partial sums
 constexpr uint32_t kTc12Smem = 1024 + kTcWBytes + kTcTileBytes + kTc12Params + sizeof(TcCtl);
-constexpr uint32_t kTc34Smem = 1024 + kTcWBytes + kTcTileBytes + kTc34Params + sizeof(TcCtl);
+template <int NOUT>
+constexpr uint32_t tc34_smem() { return 1024 + kTcWBytes + kTcTileBytes + tc34_params<NOUT>() + sizeof(TcCtl); }
+constexpr uint32_t kTc34Smem = tc34_smem<kOut>();
+static_assert(tc34_smem<16>() <= 232448, "the 16-output plan fits in one CTA's shared memory");
 
 __device__ __forceinline__ uint8_t* tc_align(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -213,6 +220,7 @@ __device__ __forceinline__ void tc_teardown(TcCtl* ctl, bool w_pending, int* err
 }
 
 // Layers 1 and 2.  x: [n][4] raw inputs; h2: [tiles][64 KB] in the operand layout.
+template <int NOUT = kOut>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restrict__ P, const __nv_bfloat16* __restrict__ wu2,
                                                             const float* __restrict__ x, long long n,
                                                             __nv_bfloat16* __restrict__ h2, int* __restrict__ err) {
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
         sb1[i] = P[MlpLayout::B1 + i];
         sb2[i] = P[MlpLayout::B2 + i];
     }
-    if (tid < 8) snorm[tid] = P[MlpLayout::NORM + tid];
+    if (tid < 8) snorm[tid] = P[MlpLayoutT<NOUT>::NORM + tid];
     tc_sync();
     const uint32_t tmem = ctl->tmem;
     if (tid == 0) {
@@ -308,7 +316,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
     tc_teardown(ctl, w_pending, err);
 }
 
-// Layers 3 and 4.  h2 as written by k_mlp_tc12; out: [n][8] normalised outputs.
+// Layers 3 and 4.  h2 as written by k_mlp_tc12; out: [n][NOUT] normalised outputs.
+template <int NOUT = kOut>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restrict__ P, const __nv_bfloat16* __restrict__ wu3,
                                                             const __nv_bfloat16* __restrict__ h2, long long n,
                                                             float* __restrict__ out, int* __restrict__ err) {
@@ -317,16 +326,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
     uint8_t* sA = sW + kTcWBytes;
     float* sb3 = reinterpret_cast<float*>(sA + kTcTileBytes);
     float* sw4 = sb3 + kHid;
-    float* sb4 = sw4 + kOut * kHid;
-    float* sred = sb4 + kOut;   // [3][128][8] partial sums of column quarters 1-3
-    TcCtl* ctl = reinterpret_cast<TcCtl*>(sred + (kTcQuarters - 1) * kTcRows * kOut);
+    float* sb4 = sw4 + NOUT * kHid;
+    float* sred = sb4 + NOUT;   // [3][128][8] partial sums of column quarters 1-3, 8 outputs a round
+    TcCtl* ctl = reinterpret_cast<TcCtl*>(sred + (kTcQuarters - 1) * kTcRows * 8);
+    static_assert(NOUT % 8 == 0, "outputs are reduced 8 at a time");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long n_tiles = (n + kTcRows - 1) / kTcRows;
 
     tc_prologue(ctl);
-    for (int i = tid; i < kHid; i += kTcThreads) sb3[i] = P[MlpLayout::B3 + i];
-    for (int i = tid; i < kOut * kHid; i += kTcThreads) sw4[i] = P[MlpLayout::W4 + i];
-    if (tid < kOut) sb4[tid] = P[MlpLayout::B4 + tid];
+    for (int i = tid; i < kHid; i += kTcThreads) sb3[i] = P[MlpLayoutT<NOUT>::B3 + i];
+    for (int i = tid; i < NOUT * kHid; i += kTcThreads) sw4[i] = P[MlpLayoutT<NOUT>::W4 + i];
+    if (tid < NOUT) sb4[tid] = P[MlpLayoutT<NOUT>::B4 + tid];
     tc_sync();
     const uint32_t tmem = ctl->tmem;
     if (tid == 0) {
@@ -368,9 +378,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
             a_pending = true;
         }
         // bias + SiLU (rounded to BF16 as in training), then the FP32 output layer
-        float acc[kOut];
+        float acc[NOUT];
 #pragma unroll
-        for (int o = 0; o < kOut; ++o) acc[o] = 0.f;
+        for (int o = 0; o < NOUT; ++o) acc[o] = 0.f;
 #pragma unroll 1
         for (int cc = 0; cc < 2; ++cc) {
             uint32_t v[32];
@@ -380,31 +390,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
                 const int col = c0 + 32 * cc + q;
                 const float h = __bfloat162float(__float2bfloat16(silu(__uint_as_float(v[q]) + sb3[col])));
 #pragma unroll
-                for (int o = 0; o < kOut; ++o) acc[o] += sw4[o * kHid + col] * h;
+                for (int o = 0; o < NOUT; ++o) acc[o] += sw4[o * kHid + col] * h;
             }
         }
-        if (quarter > 0) {
-            float4* r4 = reinterpret_cast<float4*>(sred + ((quarter - 1) * kTcRows + er) * kOut);
-            r4[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            r4[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-        }
-        tc_sync();
-        if (quarter == 0) {
-            const long long m = t * kTcRows + er;
-            if (m < n) {
 #pragma unroll
-                for (int qq = 1; qq < kTcQuarters; ++qq) {
-                    const float4* r4 = reinterpret_cast<const float4*>(sred + ((qq - 1) * kTcRows + er) * kOut);
-                    const float4 p0 = r4[0], p1 = r4[1];
-                    acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w;
-                    acc[4] += p1.x; acc[5] += p1.y; acc[6] += p1.z; acc[7] += p1.w;
-                }
-                float4* o4 = reinterpret_cast<float4*>(out + m * kOut);
-                o4[0] = make_float4(acc[0] + sb4[0], acc[1] + sb4[1], acc[2] + sb4[2], acc[3] + sb4[3]);
-                o4[1] = make_float4(acc[4] + sb4[4], acc[5] + sb4[5], acc[6] + sb4[6], acc[7] + sb4[7]);
+        for (int g = 0; g < NOUT; g += 8) {
+            if (quarter > 0) {
+                float4* r4 = reinterpret_cast<float4*>(sred + ((quarter - 1) * kTcRows + er) * 8);
+                r4[0] = make_float4(acc[g + 0], acc[g + 1], acc[g + 2], acc[g + 3]);
+                r4[1] = make_float4(acc[g + 4], acc[g + 5], acc[g + 6], acc[g + 7]);
             }
+            tc_sync();
+            if (quarter == 0) {
+                const long long m = t * kTcRows + er;
+                if (m < n) {
+#pragma unroll
+                    for (int qq = 1; qq < kTcQuarters; ++qq) {
+                        const float4* r4 = reinterpret_cast<const float4*>(sred + ((qq - 1) * kTcRows + er) * 8);
+                        const float4 p0 = r4[0], p1 = r4[1];
+                        acc[g + 0] += p0.x; acc[g + 1] += p0.y; acc[g + 2] += p0.z; acc[g + 3] += p0.w;
+                        acc[g + 4] += p1.x; acc[g + 5] += p1.y; acc[g + 6] += p1.z; acc[g + 7] += p1.w;
+                    }
+                    float4* o4 = reinterpret_cast<float4*>(out + m * NOUT + g);
+                    o4[0] = make_float4(acc[g + 0] + sb4[g + 0], acc[g + 1] + sb4[g + 1], acc[g + 2] + sb4[g + 2],
+                                        acc[g + 3] + sb4[g + 3]);
+                    o4[1] = make_float4(acc[g + 4] + sb4[g + 4], acc[g + 5] + sb4[g + 5], acc[g + 6] + sb4[g + 6],
+                                        acc[g + 7] + sb4[g + 7]);
+                }
+            }
+            tc_sync();
         }
-        tc_sync();
     }
     // an activation copy issued for a tile this CTA will not process cannot exist (the next
     // tile is fetched only if it is processed), but an aborted loop may leave one in flight
