@@ -738,7 +738,9 @@ def run_native(args):
         cand["mixed_fp64_all"] = main["prof"].get("mixed_fp64", (0.0, 0))[0] + main["prof"].get("mixed_fp64_long", (0.0, 0))[0]
     dom = max(cand, key=lambda k: cand[k])
     roof = dict(roofs[paths[0] + ":" + dom])
-    src = f"FMA-chain microbenchmark ({roof['pipe']}), measured in this run"
+    src = f"FMA-chain microbenchmark ({roof.get('pipe', roof['bound'])}), measured in this run"
+    if roof["bound"] == "tensor":
+        src = roof.get("peak_source", "MEASURED_PEAKS.json")
     if roof.get("pipe", "").startswith("fp32 (double"):
         src = (f"FP32 FMA-chain microbenchmark ({fma32:.1f} TFLOP/s, i.e. {fma32 / 2:.1f} T instructions/s) / "
                f"{df_ipf:.2f} FP32 instructions per algorithmic flop of a double-float step (counted from the source)")
