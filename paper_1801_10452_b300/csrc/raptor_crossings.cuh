@@ -313,6 +313,18 @@ __device__ __forceinline__ int disk_step_df(const Params& p, const DiskArgs& d, 
     // the plane is crossed when theta - pi/2 changes sign (or reaches 0), not starting on it
     if (s0.hi != 0.f && ((s0.hi > 0.f) != (s1.hi > 0.f) || s1.hi == 0.f)) {
         crossings += 1;
+        // far from [r_in, r_out] the crossing cannot hit the disk: no refinement (as in
+        // disk_step; a step changes r by at most ~eps r)
+        const float grow = 1.f + 4.f * p.f.eps + 0.05f;
+        const float r0 = xf[1], r1 = x[1].hi + x[1].lo;
+        if (fmaxf(r0, r1) * grow < (float)d.r_in || fminf(r0, r1) > (float)d.r_out * grow) {
+            if (crossings >= d.max_cross) return kDiskNone;
+            const float r = r1;
+            if (r < p.f.r_stop) return kCaptured;
+            if (r > p.f.r_esc) return kEscaped;
+            if (n >= p.max_steps) return kTruncated;
+            return -1;
+        }
         df64 xc[4], kc[4];
         disk_crossing_df(a, xo, ko, dl, x[2], xc, kc);
         const double rc = (double)xc[1];

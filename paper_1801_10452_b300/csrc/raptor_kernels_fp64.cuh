@@ -266,10 +266,15 @@ __device__ __forceinline__ int disk_step(const Params& p, const DiskArgs& d, dou
     if (!fin) return kError;
     if ((xo[2] - half_pi) * (x[2] - half_pi) <= 0.0 && xo[2] != half_pi) {
         crossings += 1;
+        // A step changes r by at most ~eps r (the step rule), so the crossing's radius lies
+        // within that of the step's end radii: a crossing far outside [r_in, r_out] cannot
+        // hit the disk and skips the refinement (same hits, same values).
+        const double grow = 1.0 + 4.0 * p.eps + 0.05;
+        const bool near = fmax(xo[1], x[1]) * grow >= d.r_in && fmin(xo[1], x[1]) <= d.r_out * grow;
         double xc[4], kc[4];
-        disk_crossing(p.a, xo, ko, dl, x[2], xc, kc);
-        const double rc = xc[1];
-        if (rc >= d.r_in && rc <= d.r_out) {
+        if (near) disk_crossing(p.a, xo, ko, dl, x[2], xc, kc);
+        const double rc = near ? xc[1] : -1.0;
+        if (near && rc >= d.r_in && rc <= d.r_out) {
             KSPoint<double> P;
             ks_point<double>(p.a, rc, xc[2], P);
             double u[4], kcov[4];
