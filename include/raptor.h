@@ -386,7 +386,8 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
  *   E_obs/E_em of a prograde Keplerian emitter at r_n (Eq. 30), trained for r_n >= r_isco.
  *
  * raptor_crossings_generate: n counter-based samples over the camera's field of view and the
- * given spin and inclination ranges (0 < i < 90), inputs_dev (device float [n][4], rounded
+ * given spin (-1 < a < 1; a < 0: the emitter's orbit retrograde relative to the hole) and
+ * inclination ranges (0 < i < 90), inputs_dev (device float [n][4], rounded
  * to FP32 before tracing) and targets_dev (device double [n][16]: presence 1/0; NaN for the
  * regression entries of absent crossings and for ratios inside the ISCO), raw_dev (optional,
  * device double [n][16]: per crossing presence, r_n, lambda_n, E_obs/E_em, NaN if absent).
@@ -407,8 +408,11 @@ int raptor_crossings_param_count(void);
 raptor_status raptor_crossings_generate(raptor_ctx* ctx, long long n, unsigned long long seed, double spin_min,
                                         double spin_max, double incl_min_deg, double incl_max_deg, float* inputs_dev,
                                         double* targets_dev, double* raw_dev, void* stream);
-raptor_status raptor_crossings_init(raptor_ctx* ctx, const double* targets_dev, long long n, unsigned long long seed,
-                                    void* stream);
+/* raptor_crossings_init: inputs_dev (device float [n][4], may be NULL) sets the spin and
+ * inclination normalisation to the range of the inputs (else a in [0, 1] and i in [5, 85] deg
+ * map to [-1, 1]); alpha and beta are normalised over the camera's field of view. */
+raptor_status raptor_crossings_init(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                    unsigned long long seed, void* stream);
 raptor_status raptor_crossings_train(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
                                      int steps, double lr, double lr_final, unsigned long long seed, double* loss_host,
                                      void* stream);

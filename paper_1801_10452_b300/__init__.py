@@ -126,7 +126,7 @@ def lib():
             "raptor_crossings_param_count": (C.c_int, []),
             "raptor_crossings_generate": (st, [vp, C.c_longlong, C.c_ulonglong, C.c_double, C.c_double, C.c_double,
                                                C.c_double, vp, vp, vp, vp]),
-            "raptor_crossings_init": (st, [vp, vp, C.c_longlong, C.c_ulonglong, vp]),
+            "raptor_crossings_init": (st, [vp, vp, vp, C.c_longlong, C.c_ulonglong, vp]),
             "raptor_crossings_train": (st, [vp, vp, vp, C.c_longlong, C.c_int, C.c_double, C.c_double, C.c_ulonglong, dp, vp]),
             "raptor_crossings_grad": (st, [vp, vp, vp, C.c_longlong, C.POINTER(C.c_float), dp, vp]),
             "raptor_crossings_eval": (st, [vp, vp, C.c_longlong, vp, vp]),
@@ -466,8 +466,11 @@ class Context:
                                                     _stream(stream)), "raptor_crossings_generate")
         return (x, y, z) if raw else (x, y)
 
-    def crossings_init(self, targets, seed=7, stream=None):
-        self._check(lib().raptor_crossings_init(self._h, C.c_void_p(targets.data_ptr()), int(targets.shape[0]), int(seed),
+    def crossings_init(self, targets, seed=7, stream=None, inputs=None):
+        """Initialise the crossing network; `inputs` (optional) sets the spin and inclination
+        normalisation to their range."""
+        self._check(lib().raptor_crossings_init(self._h, C.c_void_p(inputs.data_ptr()) if inputs is not None else None,
+                                                C.c_void_p(targets.data_ptr()), int(targets.shape[0]), int(seed),
                                                 _stream(stream)), "raptor_crossings_init")
 
     def crossings_train(self, inputs, targets, steps, lr=2e-3, lr_final=2e-5, seed=11, record_loss=False, stream=None):

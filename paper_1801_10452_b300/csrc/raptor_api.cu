@@ -2269,7 +2269,7 @@ raptor_status raptor_crossings_generate(raptor_ctx* ctx, long long n, unsigned l
     if (!ctx) return RAPTOR_EINVAL;
     ctx->err.clear();
     if (n < 1 || !inputs_dev || !targets_dev) return fail(ctx, RAPTOR_EINVAL, "need n >= 1 and output buffers");
-    if (!(spin_min >= 0.0 && spin_max >= spin_min && spin_max < 1.0)) return fail(ctx, RAPTOR_EINVAL, "spin range invalid");
+    if (!(spin_min > -1.0 && spin_max >= spin_min && spin_max < 1.0)) return fail(ctx, RAPTOR_EINVAL, "spin range invalid");
     if (!(incl_min_deg > 0.0 && incl_max_deg >= incl_min_deg && incl_max_deg < 90.0))
         return fail(ctx, RAPTOR_EINVAL, "inclination range invalid (0 < i < 90 deg: the camera above the plane)");
     SurrogateRange R{ctx->cam.alpha_min, ctx->cam.alpha_max, ctx->cam.beta_min, ctx->cam.beta_max, spin_min, spin_max,
@@ -2285,8 +2285,8 @@ raptor_status raptor_crossings_generate(raptor_ctx* ctx, long long n, unsigned l
     return RAPTOR_OK;
 }
 
-raptor_status raptor_crossings_init(raptor_ctx* ctx, const double* targets_dev, long long n, unsigned long long seed,
-                                    void* stream) {
+raptor_status raptor_crossings_init(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
+                                    unsigned long long seed, void* stream) {
     if (!ctx) return RAPTOR_EINVAL;
     ctx->err.clear();
     if (!targets_dev || n < 2) return fail(ctx, RAPTOR_EINVAL, "need targets and n >= 2");
@@ -2305,9 +2305,24 @@ raptor_status raptor_crossings_init(raptor_ctx* ctx, const double* targets_dev, 
     for (int i = 0; i < kHid * kHid; ++i) P[XLayout::W3 + i] = uni(std::sqrt(6.0 / kHid));
     for (int i = 0; i < kXOut * kHid; ++i) P[XLayout::W4 + i] = uni(std::sqrt(3.0 / kHid));
     const double ha = 0.5 * (ctx->cam.alpha_max - ctx->cam.alpha_min), hb = 0.5 * (ctx->cam.beta_max - ctx->cam.beta_min);
-    const float scale[4] = {(float)(1.0 / ha), (float)(1.0 / hb), 2.0f, 1.0f / 40.0f};
-    const float shift[4] = {(float)(0.5 * (ctx->cam.alpha_max + ctx->cam.alpha_min)),
-                            (float)(0.5 * (ctx->cam.beta_max + ctx->cam.beta_min)), 0.5f, 45.0f};
+    float scale[4] = {(float)(1.0 / ha), (float)(1.0 / hb), 2.0f, 1.0f / 40.0f};
+    float shift[4] = {(float)(0.5 * (ctx->cam.alpha_max + ctx->cam.alpha_min)),
+                      (float)(0.5 * (ctx->cam.beta_max + ctx->cam.beta_min)), 0.5f, 45.0f};
+    if (inputs_dev) {
+        // spin and inclination mapped to [-1, 1] over the range of the given inputs
+        std::vector<float> x((size_t)m * kIn);
+        RCK(cudaMemcpyAsync(x.data(), inputs_dev, x.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+        RCK(cudaStreamSynchronize(s));
+        for (int c = 2; c < 4; ++c) {
+            float lo = x[c], hi = x[c];
+            for (long long i = 1; i < m; ++i) {
+                lo = std::min(lo, x[i * kIn + c]);
+                hi = std::max(hi, x[i * kIn + c]);
+            }
+            shift[c] = 0.5f * (lo + hi);
+            scale[c] = hi > lo ? 2.0f / (hi - lo) : 1.0f;
+        }
+    }
     for (int c = 0; c < 4; ++c) {
         P[XLayout::NORM + c] = scale[c];
         P[XLayout::NORM + 4 + c] = shift[c];
