@@ -29,6 +29,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "kerr_analytic_1024x1024_a0.9375_i60_230GHz"
 METRIC = "rays/s and geodesic steps/s at 1024^2 Kerr image, mixed+MLP vs FP64 at <=1e-3 flux"
 CPU_SAMPLE_STRIDE = 8  # oracle traces every 8th pixel in each direction (128 x 128 rays)
+PROFILED_RENDERS = 2   # renders of the separate pass that records per-kernel times
+FINAL_LINE_MAX = 2000  # bytes: the last stdout line carries the headline only
 
 
 def _env_rank():
@@ -234,7 +236,7 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
     if sampler:
         sampler.start()
     ctx.stats_reset()
-    ctx.profile(True)
+    ctx.profile(False)
     wall0 = time.perf_counter()
     dev_ms = _time_render(ctx, torch, freqs, image, flush, n_steps, stream)
     torch.cuda.synchronize()
@@ -242,15 +244,22 @@ def _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sa
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    prof = ctx.profile_read()
-    ctx.profile(False)
     st = ctx.stats_ex()
     if world > 1:
         dev_ms = max_over_ranks(dev_ms, dist)
+    # per-kernel breakdown in a separate pass with the library's per-launch events on (the
+    # timed renders above run without them)
+    ctx.stats_reset()
+    ctx.profile(True)
+    prof_ms = _time_render(ctx, torch, freqs, image, flush, PROFILED_RENDERS, stream)
+    prof = ctx.profile_read()
+    timeline = ctx.profile_timeline()
+    ctx.profile(False)
+    st_prof = ctx.stats_ex()
     _, flux = ctx.render(freqs, image=image, stream=stream)
     torch.cuda.synchronize()
     return dict(ctx=ctx, image=image, ms=dev_ms / n_steps, wall=wall, clocks=clocks, prof=prof, stats=st, flux=flux,
-                tuned=tuned)
+                tuned=tuned, st_prof=st_prof, prof_ms=prof_ms / PROFILED_RENDERS, timeline=timeline)
 
 
 def _lightcurve_extra(R, torch, args, stream, params, n=100, size=256):
@@ -659,7 +668,9 @@ def run_native(args):
     value = aggregate_rate(world, rays_step, ms_step)
     st = main["stats"]
     steps_per_s = world * (st["steps"] / args.steps) / (ms_step * 1e-3)
-    launches = sum(v[1] for v in main["prof"].values())
+    # kernel launches per render (counted by the library in the profiled pass) x timed renders
+    launches_per_render = sum(v[1] for v in main["prof"].values()) / PROFILED_RENDERS
+    launches = int(round(launches_per_render * args.steps))
 
     # ---- end to end through the C ABI with host buffers --------------------------------
     e2e = None
@@ -685,85 +696,22 @@ def run_native(args):
         return
 
     # ---- rooflines: algorithmic flops (from the kernel source) / measured FMA peaks -------
-    peaks = _peaks()
     fma32 = R.measure_fma_peak(False)
     fma64 = R.measure_fma_peak(True)
-    flops = _flops_per_step()
-    from paper_1801_10452_b300 import flopcount as _fc
-
-    df_ipf = _fc.df64_instructions_per_step(1, "analytic")["instructions_per_flop"]
-    roofs = {}
-    for pth, r in res.items():
-        prof, s = r["prof"], r["stats"]
-        for kname, (kms, kn) in prof.items():
-            if kn == 0 or kname in ("reduce", "trace", "load", "peak"):
-                continue
-            if kname == "surrogate_mlp":
-                # the two 256 x 256 hidden layers on the tensor cores: 2 x 2 x 256^2 flops per ray
-                fl_render = 2.0 * 2 * 256 * 256 * npix
-                per_ms = kms / args.steps
-                ach = fl_render / (per_ms * 1e-3) / 1e12
-                pkb = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1400.0))
-                roofs[pth + ":" + kname] = {
-                    "bound": "tensor", "achieved": ach, "peak": pkb, "unit": "TFLOP/s", "frac": ach / pkb,
-                    "kernel_ms_per_render": per_ms, "launches_per_render": kn / args.steps,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)",
-                    "note": "k_mlp_tc12 + k_mlp_tc34 (tcgen05.mma, BF16 -> FP32 in TMEM); their FP32 input/output "
-                            "layers and SiLU run on the CUDA cores inside the same kernels"}
-                continue
-            if kname == "surrogate":
-                continue  # the stage interval (inputs, network, start states): kernels_ms_per_step
-            if kname == "render_fp64":
-                steps_k, pk, pipe = s["steps"], fma64, "fp64"
-            elif kname in ("mixed_fp64", "mixed_fp64_long"):
-                # double-float: the FP32 pipe's instruction rate divided by the FP32
-                # instructions that one algorithmic flop of the step costs in double-float.
-                # mixed_fp64: the first stream's passes; mixed_fp64_long: the near-critical
-                # rays' FP64 phase on the second stream
-                n_long = s.get("fp64_steps_long", 0)
-                steps_k = s["fp64_steps"] - n_long if kname == "mixed_fp64" else n_long
-                pk, pipe = (fma32 / (2.0 * df_ipf) if pth.endswith("_df") else fma64), (
-                    "fp32 (double-float)" if pth.endswith("_df") else "fp64")
-            else:
-                steps_k, pk, pipe = ctx_phase_steps(s, prof).get(kname, 0), fma32, "fp32"
-            fl_launch = flops["fp64_step"] * steps_k / kn
-            per_ms = kms / kn
-            ach = fl_launch / (per_ms * 1e-3) / 1e12
-            roofs[pth + ":" + kname] = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                            "frac": ach / pk, "kernel_ms_per_launch": per_ms, "steps_per_launch": steps_k / kn,
-                            "share_of_step": kms / max(1e-9, sum(v[0] for k2, v in prof.items()
-                                                                 if k2 not in ("peak", "surrogate_mlp")))}
-    # the whole FP64 phase (both streams' launches): all FP64 steps over the summed launch time
-    for pth, r in res.items():
-        prof, s = r["prof"], r["stats"]
-        a, b = prof.get("mixed_fp64", (0.0, 0)), prof.get("mixed_fp64_long", (0.0, 0))
-        if a[1] + b[1] == 0:
-            continue
-        pk = fma32 / (2.0 * df_ipf) if pth.endswith("_df") else fma64
-        kms, kn = a[0] + b[0], a[1] + b[1]
-        ach = flops["fp64_step"] * s["fp64_steps"] / (kms * 1e-3) / 1e12
-        roofs[pth + ":mixed_fp64_all"] = {
-            "bound": "alu", "pipe": "fp32 (double-float)" if pth.endswith("_df") else "fp64", "achieved": ach, "peak": pk,
-            "unit": "TFLOP/s", "frac": ach / pk, "kernel_ms_per_launch": kms / kn, "steps_per_launch": s["fp64_steps"] / kn,
-            "note": "both streams' FP64-phase launches: the passes (mixed_fp64, throughput) and the near-critical "
-                    "rays' chains (mixed_fp64_long, latency: a few warps per SM for most of the frame)"}
-    cand = {k: v[0] for k, v in main["prof"].items() if v[1] and (paths[0] + ":" + k) in roofs
-            and k not in ("mixed_fp64", "mixed_fp64_long")}
-    if paths[0] + ":mixed_fp64_all" in roofs:
-        cand["mixed_fp64_all"] = main["prof"].get("mixed_fp64", (0.0, 0))[0] + main["prof"].get("mixed_fp64_long", (0.0, 0))[0]
-    dom = max(cand, key=lambda k: cand[k])
+    roofs = _rooflines(res, fma32, fma64, npix)
+    dom = _dominant_kernel(main["prof"], paths[0], roofs)
     roof = dict(roofs[paths[0] + ":" + dom])
-    src = f"FMA-chain microbenchmark ({roof.get('pipe', roof['bound'])}), measured in this run"
+    df_ipf = roof.get("df64_instructions_per_flop")
     if roof["bound"] == "tensor":
-        src = roof.get("peak_source", "MEASURED_PEAKS.json")
-    if roof.get("pipe", "").startswith("fp32 (double"):
-        src = (f"FP32 FMA-chain microbenchmark ({fma32:.1f} TFLOP/s, i.e. {fma32 / 2:.1f} T instructions/s) / "
-               f"{df_ipf:.2f} FP32 instructions per algorithmic flop of a double-float step (counted from the source)")
-    roof.update({"kernel": dom, "traffic": None, "peak_source": src,
-                 "flops_per_step": flops["fp64_step"], "flops_note": "algorithmic, counted from the kernel source, FMA = 2"})
+        src = "MEASURED_PEAKS.json bf16_tflops_sustained"
+    elif df_ipf:
+        src = f"FP32 FMA-chain probe {fma32:.1f} TFLOP/s / (2 x {df_ipf:.2f} FP32 instr per flop, double-float)"
+    else:
+        src = f"{roof['pipe'].upper()} FMA-chain probe, this run"
+    roof.update({"kernel": dom, "traffic": None, "peak_source": src})
 
     # ---- CPU oracle on a bounded sample of the same workload -----------------------------
-    cpu = None
+    cpu, parity = None, {}
     if not args.no_cpu_baseline:
         r = oracle_sample(cam, freqs, CPU_SAMPLE_STRIDE)
         cpu = {"value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"], "kind": "oracle",
@@ -781,60 +729,152 @@ def run_native(args):
             g = rr["image"].cpu().numpy()[sl]
             den = np.maximum(np.abs(o), 1e-12 * np.abs(o).max())
             e = np.abs(g - o) / den
-            cpu[f"{pth}_max_rel_err_sampled"] = float(e.max())
-            cpu[f"{pth}_max_rel_err_sampled_bright"] = float(e[big].max())
-            cpu[f"{pth}_flux_rel_err_sampled"] = float(abs(g.sum() / o.sum() - 1))
+            parity[pth] = {"max_rel_err_sampled": float(e.max()), "max_rel_err_sampled_bright": float(e[big].max()),
+                           "flux_rel_err_sampled": float(abs(g.sum() / o.sum() - 1))}
+
+    dtype = {"mlp": "f32+f64+bf16", "mixed": "f32+f64", "fp64": "f64", "mlp_df": "f32+df64+bf16",
+             "mixed_df": "f32+df64"}[paths[0]]
+    detail = {
+        "headline": {"workload": workload, "precision": paths[0], "ms_per_step": ms_step, "value": value,
+                     "steps_per_ray": st["steps"] / (args.steps * npix),
+                     "fp64_step_fraction": st["fp64_steps"] / max(st["steps"], 1),
+                     "stats_per_render": {k: v / args.steps for k, v in st.items()},
+                     "launch": main["tuned"], "wall_s_timed_region": main["wall"],
+                     "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64}},
+        "kernels": {pth: {"profiled_ms_per_render": r["prof_ms"],
+                          "kernel_ms_per_render": {k: v[0] / PROFILED_RENDERS for k, v in r["prof"].items() if v[1]},
+                          "launches_per_render": {k: v[1] / PROFILED_RENDERS for k, v in r["prof"].items() if v[1]},
+                          "timeline_last_render": _timeline_summary(r["timeline"])}
+                    for pth, r in res.items()},
+        "rooflines": roofs,
+        "paths": {pth: {"ms_per_step": r["ms"], "rays_per_s": world * rays_step / (r["ms"] * 1e-3),
+                        "geodesic_steps_per_s": world * (r["stats"]["steps"] / args.steps) / (r["ms"] * 1e-3),
+                        "flux_jy": float(r["flux"][0])} for pth, r in res.items()},
+        "cpu_baseline": cpu, "oracle_parity_sampled": parity,
+        "surrogate": sur, "grid_workload": grid, "lightcurve_workload": lcurve, "thin_disk_workload": disk,
+        "learned_thin_disk_workload": ldisk, "verlet_workload": verlet, "emissivity_options": emis,
+    }
+    if "fp64" in res:
+        detail["flux_rel_err_vs_fp64"] = {pth: float(abs(r["flux"][0] / res["fp64"]["flux"][0] - 1))
+                                          for pth, r in res.items() if pth != "fp64"}
+    # the side workloads and the breakdown: one line each before the headline, and a file
+    for name, obj in detail.items():
+        if obj is not None:
+            print(json.dumps({"bench_part": name, "data": obj}), flush=True)
+    if args.detail_json:
+        with open(args.detail_json, "w") as f:
+            json.dump(detail, f, indent=1)
 
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": {"mlp": "f32+f64+bf16", "mixed": "f32+f64", "fp64": "f64", "mlp_df": "f32+df64+bf16",
-                  "mixed_df": "f32+df64"}[paths[0]],
-        "data": "synthetic (analytic plasma, deterministic)",
-        "config": {"workload": workload, "pixels": npix, "freqs_hz": freqs, "precision": paths[0],
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic (analytic plasma, deterministic)",
+        "config": {"workload": workload, "precision": paths[0], "pixels": npix, "freqs_hz": freqs,
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed render"},
-        "geodesic_steps_per_s": steps_per_s, "steps_per_ray": st["steps"] / (args.steps * npix),
-        "fp64_step_fraction": st["fp64_steps"] / max(st["steps"], 1),
-        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in main["prof"].items() if v[1]},
-        "roofline": roof, "rooflines": roofs, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": main["clocks"], "wall_s_timed_region": main["wall"],
-        "fma_peaks_tflops": {"fp32": fma32, "fp64": fma64},
-        "launch": main["tuned"],
-        "surrogate": sur,
-        "grid_workload": grid,
-        "lightcurve_workload": lcurve,
-        "thin_disk_workload": disk,
-        "learned_thin_disk_workload": ldisk,
-        "verlet_workload": verlet,
-        "emissivity_options": emis,
+        "geodesic_steps_per_s": steps_per_s,
+        "roofline": {k: _round(roof.get(k)) for k in ("bound", "kernel", "pipe", "achieved", "peak", "unit", "frac",
+                                                       "traffic", "peak_source")},
+        "cpu_baseline": None if cpu is None else {k: _round(cpu[k]) for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": None if e2e is None else {k: _round(v) for k, v in e2e.items()},
+        "gpu_launches": launches,
+        "clocks": None if main["clocks"] is None else {k: main["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "rays_per_s": {pth: _round(world * rays_step / (r["ms"] * 1e-3)) for pth, r in res.items()},
     }
-    for pth, r in res.items():
-        if pth == paths[0]:
-            continue
-        line[f"{pth}_path"] = {"value": world * rays_step / (r["ms"] * 1e-3), "unit": "rays/s", "ms_per_step": r["ms"],
-                               "geodesic_steps_per_s": world * (r["stats"]["steps"] / args.steps) / (r["ms"] * 1e-3)}
-        line[f"speedup_vs_{pth}"] = r["ms"] / ms_step
-    line["flux_jy"] = {pth: float(r["flux"][0]) for pth, r in res.items()}
-    if "fp64" in res:
-        line["flux_rel_err_vs_fp64"] = {pth: float(abs(r["flux"][0] / res["fp64"]["flux"][0] - 1))
-                                        for pth, r in res.items() if pth != "fp64"}
-    print(json.dumps(line), flush=True)
+    if roof.get("frac_of_fp64_native") is not None:
+        line["roofline"]["frac_of_fp64_native"] = _round(roof["frac_of_fp64_native"])
+    if "flux_rel_err_vs_fp64" in detail:
+        line["flux_rel_err_vs_fp64"] = {k: _round(v) for k, v in detail["flux_rel_err_vs_fp64"].items()}
+    if parity:
+        line["oracle_max_rel_err_sampled"] = {k: _round(v["max_rel_err_sampled"]) for k, v in parity.items()}
+    line["detail"] = "bench_part lines above" + (f"; {os.path.basename(args.detail_json)}" if args.detail_json else "")
+    out = json.dumps(line)
+    if len(out) > FINAL_LINE_MAX:
+        for k in ("oracle_max_rel_err_sampled", "rays_per_s", "detail"):
+            line.pop(k, None)
+            out = json.dumps(line)
+            if len(out) <= FINAL_LINE_MAX:
+                break
+    print(out, flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def ctx_phase_steps(st, prof):
-    """Steps per mixed phase: FP64 steps are counted; the FP32 steps are split between the
-    inbound and outbound phases in proportion to their device time."""
-    s32 = st["steps"] - st["fp64_steps"]
-    a = prof.get("mixed_fp32_in", (0, 0))[0]
-    c = prof.get("mixed_fp32_out", (0, 0))[0]
-    tot = a + c
-    if tot <= 0:
-        return {}
-    return {"mixed_fp32_in": s32 * a / tot, "mixed_fp32_out": s32 * c / tot, "mixed_fp64": st["fp64_steps"]}
+def _round(v, digits=5):
+    """Round floats to `digits` significant digits (compact output)."""
+    if isinstance(v, float) and np.isfinite(v) and v != 0.0:
+        return float(f"{v:.{digits}g}")
+    return v
+
+
+def _timeline_summary(tl):
+    """Per-launch timeline of the last profiled render: (kernel, stream lane, start ms, ms)."""
+    if not tl:
+        return []
+    # launches of the last render: from the last launch that starts a render (the first
+    # kernel of the first lane after the previous render's flux reduction)
+    starts = [i for i, e in enumerate(tl) if i > 0 and tl[i - 1][0] == "reduce" and e[0] != "reduce"]
+    first = starts[-1] if starts else 0
+    t0 = tl[first][2]
+    return [[e[0], e[1], round(e[2] - t0, 4), round(e[3], 4)] for e in tl[first:]]
+
+
+def _rooflines(res, fma32, fma64, npix):
+    """Per path and kernel: algorithmic flops (counted from the kernel source, FMA = 2) x the
+    steps the kernel took (device counters) / its CUDA-event time, against the measured
+    FMA-chain peak of the pipe it runs on (FP32, FP64, or the double-float rate derived from
+    the FP32 one); the network against the sustained BF16 figure of MEASURED_PEAKS.json."""
+    from paper_1801_10452_b300 import flopcount as _fc
+
+    peaks = _peaks()
+    fl = _flops_per_step()["fp64_step"]
+    df_ipf = _fc.df64_instructions_per_step(1, "analytic")["instructions_per_flop"]
+    pk_df = fma32 / (2.0 * df_ipf)
+    roofs = {}
+    for pth, r in res.items():
+        prof, s = r["prof"], r["st_prof"]
+        df = pth.endswith("_df")
+        for kname, (kms, kn) in prof.items():
+            if kn == 0 or kname in ("reduce", "trace", "load", "peak", "surrogate"):
+                continue
+            if kname == "surrogate_mlp":
+                # the two 256 x 256 hidden layers on the tensor cores: 2 x 2 x 256^2 flops per ray
+                per_ms = kms / PROFILED_RENDERS
+                ach = 2.0 * 2 * 256 * 256 * npix / (per_ms * 1e-3) / 1e12
+                pkb = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1400.0))
+                roofs[pth + ":" + kname] = {"bound": "tensor", "pipe": "bf16 tcgen05", "achieved": ach, "peak": pkb,
+                                            "unit": "TFLOP/s", "frac": ach / pkb, "kernel_ms_per_render": per_ms}
+                continue
+            entry = {"bound": "alu", "unit": "TFLOP/s"}
+            if kname == "render_fp64":
+                steps_k, pk, pipe = s["steps"], fma64, "fp64"
+            elif kname in ("mixed_fp64", "mixed_fp64_long"):
+                # mixed_fp64: the first stream's passes; mixed_fp64_long: the near-critical
+                # rays' FP64 phase on the second stream
+                n_long = s.get("fp64_steps_long", 0)
+                steps_k = s["fp64_steps"] - n_long if kname == "mixed_fp64" else n_long
+                pk, pipe = (pk_df, "fp32 (double-float)") if df else (fma64, "fp64")
+                if df:
+                    entry["df64_instructions_per_flop"] = df_ipf
+            else:
+                steps_k = s["fp32_steps_in"] if kname == "mixed_fp32_in" else s["fp32_steps_out"]
+                pk, pipe = fma32, "fp32"
+            ach = fl * steps_k / (kms * 1e-3) / 1e12
+            entry.update({"pipe": pipe, "achieved": ach, "peak": pk, "frac": ach / pk,
+                          "kernel_ms_per_launch": kms / kn, "launches_per_render": kn / PROFILED_RENDERS,
+                          "steps_per_render": steps_k / PROFILED_RENDERS, "flops_per_step": fl})
+            if pipe.startswith("fp32 (double"):
+                entry["frac_of_fp64_native"] = ach / fma64
+            roofs[pth + ":" + kname] = entry
+    return roofs
+
+
+def _dominant_kernel(prof, path, roofs):
+    """The kernel with the most device time per render among those with a roofline; on the
+    mixed path the second stream's FP64 launch overlaps the first stream's, and each counts
+    with its own CUDA-event duration."""
+    cand = {k: v[0] for k, v in prof.items() if v[1] and (path + ":" + k) in roofs}
+    return max(cand, key=lambda k: cand[k])
 
 
 def _flops_per_step():
@@ -863,6 +903,7 @@ def main():
     ap.add_argument("--no-learned-disk", action="store_true", help="skip the crossing network and the learned thin disk")
     ap.add_argument("--no-verlet", action="store_true", help="skip the FP64 velocity-Verlet workload")
     ap.add_argument("--no-emissivity", action="store_true", help="skip the exact-K2 / Theta_e-mask comparison")
+    ap.add_argument("--detail-json", default=None, help="also write the side workloads and breakdown to this file")
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-rays", type=int, default=10_000_000)
     args = ap.parse_args()

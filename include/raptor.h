@@ -158,15 +158,34 @@ raptor_status raptor_camera_init(const raptor_camera_desc* desc, raptor_ctx** ou
 /* Replace the camera settings of an existing context (same rules as camera_init). */
 raptor_status raptor_camera_set(raptor_ctx* ctx, const raptor_camera_desc* desc);
 
-/* Load the plasma model.  ANALYTIC copies the profile constants.  GRID copies the snapshot
- * array into a context-owned device buffer (host->device or device->device on `stream`);
- * the caller's buffer may be freed once the call returns. */
+/* Load the plasma model the transfer samples (sec. 4.2.2; sec. 5).  ANALYTIC copies the
+ * profile constants (power laws in r of n_e, Theta_e and B, Keplerian / free-fall velocity;
+ * not a model of the paper).  GRID copies the snapshot array into a context-owned device
+ * buffer (host->device or device->device on `stream`; the caller's buffer may be freed once
+ * the call returns): HARM primitives on a modified Kerr-Schild grid (sec. 4.2.2 and App. A.2,
+ * the theta map inverted by Newton's iteration), scaled to CGS by the mass unit of Eq. 45
+ * (rho_0 = M_unit / L^3, n_e = rho rho_0 / (m_e + m_p), B from b.b and rho_0), electron
+ * temperature from the R-beta prescription of Eq. 46 with R_high and R_low, and with
+ * slow_light a time series of snapshots dt_snap apart interpolated linearly in the ray's
+ * coordinate time (sec. 5.1).  RAPTOR_EINVAL for an unknown kind, non-positive sizes or
+ * spacings, a NULL field pointer or non-finite constants; RAPTOR_ENOMEM / RAPTOR_ECUDA when
+ * the copy fails (the previous plasma is then kept). */
 raptor_status raptor_load_plasma(raptor_ctx* ctx, const raptor_plasma_desc* desc, void* stream);
 
-/* Render one image at camera time t_obs (fast light).  freqs_hz[n_freq] is a host array
- * (1 <= n_freq <= 64).  image_dev: device double [n_freq][ny][nx], Jy per pixel, written
+/* Render one image at camera time t_obs (fast light): every pixel's ray is integrated
+ * backwards from the camera (sec. 2.3, Eqs. 24-28) with the adaptive step of Eqs. 20-23 and
+ * the integrator of sec. 2.2.2, and the invariant intensity is accumulated by the backward
+ * transfer scheme of Eqs. 35-36 with the per-step formal solution of Eq. 34 and the
+ * thermal-synchrotron coefficients of Eqs. 41-44.  The image holds each pixel's flux density
+ * in Jy, I_nu dalpha dbeta L^2 / D^2 / 1e-23 with L = GM/c^2 (the pixel sum is the total flux
+ * density of sec. 4.2.2 and Table 3).  freqs_hz[n_freq] is a host array (1 <= n_freq <= 64).
+ * image_dev: device double [n_freq][ny][nx] (row 0 = beta_min), caller-owned, written
  * completely.  flux_jy_host: optional host double [n_freq] (NULL to skip; otherwise the
- * stream is synchronised).  Grid plasma uses snapshot 0 unless slow_light is set. */
+ * stream is synchronised).  Grid plasma uses snapshot 0 unless slow_light is set.
+ * RAPTOR_EINVAL for a NULL image, n_freq outside 1..64 or a non-positive frequency;
+ * RAPTOR_ENOPLASMA before raptor_load_plasma; RAPTOR_ETIMEOUT when a bounded wait of the
+ * learned path's tensor-core kernels expires; RAPTOR_ECUDA on a CUDA error (message in
+ * raptor_last_error). */
 raptor_status raptor_render(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs,
                             double* image_dev, double* flux_jy_host, void* stream);
 
@@ -235,8 +254,13 @@ raptor_status raptor_trace_ray(raptor_ctx* ctx, double alpha, double beta, doubl
                                int* n_steps, int* ray_status, double* intensity_host, void* stream);
 
 /* Counters accumulated over all launches since the context was created (synchronises the
- * last stream used): rays traced, accepted RK4 steps, of which FP64 steps, rays truncated at
- * max_steps, rays with an error status, learned-surrogate fallbacks. */
+ * last stream used): rays traced (one ray = one pixel x frame; a ray carries all
+ * frequencies of the call), accepted integration steps (one step of the integrator of
+ * sec. 2.2.2: an RK4 step, Eqs. 7-15, with its four right-hand sides, or a velocity-Verlet
+ * step, Eqs. 16-19, with the step length of Eqs. 20-23; the steps a learned start state
+ * replaces are counted as taken), of which FP64 steps, rays truncated at max_steps, rays
+ * with an error status, learned-surrogate fallbacks.  The host pointers are caller-owned;
+ * NULL skips a value.  RAPTOR_EINVAL for a NULL context, RAPTOR_ECUDA on a CUDA error. */
 raptor_status raptor_stats(raptor_ctx* ctx, unsigned long long* rays, unsigned long long* steps,
                            unsigned long long* fp64_steps, unsigned long long* truncated,
                            unsigned long long* errors, unsigned long long* fallback);
@@ -245,11 +269,14 @@ raptor_status raptor_stats(raptor_ctx* ctx, unsigned long long* rays, unsigned l
 raptor_status raptor_stats_reset(raptor_ctx* ctx);
 
 /* All counters behind raptor_stats (synchronises the context's last stream): values[count]
- * (caller's host array, 1 <= count <= 16) receives, in order, rays, accepted steps, FP64
- * steps, truncated rays, rays with an error status, surrogate fallbacks, re-entries of the
- * FP64 region during the outbound FP32 phase (counted, not moved), clamped slow-light
- * samples, and the FP64 steps taken on the mixed path's second stream (near-critical rays);
- * later slots are zero.  RAPTOR_EINVAL for a count outside 1..16. */
+ * (caller's host array, 1 <= count <= 16) receives, in order, rays, accepted steps (as in
+ * raptor_stats), FP64 steps, truncated rays, rays with an error status, surrogate
+ * fallbacks, re-entries of the FP64 region during the outbound FP32 phase (counted, not
+ * moved), clamped slow-light samples, the FP64 steps taken on the mixed path's second
+ * stream (near-critical rays), and the FP32 steps executed by the mixed path's inbound
+ * phase (A) and outbound phase (C) launches (steps a learned start state replaces are not
+ * executed and not counted there); later slots are zero.  RAPTOR_EINVAL for a count outside
+ * 1..16. */
 raptor_status raptor_stats_ex(raptor_ctx* ctx, unsigned long long* values, int count);
 
 /* Launch shape of the persistent kernels (used by the autotuner): threads per block in
@@ -375,6 +402,16 @@ raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind);
  * outbound rays stop at r > r_exit in RAPTOR_MIXED_MLP (0 = off) [50]. */
 raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit);
 
+/* Host-side fault injection for failure-handling tests (no counterpart in the paper; no
+ * device fault is raised).  RAPTOR_FAULT_TC_WAIT: set, from the host and after the context's
+ * last stream has drained, the device flag that a bounded mbarrier wait of the tensor-core
+ * network kernels sets when it runs out, so that the next learned render (or crossing
+ * network evaluation) that synchronises returns RAPTOR_ETIMEOUT with the reason in
+ * raptor_last_error, clears the flag and leaves the context usable.  RAPTOR_EINVAL for an
+ * unknown kind; RAPTOR_EUNSUPPORTED when the context has no network yet. */
+enum { RAPTOR_FAULT_TC_WAIT = 1 };
+raptor_status raptor_inject_fault(raptor_ctx* ctx, int kind);
+
 /* Learned equatorial crossings (the learned surrogate's thin-disk outputs; the geometry is
  * sec. 4.2.1's disk plane theta = pi/2, the network has no counterpart in the paper).  A
  * second network of the same shape (4 -> 256 -> 256 -> 256 -> 16, SiLU; BF16 hidden layers
@@ -430,6 +467,14 @@ raptor_status raptor_crossings_get(raptor_ctx* ctx, float* params_host, int n);
  * FP64; 0: in FP64, equal to raptor_disk_render bit for bit.  RAPTOR_EINVAL for a negative
  * or non-finite band or another flag value. */
 raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band, int fallback_df64);
+
+/* Confidence fallback of the learned thin disk (sec. 4.2.1 geometry; no counterpart in the
+ * paper): a pixel whose decoding reads a presence logit within presence_margin of 0 [2.0],
+ * or a predicted crossing radius within radius_margin of r_in or r_out in ln r [0.01], is
+ * integrated by the fallback disk ray as well, because there a wrong decision of the network
+ * (a false hit or a false miss) would be an O(1) intensity error.  0, 0: the band alone.
+ * RAPTOR_EINVAL for a negative or non-finite margin. */
+raptor_status raptor_crossings_confidence(raptor_ctx* ctx, double presence_margin, double radius_margin);
 raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, int n);
 
 /* The thin disk of raptor_disk_render from the learned crossings (sec. 4.2.1): pixels whose
@@ -511,7 +556,9 @@ raptor_status raptor_measure_fma_peak(int fp64, double* tflops);
  * the process exits and shared by every call; each call clears what must start at zero.
  * Calls whose GPU work overlaps in time (other streams or host threads) race on that array:
  * the caller must serialise them.  The first call on a device looks up the array's device
- * address with that device current; make that first call before any stream capture.
+ * address with that device current and loads every kernel this entry point can launch (with
+ * lazy module loading, a kernel's first launch would otherwise load its code then, which can
+ * allocate in the driver); make that first call before any stream capture.
  * Limits: cam->precision must be RAPTOR_FP64 (else RAPTOR_EINVAL); plasma->kind must be
  * RAPTOR_PLASMA_ANALYTIC (else RAPTOR_EUNSUPPORTED); 1 <= n_freq <= RAPTOR_NOALLOC_MAX_FREQ
  * (else RAPTOR_EINVAL).  Invalid descriptors return RAPTOR_EINVAL before any launch. */

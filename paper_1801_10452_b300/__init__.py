@@ -22,6 +22,7 @@ PLASMA_ANALYTIC, PLASMA_GRID = 0, 1
 FLAG_K2_EXACT, FLAG_STEP_LINEAR_R, FLAG_INNER_DF64, FLAG_VERLET, FLAG_VERLET_REEVAL = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_FORWARD_RT = 0x20
 MLP_TCGEN05, MLP_MMA_SYNC = 0, 1
+FAULT_TC_WAIT = 1
 RAY_ESCAPED, RAY_CAPTURED, RAY_THICK, RAY_TRUNCATED, RAY_ERROR = range(5)
 
 EXPORTS = [
@@ -35,6 +36,7 @@ EXPORTS = [
     "raptor_disk_desc_default", "raptor_disk_render", "raptor_disk_render_learned", "raptor_crossings_param_count",
     "raptor_crossings_generate", "raptor_crossings_init", "raptor_crossings_train", "raptor_crossings_grad",
     "raptor_crossings_eval", "raptor_crossings_get", "raptor_crossings_set", "raptor_crossings_config", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
+    "raptor_inject_fault", "raptor_crossings_confidence",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp", "disk", "mixed_fp64_long"]
@@ -122,6 +124,8 @@ def lib():
             "raptor_surrogate_save": (st, [vp, C.c_char_p]),
             "raptor_surrogate_load": (st, [vp, C.c_char_p]),
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
+            "raptor_inject_fault": (st, [vp, C.c_int]),
+            "raptor_crossings_confidence": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
             "raptor_crossings_param_count": (C.c_int, []),
             "raptor_crossings_generate": (st, [vp, C.c_longlong, C.c_ulonglong, C.c_double, C.c_double, C.c_double,
@@ -319,11 +323,12 @@ class Context:
 
     def stats_ex(self):
         """All counters: rays, steps, fp64_steps, truncated, errors, fallback, reentries,
-        clamped, fp64_steps_long (second stream)."""
-        v = (C.c_ulonglong * 9)()
-        self._check(lib().raptor_stats_ex(self._h, v, 9), "raptor_stats_ex")
+        clamped, fp64_steps_long (second stream), fp32_steps_in / fp32_steps_out (FP32 steps
+        executed by the mixed path's inbound and outbound phases)."""
+        v = (C.c_ulonglong * 11)()
+        self._check(lib().raptor_stats_ex(self._h, v, 11), "raptor_stats_ex")
         return dict(zip(["rays", "steps", "fp64_steps", "truncated", "errors", "fallback", "reentries", "clamped",
-                         "fp64_steps_long"], [int(x) for x in v]))
+                         "fp64_steps_long", "fp32_steps_in", "fp32_steps_out"], [int(x) for x in v]))
 
     def stats_reset(self):
         self._check(lib().raptor_stats_reset(self._h), "raptor_stats_reset")
@@ -518,6 +523,12 @@ class Context:
         self._check(lib().raptor_crossings_config(self._h, float(fallback_band), int(bool(fallback_df64))),
                     "raptor_crossings_config")
 
+    def crossings_confidence(self, presence_margin=2.0, radius_margin=0.01):
+        """Learned thin disk: pixels with a presence logit within presence_margin of 0, or a
+        predicted radius within radius_margin (in ln r) of r_in or r_out, fall back too."""
+        self._check(lib().raptor_crossings_confidence(self._h, float(presence_margin), float(radius_margin)),
+                    "raptor_crossings_confidence")
+
     def long_config(self, threads_per_block=0, budgets=None):
         """Schedule of the near-critical rays' FP64 phase on the second stream: block size
         (0: the other launches') and the step budgets of its passes (None: one unlimited
@@ -563,6 +574,11 @@ class Context:
 
     def surrogate_config(self, fallback_band=0.5, r_exit=50.0):
         self._check(lib().raptor_surrogate_config(self._h, float(fallback_band), float(r_exit)), "raptor_surrogate_config")
+
+    def inject_fault(self, kind=1):
+        """Host-side fault injection (raptor_inject_fault): kind 1 sets the tensor-core wait
+        flag, so that the next synchronising learned render returns RAPTOR_ETIMEOUT."""
+        self._check(lib().raptor_inject_fault(self._h, int(kind)), "raptor_inject_fault")
 
     def close(self):
         if getattr(self, "_h", None):

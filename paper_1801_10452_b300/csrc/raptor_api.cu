@@ -111,6 +111,8 @@ struct raptor_ctx {
     unsigned long long x_step = 0;
     double x_band = 1.0;             // learned disk: fallback band around the critical curve (M)
     bool x_df = true;                // learned disk: fallback pixels in double-float arithmetic
+    double x_zmargin = 2.0;          // learned disk: presence logits within this of 0 fall back
+    double x_lnr_margin = 0.01;      // learned disk: radii within this (in ln r) of r_in, r_out fall back
     __nv_bfloat16* x_h2tc = nullptr; // tcgen05 inference: h2 tiles (64 KB each)
     size_t x_h2tc_tiles = 0;
     int* x_list = nullptr;           // learned disk: fallback pixels
@@ -1374,7 +1376,7 @@ raptor_status check_tc_err(raptor_ctx* ctx) {
     RCK(cudaMemcpy(&flag, ctx->s_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (!flag) return RAPTOR_OK;
     RCK(cudaMemset(ctx->s_err, 0, sizeof(int)));
-    return fail(ctx, RAPTOR_ECUDA, "surrogate inference: a tensor-core wait exceeded its time limit");
+    return fail(ctx, RAPTOR_ETIMEOUT, "surrogate inference: a tensor-core wait exceeded its time limit");
 }
 
 // Critical curve on the image plane (Bardeen 1973): photon-orbit radius r gives
@@ -1719,6 +1721,17 @@ raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind) {
     return RAPTOR_OK;
 }
 
+raptor_status raptor_inject_fault(raptor_ctx* ctx, int kind) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (kind != RAPTOR_FAULT_TC_WAIT) return fail(ctx, RAPTOR_EINVAL, "unknown fault kind");
+    if (!ctx->s_err) return fail(ctx, RAPTOR_EUNSUPPORTED, "no surrogate network: nothing waits on the tensor cores");
+    // the value a bounded wait of the tensor-core kernels leaves when it runs out
+    const int flag = 1;
+    RCK(cudaStreamSynchronize(ctx->last_stream));
+    RCK(cudaMemcpy(ctx->s_err, &flag, sizeof(int), cudaMemcpyHostToDevice));
+    return RAPTOR_OK;
+}
+
 raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit) {
     if (!ctx) return RAPTOR_EINVAL;
     if (!(fallback_band >= 0.0) || !std::isfinite(fallback_band) || !(r_exit >= 0.0) || !std::isfinite(r_exit))
@@ -1832,12 +1845,33 @@ void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the scratch array on device `dev` (which must be current).
+// Every kernel the allocation-free path may launch.  With lazy module loading a kernel's
+// code is loaded onto the device on its first use, which can allocate device memory in the
+// driver; querying its attributes loads it too, so the first call per device loads them all.
+static cudaError_t noalloc_load_kernels() {
+    const void* fns[] = {(const void*)k_render_fp64<1, false>, (const void*)k_render_fp64<2, false>,
+                         (const void*)k_render_fp64<4, false>, (const void*)k_render_fp64<8, false>,
+                         (const void*)k_render_fp64<16, false>, (const void*)k_render_fp64<1, true>,
+                         (const void*)k_render_fp64<2, true>, (const void*)k_render_fp64<4, true>,
+                         (const void*)k_render_fp64<8, true>, (const void*)k_render_fp64<16, true>,
+                         (const void*)k_reduce_partial, (const void*)k_reduce_final};
+    for (const void* f : fns) {
+        cudaFuncAttributes attr;
+        const cudaError_t e = cudaFuncGetAttributes(&attr, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Device address of the scratch array on device `dev` (which must be current); the first
+// call per device also loads the kernels this path launches.
 static cudaError_t noalloc_scratch(int dev, void** out) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void* ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        e = noalloc_load_kernels();
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = ptr;
     }
@@ -2246,7 +2280,8 @@ raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, 
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->x_list, 0xFF, n * sizeof(int), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->x_nlist, 0, sizeof(unsigned int), s);
         if (e == cudaSuccess) {
-            k_disk_learned<<<ew_blocks((long long)n), 256, 0, s>>>(p, a, ctx->x_P, out, ctx->s_fb, ctx->x_list, ctx->x_nlist);
+            k_disk_learned<<<ew_blocks((long long)n), 256, 0, s>>>(p, a, ctx->x_P, out, ctx->s_fb, ctx->x_list, ctx->x_nlist,
+                                                                   (float)ctx->x_zmargin, (float)ctx->x_lnr_margin);
             e = cudaGetLastError();
         }
     }
@@ -2447,6 +2482,17 @@ raptor_status raptor_crossings_config(raptor_ctx* ctx, double fallback_band, int
     if (fallback_df64 != 0 && fallback_df64 != 1) return fail(ctx, RAPTOR_EINVAL, "fallback_df64 must be 0 or 1");
     ctx->x_band = fallback_band;
     ctx->x_df = fallback_df64 != 0;
+    return RAPTOR_OK;
+}
+
+raptor_status raptor_crossings_confidence(raptor_ctx* ctx, double presence_margin, double radius_margin) {
+    if (!ctx) return RAPTOR_EINVAL;
+    ctx->err.clear();
+    if (!(presence_margin >= 0.0) || !std::isfinite(presence_margin) || !(radius_margin >= 0.0) ||
+        !std::isfinite(radius_margin))
+        return fail(ctx, RAPTOR_EINVAL, "presence_margin and radius_margin must be finite and >= 0");
+    ctx->x_zmargin = presence_margin;
+    ctx->x_lnr_margin = radius_margin;
     return RAPTOR_OK;
 }
 

@@ -223,9 +223,15 @@ __global__ void k_crossings_decode(const float* __restrict__ P, const float* __r
 // given the radius), I = (E_obs/E_em)^4 r^-q, order = its crossing number; no such crossing:
 // no hit.  Fallback pixels are appended to `list` (its unused tail holds -1) for
 // k_disk_fp64.
+// Pixels whose decoded hit is uncertain also join the fallback list: a presence logit within
+// z_margin of 0 on a crossing the decoding reads (the network cannot tell whether the ray
+// crosses there), or a predicted radius within a factor exp(lnr_margin) of r_in or r_out
+// (a small radius error would move the hit onto or off the disk).  There a wrong decision
+// is an O(1) intensity error, not a small one.
 __global__ void __launch_bounds__(256) k_disk_learned(const Params p, const DiskArgs d, const float* __restrict__ P,
                                                       const float* __restrict__ out, const unsigned char* __restrict__ fallback,
-                                                      int* __restrict__ list, unsigned int* __restrict__ n_list) {
+                                                      int* __restrict__ list, unsigned int* __restrict__ n_list,
+                                                      float z_margin, float lnr_margin) {
     float mu[kCross], sd[kCross];
 #pragma unroll
     for (int c = 0; c < kCross; ++c) {
@@ -246,18 +252,27 @@ __global__ void __launch_bounds__(256) k_disk_learned(const Params p, const Disk
         crossing_flat(p.f.a, sif, cif, rcf, (float)al, (float)be, &lam_f, &lnr_f);
         double ratio = 0.0, inten = 0.0;
         int order = 0;
+        bool unsure = false;
         const float4* o4 = reinterpret_cast<const float4*>(out + id * kXOut);
+        const double ln_in = log(d.r_in), ln_out = log(d.r_out);
 #pragma unroll
         for (int c = 0; c < kCross; ++c) {
             const float4 o = o4[c];
+            if (fabsf(o.x) < z_margin) { unsure = true; break; }
             if (!(o.x > 0.f)) break;
-            const double r = exp((double)(o.y * sd[c] + mu[c]) + (c == 0 ? (double)lnr_f : 0.0));
+            const double lnr = (double)(o.y * sd[c] + mu[c]) + (c == 0 ? (double)lnr_f : 0.0);
+            if (fabs(lnr - ln_in) < lnr_margin || fabs(lnr - ln_out) < lnr_margin) { unsure = true; break; }
+            const double r = exp(lnr);
             if (r >= d.r_in && r <= d.r_out) {
                 ratio = kepler_ratio(r, p.a, -al * p.sin_i);
                 inten = ratio * ratio * ratio * ratio * pow(r, -d.q);
                 order = ratio > 0.0 ? c + 1 : 0;
                 break;
             }
+        }
+        if (unsure) {
+            list[atomicAdd(n_list, 1u)] = pix;
+            continue;
         }
         d.ratio[pix] = ratio;
         d.inten[pix] = inten;

@@ -25,7 +25,8 @@ enum : int { kProfRenderFp64 = 0, kProfMixedA = 1, kProfMixedB = 2, kProfMixedC 
 
 // Stats slots (device unsigned long long[kNumStats]).
 enum : int { kStatRays = 0, kStatSteps = 1, kStatFp64Steps = 2, kStatTrunc = 3, kStatErr = 4, kStatFallback = 5,
-             kStatReentry = 6, kStatClamp = 7, kStatFp64Long = 8, kNumStats = 16 };
+             kStatReentry = 6, kStatClamp = 7, kStatFp64Long = 8, kStatFp32In = 9, kStatFp32Out = 10,
+             kNumStats = 16 };
 
 template <int NF>
 struct RayD {

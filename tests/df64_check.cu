@@ -1,4 +1,4 @@
-// df64_check.cu -- host check of the double-float arithmetic against long double: prints
+// df64_check.cu (test harness, built by tests/test_df64.py) -- host check of the double-float arithmetic against long double: prints
 // the largest relative errors of add, mul, div, sqrt and sincos over seeded random operands.
 #include <cmath>
 #include <cstdio>

@@ -9,7 +9,8 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "paper_1801_10452_b300", "csrc", "df64_check.cu")
+SRC = os.path.join(ROOT, "tests", "df64_check.cu")
+INC = os.path.join(ROOT, "paper_1801_10452_b300", "csrc")
 
 
 def test_df64_accuracy(tmp_path):
@@ -17,7 +18,7 @@ def test_df64_accuracy(tmp_path):
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
-    subprocess.run([nvcc, "-O2", "-std=c++17", "-o", exe, SRC], check=True, capture_output=True)
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-I", INC, "-o", exe, SRC], check=True, capture_output=True)
     r = json.loads(subprocess.run([exe], check=True, capture_output=True, text=True).stdout)
     # a 48-bit significand: a few units of 2^-48 = 3.6e-15 per operation
     for k in ("add", "mul", "div", "sqrt", "sin_abs", "cos_abs", "sincos_table_abs"):

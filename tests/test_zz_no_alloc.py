@@ -51,10 +51,15 @@ def test_noalloc_render_matches_render_twice():
     for call in range(2):
         img = torch.full((3, 30, 40), -1.0, dtype=torch.float64, device="cuda")
         flux = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         st = L.raptor_render_noalloc(C.byref(cam), C.byref(pl), fptr, 3, C.c_double(0.0), C.c_void_p(img.data_ptr()),
                                      C.c_void_p(flux.data_ptr()), stream)
         assert st == 0, (call, st)
         torch.cuda.synchronize()
+        if call == 1:
+            # after the first call's one-time set-up, a call takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free_before
         g = img.cpu().numpy()
         fl = flux.cpu().numpy()
         den = np.maximum(np.abs(ref_img), 1e-12 * np.abs(ref_img).max())
