@@ -448,15 +448,19 @@ def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
         ctx.profile(False)
         return e0.elapsed_time(e1) / reps, {k: v.cpu().numpy() if hasattr(v, "cpu") else v for k, v in r.items()}, prof
 
-    variants = [("", 1.0, True), ("_fp64fallback", 1.0, False), ("_band0.5", 0.5, True)]
+    # (suffix, band, double-float fallback, confidence margins: presence logit, ln r)
+    variants = [("", 1.0, True, (2.0, 0.01)), ("_noconfidence", 1.0, True, (0.0, 0.0)),
+                ("_fp64fallback", 1.0, False, (2.0, 0.01)), ("_band0.5", 0.5, True, (2.0, 0.01))]
     for a in scenes.THIN_DISK_SPINS:
         ctx = R.Context(R.camera_desc(**dict(cam0, spin=a)))
         ctx.crossings_set(P if a >= 0.0 else P_retro)
         ms_f, f, _ = timed(ctx, False)
         # retrograde: a larger critical curve, whose strongly deflected surroundings need a
         # 1.5 M band at a = -0.99 to keep every pixel within 1e-2 (measured; 1.0 M reported too)
-        for suffix, band, df in (variants if a >= 0.0 else [("", 1.5, True), ("_band1", 1.0, True)]):
+        for suffix, band, df, conf in (variants if a >= 0.0 else [("", 1.5, True, (2.0, 0.01)),
+                                                                   ("_band1", 1.0, True, (2.0, 0.01))]):
             ctx.crossings_config(fallback_band=band, fallback_df64=df)
+            ctx.crossings_confidence(*conf)
             ms_l, g, prof = timed(ctx, True)
             fb = g["steps"] > 0
             nb = ~fb
@@ -464,6 +468,11 @@ def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
             rel = np.abs(g["ratio"][hit] / f["ratio"][hit] - 1)
             fbh = fb & (f["order"] > 0) & (g["order"] == f["order"])
             rel_fb = np.abs(g["ratio"][fbh] / f["ratio"][fbh] - 1)
+            # every learned pixel, misclassified ones included: intensity error relative to
+            # the larger of the two intensities (a false hit or a false miss counts as 1)
+            Il, If = g["intensity"][nb], f["intensity"][nb]
+            big = np.maximum(np.abs(Il), np.abs(If))
+            rel_all = np.where(big > 0, np.abs(Il - If) / np.where(big > 0, big, 1.0), 0.0)
             sf, sg = f["spectrum"], g["spectrum"]
             rays = cam0["nx"] * cam0["ny"]
             mlp_ms = prof["surrogate_mlp"][0] / reps
@@ -471,6 +480,11 @@ def _learned_disk_extra(R, torch, stream, bf16_peak, steps, n_train, reps=3):
             w = np.nonzero(hit)
             out["per_spin"][f"{a:g}{suffix}"] = {
                 "fallback_band_M": band, "fallback_arithmetic": "double-float" if df else "fp64",
+                "confidence_margins": list(conf),
+                "order_mismatch_learned_pixels": int((g["order"][nb] != f["order"][nb]).sum()),
+                "intensity_rel_err_max_all_learned": float(rel_all.max()) if rel_all.size else 0.0,
+                "intensity_rel_err_p99_all_learned": float(np.quantile(rel_all, 0.99)) if rel_all.size else 0.0,
+                "intensity_pixels_over_1e-2_all_learned": int((rel_all > 1e-2).sum()),
                 "ms_learned": ms_l, "ms_fp64": ms_f, "speedup": ms_f / ms_l, "rays_per_s_learned": rays / (ms_l * 1e-3),
                 "fallback_fraction": float(fb.mean()),
                 "fallback_order_agreement": float((g["order"][fb] == f["order"][fb]).mean()),

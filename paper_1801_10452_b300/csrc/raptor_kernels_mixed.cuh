@@ -399,17 +399,24 @@ __device__ __forceinline__ long long load_ray_f(const Params& p, const RayQueue&
 // FP32 phases.  Phase A (io.fresh set): camera rays (or the surrogate's predicted states)
 // from the id list; rays entering the FP64 region go to io.push.  Phase C: rays from io.in,
 // integrated to termination (re-entries into the region are counted, not moved).
+// The FP32 step is issue-bound and more resident warps hide its latencies: one frequency
+// at most 102 registers (five 128-thread blocks, 20 warps per SM), two to four at most 128
+// (four blocks).
 template <int NF>
-__global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, size_t cap, unsigned long long* cnt,
+constexpr int kMixed32MinBlocks = NF == 1 ? 5 : (NF <= 4 ? 4 : 1);
+
+template <int NF>
+__global__ void __launch_bounds__(128, kMixed32MinBlocks<NF>) k_mixed_fp32(const Params p, PhaseIO io, size_t cap, unsigned long long* cnt,
                                                     unsigned long long* stats) {
     RayF<NF> R;
     long long id = -1;
-    int frame = 0, pix = 0, n_in = 0;
+    int frame = 0, pix = 0;
     bool drained = false;
     const bool fresh = io.fresh != nullptr;
     const long long n_total = (long long)cnt[io.total];
     const long long push_off = io.push_top >= 0 ? (long long)cap - (long long)cnt[io.push_top] : 0;
-    unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0, c_re = 0, c_ph = 0;
+    unsigned long long c_rays = 0, c_steps = 0, c_trunc = 0, c_err = 0, c_re = 0;
+    unsigned c_ph = 0;  // steps taken in this launch: the step count at exit minus that at entry
     for (;;) {
         const long long nid = warp_fetch(&cnt[io.fetch], n_total, id < 0, drained);
         if (id < 0 && nid >= 0) {
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, 
                 pix = (int)(id - (long long)frame * p.n_pix);
                 R.snap = p.lc_fast ? p.frame_snap0 + frame : p.snap;
             }
-            n_in = R.n;
+            c_ph -= (unsigned)R.n;
         }
         if (!__any_sync(0xffffffffu, id >= 0)) break;
         int st = -1;
@@ -462,7 +469,7 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, 
 #pragma unroll
             for (int f = 0; f < NF; ++f) tau[f] = double(R.tau[f]) + double(R.tau_hi[f]);
             store_ray<NF>(io.push, cap, slot + push_off, id, x, k, R.I, tau, R.n, p.nf);
-            c_ph += (unsigned long long)(R.n - n_in);
+            c_ph += (unsigned)R.n;
             id = -1;
         } else if (id >= 0 && st >= 0) {
             double I[NF];
@@ -471,7 +478,7 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, 
             write_ray<NF>(p, frame, pix, I, R.n, st);
             c_rays += 1;
             c_steps += (unsigned long long)R.n;
-            c_ph += (unsigned long long)(R.n - n_in);
+            c_ph += (unsigned)R.n;
             c_trunc += (st == kTruncated);
             c_err += (st == kError);
             id = -1;
@@ -480,9 +487,10 @@ __global__ void __launch_bounds__(128) k_mixed_fp32(const Params p, PhaseIO io, 
     warp_add_stats(stats, c_rays, c_steps, 0, c_trunc, c_err);
     if (c_re) atomicAdd(&stats[kStatReentry], c_re);
     // FP32 steps taken in this launch, per phase (inbound A, outbound C)
+    unsigned long long c_ph64 = c_ph;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c_ph += __shfl_down_sync(0xffffffffu, c_ph, o);
-    if ((threadIdx.x & 31) == 0 && c_ph) atomicAdd(&stats[fresh ? kStatFp32In : kStatFp32Out], c_ph);
+    for (int o = 16; o > 0; o >>= 1) c_ph64 += __shfl_down_sync(0xffffffffu, c_ph64, o);
+    if ((threadIdx.x & 31) == 0 && c_ph64) atomicAdd(&stats[fresh ? kStatFp32In : kStatFp32Out], c_ph64);
 }
 
 // FP64 phase: rays from io.in; FP64 (or double-float) geodesic steps, FP32 transfer samples.

@@ -1,8 +1,8 @@
 """Failure handling, exercised without any device fault: a tensor-core wait that ran out is
 reported and the context recovers (the flag is set from the host), and corrupt snapshot
-cells (NaN velocities, negative or NaN densities, written into the arrays on the host) end
-the affected rays with the error status, counted, with the image and the flux finite and
-equal to the oracle's on the same arrays.  Needs a GPU."""
+cells (NaN velocities, negative or NaN densities, a NaN internal energy, an infinite field,
+written into the arrays on the host) act as empty space: no ray ends in error, the image
+and the flux stay finite and equal the oracle's on the same arrays.  Needs a GPU."""
 import numpy as np
 import pytest
 
@@ -59,56 +59,51 @@ def test_tensor_core_wait_timeout_reported_then_recovered(R):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_corrupt_snapshot_cells(R, ora, prec):
-    """NaN velocity cells make the frequency ratio undefined: rays sampling them end with
-    RAPTOR_RAY_ERROR (as in the oracle, whose rays stop with its error status), keep the
-    intensity accumulated before, and are counted in the error statistics.  Cells with a
-    negative or NaN density or internal energy emit nothing (no plasma there, both sides).
-    The image and the flux stay finite; on the FP64 path every pixel and status equals the
-    oracle's on the same corrupted arrays."""
+    """Snapshot cells with NaN velocities, negative or NaN densities, a NaN internal energy or
+    an infinite field strength (written into the arrays on the host) emit and absorb nothing:
+    a sample whose interpolated primitives are not a valid plasma state (rho <= 0, u <= 0, or
+    b.b not positive, which NaN and infinite inputs make it) is treated as empty space, on
+    both sides.  No ray ends in error, the error counter agrees with the status image, the
+    image and the flux stay finite, the corrupted cells change the flux, and on the FP64
+    path every pixel and status equals the oracle's on the same corrupted arrays."""
     import torch
 
     fields, meta = scenes.torus_snapshots(1, n1=64, n2=64, n_modes=128)
     bad = np.array(fields, copy=True)
-    n1, n2 = meta["n1"], meta["n2"]
-    # a block of NaN velocities inside the torus, behind the hole from the camera
+    n2 = meta["n2"]
+    # NaN velocities in the torus body near the equator (r ~ 6.6-9 M)
     bad[0, 2:5, n2 // 2 - 3:n2 // 2 + 3, 28:34] = np.nan
-    # negative and NaN densities and a NaN internal energy elsewhere in the emitting region
+    # negative and NaN densities, a NaN internal energy and an infinite field elsewhere in it
     bad[0, 0, n2 // 2 - 8:n2 // 2 - 4, 20:26] = -1.0
     bad[0, 0, n2 // 2 + 4:n2 // 2 + 8, 36:40] = np.nan
     bad[0, 1, n2 // 2 + 10:n2 // 2 + 12, 22:30] = np.nan
+    bad[0, 6, n2 // 2 - 12:n2 // 2 - 9, 30:36] = np.inf
     cam = dict(scenes.SMALL, spin=scenes.TORUS["spin"], nx=48, ny=40)
     freqs = [230e9]
     model = scenes.DISK_MODEL
     precision = R.FP64 if prec == "fp64" else R.MIXED
-    ctx = R.Context(R.camera_desc(**cam, precision=precision))
-    ctx.load_plasma(R.plasma_desc(**grid_plasma_kwargs(meta, model)), fields=bad)
-    ctx.stats_reset()
-    steps = torch.zeros((cam["ny"], cam["nx"]), dtype=torch.int32, device="cuda")
-    status = torch.zeros_like(steps)
-    img, fl = ctx.render(freqs, steps=steps, status=status)
-    torch.cuda.synchronize()
-    img, status = img.cpu().numpy(), status.cpu().numpy()
-    st = ctx.stats()
-    n_err = int((status == R.RAY_ERROR).sum())
-    assert n_err > 0
-    assert st["errors"] == n_err
+
+    def run(arr):
+        ctx = R.Context(R.camera_desc(**cam, precision=precision))
+        ctx.load_plasma(R.plasma_desc(**grid_plasma_kwargs(meta, model)), fields=arr)
+        ctx.stats_reset()
+        steps = torch.zeros((cam["ny"], cam["nx"]), dtype=torch.int32, device="cuda")
+        status = torch.zeros_like(steps)
+        img, fl = ctx.render(freqs, steps=steps, status=status)
+        torch.cuda.synchronize()
+        return img.cpu().numpy(), fl, status.cpu().numpy(), ctx.stats(), ctx.cam.t_delay
+
+    img, fl, status, st, t_delay = run(bad)
+    assert st["errors"] == int((status == R.RAY_ERROR).sum()) == 0
     assert np.all(np.isfinite(img)) and np.all(np.isfinite(fl)) and fl[0] > 0
+    clean_img, clean_fl, _, _, _ = run(fields)
+    assert abs(fl[0] / clean_fl[0] - 1) > 1e-3
     s = grid_oracle_scene(ora, cam, bad, meta, model)
-    oimg, _, ostat = ora.render(s, freqs, t_cam=ctx.cam.t_delay)
+    oimg, _, ostat = ora.render(s, freqs, t_cam=t_delay)
     assert np.all(np.isfinite(oimg))
     if prec == "fp64":
         assert np.array_equal(status, ostat)
         assert rel_err(img[0], oimg[0]).max() <= 1e-8
         assert abs(fl[0] / oimg[0].sum() - 1) <= 1e-10
     else:
-        # the mixed path takes the same decisions on the rays away from the corrupted cells'
-        # edges; its flux stays within the mixed path's bound of the oracle's
-        assert (status == ostat).mean() > 0.99
         assert abs(fl[0] / oimg[0].sum() - 1) <= 1e-3
-    # the clean snapshot has no error rays
-    clean = R.Context(R.camera_desc(**cam, precision=precision))
-    clean.load_plasma(R.plasma_desc(**grid_plasma_kwargs(meta, model)), fields=fields)
-    clean.stats_reset()
-    clean.render(freqs)
-    torch.cuda.synchronize()
-    assert clean.stats()["errors"] == 0
