@@ -42,7 +42,8 @@ typedef enum {
     RAPTOR_EINVAL = 1,       /* invalid argument or descriptor; nothing was enqueued      */
     RAPTOR_ENOMEM = 2,       /* device or host allocation failed                          */
     RAPTOR_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed               */
-    RAPTOR_ETIMEOUT = 4,     /* a bounded device-side wait expired (see raptor_stats)     */
+    RAPTOR_ETIMEOUT = 4,     /* a bounded device-side wait of the tensor-core kernels
+                                expired; the context stays usable                         */
     RAPTOR_ENOPLASMA = 5,    /* render before raptor_load_plasma                          */
     RAPTOR_EUNSUPPORTED = 6  /* option recognised but not available in this build         */
 } raptor_status;
@@ -392,7 +393,7 @@ raptor_status raptor_surrogate_load(raptor_ctx* ctx, const char* path);
  * Both compute the training forward pass's arithmetic (BF16 operands, FP32 accumulation)
  * and differ only in FP32 summation order.  A tensor-core wait that exceeds 2 s makes the
  * next synchronising call (raptor_surrogate_eval, a render that returns fluxes) fail with
- * RAPTOR_ECUDA.  RAPTOR_EINVAL for another value. */
+ * RAPTOR_ETIMEOUT.  RAPTOR_EINVAL for another value. */
 #define RAPTOR_MLP_TCGEN05 0
 #define RAPTOR_MLP_MMA_SYNC 1
 raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind);
@@ -439,15 +440,16 @@ raptor_status raptor_inject_fault(raptor_ctx* ctx, int kind);
  * presence probability, r_n, lambda_n, E_obs/E_em.  Asynchronous on `stream`.  Inference runs
  * on the kernel raptor_surrogate_kernel selects (tcgen05 by default, the 16 output sums
  * reduced in two rounds of 8; or mma.sync); a tensor-core wait that runs out is reported by
- * the next learned disk render that returns a spectrum (RAPTOR_ECUDA).
+ * the next learned disk render that returns a spectrum (RAPTOR_ETIMEOUT).
  * RAPTOR_EUNSUPPORTED before init or set; RAPTOR_EINVAL for bad sizes or ranges. */
 int raptor_crossings_param_count(void);
 raptor_status raptor_crossings_generate(raptor_ctx* ctx, long long n, unsigned long long seed, double spin_min,
                                         double spin_max, double incl_min_deg, double incl_max_deg, float* inputs_dev,
                                         double* targets_dev, double* raw_dev, void* stream);
 /* raptor_crossings_init: inputs_dev (device float [n][4], may be NULL) sets the spin and
- * inclination normalisation to the range of the inputs (else a in [0, 1] and i in [5, 85] deg
- * map to [-1, 1]); alpha and beta are normalised over the camera's field of view. */
+ * inclination normalisation to the range of all n inputs, found on the device (else a in
+ * [0, 1] and i in [5, 85] deg map to [-1, 1]); alpha and beta are normalised over the
+ * camera's field of view.  RAPTOR_EINVAL for a non-finite spin or inclination input. */
 raptor_status raptor_crossings_init(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
                                     unsigned long long seed, void* stream);
 raptor_status raptor_crossings_train(raptor_ctx* ctx, const float* inputs_dev, const double* targets_dev, long long n,
@@ -487,7 +489,9 @@ raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, in
  * raptor_disk_render (in double-float arithmetic by default: raptor_crossings_config).  The network is valid inside the spin, inclination and field-of-view
  * range of its training data; the caller keeps the camera there.  Same arguments and
  * outputs; r_in must not lie inside the ISCO
- * (RAPTOR_EUNSUPPORTED), nor may the crossing network be missing (RAPTOR_EUNSUPPORTED). */
+ * (RAPTOR_EUNSUPPORTED), nor may the crossing network be missing (RAPTOR_EUNSUPPORTED), nor
+ * may the camera's spin or inclination lie outside the network's training range (more than
+ * 1 % of the range beyond it after the network's normalisation: RAPTOR_EUNSUPPORTED). */
 raptor_status raptor_disk_render_learned(raptor_ctx* ctx, const raptor_disk_desc* d, double* ratio_dev,
                                          double* intensity_dev, int* order_dev, int* status_dev, int* steps_dev,
                                          double* profile_host, void* stream);

@@ -111,6 +111,7 @@ struct raptor_ctx {
     unsigned long long x_step = 0;
     double x_band = 1.0;             // learned disk: fallback band around the critical curve (M)
     bool x_df = true;                // learned disk: fallback pixels in double-float arithmetic
+    float x_norm[8] = {0.f};         // crossing network: input scale[4], shift[4] (host copy)
     double x_zmargin = 2.0;          // learned disk: presence logits within this of 0 fall back
     double x_lnr_margin = 0.01;      // learned disk: radii within this (in ln r) of r_in, r_out fall back
     __nv_bfloat16* x_h2tc = nullptr; // tcgen05 inference: h2 tiles (64 KB each)
@@ -2238,6 +2239,12 @@ raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, 
     if (!ctx->x_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "the learned disk needs a trained crossing network");
     if (a.r_in < r_isco_prograde(ctx->cam.spin) * (1.0 - 1e-12))
         return fail(ctx, RAPTOR_EUNSUPPORTED, "the learned disk starts at or outside the ISCO (its ratios are trained there)");
+    // the network maps its training range of spin and inclination to [-1, 1]; outside it
+    // (beyond a small margin) its outputs are extrapolations
+    const double na = (ctx->cam.spin - ctx->x_norm[4 + 2]) * ctx->x_norm[2];
+    const double ni = (ctx->cam.incl_deg - ctx->x_norm[4 + 3]) * ctx->x_norm[3];
+    if (!(std::fabs(na) <= 1.02) || !(std::fabs(ni) <= 1.02))
+        return fail(ctx, RAPTOR_EUNSUPPORTED, "camera spin or inclination outside the crossing network's training range");
     const size_t n = (size_t)p.n_rays;
     if (ctx->s_ray_cap < n) {
         ctx->epoch += 1;
@@ -2344,16 +2351,24 @@ raptor_status raptor_crossings_init(raptor_ctx* ctx, const float* inputs_dev, co
     float shift[4] = {(float)(0.5 * (ctx->cam.alpha_max + ctx->cam.alpha_min)),
                       (float)(0.5 * (ctx->cam.beta_max + ctx->cam.beta_min)), 0.5f, 45.0f};
     if (inputs_dev) {
-        // spin and inclination mapped to [-1, 1] over the range of the given inputs
-        std::vector<float> x((size_t)m * kIn);
-        RCK(cudaMemcpyAsync(x.data(), inputs_dev, x.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
-        RCK(cudaStreamSynchronize(s));
+        // spin and inclination mapped to [-1, 1] over the range of all n given inputs
+        unsigned* mm = nullptr;
+        RCK(cudaMallocAsync((void**)&mm, 4 * sizeof(unsigned), s));
+        const unsigned init[4] = {0xFFFFFFFFu, 0u, 0xFFFFFFFFu, 0u};
+        cudaError_t e = cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            k_input_range<<<ew_blocks(n), 256, 0, s>>>(inputs_dev, n, mm);
+            e = cudaGetLastError();
+        }
+        unsigned h[4] = {0u, 0u, 0u, 0u};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        const cudaError_t ef = cudaFreeAsync(mm, s);
+        if (e == cudaSuccess) e = ef;
+        if (e != cudaSuccess) return fail(ctx, RAPTOR_ECUDA, cudaGetErrorString(e));
         for (int c = 2; c < 4; ++c) {
-            float lo = x[c], hi = x[c];
-            for (long long i = 1; i < m; ++i) {
-                lo = std::min(lo, x[i * kIn + c]);
-                hi = std::max(hi, x[i * kIn + c]);
-            }
+            const float lo = ordered_to_float(h[2 * (c - 2)]), hi = ordered_to_float(h[2 * (c - 2) + 1]);
+            if (!std::isfinite(lo) || !std::isfinite(hi)) return fail(ctx, RAPTOR_EINVAL, "non-finite spin or inclination input");
             shift[c] = 0.5f * (lo + hi);
             scale[c] = hi > lo ? 2.0f / (hi - lo) : 1.0f;
         }
@@ -2361,6 +2376,8 @@ raptor_status raptor_crossings_init(raptor_ctx* ctx, const float* inputs_dev, co
     for (int c = 0; c < 4; ++c) {
         P[XLayout::NORM + c] = scale[c];
         P[XLayout::NORM + 4 + c] = shift[c];
+        ctx->x_norm[c] = scale[c];
+        ctx->x_norm[4 + c] = shift[c];
     }
     // output normalisation over the targets present (presence logits: none)
     for (int q = 0; q < kXOut; ++q) {
@@ -2517,6 +2534,7 @@ raptor_status raptor_crossings_set(raptor_ctx* ctx, const float* params_host, in
     RCK(x_alloc(ctx));
     RCK(cudaStreamSynchronize(ctx->last_stream));
     RCK(cudaMemcpy(ctx->x_P, params_host, n * sizeof(float), cudaMemcpyHostToDevice));
+    for (int c = 0; c < 8; ++c) ctx->x_norm[c] = params_host[XLayout::NORM + c];
     RCK(cudaMemset(ctx->x_m1, 0, n * sizeof(float)));
     RCK(cudaMemset(ctx->x_m2, 0, n * sizeof(float)));
     RCK(x_refresh(ctx, nullptr));

@@ -160,6 +160,47 @@ __global__ void __launch_bounds__(128) k_crossing_data(SurrogateRange R, double 
 // loss log(1 + e^z) - y z on the presence logits (o % 4 == 0), (z - (y - mu)/sigma)^2 on the
 // others, nothing where the target is NaN.  dout = d loss / d out; per-block partial sums
 // of the loss in loss_acc (fixed order).
+// Floats as unsigned integers whose order is the floats' order (sign bit flipped for
+// non-negative values, all bits flipped for negative ones), for atomicMin / atomicMax.
+__host__ __device__ __forceinline__ unsigned float_to_ordered(float v) {
+    unsigned u;
+    memcpy(&u, &v, sizeof(u));
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float ordered_to_float(unsigned o) {
+    const unsigned u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+    float v;
+    memcpy(&v, &u, sizeof(v));
+    return v;
+}
+
+// Smallest and largest spin (column 2) and inclination (column 3) of n network inputs [n][4]:
+// mm = {min a, max a, min i, max i} as ordered integers (initialised by the caller to
+// {UINT_MAX, 0, UINT_MAX, 0}).
+__global__ void __launch_bounds__(256) k_input_range(const float* __restrict__ x, long long n, unsigned* __restrict__ mm) {
+    unsigned lo_a = 0xFFFFFFFFu, hi_a = 0u, lo_i = 0xFFFFFFFFu, hi_i = 0u;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+        const unsigned oa = float_to_ordered(x[m * 4 + 2]), oi = float_to_ordered(x[m * 4 + 3]);
+        lo_a = min(lo_a, oa);
+        hi_a = max(hi_a, oa);
+        lo_i = min(lo_i, oi);
+        hi_i = max(hi_i, oi);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo_a = min(lo_a, __shfl_down_sync(0xffffffffu, lo_a, o));
+        hi_a = max(hi_a, __shfl_down_sync(0xffffffffu, hi_a, o));
+        lo_i = min(lo_i, __shfl_down_sync(0xffffffffu, lo_i, o));
+        hi_i = max(hi_i, __shfl_down_sync(0xffffffffu, hi_i, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mm + 0, lo_a);
+        atomicMax(mm + 1, hi_a);
+        atomicMin(mm + 2, lo_i);
+        atomicMax(mm + 3, hi_i);
+    }
+}
+
 __global__ void k_cross_grad(const float* __restrict__ P, const float* __restrict__ out, const double* __restrict__ y,
                              long long rows, float* __restrict__ dout, double* __restrict__ loss_acc) {
     __shared__ double sh[256];

@@ -271,7 +271,19 @@ def test_learned_disk_argument_checks(R, trained):
         assert e.value.status == R.EINVAL
     from paper_1801_10452_b300 import lib
     assert lib().raptor_crossings_config(ctx.handle, 1.0, 2) == R.EINVAL
+    for bad in ((-0.1, 0.01), (1.0, float("nan"))):
+        with pytest.raises(R.RaptorError) as e:
+            ctx.crossings_confidence(*bad)
+        assert e.value.status == R.EINVAL
     ctx.disk_render(**DISK, learned=True)
+    # a camera outside the network's training range (spin in [0, 0.99], inclination in
+    # [5, 85] deg) is refused rather than extrapolated
+    for over in (dict(spin=-0.5), dict(incl_deg=89.0)):
+        out = R.Context(R.camera_desc(**dict(cam, **over)))
+        out.crossings_set(trained)
+        with pytest.raises(R.RaptorError) as e:
+            out.disk_render(r_in=8.0, r_out=15.0, learned=True)
+        assert e.value.status == R.EUNSUPPORTED
 
 
 def test_learned_disk_band_zero_and_wide(R, trained):
