@@ -208,8 +208,10 @@ def test_surrogate_gain_over_the_method_without_it(R, trained):
 def test_learned_path_full_size(R, ora, trained, size):
     """The headline image (1024^2) and the learned-surrogate workload's render (2048^2),
     a = 0.9375, 230 GHz, through RAPTOR_MIXED_MLP with double-float inner steps, as the
-    benchmark runs it: flux against the FP64 GPU path, seeded sample pixels outside the
-    photon-ring band against the oracle tracing them one by one."""
+    benchmark runs it: flux against the FP64 GPU path; every pixel outside the photon-ring
+    band against the FP64 GPU path (itself within 1e-8 of the oracle), relative to the pixel
+    for the pixels above 1e-6 of the peak and to 1e-8 of the peak below; seeded sample pixels
+    and the brightest ones outside the band against the oracle tracing them one by one."""
     import torch
 
     cam = dict(scenes.HEADLINE, nx=size, ny=size)
@@ -220,21 +222,45 @@ def test_learned_path_full_size(R, ora, trained, size):
     img, fl = ctx.render(freqs)
     c64 = R.Context(R.camera_desc(**cam, precision=R.FP64))
     c64.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
-    _, f64 = c64.render(freqs)
+    img64, f64 = c64.render(freqs)
     torch.cuda.synchronize()
     assert abs(fl[0] / f64[0] - 1) <= FLUX_TOL
     img = img.cpu().numpy()
-    s = ora.scene(**oracle_kwargs(cam))
+    img64 = img64.cpu().numpy()
     al, be = R.pixel_centres(ctx.cam)
+    band = _band_tree(al, be, cam)
+    peak = img64[0].max()
+    bright = np.abs(img64[0]) >= 1e-6 * peak
+    d = np.abs(img[0] - img64[0])
+    rel = d / np.maximum(np.abs(img64[0]), 1e-300)
+    print(f"{size}^2 learned vs FP64 outside the band: max rel {rel[~band & bright].max():.2e} over "
+          f"{int((~band & bright).sum())} pixels above 1e-6 of the peak; fainter {int((~band & ~bright).sum())} "
+          f"pixels within {d[~band & ~bright].max() / peak:.1e} of the peak")
+    assert rel[~band & bright].max() <= PIX_TOL
+    assert d[~band & ~bright].max() <= 1e-8 * peak
+    s = ora.scene(**oracle_kwargs(cam))
     Lcm = ora.length_unit_cm(cam["mass_msun"])
     D = cam["distance_pc"] * 3.0856775814913673e18
     pix_jy = (al[1] - al[0]) * (be[1] - be[0]) * Lcm**2 / D**2 / 1e-23
-    pix = scenes.sample_pixels(size, size, 48, seed=size)
-    keep = ~near_ring(al[pix[:, 1]], be[pix[:, 0]], cam["spin"], cam["incl_deg"], 0.5)
-    peak = img[0].max()
-    for (i, j) in pix[keep]:
+    pix = scenes.sample_pixels(size, size, 64, seed=size)
+    keep = ~band[pix[:, 0], pix[:, 1]]
+    top = np.argsort(np.where(band, -np.inf, img64[0]).ravel())[-16:]
+    pix = np.concatenate([pix[keep], np.stack(np.unravel_index(top, img64[0].shape), 1)])
+    for (i, j) in pix:
         ov = ora.trace_ray(s, al[j], be[i], freqs)["I"][0] * pix_jy
         assert abs(img[0, i, j] - ov) <= PIX_TOL * max(abs(ov), 1e-6 * peak), (i, j)
+
+
+def _band_tree(al, be, cam, width=0.5):
+    """Pixels within `width` M of the critical curve, for large images (nearest vertex of a
+    densely sampled curve by a k-d tree)."""
+    from scipy.spatial import cKDTree
+
+    from helpers import bardeen_critical_curve
+
+    A, B = np.meshgrid(al, be)
+    d, _ = cKDTree(bardeen_critical_curve(cam["spin"], cam["incl_deg"], 20000)).query(np.stack([A.ravel(), B.ravel()], 1))
+    return (d < width).reshape(A.shape)
 
 
 @pytest.mark.parametrize("fb_band", [0.5, 0.2])
