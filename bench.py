@@ -30,6 +30,10 @@ WORKLOAD = "kerr_analytic_1024x1024_a0.9375_i60_230GHz"
 METRIC = "rays/s and geodesic steps/s at 1024^2 Kerr image, mixed+MLP vs FP64 at <=1e-3 flux"
 CPU_SAMPLE_STRIDE = 8  # oracle traces every 8th pixel in each direction (128 x 128 rays)
 PROFILED_RENDERS = 2   # renders of the separate pass that records per-kernel times
+# DRAM bytes (read + write) of one launch of a kernel at the headline size, from the ncu
+# capture summarised in profiles/launches_kerr_analytic_1024_mlp_df.md (null for kernels
+# without a capture of their current source)
+DRAM_BYTES_PER_LAUNCH = {"mixed_fp64_long": 1954816}
 FINAL_LINE_MAX = 2000  # bytes: the last stdout line carries the headline only
 
 
@@ -187,11 +191,13 @@ def _time_render(ctx, torch, freqs, image, flush_buf, n, stream):
     return tot
 
 
-def train_surrogate(R, torch, cam, steps, n_train):
+def train_surrogate(R, torch, cam, steps, n_train, handoff=60):
     """Train the learned far-field surrogate on integrator-generated rays (not timed as part
-    of a render step); returns its parameters and a summary."""
+    of a render step), for a hand-off after `handoff` steps; returns its parameters and a
+    summary."""
     ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED_MLP))
     ctx.load_plasma(R.plasma_desc(**scenes_mod().ANALYTIC_PLASMA))
+    ctx.surrogate_handoff(handoff)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     x, y = ctx.surrogate_generate(n_train, seed=0x1801104520000005)
@@ -205,7 +211,7 @@ def train_surrogate(R, torch, cam, steps, n_train):
     xh, yh = ctx.surrogate_generate(100_000, seed=0x1801104520000006)
     err = np.abs(ctx.surrogate_eval(xh).cpu().numpy() - yh.cpu().numpy())
     names = ["dt", "ln_r", "theta", "phi", "k_theta", "k_r"]
-    summ = {"rays": n_train, "steps": steps, "batch": 4096, "generate_s": t_gen, "train_s": t_train,
+    summ = {"rays": n_train, "steps": steps, "batch": 4096, "handoff_steps": handoff, "generate_s": t_gen, "train_s": t_train,
             "heldout_median_abs_err": dict(zip(names, np.median(err, 0).tolist())),
             "heldout_p99_abs_err": dict(zip(names, np.percentile(err, 99, axis=0).tolist())),
             "range": "alpha, beta in +-20 M; a in [0, 0.99]; i in [5, 85] deg"}
@@ -617,9 +623,14 @@ def run_native(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     rays_step = npix * len(freqs)
 
-    params, sur = None, None
+    params, sur, params_grid = None, None, None
     if any(p.startswith("mlp") for p in paths):
         params, sur = train_surrogate(R, torch, cam, args.train_steps, args.train_rays)
+        if not (args.no_grid and args.no_lightcurve):
+            # the torus's fine structure wants the earlier hand-off (smaller angular error of
+            # the learned start states; measured per pixel in the grid workload)
+            params_grid, sur_grid = train_surrogate(R, torch, cam, args.train_steps, args.train_rays, handoff=30)
+            sur = {"analytic": sur, "grid": sur_grid}
     res = {}
     for pth in paths:
         prec = {"mlp": R.MIXED_MLP, "mixed": R.MIXED, "fp64": R.FP64, "mlp_df": R.MIXED_MLP, "mixed_df": R.MIXED}[pth]
@@ -635,10 +646,10 @@ def run_native(args):
         gres = {}
         for pth in ("mlp_df", "mixed_df", "fp64"):
             prec = {"mlp_df": R.MIXED_MLP, "mixed_df": R.MIXED, "fp64": R.FP64}[pth]
-            if prec == R.MIXED_MLP and params is None:
+            if prec == R.MIXED_MLP and params_grid is None:
                 continue
             gres[pth] = _timed_path(R, torch, cam, prec, freqs, args, flush, stream, world, dist, sample_clocks=False,
-                                    params=params if prec == R.MIXED_MLP else None,
+                                    params=params_grid if prec == R.MIXED_MLP else None,
                                     flags=R.FLAG_INNER_DF64 if pth.endswith("_df") else 0, plasma=gplasma,
                                     fields=fields, steps=2 if pth == "fp64" else None)
         grid = {"workload": workload.replace("kerr_analytic", "grid_torus"),
@@ -652,15 +663,25 @@ def run_native(args):
                          "grid_sample_GBps": samples_s * 128 / 1e9,
                          "grid_sample_note": "128 B of FP32 fields per plasma sample (4 corners x 8 fields), "
                                              "served from L2: the snapshot is 2 MiB"}
-            r["ctx"].close()
         if "fp64" in gres:
+            ref = gres["fp64"]["image"].cpu().numpy()[0]
+            band = _band_mask(cam)
+            pk = np.abs(ref).max()
+            m = ~band & (np.abs(ref) >= 1e-6 * pk)
             for pth in gres:
                 if pth != "fp64":
                     grid[pth]["flux_rel_err_vs_fp64"] = float(abs(gres[pth]["flux"][0] / gres["fp64"]["flux"][0] - 1))
+                    rel = np.abs(gres[pth]["image"].cpu().numpy()[0] - ref) / np.maximum(np.abs(ref), 1e-300)
+                    grid[pth]["pixels_vs_fp64_outside_band"] = {
+                        "compared": int(m.sum()), "max_rel": float(rel[m].max()),
+                        "p999_rel": float(np.quantile(rel[m], 0.999)), "over_1e-2": int((rel[m] > 1e-2).sum()),
+                        "note": "pixels above 1e-6 of the peak, more than 0.5 M from the critical curve"}
+        for r in gres.values():
+            r["ctx"].close()
     # ---- the slow-light light curve (100 snapshots 10 M apart, 100 frames of 256^2) ----
     lcurve = None
     if not args.no_lightcurve:
-        lcurve = _lightcurve_extra(R, torch, args, stream, params)
+        lcurve = _lightcurve_extra(R, torch, args, stream, params_grid)
     # ---- the FP64 path with the velocity-Verlet integrator (sec. 2.2.2) ----
     verlet = None
     if not args.no_verlet and rank == 0:
@@ -722,7 +743,8 @@ def run_native(args):
         src = f"FP32 FMA-chain probe {fma32:.1f} TFLOP/s / (2 x {df_ipf:.2f} FP32 instr per flop, double-float)"
     else:
         src = f"{roof['pipe'].upper()} FMA-chain probe, this run"
-    roof.update({"kernel": dom, "traffic": None, "peak_source": src})
+    traffic = DRAM_BYTES_PER_LAUNCH.get(dom) if args.size == 1024 else None
+    roof.update({"kernel": dom, "traffic": traffic, "peak_source": src})
 
     # ---- CPU oracle on a bounded sample of the same workload -----------------------------
     cpu, parity = None, {}
@@ -812,6 +834,28 @@ def run_native(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _band_mask(cam, width=0.5):
+    """Pixel centres within `width` M of the critical curve (Bardeen's closed form, nearest
+    vertex of a densely sampled curve)."""
+    from scipy.spatial import cKDTree
+
+    a, inc = cam["spin"], np.radians(cam["incl_deg"])
+    rp = 2 * (1 + np.cos(2 / 3 * np.arccos(-abs(a))))
+    rm = 2 * (1 + np.cos(2 / 3 * np.arccos(abs(a))))
+    r = np.linspace(rp, rm, 20000)
+    xi = -(r**3 - 3 * r**2 + a * a * r + a * a) / (a * (r - 1))
+    eta = r**3 * (4 * a * a - r * (r - 3) ** 2) / (a * a * (r - 1) ** 2)
+    b2 = eta + a * a * np.cos(inc) ** 2 - xi * xi / np.tan(inc) ** 2
+    ok = b2 >= 0
+    al_c, be_c = -xi[ok] / np.sin(inc), np.sqrt(b2[ok])
+    curve = np.concatenate([np.stack([al_c, be_c], 1), np.stack([al_c, -be_c], 1)])
+    al = cam["alpha_min"] + (np.arange(cam["nx"]) + 0.5) * (cam["alpha_max"] - cam["alpha_min"]) / cam["nx"]
+    be = cam["beta_min"] + (np.arange(cam["ny"]) + 0.5) * (cam["beta_max"] - cam["beta_min"]) / cam["ny"]
+    A, B = np.meshgrid(al, be)
+    d, _ = cKDTree(curve).query(np.stack([A.ravel(), B.ravel()], 1))
+    return (d < width).reshape(A.shape)
 
 
 def _round(v, digits=5):

@@ -403,6 +403,19 @@ raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind);
  * outbound rays stop at r > r_exit in RAPTOR_MIXED_MLP (0 = off) [50]. */
 raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit);
 
+/* Hand-off step count of the learned start states (no counterpart in the paper): the state
+ * network predicts the integrator's state after n_steps adaptive steps from the camera
+ * [60].  This call sets the count for the data raptor_surrogate_generate writes next;
+ * raptor_surrogate_init stores it with the network's parameters (an unused output-mean
+ * slot), and a render uses the count of the network in use (raptor_surrogate_set / _load
+ * read it back; 0 there reads as 60).  The network's angular error at the hand-off carries
+ * over to the ray's path in the emitting region, and the deflection it learns relative to
+ * the flat-space baseline falls like r^-2 with the hand-off radius (r ~ r_cam e^{-eps n}):
+ * fewer steps give more accurate paths and skip less integration.  RAPTOR_EINVAL outside
+ * [1, 1000]; raptor_surrogate_set: RAPTOR_EINVAL when the stored count is not 0 or an
+ * integer in [1, 1000]. */
+raptor_status raptor_surrogate_handoff(raptor_ctx* ctx, int n_steps);
+
 /* Host-side fault injection for failure-handling tests (no counterpart in the paper; no
  * device fault is raised).  RAPTOR_FAULT_TC_WAIT: set, from the host and after the context's
  * last stream has drained, the device flag that a bounded mbarrier wait of the tensor-core

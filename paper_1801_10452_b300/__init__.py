@@ -36,7 +36,7 @@ EXPORTS = [
     "raptor_disk_desc_default", "raptor_disk_render", "raptor_disk_render_learned", "raptor_crossings_param_count",
     "raptor_crossings_generate", "raptor_crossings_init", "raptor_crossings_train", "raptor_crossings_grad",
     "raptor_crossings_eval", "raptor_crossings_get", "raptor_crossings_set", "raptor_crossings_config", "raptor_mixed_config", "raptor_long_config", "raptor_profile_timeline", "raptor_graph_config", "raptor_graph_stats", "raptor_check_fp32_math",
-    "raptor_inject_fault", "raptor_crossings_confidence",
+    "raptor_inject_fault", "raptor_crossings_confidence", "raptor_surrogate_handoff",
 ]
 KERNEL_NAMES = ["render_fp64", "mixed_fp32_in", "mixed_fp64", "mixed_fp32_out", "reduce", "trace", "load", "peak",
                 "surrogate", "train", "surrogate_mlp", "disk", "mixed_fp64_long"]
@@ -125,6 +125,7 @@ def lib():
             "raptor_surrogate_load": (st, [vp, C.c_char_p]),
             "raptor_surrogate_config": (st, [vp, C.c_double, C.c_double]),
             "raptor_inject_fault": (st, [vp, C.c_int]),
+            "raptor_surrogate_handoff": (st, [vp, C.c_int]),
             "raptor_crossings_confidence": (st, [vp, C.c_double, C.c_double]),
             "raptor_surrogate_kernel": (st, [vp, C.c_int]),
             "raptor_crossings_param_count": (C.c_int, []),
@@ -571,6 +572,11 @@ class Context:
     def surrogate_load(self, path):
         """Load a network written by surrogate_save (validated; as surrogate_set)."""
         self._check(lib().raptor_surrogate_load(self._h, str(path).encode()), "raptor_surrogate_load")
+
+    def surrogate_handoff(self, n_steps=60):
+        """Hand-off step count for the next surrogate_generate / surrogate_init (the network
+        carries it; renders use the count of the network in use)."""
+        self._check(lib().raptor_surrogate_handoff(self._h, int(n_steps)), "raptor_surrogate_handoff")
 
     def surrogate_config(self, fallback_band=0.5, r_exit=50.0):
         self._check(lib().raptor_surrogate_config(self._h, float(fallback_band), float(r_exit)), "raptor_surrogate_config")

@@ -101,6 +101,8 @@ struct raptor_ctx {
     float2* s_start = nullptr;       // render: start states [8][rays] (float pairs)
     size_t s_ray_cap = 0;
     double s_band = 0.5, s_r_exit = 50.0;
+    int s_handoff = kSurrogateSteps;      // hand-off steps of the data raptor_surrogate_generate writes
+    int s_handoff_net = kSurrogateSteps;  // hand-off steps of the network in use (from its parameters)
     unsigned long long s_step = 0;   // Adam step counter
     // crossing network (the surrogate's equatorial outputs); shares the work buffers above
     bool x_ready = false;
@@ -281,6 +283,7 @@ void fill_float_params(Params& p) {
     f.h_mks = (float)p.h_mks; f.t0 = (float)p.t0; f.dt_snap = (float)p.dt_snap; f.rho0_ne = (float)p.rho0_ne;
     f.B_unit = (float)p.B_unit; f.r_high = (float)p.r_high; f.r_low = (float)p.r_low; f.gam = (float)p.gam;
     f.r_fp64 = (float)p.r_fp64; f.turn_kr = (float)p.turn_kr;
+    f.r_isco_p = make_float2((float)p.r_isco, (float)(p.r_isco - (double)(float)p.r_isco));
     for (int i = 0; i < 16; ++i) f.nu[i] = (float)p.nu[i];
     auto pair = [](double v) {
         const float hi = (float)v;
@@ -710,7 +713,7 @@ raptor_status run_rays_graph(raptor_ctx* ctx, const Params& p, const double* fre
     put(&n_frames, sizeof(n_frames));
     put(&ctx->cam, sizeof(ctx->cam));
     int cfg[] = {ctx->launch_block, ctx->launch_bps, ctx->launch_bps64, ctx->n_passes, ctx->tail_split, ctx->s_kernel,
-                 ctx->sur_ready ? 1 : 0, ctx->long_block, ctx->long_passes};
+                 ctx->sur_ready ? 1 : 0, ctx->long_block, ctx->long_passes, ctx->s_handoff_net};
     put(cfg, sizeof(cfg));
     put(ctx->pass_budget, sizeof(ctx->pass_budget));
     put(ctx->long_budget, sizeof(ctx->long_budget));
@@ -1439,7 +1442,7 @@ raptor_status raptor_surrogate_generate(raptor_ctx* ctx, long long n, unsigned l
     if (!(incl_min_deg > 0.0 && incl_max_deg >= incl_min_deg && incl_max_deg < 180.0))
         return fail(ctx, RAPTOR_EINVAL, "inclination range invalid");
     SurrogateRange R{ctx->cam.alpha_min, ctx->cam.alpha_max, ctx->cam.beta_min, ctx->cam.beta_max, spin_min, spin_max,
-                     incl_min_deg, incl_max_deg, ctx->cam.r_cam, ctx->cam.eps};
+                     incl_min_deg, incl_max_deg, ctx->cam.r_cam, ctx->cam.eps, ctx->s_handoff};
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
     {
@@ -1488,6 +1491,8 @@ raptor_status raptor_surrogate_init(raptor_ctx* ctx, const double* targets_dev, 
         P[MlpLayout::NORM + 8 + q] = (float)mu;
         P[MlpLayout::NORM + 16 + q] = (float)std::max(std::sqrt(var), 1e-6);
     }
+    P[MlpLayout::HANDOFF] = (float)ctx->s_handoff;  // the network carries its hand-off step count
+    ctx->s_handoff_net = ctx->s_handoff;
     RCK(cudaMemcpyAsync(ctx->s_P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     RCK(cudaMemsetAsync(ctx->s_m1, 0, MlpLayout::SIZE * sizeof(float), s));
     RCK(cudaMemsetAsync(ctx->s_m2, 0, MlpLayout::SIZE * sizeof(float), s));
@@ -1607,6 +1612,12 @@ raptor_status raptor_surrogate_get(raptor_ctx* ctx, float* params_host, int n) {
 raptor_status raptor_surrogate_set(raptor_ctx* ctx, const float* params_host, int n) {
     if (!ctx) return RAPTOR_EINVAL;
     if (!params_host || n != MlpLayout::SIZE) return fail(ctx, RAPTOR_EINVAL, "n must equal raptor_surrogate_param_count()");
+    // hand-off step count stored with the parameters (0: a network written before the count
+    // was stored, trained for the default)
+    const float hf = params_host[MlpLayout::HANDOFF];
+    if (!(hf == 0.f || (hf >= 1.f && hf <= (float)kMaxHandoffSteps && hf == std::floor(hf))))
+        return fail(ctx, RAPTOR_EINVAL, "the parameters' hand-off step count is not an integer in [1, 1000]");
+    ctx->s_handoff_net = hf == 0.f ? kSurrogateSteps : (int)hf;
     RCK(sur_alloc(ctx));
     RCK(cudaStreamSynchronize(ctx->last_stream));
     RCK(cudaMemcpy(ctx->s_P, params_host, n * sizeof(float), cudaMemcpyHostToDevice));
@@ -1733,6 +1744,13 @@ raptor_status raptor_inject_fault(raptor_ctx* ctx, int kind) {
     return RAPTOR_OK;
 }
 
+raptor_status raptor_surrogate_handoff(raptor_ctx* ctx, int n_steps) {
+    if (!ctx) return RAPTOR_EINVAL;
+    if (n_steps < 1 || n_steps > kMaxHandoffSteps) return fail(ctx, RAPTOR_EINVAL, "n_steps must lie in [1, 1000]");
+    ctx->s_handoff = n_steps;
+    return RAPTOR_OK;
+}
+
 raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit) {
     if (!ctx) return RAPTOR_EINVAL;
     if (!(fallback_band >= 0.0) || !std::isfinite(fallback_band) || !(r_exit >= 0.0) || !std::isfinite(r_exit))
@@ -1769,7 +1787,7 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
     RCK(upload_curve(ctx, p, s));
     p.start_xk = ctx->s_start;
     p.fallback = ctx->s_fb;
-    p.start_n = kSurrogateSteps;
+    p.start_n = ctx->s_handoff_net;
     p.r_exit = ctx->s_r_exit;
     p.r_exit_f = (float)ctx->s_r_exit;
     return RAPTOR_OK;

@@ -179,13 +179,13 @@ RAPTOR_HD int grid_sample(const Params& p, const KSPoint<T>& P, const T x[4], in
 // -1 error.  On success fills ne, the, B, g = nu_fluid/nu_obs and sinb.
 template <typename T>
 RAPTOR_HD int plasma_sample_sc(const Params& p, const T x[4], const T k[4], T sn, T cs, int snap, T& ne, T& the,
-                               T& B, T& g, T& sinb) {
+                               T& B, T& g, T& sinb, int kepler = -1) {
     KSPoint<T> P;
     ks_point_sc(RAPTOR_P(T, a), x[1], sn, cs, P);
     T u[4], kc[4];
     T kb;  // k . b_hat
     if (p.kind == 0) {
-        const int ok = analytic_velocity(RAPTOR_P(T, a), RAPTOR_P(T, r_isco), P, u);
+        const int ok = analytic_velocity(RAPTOR_P(T, a), RAPTOR_P(T, r_isco), P, u, kepler);
         if (ok < 0) return -1;
         const T r = x[1];
         if constexpr (std::is_same<T, float>::value) {

@@ -175,12 +175,17 @@ constexpr float kIScale = 1.2676506002282294e30f;      // 2^100
 constexpr double kIUnscale = 7.888609052210118e-31;    // 2^-100
 
 // (sn, cs): sin and cos of x[2], when the caller has them (sn > 1: compute them here).
+// r_lo: the radius's low part (the radius is x[1] + r_lo): the analytic flow changes from
+// Keplerian to free fall at r_isco, and that branch is decided on the radius to ~48 bits
+// against r_isco as a float pair, as the FP64 path decides it (a sample within FP32
+// rounding of r_isco would otherwise take the other branch).
 template <int NF, typename TI>
 __device__ __forceinline__ int rt_sample_fp32(const Params& p, const float x[4], const float k[4], float dl, int snap,
-                                              TI* I, float* tau, df64* tau_hi, float sn = 2.f, float cs = 0.f) {
+                                              TI* I, float* tau, df64* tau_hi, float r_lo, float sn = 2.f, float cs = 0.f) {
     float ne, the, B, g, sinb;
     if (sn > 1.f) sc(x[2], &sn, &cs);
-    const int ok = plasma_sample_sc<float>(p, x, k, sn, cs, snap, ne, the, B, g, sinb);
+    const int kepler = ((x[1] - p.f.r_isco_p.x) + (r_lo - p.f.r_isco_p.y)) >= 0.f ? 1 : 0;
+    const int ok = plasma_sample_sc<float>(p, x, k, sn, cs, snap, ne, the, B, g, sinb, kepler);
     if (ok <= 0) return ok;
     const float dlcm = dl * p.f.Lcm;
     const float gdl_unscaled = g * dlcm * float(kIUnscale);
@@ -229,7 +234,7 @@ __device__ __forceinline__ int step_fp32(const Params& p, RayF<NF>& R) {
     if (R.x[1] < p.f.r_stop) return kCaptured;
     if (R.x[1] > p.f.r_esc) return kEscaped;
     if (p.r_exit_f > 0.f && R.x[1] > p.r_exit_f && R.k[1] > 0.f) return kEscaped;  // surrogate path only
-    if (rt_sample_fp32<NF, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi, sn, cs) < 0) return kError;
+    if (rt_sample_fp32<NF, float>(p, R.x, R.k, dl, R.snap, R.I, R.tau, R.tau_hi, R.xl[1], sn, cs) < 0) return kError;
     return thick_or_capped<NF>(p, R.tau, R.tau_hi, R.n);
 }
 
@@ -300,7 +305,8 @@ __device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF, S>& R, S a
         if (R.x[1] > p.r_esc) return kEscaped;
 #pragma unroll
         for (int i = 0; i < 4; ++i) { xf[i] = float(R.x[i]); kf[i] = float(R.k[i]); }
-        if (rt_sample_fp32<NF, double>(p, xf, kf, float(dl), R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+        if (rt_sample_fp32<NF, double>(p, xf, kf, float(dl), R.snap, R.I, R.tau, R.tau_hi, float(R.x[1] - double(xf[1]))) < 0)
+            return kError;
     } else {
         // step size from the FP32 view of the state (the rule is a heuristic; its value only
         // needs to be a smooth function of the state), RK4 in df64
@@ -317,7 +323,8 @@ __device__ __forceinline__ int step_mixed64(const Params& p, RayM<NF, S>& R, S a
         for (int i = 0; i < 4; ++i) { xf[i] = StateT<S>::f(R.x[i]); kf[i] = StateT<S>::f(R.k[i]); }
         if (xf[1] < p.f.r_stop) return kCaptured;
         if (xf[1] > p.f.r_esc) return kEscaped;
-        if (rt_sample_fp32<NF, float>(p, xf, kf, dl, R.snap, R.I, R.tau, R.tau_hi) < 0) return kError;
+        const float r_lo = (R.x[1].hi - xf[1]) + R.x[1].lo;  // the first difference is exact
+        if (rt_sample_fp32<NF, float>(p, xf, kf, dl, R.snap, R.I, R.tau, R.tau_hi, r_lo) < 0) return kError;
     }
     return thick_or_capped<NF>(p, R.tau, R.tau_hi, R.n);
 }

@@ -12,6 +12,7 @@ struct ParamsF {
     float n0, n_pow, the0, the_pow, B0, B_pow, r_isco, the_min;
     float x1_min, x1_max, dx1, dx2, h_mks, t0, dt_snap, rho0_ne, B_unit, r_high, r_low, gam;
     float r_fp64, turn_kr;
+    float2 r_isco_p;  // r_isco as an unevaluated float pair (hi, lo): the ISCO branch decision
     float nu[16];
     // camera parameters as unevaluated float pairs (hi, lo) for the double-float camera
     float2 a_p, sin_i_p, cos_i_p, r_cam_p, incl_p, cam_phi_p, amin_p, da_p, bmin_p, db_p;
@@ -184,10 +185,13 @@ struct Sample {
 //   u^t = [P (P^2 + 2 r P + 4 r^2)/(P^2 + 2 r s) - a^2 sin^2] / Sigma,
 //   u^r = -s / Sigma, u^phi = -2 a r / (Sigma (2 r + s)), P = r^2 + a^2, s = sqrt(2 r P).
 template <typename T>
-RAPTOR_HD int analytic_velocity(T a, T r_isco, const KSPoint<T>& P, T u[4]) {
+RAPTOR_HD int analytic_velocity(T a, T r_isco, const KSPoint<T>& P, T u[4], int kepler = -1) {
     const T r = P.r;
     u[2] = T(0);
-    if (r >= r_isco) {
+    // kepler: the branch decided by the caller (1: r >= r_isco, 0: inside); -1: decide here.
+    // The flow changes discontinuously at r_isco, so the decision is taken with the radius's
+    // full precision where the caller has more than T's.
+    if (kepler > 0 || (kepler < 0 && r >= r_isco)) {
         const T Om = Real<T>::rcp(r * Real<T>::sqrt_(r) + a);
         const T nrm = P.gtt + T(2) * Om * P.gtp + Om * Om * P.gpp;
         if (!(nrm < T(0))) return -1;

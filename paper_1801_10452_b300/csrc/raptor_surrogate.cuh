@@ -2,11 +2,14 @@
 // a 4-layer MLP trained and evaluated with hand-written kernels, and the reconstruction of
 // an integrator state from its prediction.
 //
-// What is learned: the FP64 integrator's state after exactly kSurrogateSteps adaptive RK4
-// steps from the camera, as a function of (alpha, beta, a, i).  For a fixed step count the
-// state is a smooth function of the inputs (no quantisation of the step sequence), and all
-// rays of a +-20 M camera are still at r >~ 40 M there, where the transfer contributes
-// nothing.  The exact integrator continues from the predicted state, so the transfer is
+// What is learned: the FP64 integrator's state after exactly n_steps adaptive RK4 steps from
+// the camera (the hand-off step count, raptor_surrogate_handoff; stored with the network's
+// parameters), as a function of (alpha, beta, a, i).  For a fixed step count the state is a
+// smooth function of the inputs (no quantisation of the step sequence), and the rays of a
+// +-20 M camera are still far outside the emitting region there (r >~ 40 M after 60 steps).
+// The network's angular error at the hand-off carries over to the path inside the emitting
+// region, and the residual it learns (the deflection accumulated since the camera) falls
+// like r^-2 with the hand-off radius: an earlier hand-off gives a more accurate path.  The exact integrator continues from the predicted state, so the transfer is
 // sampled on the same step sequence as the full integration.  E, L and Q follow exactly from
 // the inputs; the network predicts the position (t - t_cam, ln r, theta, phi) and the signs
 // of k^theta and k^r, and the wave vector is rebuilt from the constants of motion.
@@ -24,7 +27,8 @@
 
 namespace raptor {
 
-constexpr int kSurrogateSteps = 60;
+constexpr int kSurrogateSteps = 60;   // default hand-off step count (raptor_surrogate_handoff)
+constexpr int kMaxHandoffSteps = 1000;
 constexpr int kHid = 256;
 constexpr int kIn = 4;
 constexpr int kOut = 8;      // 6 used: dt, ln r, theta, phi, k^theta, k^r
@@ -47,15 +51,16 @@ struct SurrogateRange {
     double smin, smax;               // spin
     double imin, imax;               // inclination, degrees
     double r_cam, eps;
+    int n_steps = kSurrogateSteps;   // state after this many steps (the hand-off)
 };
 
 // Flat-space baseline: the camera ray's initial state (KS at r_cam) continued as a straight
 // line (r, theta, phi read as spherical coordinates, M -> 0), advanced by the same step rule
-// for kSurrogateSteps steps, all in FP32.  It is a fixed, smooth function of the inputs; the
+// for n_steps steps (the hand-off step count), all in FP32.  It is a fixed, smooth function of the inputs; the
 // network learns only the difference between the integrator and this baseline (the
 // gravitational deflection and delay, a few per cent), which BF16 layers resolve far better
 // than the state itself.  Output as the targets: dt, ln r, theta, phi, k^theta, k^r.
-RAPTOR_HD void surrogate_baseline(const float x0[4], const float k0[4], float eps, float out[kOutUsed]) {
+RAPTOR_HD void surrogate_baseline(const float x0[4], const float k0[4], float eps, int n_steps, float out[kOutUsed]) {
     const float r = x0[1], th = x0[2], ph = x0[3];
     const float st = sinf(th), ct = cosf(th), sp = sinf(ph), cp = cosf(ph);
     // position and velocity in Cartesian components
@@ -66,7 +71,7 @@ RAPTOR_HD void surrogate_baseline(const float x0[4], const float k0[4], float ep
     const float vz = kr * ct - r * kh * st;
     const float kt = k0[0];
     float lam = 0.f, rr = r, thn = th, vr = kr, vth = kh;
-    for (int n = 0; n <= kSurrogateSteps; ++n) {
+    for (int n = 0; n <= n_steps; ++n) {
         // spherical components: r, theta and the rates dr, dtheta, dphi per unit lambda
         const float rho2 = px * px + py * py;
         rr = sqrtf(rho2 + pz * pz);
@@ -75,7 +80,7 @@ RAPTOR_HD void surrogate_baseline(const float x0[4], const float k0[4], float ep
         const float vp = vx * px + vy * py;
         vr = (vp + vz * pz) * irr;
         vth = (pz * vp / fmaxf(rho, 1e-30f) - vz * rho) * irr * irr;
-        if (n == kSurrogateSteps) break;
+        if (n == n_steps) break;
         const float vph = (vy * px - vx * py) / fmaxf(rho2, 1e-30f);
         const float xs[4] = {0.f, rr, thn, 0.f}, ks[4] = {kt, vr, vth, vph};
         const float dl = step_size<float>(eps, false, xs, ks);
@@ -95,26 +100,26 @@ RAPTOR_HD void surrogate_baseline(const float x0[4], const float k0[4], float ep
 // The baseline of the ray through (alpha, beta) from the camera parameters: the camera wave
 // vector in FP32 (phi0: the camera's KS azimuth).  Training and rendering both use this.
 RAPTOR_HD void surrogate_base(float a, float sn_i, float cs_i, float incl, float r_cam, float phi0, float alpha, float beta,
-                              float eps, float out[kOutUsed]) {
+                              float eps, int n_steps, float out[kOutUsed]) {
     float k0[4];
     camera_k_t<float>(a, sn_i, cs_i, r_cam, alpha, beta, k0);
     const float x0[4] = {0.f, r_cam, incl, phi0};
-    surrogate_baseline(x0, k0, eps, out);
+    surrogate_baseline(x0, k0, eps, n_steps, out);
 }
 
-// Integrator state after kSurrogateSteps steps (FP64) minus the baseline: the targets
-// (raw, optional: the state itself in the same six components).
+// Integrator state after n_steps steps (FP64) minus the baseline: the targets (raw,
+// optional: the state itself in the same six components).
 RAPTOR_HD void surrogate_targets(double a, double incl_deg, double r_cam, double eps, double alpha, double beta,
-                                 double out[kOutUsed], double* raw = nullptr) {
+                                 int n_steps, double out[kOutUsed], double* raw = nullptr) {
     const double inc = incl_deg * (kPi / 180.0);
     const double sn = sin(inc), cs = cos(inc);
     double x[4], k[4];
     camera_ray_ai(a, sn, cs, inc, r_cam, alpha, beta, 0.0, x, k);
     float base[kOutUsed];
     surrogate_base((float)a, (float)sn, (float)cs, (float)inc, (float)r_cam, (float)x[3], (float)alpha, (float)beta,
-                   (float)eps, base);
+                   (float)eps, n_steps, base);
     const double t0 = x[0];
-    for (int n = 0; n < kSurrogateSteps; ++n) rk4_step<double>(a, x, k, step_size<double>(eps, false, x, k));
+    for (int n = 0; n < n_steps; ++n) rk4_step<double>(a, x, k, step_size<double>(eps, false, x, k));
     out[0] = x[0] - t0 - base[0];
     out[1] = log(x[1]) - base[1];
     out[2] = x[2] - base[2];
@@ -144,7 +149,7 @@ __global__ void k_surrogate_data(SurrogateRange R, uint64_t seed, long long n, f
         inputs[i * kIn + 2] = (float)a;
         inputs[i * kIn + 3] = (float)inc;
         double t[kOutUsed], rw[kOutUsed];
-        surrogate_targets(a, inc, R.r_cam, R.eps, al, be, t, rw);
+        surrogate_targets(a, inc, R.r_cam, R.eps, al, be, R.n_steps, t, rw);
         for (int q = 0; q < kOutUsed; ++q) targets[i * kOutUsed + q] = t[q];
         if (raw)
             for (int q = 0; q < kOutUsed; ++q) raw[i * kOutUsed + q] = rw[q];
@@ -168,6 +173,7 @@ struct MlpLayoutT {
     static constexpr int NORM = B4 + NOUT;               // input scale[4], shift[4], output mean[NOUT], std[NOUT]
     static constexpr int MU = NORM + 8;
     static constexpr int SD = MU + NOUT;
+    static constexpr int HANDOFF = MU + NOUT - 1;        // unused output's mean slot: the hand-off step count
     static constexpr int SIZE = SD + NOUT;
 };
 using MlpLayout = MlpLayoutT<kOut>;
@@ -702,7 +708,7 @@ __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, 
         const int row = p.row0 + pix / p.nx, col = pix % p.nx;
         const float al = (float)(p.amin + (col + 0.5) * p.da), be = (float)(p.bmin + (row + 0.5) * p.db);
         float base[kOutUsed];
-        surrogate_base(af, sif, cif, incf, rcf, ph0, al, be, p.f.eps, base);
+        surrogate_base(af, sif, cif, incf, rcf, ph0, al, be, p.f.eps, p.start_n, base);
         const float4 o0 = reinterpret_cast<const float4*>(out)[2 * id];
         const float4 o1 = reinterpret_cast<const float4*>(out)[2 * id + 1];
         const float o[kOutUsed] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y};

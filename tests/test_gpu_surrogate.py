@@ -57,6 +57,41 @@ def test_training_data_is_the_integrator_state(R, ora):
         assert np.all(np.abs(zs[i] - ref) <= 1e-9 * np.maximum(np.abs(ref), 1.0)), (i, zs[i] - ref)
 
 
+def test_handoff_step_count(R, ora):
+    """A non-default hand-off: the generator's raw states equal the oracle's FP64 geodesic
+    after that many steps, the network initialised on them carries the count in its
+    parameters (read back by raptor_surrogate_set), and counts outside [1, 1000] are
+    refused."""
+    ctx = R.Context(R.camera_desc(**scenes.SMALL))
+    ctx.surrogate_handoff(36)
+    x, y, z = ctx.surrogate_generate(32, seed=4, states=True)
+    xs, zs = x.cpu().numpy(), z.cpu().numpy()
+    for i in range(32):
+        al, be, a, inc = map(float, xs[i])
+        s = ora.scene(a=a, incl_deg=inc)
+        st, xf, kf, n = ora.geodesic(s, al, be, max_steps=36)
+        x0, _ = ora.camera(s, al, be)
+        assert n == 36
+        ref = np.array([xf[0] - x0[0], np.log(xf[1]), xf[2], xf[3], kf[2], kf[1]])
+        assert np.all(np.abs(zs[i] - ref) <= 1e-9 * np.maximum(np.abs(ref), 1.0)), (i, zs[i] - ref)
+    ctx.surrogate_init(y, seed=7)
+    P = ctx.surrogate_get()
+    assert 36.0 in P.tolist()
+    for bad in (0, -3, 1001):
+        with pytest.raises(R.RaptorError) as e:
+            ctx.surrogate_handoff(bad)
+        assert e.value.status == R.EINVAL
+    other = R.Context(R.camera_desc(**scenes.SMALL, precision=R.MIXED_MLP))
+    other.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    other.surrogate_set(P)
+    other.render([230e9])
+    Q = P.copy()
+    Q[np.asarray(P) == 36.0] = 2.5   # not an integer count
+    with pytest.raises(R.RaptorError) as e:
+        other.surrogate_set(Q)
+    assert e.value.status == R.EINVAL
+
+
 def test_backward_pass_matches_fp64_oracle(R):
     """Gradient of the batch loss from the library's kernels (BF16 hidden layers, FP32
     accumulation) against the FP64 chain rule of oracle/mlp.py, per parameter tensor, at the
