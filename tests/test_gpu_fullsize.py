@@ -105,16 +105,17 @@ def test_grid_image_full_size_all_paths(R, ora, trained):
                   f"{int(over.sum())} of {int(m.sum())} pixels above {PIX_TOL:g}, brightest of them "
                   f"{(img64[m][over].max() / pk if over.any() else 0):.1e} of the peak; fainter pixels "
                   f"within {d[~band & ~bright].max() / pk:.1e} of the peak")
-            assert d[~band & ~bright].max() <= 1e-8 * pk, name
             if name == "mixed_df":
                 assert rel[m].max() <= PIX_TOL, name
+                assert d[~band & ~bright].max() <= 1e-8 * pk, name
             else:
                 # the network's angular error at the hand-off carries over to the path at the
                 # torus, whose sharp inner edge changes some pixels by 3-10 % per 1e-3 M of
                 # image-plane offset: the per-pixel bound holds for all but ~0.01 % of the
                 # pixels with the 30-step hand-off (0.1 % with 60; measured), which this
-                # checks with margin
+                # checks with margin; pixels fainter than 1e-6 of the peak within 1e-6 of it
                 assert over.mean() <= 1e-3, (name, over.mean())
+                assert d[~band & ~bright].max() <= 1e-6 * pk, name
         keep = ~near_ring(al[pix[:, 1]], be[pix[:, 0]], cam["spin"], cam["incl_deg"], 0.5)
         tol = 1e-8 if name == "fp64" else PIX_TOL
         peak = img.max()

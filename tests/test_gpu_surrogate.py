@@ -271,7 +271,24 @@ def test_learned_path_full_size(R, ora, trained, size):
     print(f"{size}^2 learned vs FP64 outside the band: max rel {rel[~band & bright].max():.2e} over "
           f"{int((~band & bright).sum())} pixels above 1e-6 of the peak; fainter {int((~band & ~bright).sum())} "
           f"pixels within {d[~band & ~bright].max() / peak:.1e} of the peak")
-    assert rel[~band & bright].max() <= PIX_TOL
+    # a pixel beyond the bound must sit on a discontinuity of the FP64 image itself (the
+    # analytic flow switches from Keplerian to free fall at r_isco, so the image jumps where
+    # an emitting sample crosses r_isco): there the paths disagree on an interval as wide as
+    # their trajectories differ (~1e-7 M), and the FP64 image changes by more than the bound
+    # within a few 1e-6 M of the pixel centre
+    bad = np.argwhere(~band & bright & (rel > PIX_TOL))
+    assert len(bad) <= 2, len(bad)
+    for i, j in bad:
+        span = 1.6e-5
+        line = dict(cam, nx=16, ny=1, alpha_min=al[j] - span / 2, alpha_max=al[j] + span / 2, beta_min=be[i] - 1e-9,
+                    beta_max=be[i] + 1e-9)
+        cl = R.Context(R.camera_desc(**line, precision=R.FP64))
+        cl.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+        v, _ = cl.render(freqs)
+        v = v.cpu().numpy()[0, 0]
+        print(f"pixel ({al[j]:.4f}, {be[i]:.4f}) off by {rel[i, j]:.2e}: FP64 within +-{span / 2:.0e} M spans "
+              f"{v.min() / v.max():.4f} .. 1 of its largest value")
+        assert v.max() / v.min() - 1 > PIX_TOL, (i, j)
     assert d[~band & ~bright].max() <= 1e-8 * peak
     s = ora.scene(**oracle_kwargs(cam))
     Lcm = ora.length_unit_cm(cam["mass_msun"])
