@@ -1807,7 +1807,7 @@ cudaError_t surrogate_stage(raptor_ctx* ctx, const Params& p, cudaStream_t s) {
     {
         ProfScope ps(ctx, kProfSurrogate, s, 2);  // inputs and start states; the network nests below
         k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->d_curve, nc, (float)ctx->s_band, box,
-                                                                       ctx->s_in, ctx->s_fb);
+                                                                       ctx->s_in, ctx->s_fb, ctx->d_stats + kStatFallback);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
             ProfScope pm(ctx, kProfSurrogateMlp, s, ctx->s_kernel == RAPTOR_MLP_MMA_SYNC ? 1 : 2);
@@ -2296,7 +2296,7 @@ raptor_status disk_learned_stage(raptor_ctx* ctx, const Params& p, DiskArgs& a, 
     {
         ProfScope ps(ctx, kProfSurrogate, s, 2);
         k_surrogate_prepare<<<ew_blocks((long long)n), 256, 0, s>>>(p, ctx->d_curve, ctx->n_curve, (float)ctx->x_band, box,
-                                                                    ctx->s_in, ctx->s_fb);
+                                                                    ctx->s_in, ctx->s_fb, ctx->d_stats + kStatFallback);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
             ProfScope pm(ctx, kProfSurrogateMlp, s, ctx->s_kernel == RAPTOR_MLP_MMA_SYNC ? 1 : 2);

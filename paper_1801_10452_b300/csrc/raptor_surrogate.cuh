@@ -662,10 +662,14 @@ __device__ __forceinline__ void curve_relation(float alf, float bef, const float
 constexpr int kMaxCurve = 512;
 __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const float2* __restrict__ curve, int n_curve,
                                                            float band, float4 box, float* __restrict__ inputs,
-                                                           unsigned char* __restrict__ fallback) {
+                                                           unsigned char* __restrict__ fallback,
+                                                           unsigned long long* __restrict__ n_fallback) {
     __shared__ float2 sc[kMaxCurve];
+    __shared__ unsigned int block_fb;
+    if (threadIdx.x == 0) block_fb = 0;
     for (int c = threadIdx.x; c < n_curve; c += blockDim.x) sc[c] = curve[c];
     __syncthreads();
+    unsigned int my_fb = 0;
     const float a_f = p.f.a, inc_deg = (float)(p.incl * (180.0 / kPi));
     const float band2 = band * band;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < p.n_rays;
@@ -684,7 +688,12 @@ __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const
             fb = (inside || d2 < band2) ? 1 : 0;
         }
         fallback[id] = fb;
+        my_fb += fb;
     }
+    // rays that start at the camera (counted in the context's statistics)
+    if (my_fb) atomicAdd(&block_fb, my_fb);
+    __syncthreads();
+    if (threadIdx.x == 0 && block_fb && n_fallback) atomicAdd(n_fallback, (unsigned long long)block_fb);
 }
 
 // Denormalise the network outputs and rebuild the start states [8][n_rays] (FP32 except the

@@ -203,3 +203,34 @@ def test_results_independent_of_schedule(R, flags):
         torch.cuda.synchronize()
         assert np.array_equal(img.cpu().numpy(), ref), (band, budgets, tail, long)
         assert np.array_equal(fl, fref), (band, budgets, tail, long)
+
+
+def test_phase_step_counters_partition_the_steps(R):
+    """The per-phase device counters (raptor_stats_ex) account for every step of a mixed
+    render exactly once: FP32 inbound + FP32 outbound + FP64 (both streams) = all steps, the
+    second stream's FP64 steps a part of the FP64 ones; with the learned surrogate the steps
+    its start states replace (hand-off count x rays it serves) make up the difference."""
+    import torch
+
+    cam = dict(scenes.SMALL, nx=96, ny=80)
+    for flags in (0, R.FLAG_INNER_DF64):
+        ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED, flags=flags))
+        ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+        ctx.stats_reset()
+        ctx.render([230e9])
+        torch.cuda.synchronize()
+        st = ctx.stats_ex()
+        assert st["fp32_steps_in"] > 0 and st["fp32_steps_out"] > 0 and st["fp64_steps"] > 0
+        assert st["fp32_steps_in"] + st["fp32_steps_out"] + st["fp64_steps"] == st["steps"], st
+        assert 0 < st["fp64_steps_long"] < st["fp64_steps"]
+    ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED_MLP, flags=R.FLAG_INNER_DF64))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    x, y = ctx.surrogate_generate(4096, seed=1)
+    ctx.surrogate_init(y, seed=2)
+    ctx.stats_reset()
+    ctx.render([230e9])
+    torch.cuda.synchronize()
+    st = ctx.stats_ex()
+    served = st["rays"] - st["fallback"]
+    assert served > 0
+    assert st["fp32_steps_in"] + st["fp32_steps_out"] + st["fp64_steps"] + 60 * served == st["steps"], st
