@@ -117,7 +117,14 @@ RAPTOR_HD df64 df_sqrt(df64 a) {
 }
 
 // sin and cos of x (any moderate argument; the geodesic code passes theta in (0, pi)).
-RAPTOR_HD void df_sincos(df64 x, df64* s_out, df64* c_out) {
+// Kept out of line on the device: the table form below calls it only off [0, pi], and
+// inlining it at every call site would only grow the integrators' code.
+#ifdef __CUDACC__
+static __host__ __device__ __noinline__
+#else
+inline
+#endif
+void df_sincos(df64 x, df64* s_out, df64* c_out) {
     // pi/2 = P1 + P2 + P3 (three floats; residual ~1e-23)
     const float P1 = 1.57079637f, P2 = -4.37113883e-08f, P3 = -1.71512451e-15f;
     const float kf = rintf((x.hi + x.lo) * 0.636619747f);
