@@ -438,9 +438,9 @@ cudaError_t upload_curve(raptor_ctx* c, const Params& p, cudaStream_t s) {
 
 // Mixed precision (per frequency chunk): split the rays into near-critical and other
 // (k_select_critical); phase A1 on the near-critical rays; snapshot of the FP64 queue; fork:
-// B-long (their FP64 phase, no step budget) on the context's second stream; on the caller's
-// stream phase A2, the FP64 passes of growing step budget on the other queued rays, phase C
-// on their leavers; join; phase C on B-long's leavers.
+// B-long (their FP64 phase, no step budget) and phase C on its leavers on the context's
+// second stream; on the caller's stream phase A2, the FP64 passes of growing step budget on
+// the other queued rays, phase C on their leavers; join.
 constexpr int kPassBudget[kMaxPasses] = {16, 32, 48, 64, 96, 128, 256, 1 << 30};
 constexpr long long kGraphMaxRays = 1LL << 19;  // largest call replayed from a graph
 
@@ -600,25 +600,27 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool
         e = fp64_phase(bt, b_long, long_threads, c->s_long);
         if (e != cudaSuccess) return e;
     }
-    e = cudaEventRecord(c->ev_join, c->s_long);
+    // phase C on B-long's (and B-tail's) leavers, on the second stream as soon as they are
+    // all queued: it overlaps the first stream's phase C instead of following it
+    PhaseIO cl = cc;
+    cl.in = mq.q32l;
+    cl.fetch = kCntFetch32L;
+    cl.total = kCntPush32L;
+    {
+        ProfScope ps(c, kProfMixedC, c->s_long);
+        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, c->s_long>>>(p, cl, mq.cap, cnt, c->d_stats);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->s_long);
     if (e != cudaSuccess) return e;
-    // phase C on the passes' leavers, then, after the join, on B-long's (and B-tail's)
+    // phase C on the passes' leavers; then the join
     {
         ProfScope ps(c, kProfMixedC, s);
         k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, cc, mq.cap, cnt, c->d_stats);
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
-    if (e != cudaSuccess) return e;
-    PhaseIO cl = cc;
-    cl.in = mq.q32l;
-    cl.fetch = kCntFetch32L;
-    cl.total = kCntPush32L;
-    {
-        ProfScope ps(c, kProfMixedC, s);
-        k_mixed_fp32<NF><<<std::max(1, b32), c->launch_block, 0, s>>>(p, cl, mq.cap, cnt, c->d_stats);
-    }
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_mixed(raptor_ctx* c, const Params& p, cudaStream_t s, bool sur_stage) {

@@ -51,10 +51,15 @@ def test_timeline_matches_slot_sums_and_shows_both_streams(R):
         rec = [t for t in tl if t[1] == lane]
         for a, b in zip(rec, rec[1:]):
             assert b[2] >= a[2] + a[3] - 0.01, (a, b)
-    # the join: the last C launch starts after the second stream's last launch ended
+    # phase C of B-long's leavers runs on the second stream after B-long, the other C on the
+    # first; the join: the flux reduction starts after the second stream's last launch ended
+    assert sorted(t[1] for t in tl if t[0] == "mixed_fp32_out") == [0, 1]
+    c_long = [t for t in tl if t[0] == "mixed_fp32_out" and t[1] == 1][0]
+    long_fp64_end = max(t[2] + t[3] for t in tl if t[0] == "mixed_fp64_long")
+    assert c_long[2] >= long_fp64_end - 0.01
     long_end = max(t[2] + t[3] for t in tl if t[1] == 1)
-    c_long = [t for t in tl if t[0] == "mixed_fp32_out"][-1]
-    assert c_long[2] >= long_end - 0.01
+    red = [t for t in tl if t[0] == "reduce"][0]
+    assert red[2] >= long_end - 0.01
     # a second profile(True) clears the records
     ctx.profile(True)
     assert ctx.profile_timeline() == []
