@@ -399,7 +399,9 @@ raptor_status raptor_surrogate_load(raptor_ctx* ctx, const char* path);
 raptor_status raptor_surrogate_kernel(raptor_ctx* ctx, int kind);
 
 /* Fallback: rays whose pixel centre lies inside the critical curve (Bardeen's closed form)
- * or within fallback_band M of it start at the camera (exact integration) [0.5]; r_exit:
+ * or within fallback_band M of it start at the camera (exact integration) [0.5], and so do
+ * the pixel centres within 0.01 M of alpha = 0 (rays of nearly zero angular momentum pass
+ * the polar axis, where the transfer's samples follow tiny changes of L; fixed); r_exit:
  * outbound rays stop at r > r_exit in RAPTOR_MIXED_MLP (0 = off) [50]. */
 raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, double r_exit);
 

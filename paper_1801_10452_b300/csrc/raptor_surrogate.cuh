@@ -656,10 +656,14 @@ __device__ __forceinline__ void curve_relation(float alf, float bef, const float
 // Per ray of a render: network inputs (alpha, beta, a, i in degrees) and the fallback flag:
 // pixel centre within `band` M of the critical curve (n_curve <= kMaxCurve points in order
 // around the closed curve, FP32) or inside it (captured rays, whose near-horizon emission is
-// too sensitive to the hand-off state for the surrogate's accuracy).  Pixels outside the
-// curve's bounding box grown by the band (`box` = alpha_min, alpha_max, beta_min, beta_max)
-// are neither, and skip the polygon loop.
+// too sensitive to the hand-off state for the surrogate's accuracy), or within kAxisBand M
+// of alpha = 0: rays of (nearly) zero angular momentum pass the polar axis, where the step
+// rule's min(theta, pi - theta) factor makes the transfer's samples follow tiny changes of
+// L, such as the network's error.  Pixels outside the curve's bounding box grown by the
+// band (`box` = alpha_min, alpha_max, beta_min, beta_max) are not near the curve, and skip
+// the polygon loop.
 constexpr int kMaxCurve = 512;
+constexpr float kAxisBand = 0.01f;
 __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const float2* __restrict__ curve, int n_curve,
                                                            float band, float4 box, float* __restrict__ inputs,
                                                            unsigned char* __restrict__ fallback,
@@ -679,8 +683,8 @@ __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const
         const int row = p.row0 + pix / p.nx, col = pix % p.nx;
         const float alf = (float)(p.amin + (col + 0.5) * p.da), bef = (float)(p.bmin + (row + 0.5) * p.db);
         reinterpret_cast<float4*>(inputs)[id] = make_float4(alf, bef, a_f, inc_deg);
-        unsigned char fb = 0;
-        if (alf >= box.x && alf <= box.y && bef >= box.z && bef <= box.w) {
+        unsigned char fb = fabsf(alf) < kAxisBand ? 1 : 0;
+        if (!fb && alf >= box.x && alf <= box.y && bef >= box.z && bef <= box.w) {
             // FP32 suffices: the band edge needs no more precision
             float d2;
             bool inside;

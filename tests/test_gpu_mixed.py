@@ -15,6 +15,12 @@ RING_BAND = 0.5
 # Bands whose whole emission lies beyond FP32's exponent range even with the 2^100 scaling
 # of the FP32 transfer (exp(-X^{1/3}) < 1e-45 everywhere) are reported, not bounded.
 MIN_FLUX_JY = 1e-30
+# Rays through the polar axis (pixel columns within AXIS_BAND M of alpha = 0, L ~ 0) are
+# ill-conditioned in the method itself: the steps shrink towards the axis and the turning
+# point follows the rounding of L, so the FP64 image moves by several per cent for a 1e-8 M
+# shift of alpha (test_gpu_fp64).  They are bounded at AXIS_TOL, not PIX_TOL.
+AXIS_BAND = 1e-3
+AXIS_TOL = 0.1
 
 
 @pytest.fixture(scope="module")
@@ -45,15 +51,19 @@ def _mixed(R, cam, freqs, **over):
 def _check(R, cam, img, fl, oimg, tag):
     al, be = R.pixel_centres(R.camera_desc(**cam))
     band = ring_mask(al, be, cam["spin"], cam["incl_deg"], RING_BAND)
+    axis = np.broadcast_to(np.abs(al)[None, :] < AXIS_BAND, band.shape)
     out = []
     for f in range(img.shape[0]):
         if oimg[f].sum() < MIN_FLUX_JY:
             continue
         fe = abs(fl[f] / oimg[f].sum() - 1)
-        pe = rel_err(img[f], oimg[f], floor_frac=1e-6)[~band].max()
+        rel = rel_err(img[f], oimg[f], floor_frac=1e-6)
+        pe = rel[~band & ~axis].max()
         out.append((fe, pe))
         assert fe <= FLUX_TOL, (tag, f, fe)
         assert pe <= PIX_TOL, (tag, f, pe)
+        if (axis & ~band).any():
+            assert rel[axis & ~band].max() <= AXIS_TOL, (tag, f, rel[axis & ~band].max())
     return out
 
 
@@ -115,6 +125,35 @@ def test_results_independent_of_launch_shape(R):
         img, fl = ctx.render(scenes.SPECTRAL_FREQS[:3])
         torch.cuda.synchronize()
         assert np.array_equal(img.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("flags", [0, "df64"])
+def test_many_frequencies_ragged_image(R, ora, flags):
+    """20 frequencies (two frequency chunks of 16 and 4: each chunk runs the whole two-stream
+    schedule, and the second chunk's counters are reset only after the first chunk's second
+    stream has joined) on a ragged 37 x 29 image, against the oracle with the same bounds on
+    every frequency (its odd width puts a pixel column on alpha = 0: the polar-axis rays,
+    bounded at AXIS_TOL); then a one-pixel and a one-row image (fewer rays than a warp)
+    through the same path, per pixel outside the critical-curve band."""
+    cam = dict(scenes.SMALL, nx=37, ny=29)
+    freqs = list(np.logspace(10, 13, 20))
+    over = dict(flags=R.FLAG_INNER_DF64) if flags else {}
+    _, img, fl, _, stat = _mixed(R, cam, freqs, **over)
+    assert img.shape == (20, 29, 37) and np.all(np.isfinite(img))
+    oimg, _, ostat = ora.render(ora.scene(**oracle_kwargs(cam)), freqs)
+    assert len(_check(R, cam, img, fl, oimg, f"20 freqs {flags}")) == 20
+    assert (stat == ostat).mean() > 0.99
+    for small in (dict(nx=1, ny=1, alpha_min=8.0, alpha_max=8.5, beta_min=3.0, beta_max=3.5),
+                  dict(nx=23, ny=1, beta_min=2.0, beta_max=2.5)):
+        c = dict(scenes.SMALL, **small)
+        _, im1, _, _, stat1 = _mixed(R, c, freqs[:3], **over)
+        o1, _, ostat1 = ora.render(ora.scene(**oracle_kwargs(c)), freqs[:3])
+        al, be = R.pixel_centres(R.camera_desc(**c))
+        out = ~ring_mask(al, be, c["spin"], c["incl_deg"], RING_BAND)
+        assert out.sum() >= (1 if c["nx"] == 1 else 15)
+        assert np.array_equal(stat1[out], ostat1[out])
+        for f in range(3):
+            assert rel_err(im1[f], o1[f], floor_frac=1e-6)[out].max() <= PIX_TOL, (small, f)
 
 
 def test_inner_region_in_double_float(R, ora):

@@ -199,6 +199,31 @@ def test_mixed_mlp_render_parity(R, ora, trained, spin):
         assert rel_err(img[f], oimg[f], floor_frac=1e-6)[~band].max() <= PIX_TOL
 
 
+def test_mixed_mlp_many_frequencies_ragged(R, ora, trained):
+    """20 frequencies (two frequency chunks: the network's inference runs once, in the first,
+    and both chunks start their rays from its states) on a ragged 37 x 29 image, with
+    double-float inner steps: every frequency's flux within 1e-3 of the oracle's and every
+    pixel outside the critical-curve band within 1e-2, except the pixel column on alpha = 0
+    (rays through the polar axis, ill-conditioned in the method: within 0.1)."""
+    cam = dict(scenes.SMALL, nx=37, ny=29)
+    freqs = list(np.logspace(10, 13, 20))
+    ctx = R.Context(R.camera_desc(**cam, precision=R.MIXED_MLP, flags=R.FLAG_INNER_DF64))
+    ctx.load_plasma(R.plasma_desc(**scenes.ANALYTIC_PLASMA))
+    ctx.surrogate_set(trained)
+    img, fl = ctx.render(freqs)
+    img = img.cpu().numpy()
+    oimg, _, _ = ora.render(ora.scene(**oracle_kwargs(cam)), freqs)
+    al, be = R.pixel_centres(R.camera_desc(**cam))
+    band = ring_mask(al, be, cam["spin"], cam["incl_deg"], 0.5)
+    axis = np.broadcast_to(np.abs(al)[None, :] < 1e-3, band.shape)
+    assert axis.sum() == cam["ny"]
+    for f in range(len(freqs)):
+        assert abs(fl[f] / oimg[f].sum() - 1) <= FLUX_TOL, f
+        rel = rel_err(img[f], oimg[f], floor_frac=1e-6)
+        assert rel[~band & ~axis].max() <= PIX_TOL, f
+        assert rel[~band & axis].max() <= 0.1, f
+
+
 def test_surrogate_gain_over_the_method_without_it(R, trained):
     """What the trained network gains: the 512^2 spectral-scene image (a = 0.9375) rendered by
     the mixed path with and without the surrogate, both checked against the FP64 GPU path at
