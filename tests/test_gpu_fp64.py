@@ -135,6 +135,23 @@ def test_single_pixel_and_many_frequencies(R, ora):
     assert rel_err(img.ravel(), oimg.ravel()).max() <= PIX_TOL
 
 
+@pytest.mark.parametrize("spin,incl", [(0.9, 5.0), (0.9, 90.0), (0.9, 150.0), (-0.7, 60.0), (0.998, 30.0)])
+def test_inclinations_and_retrograde_spin(R, ora, spin, incl):
+    """Camera geometry beyond the workloads' i = 60 deg: nearly face-on (the camera 5 deg
+    from the axis), edge-on, below the equatorial plane (cos i < 0), a retrograde hole
+    (a < 0: the analytic flow counter-rotates about the camera's axis, r_isco ~ 8.1 M) and a
+    near-extremal prograde one; 40 x 36 pixels, two frequencies, every pixel and status
+    against the oracle."""
+    cam = dict(scenes.SMALL, spin=spin, incl_deg=incl, nx=40, ny=36)
+    freqs = [86e9, 230e9]
+    img, fl, st, stat = _gpu_render(R, _ctx(R, cam), freqs)
+    oimg, ost, ostat = ora.render(ora.scene(**oracle_kwargs(cam)), freqs)
+    assert np.array_equal(st, ost) and np.array_equal(stat, ostat)
+    for f in range(len(freqs)):
+        assert rel_err(img[f], oimg[f]).max() <= PIX_TOL, f
+        assert abs(fl[f] / oimg[f].sum() - 1) <= FLUX_TOL, f
+
+
 def test_polar_axis_rays_are_ill_conditioned(R, ora):
     """Rays of zero angular momentum (alpha = 0) pass the polar axis; the step rule's
     min(theta, pi - theta) factor shrinks the steps towards it and the turning point follows

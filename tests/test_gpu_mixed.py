@@ -156,6 +156,19 @@ def test_many_frequencies_ragged_image(R, ora, flags):
             assert rel_err(im1[f], o1[f], floor_frac=1e-6)[out].max() <= PIX_TOL, (small, f)
 
 
+@pytest.mark.parametrize("spin,incl", [(0.9, 5.0), (0.9, 90.0), (0.9, 150.0), (-0.7, 60.0), (0.998, 30.0)])
+def test_inclinations_and_retrograde_spin(R, ora, spin, incl):
+    """The mixed path (double-float inner steps) beyond i = 60 deg: nearly face-on, edge-on,
+    below the plane, a retrograde and a near-extremal hole, against the oracle with the same
+    bounds (flux 1e-3; pixels 1e-2 outside the critical band and the polar-axis strip)."""
+    cam = dict(scenes.SMALL, spin=spin, incl_deg=incl, nx=40, ny=36)
+    freqs = [86e9, 230e9]
+    _, img, fl, _, stat = _mixed(R, cam, freqs, flags=R.FLAG_INNER_DF64)
+    oimg, _, ostat = ora.render(ora.scene(**oracle_kwargs(cam)), freqs)
+    assert len(_check(R, cam, img, fl, oimg, f"a={spin} i={incl}")) == 2
+    assert (stat == ostat).mean() > 0.99
+
+
 def test_inner_region_in_double_float(R, ora):
     """RAPTOR_FLAG_INNER_DF64: the inner-region steps in double-float arithmetic meet the same
     bounds against the FP64 oracle as native FP64, and stay close to the native-FP64 mixed path."""
