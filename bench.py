@@ -33,10 +33,10 @@ PROFILED_RENDERS = 2   # renders of the separate pass that records per-kernel ti
 # DRAM bytes (read + write) of one launch of a kernel at the headline size, from the ncu
 # capture summarised in profiles/launches_kerr_analytic_1024_mlp_df.md (null for kernels
 # without a capture of their current source)
-DRAM_BYTES_PER_LAUNCH = {"mixed_fp64_long": 1958656}
+DRAM_BYTES_PER_LAUNCH = {"mixed_fp64_long": 1955072}
 # hardware counters of the same kernel at 512^2 (profiles/k_mixed_fp64_df64_passes_512.md):
 # FP32 (FMA) pipe busy and issue-active fractions beside the algorithmic-flop roofline
-NCU_PIPES = {"mixed_fp64_long": {"fma_pipe": 0.174, "issue_active": 0.471, "at": "512^2, ncu"}}
+NCU_PIPES = {"mixed_fp64_long": {"fma_pipe": 0.162, "issue_active": 0.501, "at": "512^2, ncu"}}
 FINAL_LINE_MAX = 2000  # bytes: the last stdout line carries the headline only
 
 
