@@ -19,8 +19,11 @@
 // One MMA instruction consumes k = 16, i.e. two core matrices along k: its descriptors start
 // 256 B further for each k-step.
 //
-// Every wait on an mbarrier is bounded (kTcWaitNs); a wait that runs out sets *err, and the
-// kernel releases its TMEM and returns.
+// Each kernel holds two accumulators in TMEM (512 columns; one CTA per SM, which its shared
+// memory enforces): while the tensor cores run tile t's MMAs into one, the CUDA cores read
+// tile t-1's result out of the other (bias, SiLU, stores), so the MMAs leave the critical
+// path.  Every wait on an mbarrier is bounded (kTcWaitNs); a wait that runs out sets *err,
+// and the kernel releases its TMEM and returns.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -36,7 +39,9 @@ constexpr int kTcQuarters = kTcThreads / kTcRows;            // column quarters 
 constexpr uint32_t kTcTileBytes = kTcRows * kHid * 2;         // 64 KB of BF16 activations
 constexpr uint32_t kTcWBytes = kHid * kHid * 2;               // 128 KB: one BF16 weight matrix
 constexpr uint32_t kTcLbo = 128, kTcSbo = (kHid / 8) * 128;   // core-matrix strides (k, rows)
-constexpr uint32_t kTcCols = 256;                             // TMEM columns (FP32 256-wide accumulator)
+constexpr uint32_t kTcAcc = 256;                              // TMEM columns of one FP32 256-wide accumulator
+constexpr uint32_t kTcCols = 2 * kTcAcc;                      // two accumulators: a tile's MMAs overlap the
+                                                              // previous tile's epilogue
 constexpr unsigned long long kTcWaitNs = 2000000000ull;       // 2 s
 
 // Byte offset of element (row, k) of a [rows][256] BF16 operand in the layout above.
@@ -251,67 +256,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
     bool w_pending = true;
     uint32_t mphase = 0;
     const int row = tid & (kTcRows - 1), quarter = tid >> 7;   // layer 1: (row, column quarter)
-    const int er = 32 * (warp & 3) + lane, c0 = 64 * (warp >> 2);  // epilogue: TMEM lane, columns
-    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        // layer 1 (FP32): z1 = W1 x_n + b1, h1 = silu(z1) as BF16 into the A operand
-        const long long m = t * kTcRows + row;
-        float xn[kIn];
+    const int er = 32 * (warp & 3) + lane, c0 = 64 * quarter;  // epilogue: TMEM lane, columns
+    // Iteration k: wait for tile k-1's MMAs (they have read the A tile), layer 1 of tile k into
+    // the A tile, tile k's MMAs into accumulator k % 2, then tile k-1's epilogue from the other
+    // accumulator while those MMAs run.  The loop runs one extra iteration for the last
+    // epilogue.
+    long long prev = -1;  // the tile whose MMAs the previous iteration issued
+    uint32_t buf = 0;     // accumulator of this iteration's tile
+    for (long long t = blockIdx.x;; t += gridDim.x) {
+        const bool have = t < n_tiles;
+        if (prev >= 0) {
+            if (!tc_mbar_wait(&ctl->mbar, mphase)) ctl->abort = 1;
+            mphase ^= 1u;
+            __syncthreads();
+            if (ctl->abort) break;
+            tc_fence_after();
+        }
+        if (have) {
+            // layer 1 (FP32): z1 = W1 x_n + b1, h1 = silu(z1) as BF16 into the A operand
+            const long long m = t * kTcRows + row;
+            float xn[kIn];
 #pragma unroll
-        for (int c = 0; c < kIn; ++c) xn[c] = m < n ? (x[m * kIn + c] - snorm[4 + c]) * snorm[c] : 0.f;
+            for (int c = 0; c < kIn; ++c) xn[c] = m < n ? (x[m * kIn + c] - snorm[4 + c]) * snorm[c] : 0.f;
 #pragma unroll 2
-        for (int j0 = quarter * 64; j0 < quarter * 64 + 64; j0 += 8) {
-            uint32_t pk[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                float z[2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int j = j0 + 2 * u + q;
-                    float acc = sb1[j];
-#pragma unroll
-                    for (int c = 0; c < kIn; ++c) acc += sw1[j * kIn + c] * xn[c];
-                    z[q] = silu(acc);
-                }
-                pk[u] = tc_pack_bf16(z[0], z[1]);
-            }
-            *reinterpret_cast<uint4*>(sA + tc_off(row, j0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
-        tc_fence_proxy();
-        tc_sync();
-        // layer 2 on the tensor cores
-        if (tid == 0) {
-            if (w_pending) {
-                if (!tc_mbar_wait(&ctl->wbar, 0)) ctl->abort = 1;
-                w_pending = false;
-            }
-            if (!ctl->abort) tc_issue_layer(tmem, sA, sW, &ctl->mbar);
-        }
-        __syncthreads();
-        if (ctl->abort) break;
-        if (!tc_mbar_wait(&ctl->mbar, mphase)) ctl->abort = 1;
-        mphase ^= 1u;
-        __syncthreads();
-        if (ctl->abort) break;
-        tc_fence_after();
-        // bias + SiLU from TMEM -> BF16 h2 in the operand layout
-        uint8_t* dst = reinterpret_cast<uint8_t*>(h2) + (size_t)t * kTcTileBytes;
-#pragma unroll 1
-        for (int cc = 0; cc < 2; ++cc) {
-            uint32_t v[32];
-            tc_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * cc), v);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int j0 = quarter * 64; j0 < quarter * 64 + 64; j0 += 8) {
                 uint32_t pk[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int col = c0 + 32 * cc + 8 * u + 2 * q;
-                    pk[q] = tc_pack_bf16(silu(__uint_as_float(v[8 * u + 2 * q]) + sb2[col]),
-                                         silu(__uint_as_float(v[8 * u + 2 * q + 1]) + sb2[col + 1]));
+                for (int u = 0; u < 4; ++u) {
+                    float z[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int j = j0 + 2 * u + q;
+                        float acc = sb1[j];
+#pragma unroll
+                        for (int c = 0; c < kIn; ++c) acc += sw1[j * kIn + c] * xn[c];
+                        z[q] = silu(acc);
+                    }
+                    pk[u] = tc_pack_bf16(z[0], z[1]);
                 }
-                *reinterpret_cast<uint4*>(dst + tc_off(er, c0 + 32 * cc + 8 * u)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(sA + tc_off(row, j0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
+            tc_fence_proxy();
+            tc_sync();
+            // layer 2 on the tensor cores
+            if (tid == 0) {
+                if (w_pending) {
+                    if (!tc_mbar_wait(&ctl->wbar, 0)) ctl->abort = 1;
+                    w_pending = false;
+                }
+                if (!ctl->abort) tc_issue_layer(tmem + kTcAcc * buf, sA, sW, &ctl->mbar);
+            }
+            __syncthreads();
+            if (ctl->abort) break;
         }
-        tc_sync();
+        if (prev >= 0) {
+            // bias + SiLU of tile prev from the other accumulator -> BF16 h2 in the operand layout
+            uint8_t* dst = reinterpret_cast<uint8_t*>(h2) + (size_t)prev * kTcTileBytes;
+            const uint32_t acc = tmem + kTcAcc * (buf ^ 1u) + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+            for (int cc = 0; cc < 2; ++cc) {
+                uint32_t v[32];
+                tc_ld32(acc + (uint32_t)(c0 + 32 * cc), v);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int col = c0 + 32 * cc + 8 * u + 2 * q;
+                        pk[q] = tc_pack_bf16(silu(__uint_as_float(v[8 * u + 2 * q]) + sb2[col]),
+                                             silu(__uint_as_float(v[8 * u + 2 * q + 1]) + sb2[col + 1]));
+                    }
+                    *reinterpret_cast<uint4*>(dst + tc_off(er, c0 + 32 * cc + 8 * u)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+            }
+            // every read of this accumulator is done before the MMAs two tiles on overwrite it
+            tc_sync();
+        }
+        if (!have) break;
+        prev = t;
+        buf ^= 1u;
     }
     tc_teardown(ctl, w_pending, err);
 }
@@ -350,8 +373,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
     bool w_pending = true, a_pending = blockIdx.x < n_tiles;
     uint32_t mphase = 0, aphase = 0;
     const int er = 32 * (warp & 3) + lane, quarter = warp >> 2, c0 = 64 * quarter;
+    // Tile t's MMAs write accumulator buf; the next tile's activations are fetched as soon as
+    // they have read the A tile, and its MMAs (into the other accumulator) are issued once the
+    // copy has landed, before this tile's cross-quarter reduction: they run while this tile's
+    // epilogue finishes and the next one starts.  The first tile's MMAs are issued here.
+    uint32_t buf = 0;
     for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        if (tid == 0) {
+        const bool has_next = t + gridDim.x < n_tiles;
+        if (tid == 0 && t == blockIdx.x) {
             if (w_pending) {
                 if (!tc_mbar_wait(&ctl->wbar, 0)) ctl->abort = 1;
                 w_pending = false;
@@ -361,7 +390,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
             aphase ^= 1u;
             if (!ctl->abort) {
                 tc_fence_after();
-                tc_issue_layer(tmem, sA, sW, &ctl->mbar);
+                tc_issue_layer(tmem + kTcAcc * buf, sA, sW, &ctl->mbar);
             }
         }
         __syncthreads();
@@ -372,7 +401,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
         if (ctl->abort) break;
         tc_fence_after();
         // the MMAs have read the tile: fetch the next one while this one's epilogue runs
-        if (tid == 0 && t + gridDim.x < n_tiles) {
+        if (tid == 0 && has_next) {
             tc_mbar_expect_tx(&ctl->abar, kTcTileBytes);
             tc_bulk_g2s(sA, reinterpret_cast<const uint8_t*>(h2) + (size_t)(t + gridDim.x) * kTcTileBytes, kTcTileBytes, &ctl->abar);
             a_pending = true;
@@ -384,13 +413,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
 #pragma unroll 1
         for (int cc = 0; cc < 2; ++cc) {
             uint32_t v[32];
-            tc_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * cc), v);
+            tc_ld32(tmem + kTcAcc * buf + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 32 * cc), v);
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int col = c0 + 32 * cc + q;
                 const float h = __bfloat162float(__float2bfloat16(silu(__uint_as_float(v[q]) + sb3[col])));
 #pragma unroll
                 for (int o = 0; o < NOUT; ++o) acc[o] += sw4[o * kHid + col] * h;
+            }
+        }
+        // the next tile's MMAs into the other accumulator (its last reads ended with the
+        // previous tile's reduction barriers)
+        if (tid == 0 && has_next && !ctl->abort) {
+            if (!tc_mbar_wait(&ctl->abar, aphase)) ctl->abort = 1;
+            a_pending = false;
+            aphase ^= 1u;
+            if (!ctl->abort) {
+                tc_fence_after();
+                tc_issue_layer(tmem + kTcAcc * (buf ^ 1u), sA, sW, &ctl->mbar);
             }
         }
 #pragma unroll
@@ -420,6 +460,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
             }
             tc_sync();
         }
+        buf ^= 1u;
     }
     // an activation copy issued for a tile this CTA will not process cannot exist (the next
     // tile is fetched only if it is processed), but an aborted loop may leave one in flight
