@@ -187,11 +187,11 @@ __global__ void k_tc_pack(const float* __restrict__ P, __nv_bfloat16* __restrict
 }
 
 // Shared-memory plan of the two kernels (after aligning the dynamic base to 1024 B).
-// Output layer of NOUT outputs: its FP32 weights and biases, and the partial sums of column
-// quarters 1-3 for 8 outputs at a time ([3][128][8]; NOUT / 8 rounds).
+// Output layer of NOUT outputs: its FP32 weights and biases, and the partial sums of the
+// four column quarters for 8 outputs at a time ([4][128][8]; NOUT / 8 rounds).
 constexpr uint32_t kTc12Params = (kHid * kIn + 2 * kHid + 8) * 4;          // w1, b1, b2, norm
 template <int NOUT>
-constexpr uint32_t tc34_params() { return (kHid + NOUT * kHid + NOUT + (kTcQuarters - 1) * kTcRows * 8) * 4; }
+constexpr uint32_t tc34_params() { return (kHid + NOUT * kHid + NOUT + kTcQuarters * kTcRows * 8) * 4; }
 constexpr uint32_t kTc34Params = tc34_params<kOut>();  // b3, w4, b4, partial sums
 constexpr uint32_t kTc12Smem = 1024 + kTcWBytes + kTcTileBytes + kTc12Params + sizeof(TcCtl);
 template <int NOUT>
@@ -263,6 +263,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
     // epilogue.
     long long prev = -1;  // the tile whose MMAs the previous iteration issued
     uint32_t buf = 0;     // accumulator of this iteration's tile
+    // raw inputs of this thread's row in the next tile, loaded a tile ahead (their latency
+    // hides behind the epilogue)
+    float xr[kIn];
+    auto load_inputs = [&](long long tt) {
+        const long long m = tt * kTcRows + row;
+#pragma unroll
+        for (int c = 0; c < kIn; ++c) xr[c] = (tt < n_tiles && m < n) ? x[m * kIn + c] : 0.f;
+    };
+    load_inputs(blockIdx.x);
     for (long long t = blockIdx.x;; t += gridDim.x) {
         const bool have = t < n_tiles;
         if (prev >= 0) {
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
             const long long m = t * kTcRows + row;
             float xn[kIn];
 #pragma unroll
-            for (int c = 0; c < kIn; ++c) xn[c] = m < n ? (x[m * kIn + c] - snorm[4 + c]) * snorm[c] : 0.f;
+            for (int c = 0; c < kIn; ++c) xn[c] = m < n ? (xr[c] - snorm[4 + c]) * snorm[c] : 0.f;
 #pragma unroll 2
             for (int j0 = quarter * 64; j0 < quarter * 64 + 64; j0 += 8) {
                 uint32_t pk[4];
@@ -306,6 +315,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
                 }
                 if (!ctl->abort) tc_issue_layer(tmem + kTcAcc * buf, sA, sW, &ctl->mbar);
             }
+            load_inputs(t + gridDim.x);
             __syncthreads();
             if (ctl->abort) break;
         }
@@ -350,8 +360,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
     float* sb3 = reinterpret_cast<float*>(sA + kTcTileBytes);
     float* sw4 = sb3 + kHid;
     float* sb4 = sw4 + NOUT * kHid;
-    float* sred = sb4 + NOUT;   // [3][128][8] partial sums of column quarters 1-3, 8 outputs a round
-    TcCtl* ctl = reinterpret_cast<TcCtl*>(sred + (kTcQuarters - 1) * kTcRows * 8);
+    float* sred = sb4 + NOUT;   // [4][128][8] partial sums of the column quarters, 8 outputs a round
+    TcCtl* ctl = reinterpret_cast<TcCtl*>(sred + kTcQuarters * kTcRows * 8);
     static_assert(NOUT % 8 == 0, "outputs are reduced 8 at a time");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long n_tiles = (n + kTcRows - 1) / kTcRows;
@@ -433,30 +443,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
                 tc_issue_layer(tmem + kTcAcc * (buf ^ 1u), sA, sW, &ctl->mbar);
             }
         }
+        // the row's sum over the four quarters, 8 outputs a round: every quarter writes its
+        // partial sums, then each thread adds up two of the 8 outputs (quarter order 0-3) and
+        // stores them with their biases
 #pragma unroll
         for (int g = 0; g < NOUT; g += 8) {
-            if (quarter > 0) {
-                float4* r4 = reinterpret_cast<float4*>(sred + ((quarter - 1) * kTcRows + er) * 8);
-                r4[0] = make_float4(acc[g + 0], acc[g + 1], acc[g + 2], acc[g + 3]);
-                r4[1] = make_float4(acc[g + 4], acc[g + 5], acc[g + 6], acc[g + 7]);
-            }
+            float4* w4 = reinterpret_cast<float4*>(sred + (quarter * kTcRows + er) * 8);
+            w4[0] = make_float4(acc[g + 0], acc[g + 1], acc[g + 2], acc[g + 3]);
+            w4[1] = make_float4(acc[g + 4], acc[g + 5], acc[g + 6], acc[g + 7]);
             tc_sync();
-            if (quarter == 0) {
-                const long long m = t * kTcRows + er;
-                if (m < n) {
+            const long long m = t * kTcRows + er;
+            if (m < n) {
+                const int o = 2 * quarter;
+                float2 r = *reinterpret_cast<const float2*>(sred + er * 8 + o);
 #pragma unroll
-                    for (int qq = 1; qq < kTcQuarters; ++qq) {
-                        const float4* r4 = reinterpret_cast<const float4*>(sred + ((qq - 1) * kTcRows + er) * 8);
-                        const float4 p0 = r4[0], p1 = r4[1];
-                        acc[g + 0] += p0.x; acc[g + 1] += p0.y; acc[g + 2] += p0.z; acc[g + 3] += p0.w;
-                        acc[g + 4] += p1.x; acc[g + 5] += p1.y; acc[g + 6] += p1.z; acc[g + 7] += p1.w;
-                    }
-                    float4* o4 = reinterpret_cast<float4*>(out + m * NOUT + g);
-                    o4[0] = make_float4(acc[g + 0] + sb4[g + 0], acc[g + 1] + sb4[g + 1], acc[g + 2] + sb4[g + 2],
-                                        acc[g + 3] + sb4[g + 3]);
-                    o4[1] = make_float4(acc[g + 4] + sb4[g + 4], acc[g + 5] + sb4[g + 5], acc[g + 6] + sb4[g + 6],
-                                        acc[g + 7] + sb4[g + 7]);
+                for (int qq = 1; qq < kTcQuarters; ++qq) {
+                    const float2 pq = *reinterpret_cast<const float2*>(sred + (qq * kTcRows + er) * 8 + o);
+                    r.x += pq.x;
+                    r.y += pq.y;
                 }
+                *reinterpret_cast<float2*>(out + m * NOUT + g + o) = make_float2(r.x + sb4[g + o], r.y + sb4[g + o + 1]);
             }
             tc_sync();
         }
