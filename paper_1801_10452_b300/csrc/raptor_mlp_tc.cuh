@@ -9,7 +9,8 @@
 //               bias + SiLU read back from TMEM, BF16 h2 stored to global memory in the
 //               operand layout (one contiguous 64 KB block per 128-row tile);
 //   k_mlp_tc34: h2 tile loaded by one bulk copy, layer 3 by tcgen05.mma, bias + SiLU from
-//               TMEM, and the 256 -> 8 output layer in FP32 on the CUDA cores.
+//               TMEM, and the 256 -> NOUT output layer in FP32 on the CUDA cores (8 outputs
+//               for the state network, 16 for the crossing network).
 // The arithmetic is that of the training forward pass (raptor_surrogate.cuh): BF16
 // activations and weights, FP32 accumulation, FP32 thin layers, SiLU.
 //
