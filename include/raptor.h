@@ -286,13 +286,15 @@ raptor_status raptor_stats_ex(raptor_ctx* ctx, unsigned long long* values, int c
 raptor_status raptor_set_launch(raptor_ctx* ctx, int threads_per_block, int blocks_per_sm, int blocks_per_sm_fp64);
 
 /* Mixed path scheduling: rays whose pixel centre lies within crit_band M of the critical
- * curve (Bardeen's closed form) form phase A1 and run their FP64 phase on a second stream,
- * concurrently with the other rays' phases A2, B and C [0.5].  The other rays' FP64 phase
+ * curve (Bardeen's closed form) form phase A1 and run their FP64 phase, then their outbound
+ * FP32 phase, on a second stream, concurrently with the other rays' phases A2, B and C
+ * [0.5].  The other rays' FP64 phase
  * runs in n_passes passes (1..8): pass k continues each ray for at most budgets[k] steps
  * and re-queues the unfinished ones for pass k + 1; the last pass has no limit (budgets may
  * be NULL: the default schedule).  With tail_split = K in 1 .. n_passes - 1, the rays still
  * in the FP64 region after K passes finish their FP64 phase on the second stream (after the
- * near-critical rays), while the first stream goes on with phase C [0: no split].  Only the
+ * near-critical rays, and with them their outbound phase), while the first stream goes on
+ * with phase C [0: no split].  Only the
  * schedule changes: every ray's arithmetic, and so every result, is the same for any
  * setting.  RAPTOR_EINVAL for a negative or non-finite band, n_passes outside 1..8, a
  * budget < 1 or a negative tail_split. */
