@@ -216,10 +216,12 @@ __device__ __forceinline__ void tc_prologue(TcCtl* ctl) {
     }
 }
 
-// Common epilogue: every bulk copy into this CTA's shared memory has landed (bounded
-// wait), then TMEM is released.
-__device__ __forceinline__ void tc_teardown(TcCtl* ctl, bool w_pending, int* err) {
+// Common epilogue: every bulk copy into this CTA's shared memory has landed and the MMAs
+// last issued have completed (bounded waits; they are outstanding only after an aborted
+// loop), then TMEM is released.
+__device__ __forceinline__ void tc_teardown(TcCtl* ctl, bool w_pending, bool m_out, uint32_t m_phase, int* err) {
     if (threadIdx.x == 0 && w_pending && !tc_mbar_wait(&ctl->wbar, 0)) ctl->abort = 1;
+    if (threadIdx.x == 0 && m_out && !tc_mbar_wait(&ctl->mbar, m_phase)) ctl->abort = 1;
     tc_sync();
     if ((threadIdx.x >> 5) == 0) tc_tmem_free(ctl->tmem, kTcCols);
     if (threadIdx.x == 0 && ctl->abort) atomicExch(err, 1);
@@ -256,6 +258,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
     }
     bool w_pending = true;
     uint32_t mphase = 0;
+    bool m_out = false;   // thread 0: MMAs issued whose completion no wait has seen yet,
+    uint32_t m_phase = 0;  // and the barrier phase their commit completes
     const int row = tid & (kTcRows - 1), quarter = tid >> 7;   // layer 1: (row, column quarter)
     const int er = 32 * (warp & 3) + lane, c0 = 64 * quarter;  // epilogue: TMEM lane, columns
     // Iteration k: wait for tile k-1's MMAs (they have read the A tile), layer 1 of tile k into
@@ -276,7 +280,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
     for (long long t = blockIdx.x;; t += gridDim.x) {
         const bool have = t < n_tiles;
         if (prev >= 0) {
-            if (!tc_mbar_wait(&ctl->mbar, mphase)) ctl->abort = 1;
+            if (tc_mbar_wait(&ctl->mbar, mphase)) m_out = false;
+            else ctl->abort = 1;
             mphase ^= 1u;
             __syncthreads();
             if (ctl->abort) break;
@@ -311,10 +316,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
             // layer 2 on the tensor cores
             if (tid == 0) {
                 if (w_pending) {
-                    if (!tc_mbar_wait(&ctl->wbar, 0)) ctl->abort = 1;
-                    w_pending = false;
+                    if (tc_mbar_wait(&ctl->wbar, 0)) w_pending = false;
+                    else ctl->abort = 1;
                 }
-                if (!ctl->abort) tc_issue_layer(tmem + kTcAcc * buf, sA, sW, &ctl->mbar);
+                if (!ctl->abort) {
+                    tc_issue_layer(tmem + kTcAcc * buf, sA, sW, &ctl->mbar);
+                    m_out = true;
+                    m_phase = mphase;
+                }
             }
             load_inputs(t + gridDim.x);
             __syncthreads();
@@ -347,7 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
         prev = t;
         buf ^= 1u;
     }
-    tc_teardown(ctl, w_pending, err);
+    tc_teardown(ctl, w_pending, m_out, m_phase, err);
 }
 
 // Layers 3 and 4.  h2 as written by k_mlp_tc12; out: [n][NOUT] normalised outputs.
@@ -383,6 +392,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
     }
     bool w_pending = true, a_pending = blockIdx.x < n_tiles;
     uint32_t mphase = 0, aphase = 0;
+    bool m_out = false;    // thread 0: MMAs issued whose completion no wait has seen yet,
+    uint32_t m_phase = 0;  // and the barrier phase their commit completes
     const int er = 32 * (warp & 3) + lane, quarter = warp >> 2, c0 = 64 * quarter;
     // Tile t's MMAs write accumulator buf; the next tile's activations are fetched as soon as
     // they have read the A tile, and its MMAs (into the other accumulator) are issued once the
@@ -393,20 +404,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
         const bool has_next = t + gridDim.x < n_tiles;
         if (tid == 0 && t == blockIdx.x) {
             if (w_pending) {
-                if (!tc_mbar_wait(&ctl->wbar, 0)) ctl->abort = 1;
-                w_pending = false;
+                if (tc_mbar_wait(&ctl->wbar, 0)) w_pending = false;
+                else ctl->abort = 1;
             }
-            if (!ctl->abort && !tc_mbar_wait(&ctl->abar, aphase)) ctl->abort = 1;
-            a_pending = false;
-            aphase ^= 1u;
+            if (!ctl->abort) {
+                if (tc_mbar_wait(&ctl->abar, aphase)) {
+                    a_pending = false;
+                    aphase ^= 1u;
+                } else {
+                    ctl->abort = 1;
+                }
+            }
             if (!ctl->abort) {
                 tc_fence_after();
                 tc_issue_layer(tmem + kTcAcc * buf, sA, sW, &ctl->mbar);
+                m_out = true;
+                m_phase = mphase;
             }
         }
         __syncthreads();
         if (ctl->abort) break;
-        if (!tc_mbar_wait(&ctl->mbar, mphase)) ctl->abort = 1;
+        if (tc_mbar_wait(&ctl->mbar, mphase)) m_out = false;
+        else ctl->abort = 1;
         mphase ^= 1u;
         __syncthreads();
         if (ctl->abort) break;
@@ -436,12 +455,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
         // the next tile's MMAs into the other accumulator (its last reads ended with the
         // previous tile's reduction barriers)
         if (tid == 0 && has_next && !ctl->abort) {
-            if (!tc_mbar_wait(&ctl->abar, aphase)) ctl->abort = 1;
-            a_pending = false;
-            aphase ^= 1u;
-            if (!ctl->abort) {
+            if (tc_mbar_wait(&ctl->abar, aphase)) {
+                a_pending = false;
+                aphase ^= 1u;
                 tc_fence_after();
                 tc_issue_layer(tmem + kTcAcc * (buf ^ 1u), sA, sW, &ctl->mbar);
+                m_out = true;
+                m_phase = mphase;
+            } else {
+                ctl->abort = 1;
             }
         }
         // the row's sum over the four quarters, 8 outputs a round: every quarter writes its
@@ -472,7 +494,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
     // an activation copy issued for a tile this CTA will not process cannot exist (the next
     // tile is fetched only if it is processed), but an aborted loop may leave one in flight
     if (tid == 0 && a_pending && !tc_mbar_wait(&ctl->abar, aphase)) ctl->abort = 1;
-    tc_teardown(ctl, w_pending, err);
+    tc_teardown(ctl, w_pending, m_out, m_phase, err);
 }
 
 }  // namespace raptor
