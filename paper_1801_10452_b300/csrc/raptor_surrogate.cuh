@@ -704,10 +704,12 @@ __global__ void __launch_bounds__(256) k_surrogate_prepare(const Params p, const
 // camera time and the pixel centres).
 __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, const float* __restrict__ out,
                                    float2* __restrict__ start_xk) {
-    double xc[4];  // camera position at t_cam = 0 (the same for every pixel)
-    camera_x_ai(p.a, p.incl, p.r_cam, 0.0, xc);
+    // the camera's KS time at t_cam = 0 and azimuth, the same for every pixel: the render's
+    // terms of camera_x_ai, computed once on the host (per thread they would cost two FP64
+    // logarithms and square roots each)
+    const double xc0 = p.cam_logdel + p.cam_tterm;
     const float af = p.f.a, sif = (float)p.sin_i, cif = (float)p.cos_i, incf = (float)p.incl, rcf = (float)p.r_cam;
-    const float ph0 = (float)xc[3];
+    const float ph0 = (float)p.cam_phi;
     float mu[kOutUsed], sd[kOutUsed];
 #pragma unroll
     for (int q = 0; q < kOutUsed; ++q) {
@@ -731,7 +733,7 @@ __global__ void k_surrogate_states(const Params p, const float* __restrict__ P, 
         float x[4], k[4];
         surrogate_state(af, sif, cif, al, be, pred, x, k);
         const double tc = p.t_frames ? p.t_frames[frame] : p.t_cam;
-        const double t = tc + xc[0] + (double)x[0];
+        const double t = tc + xc0 + (double)x[0];
         const float th = (float)t;
         start_xk[id] = make_float2(th, (float)(t - (double)th));
 #pragma unroll
