@@ -45,7 +45,7 @@ typedef enum {
     RAPTOR_ETIMEOUT = 4,     /* a bounded device-side wait of the tensor-core kernels
                                 expired; the context stays usable                         */
     RAPTOR_ENOPLASMA = 5,    /* render before raptor_load_plasma                          */
-    RAPTOR_EUNSUPPORTED = 6  /* option recognised but not available in this build         */
+    RAPTOR_EUNSUPPORTED = 6  /* option recognised but not available in this library       */
 } raptor_status;
 
 /* Returned by the learned-surrogate calls (RAPTOR_MIXED_MLP) before a surrogate exists. */
@@ -329,7 +329,7 @@ raptor_status raptor_graph_stats(raptor_ctx* ctx, long long* captures, long long
 raptor_status raptor_autotune(raptor_ctx* ctx, const double* freqs_hz, int n_freq, double t_obs, int* best_block,
                               int* best_bps, int* best_bps64, double* best_ms, void* stream);
 
-/* ---- Learned surrogate (the benchmark spec's learned part; the paper has none) -------------------
+/* ---- Learned surrogate (a learned map of the integration; the paper has none) ------------
  * A 4-layer, 256-wide MLP maps (alpha, beta, a, i) to the FP64 integrator's state after 60
  * adaptive RK4 steps from the camera (t - t_cam, ln r, theta, phi and the signs of k^theta,
  * k^r; the wave vector is rebuilt from E, L, Q).  Training data come from the integrator
