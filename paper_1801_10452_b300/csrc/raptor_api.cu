@@ -700,7 +700,7 @@ raptor_status run_rays_graph(raptor_ctx* ctx, const Params& p, const double* fre
                              int n_frames, cudaStream_t s) {
     // Graph replay saves the launch latencies, which matter up to ~2^19 rays per call
     // (measured 3-5 % at 64^2 .. 512^2); beyond, the graph's own ordering of the two streams'
-    // kernels overlaps them worse than direct launches do (measured 7-10 % slower at 1024^2).
+    // kernels overlaps them worse than direct launches do (measured 2-7 % slower at 1024^2).
     if (!ctx->graphs || ctx->prof || p.n_rays > kGraphMaxRays) return run_rays(ctx, p, freqs, n_freq, planes_per_frame, n_frames, s);
     std::vector<unsigned char> key;
     auto put = [&key](const void* v, size_t n) {
