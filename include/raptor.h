@@ -518,8 +518,8 @@ raptor_status raptor_disk_render_learned(raptor_ctx* ctx, const raptor_disk_desc
  * recording; raptor_profile(ctx, 0) stops.  raptor_profile_read waits for the recorded
  * events and returns, per kernel slot RAPTOR_KERNEL_* (13 slots), the summed milliseconds
  * (ms[13], may be NULL) and the number of launches since the last clear (launches[13],
- * may be NULL; counted whether or not recording is on).  A slot covers all the kernels of
- * one stage (e.g. the surrogate slot times its inference as one interval). */
+ * may be NULL; counted whether or not recording is on).  A scope times its kernels as one
+ * interval (e.g. the network's two tensor-core kernels in RAPTOR_KERNEL_SURROGATE_MLP). */
 #define RAPTOR_KERNEL_RENDER_FP64 0  /* persistent FP64 ray kernel                         */
 #define RAPTOR_KERNEL_MIXED_A 1      /* mixed: FP32 phase on camera rays                   */
 #define RAPTOR_KERNEL_MIXED_B 2      /* mixed: FP64 phase (inner region, turning points) of
@@ -529,10 +529,10 @@ raptor_status raptor_disk_render_learned(raptor_ctx* ctx, const raptor_disk_desc
 #define RAPTOR_KERNEL_TRACE 5        /* single-ray trace                                   */
 #define RAPTOR_KERNEL_LOAD 6         /* grid interleave at load time                       */
 #define RAPTOR_KERNEL_PEAK 7         /* unused by the renders                              */
-#define RAPTOR_KERNEL_SURROGATE 8    /* surrogate stage of a render (interval includes the  */
-                                     /* network; launches count its own two kernels)       */
+#define RAPTOR_KERNEL_SURROGATE 8    /* surrogate stage of a render without the network:   */
+                                     /* inputs and fallback flags, start states (two scopes) */
 #define RAPTOR_KERNEL_TRAIN 9        /* surrogate data generation and training             */
-#define RAPTOR_KERNEL_SURROGATE_MLP 10 /* the network inside RAPTOR_KERNEL_SURROGATE        */
+#define RAPTOR_KERNEL_SURROGATE_MLP 10 /* the network of the surrogate stage               */
 #define RAPTOR_KERNEL_DISK 11        /* thin-disk rays and their spectrum                  */
 #define RAPTOR_KERNEL_MIXED_B_LONG 12 /* mixed: FP64 phase of the near-critical rays (second
                                         stream); RAPTOR_KERNEL_MIXED_B has the other rays'  */

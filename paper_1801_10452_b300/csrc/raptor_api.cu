@@ -55,7 +55,7 @@ struct raptor_ctx {
     int* d_crit = nullptr;        // mixed path: near-critical ray ids (phase A1)
     int* d_rest = nullptr;        // mixed path: the other ray ids (phase A2)
     cudaStream_t s_long = nullptr;  // second stream of the mixed path (B-long)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr, ev_net = nullptr;
     int tail_split = 0;           // after this many FP64 passes the rest moves to B-tail (0: never)
     int long_block = 0;           // threads per block of the second stream's FP64 passes (0: launch_block)
     int long_passes = 1;          // near-critical rays' FP64 passes and their step budgets
@@ -451,7 +451,8 @@ cudaError_t launch_fp64_phase(raptor_ctx* c, const Params& p, const PhaseIO& io,
     return cudaGetLastError();
 }
 
-cudaError_t surrogate_stage(raptor_ctx* ctx, const Params& p, cudaStream_t s);
+cudaError_t surrogate_prepare(raptor_ctx* ctx, const Params& p, cudaStream_t s);
+cudaError_t surrogate_infer(raptor_ctx* ctx, const Params& p, cudaStream_t s);
 
 // One frequency chunk of a mixed render.  sur_stage: run the surrogate's inference first
 // (the first chunk of a learned render).
@@ -467,7 +468,7 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_long, cudaStreamNonBlocking, hi);
     }
-    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join, &c->ev_tail};
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join, &c->ev_tail, &c->ev_net};
     for (cudaEvent_t* ev : evs)
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
@@ -492,9 +493,15 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool
     // blocks return their registers to the SM as soon as their warps are done
     const int long_threads = c->long_block > 0 ? c->long_block : c->launch_block;
     const int b_long = (int)(((long long)b64 * c->launch_block + long_threads - 1) / long_threads);
-    // the surrogate's inference (first frequency chunk of a learned render)
+    // the surrogate's stage (first frequency chunk of a learned render).  When every
+    // near-critical ray is a fallback ray (critical band <= fallback band: the same FP32
+    // predicate), those rays start at the camera and need nothing from the network: A1 runs
+    // on the second stream beside the network's kernels, and B-long still waits for the
+    // start states, so that it starts beside A2 as it does otherwise.
+    const bool early = sur_stage && c->crit_band <= c->s_band;
     if (sur_stage) {
-        e = surrogate_stage(c, p, s);
+        e = surrogate_prepare(c, p, s);
+        if (e == cudaSuccess && !early) e = surrogate_infer(c, p, s);
         if (e != cudaSuccess) return e;
     }
     // near-critical / other split
@@ -515,16 +522,32 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool
     a1.push_cnt = kCntPush64C;
     a1.push_top = kCntListCrit;
     a1.requeue_cnt = -1;
-    {
-        ProfScope ps(c, kProfMixedA, s);
-        k_mixed_fp32<NF><<<bA, c->launch_block, 0, s>>>(p, a1, mq.cap, cnt, c->d_stats);
+    if (early) {
+        e = cudaEventRecord(c->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_fork, 0);
+        if (e != cudaSuccess) return e;
+        {
+            ProfScope ps(c, kProfMixedA, c->s_long);
+            k_mixed_fp32<NF><<<bA, c->launch_block, 0, c->s_long>>>(p, a1, mq.cap, cnt, c->d_stats);
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = surrogate_infer(c, p, s);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_net, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_net, 0);
+        if (e != cudaSuccess) return e;
+    } else {
+        {
+            ProfScope ps(c, kProfMixedA, s);
+            k_mixed_fp32<NF><<<bA, c->launch_block, 0, s>>>(p, a1, mq.cap, cnt, c->d_stats);
+        }
+        e = cudaGetLastError();
+        // fork: the near-critical rays' FP64 phase on the second stream
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_fork, 0);
+        if (e != cudaSuccess) return e;
     }
-    e = cudaGetLastError();
-    // fork: the near-critical rays' FP64 phase on the second stream, in passes like the
-    // other rays' (each pass re-packs the unfinished rays into full warps)
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_fork, 0);
-    if (e != cudaSuccess) return e;
+    // the near-critical rays' FP64 phase on the second stream, in passes like the other
+    // rays' (each pass re-packs the unfinished rays into full warps)
     const int LK = c->long_passes;
     for (int pass = 0; pass < LK; ++pass) {
         PhaseIO bl{};
@@ -1216,7 +1239,7 @@ void raptor_destroy(raptor_ctx* ctx) {
     cudaFree(ctx->d_trace_I);
     cudaFree(ctx->d_rec);
     free_mixed_queues(ctx->mq);
-    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_tail};
+    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_tail, ctx->ev_net};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
     if (ctx->g_exec) cudaGraphExecDestroy(ctx->g_exec);
@@ -1767,7 +1790,8 @@ raptor_status raptor_surrogate_config(raptor_ctx* ctx, double fallback_band, dou
 namespace {
 
 // RAPTOR_MIXED_MLP: predicted start states for every non-fallback ray, then the mixed path.
-// Buffers and launch parameters of a learned render (the kernels run in surrogate_stage).
+// Buffers and launch parameters of a learned render (the kernels run in surrogate_prepare and
+// surrogate_infer).
 raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t s) {
     if (!ctx->sur_ready) return fail(ctx, RAPTOR_EUNSUPPORTED, "RAPTOR_MIXED_MLP needs a trained or loaded surrogate");
     RCK(sur_alloc(ctx));
@@ -1795,30 +1819,33 @@ raptor_status prepare_surrogate_render(raptor_ctx* ctx, Params& p, cudaStream_t 
     return RAPTOR_OK;
 }
 
-// The surrogate's part of a learned render on stream s: network inputs and fallback flags,
-// inference, start states.
-cudaError_t surrogate_stage(raptor_ctx* ctx, const Params& p, cudaStream_t s) {
+// The surrogate's part of a learned render on stream s, as two launch sequences:
+// surrogate_prepare writes the network inputs and the fallback flags; surrogate_infer runs
+// the network and rebuilds the start states.
+cudaError_t surrogate_prepare(raptor_ctx* ctx, const Params& p, cudaStream_t s) {
     const size_t rays = (size_t)p.n_rays;
-    const int nc = ctx->n_curve;
     const float grow = (float)ctx->s_band + 1e-3f;
     const float4 box = make_float4(ctx->curve_box.x - grow, ctx->curve_box.y + grow, ctx->curve_box.z - grow,
                                    ctx->curve_box.w + grow);
+    ProfScope ps(ctx, kProfSurrogate, s);
+    k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->d_curve, ctx->n_curve, (float)ctx->s_band, box,
+                                                                   ctx->s_in, ctx->s_fb, ctx->d_stats + kStatFallback);
+    return cudaGetLastError();
+}
+
+cudaError_t surrogate_infer(raptor_ctx* ctx, const Params& p, cudaStream_t s) {
+    const size_t rays = (size_t)p.n_rays;
     float* out = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&out, rays * kOut * sizeof(float), s);
     if (e != cudaSuccess) return e;
     {
-        ProfScope ps(ctx, kProfSurrogate, s, 2);  // inputs and start states; the network nests below
-        k_surrogate_prepare<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->d_curve, nc, (float)ctx->s_band, box,
-                                                                       ctx->s_in, ctx->s_fb, ctx->d_stats + kStatFallback);
+        ProfScope pm(ctx, kProfSurrogateMlp, s, ctx->s_kernel == RAPTOR_MLP_MMA_SYNC ? 1 : 2);
+        e = sur_eval_rows(ctx, ctx->s_in, (long long)rays, out, s);
+    }
+    if (e == cudaSuccess) {
+        ProfScope ps(ctx, kProfSurrogate, s);
+        k_surrogate_states<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_P, out, ctx->s_start);
         e = cudaGetLastError();
-        if (e == cudaSuccess) {
-            ProfScope pm(ctx, kProfSurrogateMlp, s, ctx->s_kernel == RAPTOR_MLP_MMA_SYNC ? 1 : 2);
-            e = sur_eval_rows(ctx, ctx->s_in, (long long)rays, out, s);
-        }
-        if (e == cudaSuccess) {
-            k_surrogate_states<<<ew_blocks((long long)rays), 256, 0, s>>>(p, ctx->s_P, out, ctx->s_start);
-            e = cudaGetLastError();
-        }
     }
     const cudaError_t ef = cudaFreeAsync(out, s);
     return e != cudaSuccess ? e : ef;

@@ -258,10 +258,12 @@ def test_surrogate_gain_over_the_method_without_it(R, trained):
     s0, s1 = stages[R.MIXED], stages[R.MIXED_MLP]
     fp32_saved = (s0["mixed_fp32_in"] + s0["mixed_fp32_out"]) - (s1["mixed_fp32_in"] + s1["mixed_fp32_out"])
     gain = res[R.MIXED] / res[R.MIXED_MLP]
-    print(f"surrogate at 512^2: FP32 phases {fp32_saved:.2f} ms shorter, surrogate stage {s1['surrogate']:.2f} ms "
+    # the stage: inputs and fallback flags, the network, start states
+    stage = s1["surrogate"] + s1["surrogate_mlp"]
+    print(f"surrogate at 512^2: FP32 phases {fp32_saved:.2f} ms shorter, surrogate stage {stage:.2f} ms "
           f"(network {s1['surrogate_mlp']:.2f} ms); frame {gain:.3f}x (mixed {res[R.MIXED] * 1e3:.2f} ms, "
           f"mixed+MLP {res[R.MIXED_MLP] * 1e3:.2f} ms)")
-    assert fp32_saved > s1["surrogate"]
+    assert fp32_saved > stage
 
 
 @pytest.mark.parametrize("size", [1024, 2048])
