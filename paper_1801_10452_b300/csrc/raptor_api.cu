@@ -1292,7 +1292,7 @@ cudaError_t sur_alloc(raptor_ctx* c) {
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->s_err, sizeof(int));
         // the tcgen05 kernels' shared-memory plans (set once, outside any stream capture)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc12<kOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc12Smem);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc34<kOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc34Smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_tc34_state, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc34Smem);
         if (e == cudaSuccess) e = cudaMemset(c->s_err, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->s_G, 0, n * sizeof(float));
         if (e != cudaSuccess) return e;
@@ -1394,7 +1394,7 @@ cudaError_t sur_eval_rows(raptor_ctx* c, const float* inputs, long long n, float
     }
     const unsigned grid = (unsigned)std::min<long long>(tiles, c->num_sms);
     k_mlp_tc12<<<grid, kTcThreads, kTc12Smem, s>>>(c->s_P, wtc(c), inputs, n, c->s_h2tc, c->s_err);
-    k_mlp_tc34<<<grid, kTcThreads, kTc34Smem, s>>>(c->s_P, wtc(c) + kHid * kHid, c->s_h2tc, n, out_dev, c->s_err);
+    k_mlp_tc34_state<<<grid, kTcThreads, kTc34Smem, s>>>(c->s_P, wtc(c) + kHid * kHid, c->s_h2tc, n, out_dev, c->s_err);
     return cudaGetLastError();
 }
 

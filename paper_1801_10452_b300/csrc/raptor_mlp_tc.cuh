@@ -360,10 +360,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc12(const float* __restr
 }
 
 // Layers 3 and 4.  h2 as written by k_mlp_tc12; out: [n][NOUT] normalised outputs.
-template <int NOUT = kOut>
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restrict__ P, const __nv_bfloat16* __restrict__ wu3,
-                                                            const __nv_bfloat16* __restrict__ h2, long long n,
-                                                            float* __restrict__ out, int* __restrict__ err) {
+template <int NOUT>
+__device__ __forceinline__ void mlp_tc34_body(const float* __restrict__ P, const __nv_bfloat16* __restrict__ wu3,
+                                              const __nv_bfloat16* __restrict__ h2, long long n, float* __restrict__ out,
+                                              int* __restrict__ err) {
     extern __shared__ uint8_t tc_smem_raw[];
     uint8_t* sW = tc_align(tc_smem_raw);
     uint8_t* sA = sW + kTcWBytes;
@@ -495,6 +495,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restr
     // tile is fetched only if it is processed), but an aborted loop may leave one in flight
     if (tid == 0 && a_pending && !tc_mbar_wait(&ctl->abar, aphase)) ctl->abort = 1;
     tc_teardown(ctl, w_pending, m_out, m_phase, err);
+}
+
+template <int NOUT = kOut>
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc34(const float* __restrict__ P, const __nv_bfloat16* __restrict__ wu3,
+                                                            const __nv_bfloat16* __restrict__ h2, long long n,
+                                                            float* __restrict__ out, int* __restrict__ err) {
+    mlp_tc34_body<NOUT>(P, wu3, h2, n, out, err);
+}
+
+// The state network's layers 3-4 (k_mlp_tc34_state; the crossing network's 16 outputs use
+// k_mlp_tc34<16>) run beside the near-critical rays' FP32 kernel (one
+// 128-thread block of 104 registers on most SMs while the network runs): capped at 96
+// registers a thread (512 x 96 + 128 x 104 fit the SM's 64 K) a CTA shares the SM with that
+// block instead of waiting for it to finish, at the price of a few spills.
+__global__ void __maxnreg__(96) k_mlp_tc34_state(const float* __restrict__ P, const __nv_bfloat16* __restrict__ wu3,
+                                                 const __nv_bfloat16* __restrict__ h2, long long n, float* __restrict__ out,
+                                                 int* __restrict__ err) {
+    mlp_tc34_body<kOut>(P, wu3, h2, n, out, err);
 }
 
 }  // namespace raptor
