@@ -527,8 +527,10 @@ cudaError_t launch_mixed_nf(raptor_ctx* c, const Params& p, cudaStream_t s, bool
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_long, c->ev_fork, 0);
         if (e != cudaSuccess) return e;
         {
+            // one block per SM: every SM keeps room for a network CTA beside it (A1 has
+            // time to spare until the start states are ready)
             ProfScope ps(c, kProfMixedA, c->s_long);
-            k_mixed_fp32<NF><<<bA, c->launch_block, 0, c->s_long>>>(p, a1, mq.cap, cnt, c->d_stats);
+            k_mixed_fp32<NF><<<std::min(bA, c->num_sms), c->launch_block, 0, c->s_long>>>(p, a1, mq.cap, cnt, c->d_stats);
         }
         e = cudaGetLastError();
         if (e == cudaSuccess) e = surrogate_infer(c, p, s);
