@@ -153,3 +153,29 @@ def test_image_scaling_with_mass_and_distance(ora):
     D = 7.88e3 * PC_CM
     da = 2 * R * 1.15 / n
     assert np.allclose(tb[lit], 1e-17 / 1e-8 * da * da * Lcm * Lcm / (D * D) / 1e-23, rtol=1e-9)
+
+
+def test_polar_axis_rays_are_ill_conditioned(ora):
+    """The step rule near the polar axis (Eq. 21 as read): a ray of zero angular momentum
+    (alpha = 0; L = -alpha sin i) passes within ~1e-6 rad of the axis, where the steps
+    shrink like min(theta, pi - theta), and its transfer samples there follow shifts of
+    alpha far below a pixel: at (0, 2.76 M) a 1e-8 M shift moves the intensity by more than
+    1e-2, at alpha = 0.0195 M (the 1024^2 image's nearest column) and 0.1 M by less than
+    1e-5.  This is why the mixed paths' per-pixel bound leaves out |alpha| < 1e-3 M and the
+    learned path integrates |alpha| < 0.01 M from the camera."""
+    from helpers import oracle_kwargs
+    from paper_1801_10452_b300 import scenes
+
+    s = ora.scene(**oracle_kwargs(dict(scenes.SMALL)))
+    be, freqs = 2.7586206896551726, [6.158e10, 230e9]
+
+    def trace(al):
+        return ora.trace_ray(s, al, be, freqs, max_trace=5000)
+
+    o0, o1 = trace(0.0), trace(1e-8)
+    th = o0["trace"][:, 2]
+    assert np.minimum(th, np.pi - th).min() < 1e-5
+    assert np.abs(o1["I"] / o0["I"] - 1).max() > 1e-2
+    for al in (0.01953125, 0.1):
+        a, b = trace(al), trace(al + 1e-8)
+        assert np.abs(b["I"] / a["I"] - 1).max() < 1e-5, al
